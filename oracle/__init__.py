@@ -1,0 +1,199 @@
+"""CPU oracle for exact top-k weighted triangles (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never imports, links or executes anything here, and this
+package never imports the product.
+
+The C part (``wtri_oracle.c``) is plain brute force: NodeIterator++ with a
+bounded heap, the paper's BF baseline (Sections 3 and 5.2), scoring each
+triangle with the generalized p-mean of Eq. 1 through an exact integer key.
+The numpy helpers below restate the intermediate structures the CUDA path
+builds (edge order of Algorithm 2's first step, per-vertex weight-sorted
+lists, the degree orientation) so that they can be compared one by one.
+
+Parity pins (tests/test_oracle_*.py) check this oracle against closed forms,
+an independent triangle count, hand-enumerated graphs in tests/golden/ and a
+Python brute force on random small graphs.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wtri_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+P_CODES = {-math.inf: 0, 1.0: 1, 2.0: 2, math.inf: 3}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP) into oracle/_build/liboracle.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = ctypes.CDLL(path)
+        i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+        i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+        u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+        f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+        I64P = ctypes.POINTER(ctypes.c_int64)
+        L.or_validate.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, I64P]
+        L.or_sym_csr.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p,
+                                 i64p, i32p, i32p, i64p]
+        L.or_edge_order.argtypes = [ctypes.c_int64, i32p, i64p]
+        L.or_oriented_csr.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p,
+                                      i64p, i32p, i32p, i64p]
+        L.or_score.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                               ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]
+        L.or_topk.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, ctypes.c_int,
+                              ctypes.c_int64, ctypes.c_int, i32p, u64p, f64p, I64P, I64P]
+        L.or_count_triangles.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, I64P]
+        for f in (L.or_validate, L.or_sym_csr, L.or_edge_order, L.or_oriented_csr,
+                  L.or_score, L.or_topk, L.or_count_triangles):
+            f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class OracleError(ValueError):
+    pass
+
+
+def _arr(x):
+    return np.ascontiguousarray(x, dtype=np.int32)
+
+
+def pcode(p: float) -> int:
+    if p not in P_CODES:
+        raise OracleError(f"p={p} is outside {{-inf, 1, 2, +inf}}")
+    return P_CODES[p]
+
+
+def validate(n, u, v, w):
+    """Returns -1 if the edge list is a valid simple positive-weighted graph
+    (apart from repeated pairs, which or_sym_csr detects), else the index of
+    the first offending edge."""
+    u, v, w = _arr(u), _arr(v), _arr(w)
+    bad = ctypes.c_int64(0)
+    lib().or_validate(n, u.shape[0], u, v, w, ctypes.byref(bad))
+    return int(bad.value)
+
+
+def sym_csr(n, u, v, w):
+    """Symmetric CSR, rows ascending by id: (rowptr, col, wt, eid)."""
+    u, v, w = _arr(u), _arr(v), _arr(w)
+    m = u.shape[0]
+    rowptr = np.zeros(n + 1, np.int64)
+    col = np.zeros(2 * m, np.int32)
+    wt = np.zeros(2 * m, np.int32)
+    eid = np.zeros(2 * m, np.int64)
+    rc = lib().or_sym_csr(n, m, u, v, w, rowptr, col, wt, eid)
+    if rc != 0:
+        raise OracleError(f"invalid graph (rc={rc})")
+    return rowptr, col, wt, eid
+
+
+def edge_order(w):
+    """perm[r] = index of the r-th edge by (weight desc, index asc)."""
+    w = _arr(w)
+    perm = np.zeros(w.shape[0], np.int64)
+    lib().or_edge_order(w.shape[0], w, perm)
+    return perm
+
+
+def oriented_csr(n, u, v, w):
+    """Degree-oriented CSR (rank = (degree, id), low -> high), rows by id."""
+    u, v, w = _arr(u), _arr(v), _arr(w)
+    m = u.shape[0]
+    orow = np.zeros(n + 1, np.int64)
+    ocol = np.zeros(m, np.int32)
+    owt = np.zeros(m, np.int32)
+    oeid = np.zeros(m, np.int64)
+    rc = lib().or_oriented_csr(n, m, u, v, w, orow, ocol, owt, oeid)
+    if rc != 0:
+        raise OracleError(f"invalid graph (rc={rc})")
+    return orow, ocol, owt, oeid
+
+
+def weight_sorted_rows(n, u, v, w):
+    """Per-vertex neighbour lists ordered like the global edge order
+    (weight desc, edge index asc).  Returns (rowptr, col, wt, rank) where
+    rank is the position of the edge in edge_order()."""
+    rowptr, col, wt, eid = sym_csr(n, u, v, w)
+    perm = edge_order(w)
+    rank = np.empty_like(perm)
+    rank[perm] = np.arange(perm.shape[0], dtype=np.int64)
+    r_ent = rank[eid]
+    row_of = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    order = np.lexsort((r_ent, row_of))
+    return rowptr, col[order], wt[order], r_ent[order]
+
+
+def score(p, a, b, c):
+    """(key, value) of one triangle with edge weights a, b, c (Eq. 1)."""
+    key = ctypes.c_uint64(0)
+    val = ctypes.c_double(0.0)
+    rc = lib().or_score(pcode(p), int(a), int(b), int(c), ctypes.byref(key), ctypes.byref(val))
+    if rc != 0:
+        raise OracleError("bad p")
+    return int(key.value), float(val.value)
+
+
+def topk(n, u, v, w, p, k, nthreads=0):
+    """Exact top-k triangles.  Returns dict(tri [count,3] int32, key uint64,
+    value float64, count, ntri)."""
+    u, v, w = _arr(u), _arr(v), _arr(w)
+    m = u.shape[0]
+    k = int(k)
+    tri = np.zeros(3 * max(k, 1), np.int32)
+    key = np.zeros(max(k, 1), np.uint64)
+    val = np.zeros(max(k, 1), np.float64)
+    cnt = ctypes.c_int64(0)
+    ntri = ctypes.c_int64(0)
+    rc = lib().or_topk(n, m, u, v, w, pcode(p), k, int(nthreads), tri, key, val,
+                       ctypes.byref(cnt), ctypes.byref(ntri))
+    if rc != 0:
+        raise OracleError(f"or_topk failed (rc={rc})")
+    c = int(cnt.value)
+    return {"tri": tri[: 3 * c].reshape(c, 3), "key": key[:c], "value": val[:c],
+            "count": c, "ntri": int(ntri.value)}
+
+
+def count_triangles(n, u, v, w=None):
+    u, v = _arr(u), _arr(v)
+    if w is None:
+        w = np.ones(u.shape[0], np.int32)
+    w = _arr(w)
+    out = ctypes.c_int64(0)
+    rc = lib().or_count_triangles(n, u.shape[0], u, v, w, ctypes.byref(out))
+    if rc != 0:
+        raise OracleError(f"invalid graph (rc={rc})")
+    return int(out.value)
+
+
+if __name__ == "__main__":  # pragma: no cover
+    build(force="--force" in sys.argv)
+    print(_LIB_PATH)

@@ -1,0 +1,211 @@
+"""Seeded synthetic weighted graphs shaped like the paper's workloads.
+
+This module only draws inputs.  It holds none of the top-k method's
+arithmetic (no triangle enumeration, no scoring, no ordering of edges by
+weight), so both the CPU oracle and the CUDA path can consume its output
+without sharing any code with each other.
+
+Recipe (the paper's datasets, Table 1 of Section 5, are not available; these
+graphs stand in for them):
+
+* Structure: "erased" Chung-Lu power-law graphs.  Expected degrees
+  ``theta_i = c * (i + i0) ** (-1 / (gamma - 1))`` with ``i0`` and ``c`` solved
+  so that ``theta_0 = d_max`` and ``sum(theta) = 2 m``.  Endpoint pairs are drawn
+  i.i.d. proportional to ``theta``; self-loops and repeated pairs are dropped
+  and the draw is topped up until exactly ``m`` distinct edges remain.
+* Weights: i.i.d. and independent of structure (the paper's model in the
+  analysis of Section 3.3).  Truncated Zipf ``P(w) ~ w**-s`` on ``{1..cap}`` is
+  sampled by inverse CDF over an fp64 table (not clamped).  The tiny workload
+  uses ``1 + Geometric(0.3)`` (support starting at 1) with an independent 1 %
+  of edges drawn from truncated Zipf(1.5, 1e4).
+* Edge order is shuffled and each edge's endpoint order is a coin flip, so no
+  consumer can rely on sorted input.
+
+Every array is int32, as the C-ABI takes it.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = [
+    "Graph",
+    "chung_lu",
+    "zipf_weights",
+    "tiny_weights",
+    "tiny_graph",
+    "mid_graph",
+    "batch_graph",
+    "scaled_mid_graph",
+    "random_small_graph",
+]
+
+
+@dataclasses.dataclass
+class Graph:
+    n: int
+    u: np.ndarray  # int32 [m]
+    v: np.ndarray  # int32 [m]
+    w: np.ndarray  # int32 [m]
+    name: str = ""
+
+    @property
+    def m(self) -> int:
+        return int(self.u.shape[0])
+
+
+def _rng(seed, *substream) -> np.random.Generator:
+    # Philox keyed by (seed, substream...) so that sub-draws are independent
+    # of one another and of how many values earlier draws consumed.
+    key = [int(seed) & 0xFFFFFFFFFFFFFFFF]
+    for s in substream:
+        key.append(int(s) & 0xFFFFFFFFFFFFFFFF)
+    ss = np.random.SeedSequence(key)
+    return np.random.Generator(np.random.Philox(ss))
+
+
+def _expected_degrees(n: int, m: int, gamma: float, d_max: float) -> np.ndarray:
+    a = 1.0 / (gamma - 1.0)
+    idx = np.arange(n, dtype=np.float64)
+
+    def total(i0: float) -> float:
+        c = d_max * i0 ** a
+        return float(np.sum(c * (idx + i0) ** (-a)))
+
+    target = 2.0 * m
+    lo, hi = 1e-9, 1e12
+    if total(hi) < target:
+        # Even a flat sequence cannot reach 2m below d_max: use it.
+        return np.full(n, target / n)
+    for _ in range(200):
+        mid = math.sqrt(lo * hi)
+        if total(mid) < target:
+            lo = mid
+        else:
+            hi = mid
+        if hi / lo < 1 + 1e-12:
+            break
+    i0 = hi
+    c = d_max * i0 ** a
+    return c * (idx + i0) ** (-a)
+
+
+def chung_lu(n: int, m: int, gamma: float, d_max: float, seed, substream=(0,)):
+    """Erased Chung-Lu graph with exactly ``m`` distinct undirected edges.
+
+    Returns ``(u, v)`` int32 arrays in shuffled order.
+    """
+    if m > n * (n - 1) // 2:
+        raise ValueError("m exceeds the number of vertex pairs")
+    rng = _rng(seed, 1, *substream)
+    theta = _expected_degrees(n, m, gamma, d_max)
+    cdf = np.cumsum(theta)
+    cdf /= cdf[-1]
+    keys = np.empty(0, dtype=np.int64)
+    need = m
+    rounds = 0
+    while need > 0:
+        draw = int(need * 1.15) + 1024
+        a = np.searchsorted(cdf, rng.random(draw), side="right").astype(np.int64)
+        b = np.searchsorted(cdf, rng.random(draw), side="right").astype(np.int64)
+        np.minimum(a, n - 1, out=a)
+        np.minimum(b, n - 1, out=b)
+        ok = a != b
+        a, b = a[ok], b[ok]
+        lo_ = np.minimum(a, b)
+        hi_ = np.maximum(a, b)
+        new = lo_ * n + hi_
+        keys = np.unique(np.concatenate([keys, new]))
+        if keys.shape[0] >= m:
+            # Keep a uniformly random subset of exactly m distinct pairs.
+            pick = rng.permutation(keys.shape[0])[:m]
+            keys = keys[np.sort(pick)]
+        need = m - keys.shape[0]
+        rounds += 1
+        if rounds > 1000:
+            raise RuntimeError("Chung-Lu top-up did not converge")
+    keys = keys[rng.permutation(m)]
+    u = (keys // n).astype(np.int32)
+    v = (keys % n).astype(np.int32)
+    flip = rng.random(m) < 0.5
+    u2 = np.where(flip, v, u)
+    v2 = np.where(flip, u, v)
+    return u2.astype(np.int32), v2.astype(np.int32)
+
+
+def _zipf_table(s: float, cap: int) -> np.ndarray:
+    x = np.arange(1, cap + 1, dtype=np.float64)
+    cdf = np.cumsum(x ** (-s))
+    cdf /= cdf[-1]
+    return cdf
+
+
+def zipf_weights(m: int, s: float, cap: int, rng: np.random.Generator) -> np.ndarray:
+    """Truncated Zipf on {1..cap} by inverse CDF over an fp64 table."""
+    cdf = _zipf_table(s, cap)
+    w = np.searchsorted(cdf, rng.random(m), side="right") + 1
+    np.minimum(w, cap, out=w)
+    return w.astype(np.int32)
+
+
+def tiny_weights(m: int, rng: np.random.Generator) -> np.ndarray:
+    """1 + Geometric(0.3) on {0,1,...}; an independent 1 % from Zipf(1.5, 1e4)."""
+    w = rng.geometric(0.3, size=m).astype(np.int64)  # numpy's support starts at 1
+    heavy = rng.random(m) < 0.01
+    w[heavy] = zipf_weights(int(heavy.sum()), 1.5, 10_000, rng)
+    return w.astype(np.int32)
+
+
+def tiny_graph(seed: int = 0) -> Graph:
+    """n=2,000, exponent 2.1, 20,000 edges, d_max = sqrt(2m)."""
+    n, m = 2000, 20_000
+    u, v = chung_lu(n, m, 2.1, math.sqrt(2 * m), seed)
+    w = tiny_weights(m, _rng(seed, 2))
+    return Graph(n, u, v, w, name="chung-lu n=2000 m=20000 g=2.1 geom(0.3)+1%zipf(1.5,1e4)")
+
+
+def mid_graph(seed: int = 1) -> Graph:
+    """n=1e6, m=2e7, exponent 2.1, d_max 5e4, Zipf(2) weights capped at 1e6."""
+    return scaled_mid_graph(1_000_000, 20_000_000, seed=seed)
+
+
+def scaled_mid_graph(n: int, m: int, seed: int = 1, gamma: float = 2.1,
+                     d_max: float | None = None, s: float = 2.0, cap: int = 1_000_000) -> Graph:
+    """The mid workload's recipe at another size (d_max scales with sqrt(m))."""
+    if d_max is None:
+        d_max = 50_000.0 * math.sqrt(m / 20_000_000)
+        d_max = min(d_max, n - 1)
+    u, v = chung_lu(n, m, gamma, d_max, seed)
+    w = zipf_weights(m, s, cap, _rng(seed, 2))
+    return Graph(n, u, v, w, name=f"chung-lu n={n} m={m} g={gamma} zipf({s},{cap})")
+
+
+def batch_graph(g: int, seed: int = 3) -> Graph:
+    """Graph ``g`` of the 4,096-graph batch: n log-uniform in [100, 2e5], m = 10 n,
+    exponent 2.2, Zipf(2) weights capped at 1e6."""
+    rng = _rng(seed, 10, g)
+    n = int(round(math.exp(rng.uniform(math.log(100), math.log(200_000)))))
+    m = min(10 * n, n * (n - 1) // 2)
+    d_max = min(n - 1, math.sqrt(2 * m))
+    u, v = chung_lu(n, m, 2.2, d_max, seed, substream=(11, g))
+    w = zipf_weights(m, 2.0, 1_000_000, _rng(seed, 12, g))
+    return Graph(n, u, v, w, name=f"batch[{g}] n={n} m={m}")
+
+
+def random_small_graph(n: int, p_edge: float, wmax: int, seed) -> Graph:
+    """Erdos-Renyi G(n, p) with uniform integer weights in [1, wmax] (for
+    property tests on tiny graphs, where ties are frequent)."""
+    rng = _rng(seed, 20)
+    iu, ju = np.triu_indices(n, 1)
+    keep = rng.random(iu.shape[0]) < p_edge
+    u = iu[keep].astype(np.int32)
+    v = ju[keep].astype(np.int32)
+    perm = rng.permutation(u.shape[0])
+    u, v = u[perm], v[perm]
+    flip = rng.random(u.shape[0]) < 0.5
+    u2 = np.where(flip, v, u).astype(np.int32)
+    v2 = np.where(flip, u, v).astype(np.int32)
+    w = rng.integers(1, wmax + 1, size=u.shape[0]).astype(np.int32)
+    return Graph(n, u2, v2, w, name=f"gnp n={n} p={p_edge} w<={wmax}")
