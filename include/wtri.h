@@ -1,0 +1,207 @@
+/*
+ * wtri — exact top-k weighted triangles on one GPU (sm_103a).
+ *
+ * C ABI of libwtri.so.  Plain pointers and sizes only; no exceptions cross
+ * this boundary and the library never aborts, traps or exits.  Every entry
+ * point returns one of the WTRI_* codes below; wtri_last_error() gives a
+ * thread-local message for the last failing call on the calling thread.
+ *
+ * Problem (Kumar, Liu, Charikar, Benson, "Retrieving Top Weighted Triangles
+ * in Graphs", WSDM 2020, Section 1): G = (V, E, w) is a simple undirected
+ * graph with positive integer edge weights.  A triangle {a, b, c} weighs the
+ * generalized p-mean of its three edge weights (Eq. 1):
+ *     m_p = ((w_ab^p + w_bc^p + w_ac^p) / 3)^(1/p),
+ * with p = +inf the max and p = -inf the min.  This library supports
+ * p in {-inf, 1, 2, +inf}; any other p returns WTRI_EUNSUPPORTED.
+ *
+ * Results are ranked by a total order: weight descending, then the sorted
+ * vertex triple (a < b < c) ascending.  The paper notes that ties may make
+ * several answers valid (Section 3.2); the triple order makes the answer
+ * unique.  Ranking uses exact integer keys (a+b+c for p=1, a^2+b^2+c^2 for
+ * p=2, max, min), never the floating value; the reported fp64 weight is
+ * (a+b+c)/3.0, sqrt((a^2+b^2+c^2)/3.0), max or min.
+ *
+ * A graph with fewer than k triangles returns all of them: count < k
+ * (Section 3.2, "provided the graph has at least k triangles").
+ *
+ * Device memory behind a wtri_graph is owned by the library and freed by
+ * wtri_graph_free.  A graph is immutable after wtri_build_csr; queries on
+ * one graph from several host threads are safe (each query uses its own
+ * stream-ordered scratch).
+ */
+#ifndef WTRI_H
+#define WTRI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WTRI_API __attribute__((visibility("default")))
+
+/* Return codes. */
+enum {
+    WTRI_OK = 0,
+    WTRI_PENDING = 1,         /* wtri_poll: the request is not finished yet */
+    WTRI_EINVAL = -1,         /* bad argument or invalid graph */
+    WTRI_ENOMEM = -2,         /* device or host allocation failed, or over budget */
+    WTRI_ECUDA = -3,          /* a CUDA runtime call failed */
+    WTRI_ETIMEOUT = -4,       /* a bounded device-side wait ran out */
+    WTRI_EUNSUPPORTED = -5,   /* valid request outside what this build supports */
+    WTRI_ENOTFOUND = -6       /* unknown ticket or graph id */
+};
+
+typedef struct wtri_graph wtri_graph;
+typedef struct wtri_server wtri_server;
+
+/* One triangle, vertex ids ascending (a < b < c). */
+typedef struct {
+    int32_t a, b, c;
+} wtri_tri;
+
+/* Caller-owned HOST result arrays.  capacity >= k entries in tris and weight.
+ * On success count = min(k, #triangles); entries are in rank order.  On
+ * error count = 0 and nothing else is written. */
+typedef struct {
+    wtri_tri* tris;
+    double* weight;
+    int32_t capacity;
+    int32_t count;
+} wtri_result;
+
+/*
+ * Builds the device-resident graph (the preprocessing of Algorithm 2 and of
+ * the edge sampler of Section 4.1):
+ *   - validation: ids in [0, n), no self-loops, weights > 0, no repeated
+ *     undirected pair (Section 1: simple graph, positive weights);
+ *   - the edge order: edges sorted by weight descending (Algorithm 2, first
+ *     step), ties by input index ascending, so the order is total;
+ *   - per-vertex neighbour lists N(a) in that edge order (weight-sorted);
+ *   - the symmetric adjacency with rows ascending by neighbour id;
+ *   - the degree orientation of NodeIterator++ (Section 5.2): vertices ranked
+ *     by (degree, id), each edge stored once from its lower-ranked endpoint,
+ *     rows ascending by id.
+ *
+ * n        number of vertices (ids 0..n-1), 1 <= n <= 2^31-1.
+ * m        number of undirected edges, 0 <= m <= 2^30.
+ * u, v, w  m int32 each: edge i joins u[i] and v[i] with weight w[i].  Each
+ *          undirected pair appears once, in either orientation.
+ * on_device 0: u, v, w are host pointers (copied in on the stream);
+ *          1: device pointers (read in place, not retained after return).
+ * cuda_stream a cudaStream_t to order the build on (NULL = legacy default);
+ *          the graph remembers it for wtri_topk / wtri_sample_topk.
+ * out      receives the new graph.  The call returns after the build has
+ *          completed on the device.
+ *
+ * Errors: WTRI_EINVAL (n <= 0, m < 0, NULL pointers, an invalid edge or a
+ * repeated pair; the message names the first offending edge index when it
+ * is known), WTRI_ENOMEM, WTRI_ECUDA.  *out is NULL on error.
+ */
+WTRI_API int wtri_build_csr(int32_t n, int64_t m, const int32_t* u, const int32_t* v,
+                            const int32_t* w, int on_device, void* cuda_stream,
+                            wtri_graph** out);
+
+/* Frees the graph's device memory.  NULL is a no-op. */
+WTRI_API void wtri_graph_free(wtri_graph* g);
+
+/* Basic facts about a built graph (any pointer may be NULL). */
+WTRI_API int wtri_graph_info(const wtri_graph* g, int32_t* n, int64_t* m, int32_t* max_degree,
+                             int32_t* max_weight, int64_t* device_bytes);
+
+/*
+ * Exact top-k triangles by generalized p-mean (Eq. 1), the problem that
+ * Algorithm 2 solves.  Runs on the graph's stream, then copies the k results
+ * to the caller's host arrays and returns when they are there.
+ *
+ * p   -INFINITY, 1.0, 2.0 or +INFINITY; NaN -> WTRI_EINVAL; others ->
+ *     WTRI_EUNSUPPORTED.
+ * k   1 <= k <= out->capacity and k <= 65536 (WTRI_EUNSUPPORTED above).
+ */
+WTRI_API int wtri_topk(const wtri_graph* g, double p, int32_t k, wtri_result* out);
+
+/*
+ * Same query, fully stream-ordered and with DEVICE outputs: nothing is
+ * copied to the host and the call does not synchronize (it may be captured
+ * in a CUDA graph after one warm-up call with the same g, p, k).
+ *
+ * d_tris    device array of k wtri_tri.
+ * d_weight  device array of k doubles.
+ * d_count   device int32: min(k, #triangles) on completion, or a negative
+ *           WTRI_* code if the device detected an error (e.g. an internal
+ *           buffer overflowed: the host-result wtri_topk retries such a
+ *           query with larger buffers; this variant reports it).
+ * stream    cudaStream_t to run on (NULL = the graph's stream).
+ */
+WTRI_API int wtri_topk_device(const wtri_graph* g, double p, int32_t k, wtri_tri* d_tris,
+                              double* d_weight, int32_t* d_count, void* stream);
+
+/*
+ * Weighted edge sampling (Algorithm 3, Section 4.1): draws nsamples edges
+ * with probability w_e^p / Z (Proposition 4.1), adds every triangle on each
+ * sampled edge (the common neighbours N(a) ∩ N(b)) to a set, and returns the
+ * top-k of that set in the same order and format as wtri_topk.  The edge
+ * draw is an integer inverse CDF over the weight-sorted edge order
+ * (Section 4.1's weight classes are contiguous in that order) driven by
+ * Philox4x64-10 (Salmon et al., SC'11) with key = seed and counter = the
+ * sample index, so a seed gives the same samples on any device.
+ *
+ * p in {1, 2}; +-inf -> WTRI_EUNSUPPORTED (w^p has no meaning there).
+ * nsamples >= 0 (0 returns count 0).
+ */
+WTRI_API int wtri_sample_topk(const wtri_graph* g, double p, int32_t k, int64_t nsamples,
+                              uint64_t seed, wtri_result* out);
+
+/*
+ * Copies one internal array of a built graph to host memory, for tests that
+ * compare the device structures with an independent construction.
+ * which: one of the WTRI_ARR_* values.  dst must hold bytes_capacity bytes;
+ * *bytes_out receives the array's size (also when dst is NULL, which only
+ * queries the size).
+ */
+enum {
+    WTRI_ARR_DEGREE = 0,      /* int32[n]     degree d_a */
+    WTRI_ARR_ROWPTR = 1,      /* int64[n+1]   row offsets of both symmetric layouts */
+    WTRI_ARR_ORDER_U = 2,     /* int32[m]     edge order: endpoint u of the r-th edge */
+    WTRI_ARR_ORDER_V = 3,     /* int32[m]     edge order: endpoint v */
+    WTRI_ARR_ORDER_W = 4,     /* int32[m]     edge order: weight (non-increasing) */
+    WTRI_ARR_WCOL = 5,        /* int32[2m]    weight-sorted rows: neighbour */
+    WTRI_ARR_WWT = 6,         /* int32[2m]    weight-sorted rows: weight */
+    WTRI_ARR_WRANK = 7,       /* int32[2m]    weight-sorted rows: edge rank r */
+    WTRI_ARR_SCOL = 8,        /* int32[2m]    id-sorted rows: neighbour */
+    WTRI_ARR_SWT = 9,         /* int32[2m]    id-sorted rows: weight */
+    WTRI_ARR_SRANK = 10,      /* int32[2m]    id-sorted rows: edge rank r */
+    WTRI_ARR_OROWPTR = 11,    /* int64[n+1]   oriented row offsets */
+    WTRI_ARR_OCOL = 12,       /* int32[m]     oriented rows: higher-ranked endpoint */
+    WTRI_ARR_OWT = 13,        /* int32[m]     oriented rows: weight */
+    WTRI_ARR_ORANK = 14       /* int32[m]     oriented rows: edge rank r */
+};
+WTRI_API int wtri_graph_copy_array(const wtri_graph* g, int which, void* dst,
+                                   int64_t bytes_capacity, int64_t* bytes_out);
+
+/*
+ * Profiling (no counterpart in the paper; used to attribute device time).
+ * wtri_launch_count: kernels launched by this library since load (always on).
+ * wtri_prof_enable(1): every library phase is bracketed by CUDA events on its
+ * stream; wtri_prof_read(i, ...) returns phase i (sorted by name) with its
+ * number of calls, summed device milliseconds and summed algorithmic bytes
+ * (the bytes the phase must read and write once), WTRI_ENOTFOUND past the
+ * last phase.  wtri_prof_reset clears the totals.
+ */
+WTRI_API void wtri_prof_enable(int on);
+WTRI_API void wtri_prof_reset(void);
+WTRI_API long long wtri_launch_count(void);
+WTRI_API int wtri_prof_read(int idx, char* name, int name_cap, long long* calls, double* ms,
+                            double* bytes);
+
+/* Thread-local message for the last failing call on this thread ("" if none). */
+WTRI_API const char* wtri_last_error(void);
+
+/* Library version string. */
+WTRI_API const char* wtri_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WTRI_H */

@@ -1,0 +1,25 @@
+"""Exact top-k weighted triangles on GB300 (sm_103a).
+
+A thin ctypes binding over ``libwtri.so`` (C ABI in ``include/wtri.h``).  The
+binding only marshals arguments: every step of the path runs in the
+library's CUDA kernels.  Importing this package does not need a GPU; calling
+into it does, and a missing library raises ``WtriUnavailable`` instead of
+falling back to anything else.
+"""
+from __future__ import annotations
+
+from .wtri import (  # noqa: F401
+    ARRAYS,
+    Graph,
+    WtriError,
+    WtriUnavailable,
+    build_csr,
+    lib,
+    lib_path,
+    sample_topk,
+    topk,
+    topk_device,
+)
+
+__all__ = ["ARRAYS", "Graph", "WtriError", "WtriUnavailable", "build_csr", "lib", "lib_path",
+           "sample_topk", "topk", "topk_device"]

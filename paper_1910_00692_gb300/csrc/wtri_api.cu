@@ -1,0 +1,229 @@
+// C ABI entry points (include/wtri.h): argument checks, error reporting and
+// host-side result copies around the device paths.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "wtri_internal.cuh"
+
+namespace wtri {
+
+static thread_local std::string t_last_error;
+
+int set_error(int code, const std::string& msg) {
+    t_last_error = msg;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" +
+                      std::to_string(line) + ")";
+    if (e == cudaErrorMemoryAllocation) return set_error(WTRI_ENOMEM, msg);
+    return set_error(WTRI_ECUDA, msg);
+}
+
+int p_to_code(double p, int* code) {
+    if (isnan(p)) return set_error(WTRI_EINVAL, "p is NaN");
+    if (p == 1.0) *code = P_ONE;
+    else if (p == 2.0) *code = P_TWO;
+    else if (isinf(p) && p > 0) *code = P_MAX;
+    else if (isinf(p) && p < 0) *code = P_MIN;
+    else return set_error(WTRI_EUNSUPPORTED, "p must be -inf, 1, 2 or +inf");
+    return WTRI_OK;
+}
+
+int sm_count() {
+    static int cached = 0;
+    if (cached == 0) {
+        int dev = 0, c = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && c > 0)
+            cached = c;
+        else
+            return 132;
+    }
+    return cached;
+}
+
+namespace {
+
+constexpr int32_t K_MAX = 65536;
+
+int check_query(const wtri_graph* g, int32_t k) {
+    if (!g) return set_error(WTRI_EINVAL, "graph is NULL");
+    if (k <= 0) return set_error(WTRI_EINVAL, "k must be positive");
+    if (k > K_MAX) return set_error(WTRI_EUNSUPPORTED, "k above 65536");
+    return WTRI_OK;
+}
+
+// Runs a device query into scratch outputs, copies them to the caller's host
+// result, retrying with larger device buffers if a bounded buffer filled.
+template <class Launch>
+int host_result_query(const wtri_graph* g, int32_t k, wtri_result* out, Launch launch) {
+    cudaStream_t s = g->stream;
+    const size_t tri_bytes = sizeof(wtri_tri) * (size_t)k;
+    const size_t w_bytes = sizeof(double) * (size_t)k;
+    void* buf = nullptr;
+    WTRI_CUDA(cudaMallocAsync(&buf, tri_bytes + w_bytes + 64, s));
+    wtri_tri* d_tri = (wtri_tri*)buf;
+    double* d_w = (double*)((char*)buf + ((tri_bytes + 15) & ~size_t(15)));
+    int32_t* d_cnt = (int32_t*)((char*)d_w + w_bytes);
+    int rc = WTRI_OK;
+    int32_t status = 0;
+    for (int scale = 1; scale <= 64; scale *= 8) {
+        rc = launch(d_tri, d_w, d_cnt, s, scale);
+        if (rc != WTRI_OK) break;
+        cudaError_t e = cudaMemcpyAsync(&status, d_cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            rc = cuda_error(e, "query", __FILE__, __LINE__);
+            break;
+        }
+        if (status == WTRI_ENOMEM && scale < 64) continue;  // bounded buffer overflowed: retry
+        break;
+    }
+    if (rc == WTRI_OK && status < 0) {
+        rc = set_error(status, status == WTRI_ENOMEM     ? "device candidate buffer overflow"
+                               : status == WTRI_ETIMEOUT ? "bounded device wait ran out"
+                                                         : "device-side error in query");
+    }
+    if (rc == WTRI_OK && status > 0) {
+        cudaError_t e = cudaMemcpyAsync(out->tris, d_tri, sizeof(wtri_tri) * (size_t)status,
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out->weight, d_w, sizeof(double) * (size_t)status,
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_error(e, "result copy", __FILE__, __LINE__);
+    }
+    cudaFreeAsync(buf, s);
+    if (rc == WTRI_OK) out->count = status;
+    return rc;
+}
+
+}  // namespace
+}  // namespace wtri
+
+using namespace wtri;
+
+extern "C" {
+
+WTRI_API const char* wtri_last_error(void) { return t_last_error.c_str(); }
+
+WTRI_API const char* wtri_version(void) { return "wtri 0.1 (sm_103a)"; }
+
+WTRI_API int wtri_build_csr(int32_t n, int64_t m, const int32_t* u, const int32_t* v,
+                            const int32_t* w, int on_device, void* cuda_stream, wtri_graph** out) {
+    if (!out) return set_error(WTRI_EINVAL, "out is NULL");
+    *out = nullptr;
+    t_last_error.clear();
+    return build_graph(n, m, u, v, w, on_device, (cudaStream_t)cuda_stream, out);
+}
+
+WTRI_API void wtri_graph_free(wtri_graph* g) {
+    if (!g) return;
+    // Queries may have run on other streams: let all device work finish.
+    cudaDeviceSynchronize();
+    cudaFreeAsync(g->base, g->stream);
+    cudaStreamSynchronize(g->stream);
+    delete g;
+}
+
+WTRI_API int wtri_graph_info(const wtri_graph* g, int32_t* n, int64_t* m, int32_t* max_degree,
+                             int32_t* max_weight, int64_t* device_bytes) {
+    if (!g) return set_error(WTRI_EINVAL, "graph is NULL");
+    if (n) *n = g->d.n;
+    if (m) *m = g->d.m;
+    if (max_degree) *max_degree = g->d.maxdeg;
+    if (max_weight) *max_weight = g->d.wmax;
+    if (device_bytes) *device_bytes = g->bytes;
+    return WTRI_OK;
+}
+
+WTRI_API int wtri_topk(const wtri_graph* g, double p, int32_t k, wtri_result* out) {
+    if (!out) return set_error(WTRI_EINVAL, "out is NULL");
+    out->count = 0;
+    int code = 0;
+    WTRI_TRY(check_query(g, k));
+    WTRI_TRY(p_to_code(p, &code));
+    if (!out->tris || !out->weight) return set_error(WTRI_EINVAL, "result arrays are NULL");
+    if (out->capacity < k) return set_error(WTRI_EINVAL, "result capacity below k");
+    if (g->d.m == 0) return WTRI_OK;
+    return host_result_query(g, k, out,
+                             [&](wtri_tri* t, double* wv, int32_t* c, cudaStream_t s, int scale) {
+                                 return topk_device(g, code, k, t, wv, c, s, scale);
+                             });
+}
+
+WTRI_API int wtri_topk_device(const wtri_graph* g, double p, int32_t k, wtri_tri* d_tris,
+                              double* d_weight, int32_t* d_count, void* stream) {
+    int code = 0;
+    WTRI_TRY(check_query(g, k));
+    WTRI_TRY(p_to_code(p, &code));
+    if (!d_tris || !d_weight || !d_count) return set_error(WTRI_EINVAL, "output pointers are NULL");
+    cudaStream_t s = stream ? (cudaStream_t)stream : g->stream;
+    if (g->d.m == 0) {
+        WTRI_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int32_t), s));
+        return WTRI_OK;
+    }
+    return topk_device(g, code, k, d_tris, d_weight, d_count, s, 1);
+}
+
+WTRI_API int wtri_sample_topk(const wtri_graph* g, double p, int32_t k, int64_t nsamples,
+                              uint64_t seed, wtri_result* out) {
+    if (!out) return set_error(WTRI_EINVAL, "out is NULL");
+    out->count = 0;
+    int code = 0;
+    WTRI_TRY(check_query(g, k));
+    WTRI_TRY(p_to_code(p, &code));
+    if (code != P_ONE && code != P_TWO)
+        return set_error(WTRI_EUNSUPPORTED, "edge sampling needs p = 1 or 2");
+    if (nsamples < 0) return set_error(WTRI_EINVAL, "nsamples must be non-negative");
+    if (!out->tris || !out->weight) return set_error(WTRI_EINVAL, "result arrays are NULL");
+    if (out->capacity < k) return set_error(WTRI_EINVAL, "result capacity below k");
+    if (g->d.m == 0 || nsamples == 0) return WTRI_OK;
+    return host_result_query(g, k, out,
+                             [&](wtri_tri* t, double* wv, int32_t* c, cudaStream_t s, int scale) {
+                                 return sample_topk_device(g, code, k, nsamples, seed, t, wv, c, s,
+                                                           scale);
+                             });
+}
+
+WTRI_API int wtri_graph_copy_array(const wtri_graph* g, int which, void* dst,
+                                   int64_t bytes_capacity, int64_t* bytes_out) {
+    if (!g) return set_error(WTRI_EINVAL, "graph is NULL");
+    const int64_t n = g->d.n, m = g->d.m;
+    const void* src = nullptr;
+    int64_t bytes = 0;
+    switch (which) {
+        case WTRI_ARR_DEGREE: src = g->d.deg; bytes = 4 * n; break;
+        case WTRI_ARR_ROWPTR: src = g->d.rowptr; bytes = 8 * (n + 1); break;
+        case WTRI_ARR_ORDER_U: src = g->d.ord_u; bytes = 4 * m; break;
+        case WTRI_ARR_ORDER_V: src = g->d.ord_v; bytes = 4 * m; break;
+        case WTRI_ARR_ORDER_W: src = g->d.ord_w; bytes = 4 * m; break;
+        case WTRI_ARR_WCOL: src = g->d.wcol; bytes = 8 * m; break;
+        case WTRI_ARR_WWT: src = g->d.wwt; bytes = 8 * m; break;
+        case WTRI_ARR_WRANK: src = g->d.wrk; bytes = 8 * m; break;
+        case WTRI_ARR_SCOL: src = g->d.scol; bytes = 8 * m; break;
+        case WTRI_ARR_SWT: src = g->d.swt; bytes = 8 * m; break;
+        case WTRI_ARR_SRANK: src = g->d.srk; bytes = 8 * m; break;
+        case WTRI_ARR_OROWPTR: src = g->d.orowptr; bytes = 8 * (n + 1); break;
+        case WTRI_ARR_OCOL: src = g->d.ocol; bytes = 4 * m; break;
+        case WTRI_ARR_OWT: src = g->d.owt; bytes = 4 * m; break;
+        case WTRI_ARR_ORANK: src = g->d.ork; bytes = 4 * m; break;
+        default: return set_error(WTRI_EINVAL, "unknown array id");
+    }
+    if (bytes_out) *bytes_out = bytes;
+    if (!dst) return WTRI_OK;
+    if (bytes_capacity < bytes) return set_error(WTRI_EINVAL, "destination too small");
+    if (bytes == 0) return WTRI_OK;
+    WTRI_CUDA(cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyDeviceToHost, g->stream));
+    WTRI_CUDA(cudaStreamSynchronize(g->stream));
+    return WTRI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,712 @@
+// Device graph build: validation, degrees, the edge order, per-vertex
+// weight-sorted lists, id-sorted lists and the degree orientation.
+//
+// Preprocessing named by the paper: "Sort E in decreasing order of weight"
+// (Algorithm 2, first step), neighbour sets N(a) and degrees d_a (Section
+// 4), and the NodeIterator++ degree ordering (Section 5.2).
+//
+// Pipeline (one stream, inputs read once from HBM or host):
+//   1. k_validate_degree: rejects bad edges, counts degrees, max weight.
+//   2. rowptr = exclusive scan of degrees (+ max degree).
+//   3. Edge order: stable LSD radix sort of key (wmax - w) carrying (u, v).
+//   4. Weight-sorted lists: the virtual stream "two entries per edge, in edge
+//      order" is stably radix-sorted by row, so each row keeps edge order.
+//   5. Id-sorted lists: the weight-sorted entries, read row by row (so the
+//      stream is ascending in its row x), are mirrored to (row c, col x) and
+//      stably sorted by row c, which leaves each row ascending in x.
+//   6. Repeated pairs show up as equal neighbours in an id-sorted row.
+//   7. Oriented lists: per row, keep neighbours of higher (degree, id) rank.
+#include <cuda_runtime.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+
+#include "wtri_internal.cuh"
+#include "wtri_radix.cuh"
+
+namespace wtri {
+
+namespace {
+
+constexpr int BLK = 256;
+
+struct BuildStatus {
+    uint32_t err;
+    int32_t wmax;
+    int32_t maxdeg;
+    int32_t pad;
+    unsigned long long first_bad;  // smallest offending edge index
+};
+
+__global__ void k_validate_degree(int32_t n, int64_t m, const int32_t* __restrict__ u,
+                                  const int32_t* __restrict__ v, const int32_t* __restrict__ w,
+                                  int32_t* __restrict__ deg, BuildStatus* st) {
+    int32_t wloc = 0;
+    uint32_t eloc = 0;
+    unsigned long long bad = ~0ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = u[i], b = v[i], x = w[i];
+        uint32_t e = 0;
+        if (a < 0 || a >= n || b < 0 || b >= n) e |= DEV_ERR_RANGE;
+        else if (a == b) e |= DEV_ERR_SELF_LOOP;
+        if (x <= 0) e |= DEV_ERR_WEIGHT;
+        if (e) {
+            eloc |= e;
+            if ((unsigned long long)i < bad) bad = (unsigned long long)i;
+            continue;
+        }
+        atomicAdd(&deg[a], 1);
+        atomicAdd(&deg[b], 1);
+        wloc = max(wloc, x);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        wloc = max(wloc, __shfl_xor_sync(0xffffffffu, wloc, o));
+        eloc |= __shfl_xor_sync(0xffffffffu, eloc, o);
+        unsigned long long ob = __shfl_xor_sync(0xffffffffu, bad, o);
+        bad = ob < bad ? ob : bad;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (wloc) atomicMax(&st->wmax, wloc);
+        if (eloc) {
+            atomicOr(&st->err, eloc);
+            atomicMin(&st->first_bad, bad);
+        }
+    }
+}
+
+// ---- exclusive scan int32 -> int64 (3 kernels) ---------------------------
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = BLK * SCAN_ITEMS;
+
+__device__ __forceinline__ int64_t block_scan_i64(int64_t x, int64_t* sh, int64_t* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) sh[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t t = lane < (BLK / 32) ? sh[lane] : 0;
+        int64_t ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        if (lane < BLK / 32) sh[lane] = ti - t;
+        if (lane == BLK / 32 - 1) *total = ti;
+    }
+    __syncthreads();
+    int64_t r = sh[wid] + inc - x;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(const int32_t* __restrict__ in, int64_t n, int64_t* tile_sums,
+                              int32_t* maxval) {
+    __shared__ int64_t sh[BLK / 32];
+    __shared__ int64_t tot;
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int64_t s = 0;
+    int32_t mx = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        int64_t i = base + j * BLK + threadIdx.x;
+        if (i < n) {
+            int32_t x = in[i];
+            s += x;
+            mx = max(mx, x);
+        }
+    }
+    block_scan_i64(s, sh, &tot);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && maxval) atomicMax(maxval, mx);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_tiles(int64_t* tile_sums, int64_t tiles, int64_t* out_total) {
+    __shared__ int64_t sh[BLK / 32];
+    __shared__ int64_t tot;
+    int64_t carry = 0;
+    for (int64_t b = 0; b < tiles; b += BLK) {
+        int64_t i = b + threadIdx.x;
+        int64_t x = i < tiles ? tile_sums[i] : 0;
+        int64_t ex = block_scan_i64(x, sh, &tot);
+        if (i < tiles) tile_sums[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out_total = carry;
+}
+
+__global__ void k_scan_apply(const int32_t* __restrict__ in, int64_t n,
+                             const int64_t* __restrict__ tile_offs, int64_t* __restrict__ out) {
+    __shared__ int64_t sh[BLK / 32];
+    __shared__ int64_t tot;
+    // blocked arrangement: thread t owns items [t*ITEMS, (t+1)*ITEMS) of the tile
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int32_t x[SCAN_ITEMS];
+    int64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        x[j] = (base + j < n) ? in[base + j] : 0;
+        s += x[j];
+    }
+    int64_t run = block_scan_i64(s, sh, &tot) + tile_offs[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        if (base + j < n) out[base + j] = run;
+        run += x[j];
+    }
+}
+
+// ---- radix loaders / storers for the build ---------------------------------
+
+// Pass input for the edge order: key = wmax - w, values (u, v).
+struct EdgeLoader {
+    static constexpr double KEY_BYTES = 4.0;   // w
+    static constexpr double REC_BYTES = 12.0;  // u, v, w
+    const int32_t* u;
+    const int32_t* v;
+    const int32_t* w;
+    int32_t wmax;
+    __device__ __forceinline__ uint32_t key(int64_t i) const {
+        return (uint32_t)(wmax - __ldg(w + i));
+    }
+    __device__ __forceinline__ uint32_t val(int q, int64_t i) const {
+        return (uint32_t)__ldg((q == 0 ? u : v) + i);
+    }
+};
+
+// Final edge-order output.
+struct EdgeOrderStorer {
+    __host__ __device__ double rec_bytes() const { return 12.0; }
+    int32_t* ou;
+    int32_t* ov;
+    int32_t* ow;
+    int32_t wmax;
+    __device__ __forceinline__ void key(int64_t p, uint32_t k) const { ow[p] = wmax - (int32_t)k; }
+    __device__ __forceinline__ void val(int q, int64_t p, uint32_t x) const {
+        (q == 0 ? ou : ov)[p] = (int32_t)x;
+    }
+};
+
+// Virtual stream of adjacency entries in edge order: entry i belongs to edge
+// r = i / 2; side 0 is (row u, col v), side 1 is (row v, col u).
+// Values: col, weight, r.
+struct OrderEntryLoader {
+    static constexpr double KEY_BYTES = 4.0;  // u or v: 8 bytes per edge, two entries
+    static constexpr double REC_BYTES = 6.0;  // u, v, w: 12 bytes per edge, two entries
+    const int32_t* ou;
+    const int32_t* ov;
+    const int32_t* ow;
+    __device__ __forceinline__ uint32_t key(int64_t i) const {
+        const int64_t r = i >> 1;
+        return (uint32_t)__ldg(((i & 1) ? ov : ou) + r);
+    }
+    __device__ __forceinline__ uint32_t val(int q, int64_t i) const {
+        const int64_t r = i >> 1;
+        if (q == 0) return (uint32_t)__ldg(((i & 1) ? ou : ov) + r);
+        if (q == 1) return (uint32_t)__ldg(ow + r);
+        return (uint32_t)r;
+    }
+};
+
+// Mirrored weight-sorted entries: entry i of row x (= wrow[i]) with
+// neighbour c becomes (row c; values x, weight, r).
+struct MirrorLoader {
+    static constexpr double KEY_BYTES = 4.0;   // wcol
+    static constexpr double REC_BYTES = 16.0;  // wcol, wrow, wwt, wrk
+    const int32_t* wrow;
+    const int32_t* wcol;
+    const int32_t* wwt;
+    const int32_t* wrk;
+    __device__ __forceinline__ uint32_t key(int64_t i) const { return (uint32_t)__ldg(wcol + i); }
+    __device__ __forceinline__ uint32_t val(int q, int64_t i) const {
+        return (uint32_t)__ldg((q == 0 ? wrow : (q == 1 ? wwt : wrk)) + i);
+    }
+};
+
+// Final row-sorted output: key (row) optional, values col, weight, r.
+struct RowsStorer {
+    __host__ __device__ double rec_bytes() const { return row ? 16.0 : 12.0; }
+    int32_t* row;  // may be null
+    int32_t* col;
+    int32_t* wt;
+    int32_t* rk;
+    __device__ __forceinline__ void key(int64_t p, uint32_t k) const {
+        if (row) row[p] = (int32_t)k;
+    }
+    __device__ __forceinline__ void val(int q, int64_t p, uint32_t x) const {
+        (q == 0 ? col : (q == 1 ? wt : rk))[p] = (int32_t)x;
+    }
+};
+
+// Runs a full LSD sort over 'bits' key bits: first pass from 'first',
+// middle passes through ping-pong arrays, last pass into 'last'.
+template <int NV, class First, class Last>
+int lsd_sort(const First& first, const Last& last, int64_t n, int bits, uint32_t* pp_a,
+             uint32_t* pp_b, int64_t cap, uint32_t* scratch, cudaStream_t s) {
+    using namespace radix;
+    const int passes = (bits + BITS - 1) / BITS;
+    (void)cap;
+    if (passes == 0) return set_error(WTRI_EINVAL, "internal: zero-pass sort");
+    uint32_t* cur = pp_a;
+    uint32_t* nxt = pp_b;
+    for (int p = 0; p < passes; p++) {
+        const int shift = p * BITS;
+        const int pb = std::min(BITS, bits - shift);
+        ArrLoader<NV> al;
+        ArrStorer<NV> as;
+        al.k = cur;
+        as.k = nxt;
+        for (int q = 0; q < NV; q++) {
+            al.v[q] = cur + (size_t)(q + 1) * n;
+            as.v[q] = nxt + (size_t)(q + 1) * n;
+        }
+        if (p == 0 && p == passes - 1) {
+            WTRI_TRY((run_pass<NV, true>(first, last, n, shift, pb, scratch, s)));
+        } else if (p == 0) {
+            WTRI_TRY((run_pass<NV, true>(first, as, n, shift, pb, scratch, s)));
+            std::swap(cur, nxt);
+        } else if (p == passes - 1) {
+            WTRI_TRY((run_pass<NV, true>(al, last, n, shift, pb, scratch, s)));
+        } else {
+            WTRI_TRY((run_pass<NV, true>(al, as, n, shift, pb, scratch, s)));
+            std::swap(cur, nxt);
+        }
+    }
+    return WTRI_OK;
+}
+
+__global__ void k_copy_identity_order(int64_t m, const int32_t* u, const int32_t* v,
+                                      const int32_t* w, int32_t* ou, int32_t* ov, int32_t* ow) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        ou[i] = u[i];
+        ov[i] = v[i];
+        ow[i] = w[i];
+    }
+}
+
+// Repeated undirected pair = equal neighbours next to each other in one
+// id-sorted row.
+__global__ void k_find_duplicates(int64_t n2, const int32_t* __restrict__ srow,
+                                  const int32_t* __restrict__ scol, BuildStatus* st) {
+    unsigned long long bad = ~0ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n2;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (srow[i] == srow[i - 1] && scol[i] == scol[i - 1]) {
+            if ((unsigned long long)i < bad) bad = (unsigned long long)i;
+        }
+    }
+    if (bad != ~0ull) {
+        atomicOr(&st->err, DEV_ERR_DUPLICATE);
+        atomicMin(&st->first_bad, bad);  // entry index, not edge index
+    }
+}
+
+__device__ __forceinline__ bool rank_less(const int32_t* deg, int32_t a, int32_t b) {
+    const int32_t da = __ldg(deg + a), db = __ldg(deg + b);
+    return da < db || (da == db && a < b);
+}
+
+// Out-degree in the orientation: the lower-ranked endpoint owns the edge.
+__global__ void k_out_degree(int64_t m, const int32_t* __restrict__ ou,
+                             const int32_t* __restrict__ ov, const int32_t* __restrict__ deg,
+                             int32_t* __restrict__ odeg) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = ou[r], b = ov[r];
+        atomicAdd(&odeg[rank_less(deg, a, b) ? a : b], 1);
+    }
+}
+
+constexpr int LONG_ROW = 1024;
+
+// Warp per row (rows shorter than LONG_ROW); long rows are queued.
+__global__ void k_orient_rows(int32_t n, const int64_t* __restrict__ rowptr,
+                              const int32_t* __restrict__ scol, const int32_t* __restrict__ swt,
+                              const int32_t* __restrict__ srk, const int32_t* __restrict__ deg,
+                              const int64_t* __restrict__ orowptr, int32_t* __restrict__ ocol,
+                              int32_t* __restrict__ owt, int32_t* __restrict__ ork,
+                              int32_t* long_rows, int32_t* long_count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = warp; x < n; x += nwarps) {
+        const int64_t s = rowptr[x], e = rowptr[x + 1];
+        if (e - s >= LONG_ROW) {
+            if (lane == 0) long_rows[atomicAdd(long_count, 1)] = (int32_t)x;
+            continue;
+        }
+        int64_t out = orowptr[x];
+        for (int64_t j0 = s; j0 < e; j0 += 32) {
+            const int64_t j = j0 + lane;
+            bool fwd = false;
+            int32_t c = 0;
+            if (j < e) {
+                c = scol[j];
+                fwd = rank_less(deg, (int32_t)x, c);
+            }
+            const uint32_t b = __ballot_sync(0xffffffffu, fwd);
+            if (fwd) {
+                const int64_t p = out + __popc(b & ((1u << lane) - 1u));
+                ocol[p] = c;
+                owt[p] = swt[j];
+                ork[p] = srk[j];
+            }
+            out += __popc(b);
+        }
+    }
+}
+
+// Block per long row.
+__global__ void k_orient_long_rows(const int32_t* __restrict__ long_rows,
+                                   const int32_t* __restrict__ long_count,
+                                   const int64_t* __restrict__ rowptr,
+                                   const int32_t* __restrict__ scol, const int32_t* __restrict__ swt,
+                                   const int32_t* __restrict__ srk, const int32_t* __restrict__ deg,
+                                   const int64_t* __restrict__ orowptr, int32_t* __restrict__ ocol,
+                                   int32_t* __restrict__ owt, int32_t* __restrict__ ork) {
+    __shared__ uint32_t warp_cnt[BLK / 32];
+    __shared__ uint32_t tot;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int cnt = *long_count;
+    for (int it = blockIdx.x; it < cnt; it += gridDim.x) {
+        const int32_t x = long_rows[it];
+        const int64_t s = rowptr[x], e = rowptr[x + 1];
+        int64_t out = orowptr[x];
+        for (int64_t j0 = s; j0 < e; j0 += BLK) {
+            const int64_t j = j0 + threadIdx.x;
+            bool fwd = false;
+            int32_t c = 0;
+            if (j < e) {
+                c = scol[j];
+                fwd = rank_less(deg, x, c);
+            }
+            const uint32_t b = __ballot_sync(0xffffffffu, fwd);
+            if (lane == 0) warp_cnt[wid] = __popc(b);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t acc = 0;
+                for (int k = 0; k < BLK / 32; k++) {
+                    uint32_t t = warp_cnt[k];
+                    warp_cnt[k] = acc;
+                    acc += t;
+                }
+                tot = acc;
+            }
+            __syncthreads();
+            if (fwd) {
+                const int64_t p = out + warp_cnt[wid] + __popc(b & ((1u << lane) - 1u));
+                ocol[p] = c;
+                owt[p] = swt[j];
+                ork[p] = srk[j];
+            }
+            out += tot;
+            __syncthreads();
+        }
+    }
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Graphs and scratch come from the device's stream-ordered pool; keep freed
+// blocks in the pool (no release at synchronization) so that rebuilding a
+// graph of the same size reuses memory instead of paying for cudaMalloc.
+void keep_pool_memory(int dev) {
+    static int done_mask = 0;  // benign race: the attribute write is idempotent
+    if (dev < 0 || dev >= 31 || (done_mask >> dev) & 1) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done_mask |= 1 << dev;
+}
+
+}  // namespace
+
+int exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s) {
+    // out has n+1 entries; out[n] = total.
+    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    int64_t* tile_sums = nullptr;
+    WTRI_CUDA(cudaMallocAsync((void**)&tile_sums, sizeof(int64_t) * (size_t)std::max<int64_t>(tiles, 1), s));
+    if (tiles > 0) {
+        ProfScope ps("scan_offsets", s, 4.0 * n * 2 + 8.0 * (n + 1), 3);
+        k_scan_reduce<<<(unsigned)tiles, BLK, 0, s>>>(in, n, tile_sums, nullptr);
+        k_scan_tiles<<<1, BLK, 0, s>>>(tile_sums, tiles, out + n);
+        k_scan_apply<<<(unsigned)tiles, BLK, 0, s>>>(in, n, tile_sums, out);
+    } else {
+        WTRI_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+    }
+    WTRI_CUDA(cudaGetLastError());
+    WTRI_CUDA(cudaFreeAsync(tile_sums, s));
+    return WTRI_OK;
+}
+
+namespace {
+
+int scan_with_max(const int32_t* in, int64_t* out, int64_t n, int32_t* d_max, cudaStream_t s) {
+    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    int64_t* tile_sums = nullptr;
+    WTRI_CUDA(cudaMallocAsync((void**)&tile_sums, sizeof(int64_t) * (size_t)std::max<int64_t>(tiles, 1), s));
+    ProfScope ps("scan_offsets", s, 4.0 * n * 2 + 8.0 * (n + 1), 3);
+    k_scan_reduce<<<(unsigned)tiles, BLK, 0, s>>>(in, n, tile_sums, d_max);
+    k_scan_tiles<<<1, BLK, 0, s>>>(tile_sums, tiles, out + n);
+    k_scan_apply<<<(unsigned)tiles, BLK, 0, s>>>(in, n, tile_sums, out);
+    WTRI_CUDA(cudaGetLastError());
+    WTRI_CUDA(cudaFreeAsync(tile_sums, s));
+    return WTRI_OK;
+}
+
+struct Scratch {
+    cudaStream_t s;
+    void* p = nullptr;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch() {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+
+unsigned grid_for(int64_t work, int per_block = BLK) {
+    int64_t g = (work + per_block - 1) / per_block;
+    const int64_t cap = (int64_t)sm_count() * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+}  // namespace
+
+int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
+                const int32_t* w_in, int on_device, cudaStream_t s, wtri_graph** out) {
+    *out = nullptr;
+    if (n <= 0) return set_error(WTRI_EINVAL, "n must be positive");
+    if (m < 0) return set_error(WTRI_EINVAL, "m must be non-negative");
+    if (m > (int64_t(1) << 30)) return set_error(WTRI_EUNSUPPORTED, "m above 2^30 edges");
+    if (m > 0 && (!u_in || !v_in || !w_in)) return set_error(WTRI_EINVAL, "null edge arrays");
+
+    int dev = 0;
+    WTRI_CUDA(cudaGetDevice(&dev));
+
+    // Inputs on the device.
+    Scratch in_buf(s);
+    const int32_t *u = u_in, *v = v_in, *w = w_in;
+    if (!on_device && m > 0) {
+        WTRI_CUDA(cudaMallocAsync(&in_buf.p, sizeof(int32_t) * 3 * (size_t)m, s));
+        int32_t* d = (int32_t*)in_buf.p;
+        WTRI_CUDA(cudaMemcpyAsync(d, u_in, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+        WTRI_CUDA(cudaMemcpyAsync(d + m, v_in, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+        WTRI_CUDA(cudaMemcpyAsync(d + 2 * m, w_in, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+        u = d;
+        v = d + m;
+        w = d + 2 * m;
+    }
+
+    // One allocation for every resident array (256-byte aligned pieces, with
+    // 16 bytes of slack after each so bulk copies may round sizes up).
+    const size_t N1 = (size_t)n, M = (size_t)m, M2 = 2 * (size_t)m;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes + 16, 256);
+        return o;
+    };
+    const size_t o_deg = take(4 * N1);
+    const size_t o_rowptr = take(8 * (N1 + 1));
+    const size_t o_orowptr = take(8 * (N1 + 1));
+    const size_t o_ou = take(4 * M), o_ov = take(4 * M), o_ow = take(4 * M);
+    const size_t o_wcol = take(4 * M2), o_wwt = take(4 * M2), o_wrk = take(4 * M2);
+    const size_t o_scol = take(4 * M2), o_swt = take(4 * M2), o_srk = take(4 * M2);
+    const size_t o_ocol = take(4 * M), o_owt = take(4 * M), o_ork = take(4 * M);
+    const size_t total = off;
+
+    wtri_graph* g = new (std::nothrow) wtri_graph();
+    if (!g) return set_error(WTRI_ENOMEM, "host allocation failed");
+    g->stream = s;
+    g->device = dev;
+    g->bytes = (int64_t)total;
+    keep_pool_memory(dev);
+    cudaError_t e = cudaMallocAsync(&g->base, total, s);
+    if (e != cudaSuccess) {
+        delete g;
+        cudaGetLastError();
+        return set_error(WTRI_ENOMEM, "device allocation of " + std::to_string(total) + " bytes failed");
+    }
+    char* B = (char*)g->base;
+    int32_t* deg = (int32_t*)(B + o_deg);
+    int64_t* rowptr = (int64_t*)(B + o_rowptr);
+    int64_t* orowptr = (int64_t*)(B + o_orowptr);
+    int32_t *ou = (int32_t*)(B + o_ou), *ov = (int32_t*)(B + o_ov), *ow = (int32_t*)(B + o_ow);
+    int32_t *wcol = (int32_t*)(B + o_wcol), *wwt = (int32_t*)(B + o_wwt), *wrk = (int32_t*)(B + o_wrk);
+    int32_t *scol = (int32_t*)(B + o_scol), *swt = (int32_t*)(B + o_swt), *srk = (int32_t*)(B + o_srk);
+    int32_t *ocol = (int32_t*)(B + o_ocol), *owt = (int32_t*)(B + o_owt), *ork = (int32_t*)(B + o_ork);
+
+    auto fail = [&](int rc) {
+        cudaFreeAsync(g->base, s);
+        cudaStreamSynchronize(s);
+        delete g;
+        return rc;
+    };
+
+    BuildStatus* d_st = nullptr;
+    BuildStatus h_st;
+    Scratch st_buf(s);
+    if (cudaMallocAsync(&st_buf.p, sizeof(BuildStatus), s) != cudaSuccess)
+        return fail(set_error(WTRI_ENOMEM, "status allocation failed"));
+    d_st = (BuildStatus*)st_buf.p;
+    {
+        BuildStatus init = {0u, 0, 0, 0, ~0ull};
+        if (cudaMemcpyAsync(d_st, &init, sizeof(init), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(deg, 0, 4 * N1, s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "memset", __FILE__, __LINE__));
+    }
+
+    // 1. validation + degrees
+    if (m > 0) {
+        ProfScope ps("validate_degree", s, 12.0 * m + 4.0 * n, 1);
+        k_validate_degree<<<grid_for(m), BLK, 0, s>>>(n, m, u, v, w, deg, d_st);
+    }
+    // 2. row offsets + max degree
+    {
+        int rc = scan_with_max(deg, rowptr, (int64_t)n, &d_st->maxdeg, s);
+        if (rc != WTRI_OK) return fail(rc);
+    }
+    if (cudaMemcpyAsync(&h_st, d_st, sizeof(h_st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(cuda_error(cudaGetLastError(), "validation", __FILE__, __LINE__));
+    if (h_st.err) {
+        std::string what = (h_st.err & DEV_ERR_RANGE) ? "vertex id outside [0, n)"
+                           : (h_st.err & DEV_ERR_SELF_LOOP) ? "self-loop"
+                                                            : "non-positive weight";
+        return fail(set_error(WTRI_EINVAL, "invalid edge " + std::to_string(h_st.first_bad) +
+                                               ": " + what));
+    }
+    g->d.n = n;
+    g->d.m = m;
+    g->d.wmax = h_st.wmax;
+    g->d.maxdeg = h_st.maxdeg;
+
+    if (m > 0) {
+        // Scratch: two ping-pong record buffers of (key + 3 values) x 2m, the
+        // radix counts, the row keys of the weight-sorted layout, long rows.
+        const int64_t n2 = 2 * m;
+        const size_t rec_words = 4 * (size_t)n2;
+        const size_t cnt_words = radix::scratch_words(n2);
+        const size_t words = 2 * rec_words + cnt_words + 2 * (size_t)n2 + 2 * N1 + 8;
+        Scratch tmp(s);
+        if (cudaMallocAsync(&tmp.p, words * 4, s) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(set_error(WTRI_ENOMEM, "device scratch allocation failed"));
+        }
+        uint32_t* pp_a = (uint32_t*)tmp.p;
+        uint32_t* pp_b = pp_a + rec_words;
+        uint32_t* counts = pp_b + rec_words;
+        int32_t* wrow = (int32_t*)(counts + cnt_words);
+        int32_t* srow = wrow + n2;
+        int32_t* odeg = srow + n2;
+        int32_t* long_rows = odeg + n;
+        int32_t* long_count = long_rows + n;
+
+        // 3. edge order
+        const int wbits = radix::bit_length((uint64_t)(h_st.wmax - 1));
+        if (wbits == 0) {
+            ProfScope ps("edge_order_copy", s, 24.0 * m, 1);
+            k_copy_identity_order<<<grid_for(m), BLK, 0, s>>>(m, u, v, w, ou, ov, ow);
+        } else {
+            EdgeLoader el{u, v, w, h_st.wmax};
+            EdgeOrderStorer es{ou, ov, ow, h_st.wmax};
+            int rc = lsd_sort<2>(el, es, m, wbits, pp_a, pp_b, m, counts, s);
+            if (rc != WTRI_OK) return fail(rc);
+        }
+        // 4. weight-sorted rows (row key kept in wrow for step 5)
+        const int nbits = std::max(1, radix::bit_length((uint64_t)(n - 1)));
+        {
+            OrderEntryLoader ol{ou, ov, ow};
+            RowsStorer rs{wrow, wcol, wwt, wrk};
+            int rc = lsd_sort<3>(ol, rs, n2, nbits, pp_a, pp_b, n2, counts, s);
+            if (rc != WTRI_OK) return fail(rc);
+        }
+        // 5. id-sorted rows; the last pass also writes each entry's row
+        {
+            MirrorLoader ml{wrow, wcol, wwt, wrk};
+            RowsStorer rs{srow, scol, swt, srk};
+            int rc = lsd_sort<3>(ml, rs, n2, nbits, pp_a, pp_b, n2, counts, s);
+            if (rc != WTRI_OK) return fail(rc);
+        }
+        // 6. repeated pairs
+        {
+            ProfScope ps("find_duplicates", s, 8.0 * n2, 1);
+            k_find_duplicates<<<grid_for(n2), BLK, 0, s>>>(n2, srow, scol, d_st);
+        }
+        // 7. orientation
+        if (cudaMemsetAsync(odeg, 0, 4 * N1, s) != cudaSuccess ||
+            cudaMemsetAsync(long_count, 0, 4, s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "memset", __FILE__, __LINE__));
+        {
+            ProfScope ps("out_degree", s, 8.0 * m + 8.0 * n, 1);
+            k_out_degree<<<grid_for(m), BLK, 0, s>>>(m, ou, ov, deg, odeg);
+        }
+        {
+            int rc = exclusive_scan_i32_to_i64(odeg, orowptr, (int64_t)n, s);
+            if (rc != WTRI_OK) return fail(rc);
+        }
+        {
+            // reads the id-sorted rows (col for every entry, weight and rank
+            // for the kept half), writes m oriented entries
+            ProfScope ps("orient_rows", s, 4.0 * n2 + 8.0 * m + 12.0 * m + 16.0 * n, 2);
+            k_orient_rows<<<grid_for((int64_t)n * 32), BLK, 0, s>>>(
+                n, rowptr, scol, swt, srk, deg, orowptr, ocol, owt, ork, long_rows, long_count);
+            k_orient_long_rows<<<sm_count() * 2, BLK, 0, s>>>(long_rows, long_count, rowptr, scol,
+                                                              swt, srk, deg, orowptr, ocol, owt, ork);
+        }
+        if (cudaGetLastError() != cudaSuccess)
+            return fail(set_error(WTRI_ECUDA, "build kernel launch failed"));
+        if (cudaMemcpyAsync(&h_st, d_st, sizeof(h_st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "build", __FILE__, __LINE__));
+        if (h_st.err & DEV_ERR_DUPLICATE) {
+            int32_t pair[2] = {-1, -1};
+            const int64_t j = (int64_t)h_st.first_bad;
+            cudaMemcpyAsync(&pair[0], srow + j, 4, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(&pair[1], scol + j, 4, cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            return fail(set_error(WTRI_EINVAL, "repeated undirected pair (" +
+                                                   std::to_string(pair[0]) + ", " +
+                                                   std::to_string(pair[1]) + ")"));
+        }
+    } else {
+        if (cudaMemsetAsync(orowptr, 0, 8 * (N1 + 1), s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "build", __FILE__, __LINE__));
+    }
+
+    g->d.deg = deg;
+    g->d.rowptr = rowptr;
+    g->d.ord_u = ou;
+    g->d.ord_v = ov;
+    g->d.ord_w = ow;
+    g->d.wcol = wcol;
+    g->d.wwt = wwt;
+    g->d.wrk = wrk;
+    g->d.scol = scol;
+    g->d.swt = swt;
+    g->d.srk = srk;
+    g->d.orowptr = orowptr;
+    g->d.ocol = ocol;
+    g->d.owt = owt;
+    g->d.ork = ork;
+    *out = g;
+    return WTRI_OK;
+}
+
+}  // namespace wtri

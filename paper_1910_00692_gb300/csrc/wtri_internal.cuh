@@ -1,0 +1,128 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/wtri.h"
+
+namespace wtri {
+
+// ---------------------------------------------------------------------------
+// Errors: every host function returns a WTRI_* code; the message goes to the
+// thread-local last-error slot.
+// ---------------------------------------------------------------------------
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+#define WTRI_CUDA(call)                                                        \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) return ::wtri::cuda_error(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define WTRI_TRY(call)                     \
+    do {                                   \
+        int rc_ = (call);                  \
+        if (rc_ != WTRI_OK) return rc_;    \
+    } while (0)
+
+// Device-side error bits (written to a status word; read by the host).
+enum : uint32_t {
+    DEV_ERR_SELF_LOOP = 1u << 0,
+    DEV_ERR_RANGE = 1u << 1,
+    DEV_ERR_WEIGHT = 1u << 2,
+    DEV_ERR_DUPLICATE = 1u << 3,
+    DEV_ERR_INTERNAL = 1u << 4,   // an invariant of the path failed
+    DEV_ERR_OVERFLOW = 1u << 5,   // a bounded device buffer filled up
+    DEV_ERR_TIMEOUT = 1u << 6,    // a bounded wait ran out
+};
+
+// p codes (template parameter of the scoring kernels).
+enum PCode : int { P_MIN = 0, P_ONE = 1, P_TWO = 2, P_MAX = 3 };
+
+int p_to_code(double p, int* code);
+
+// ---------------------------------------------------------------------------
+// Device-resident graph (all arrays library-owned device memory).
+// Layouts (r is an edge's position in the edge order: weight desc, input
+// index asc):
+//   ord_u/v/w[r]          edge order
+//   rowptr[n+1]           offsets of both symmetric layouts
+//   wcol/wwt/wrk[2m]      per-vertex lists in edge order (weight-sorted)
+//   scol/swt/srk[2m]      per-vertex lists by neighbour id
+//   orowptr[n+1]          oriented offsets
+//   ocol/owt/ork[m]       oriented lists by neighbour id
+// ---------------------------------------------------------------------------
+struct DevGraph {
+    int32_t n;
+    int64_t m;
+    int32_t wmax;
+    int32_t maxdeg;
+    const int32_t* deg;
+    const int64_t* rowptr;
+    const int32_t* ord_u;
+    const int32_t* ord_v;
+    const int32_t* ord_w;
+    const int32_t* wcol;
+    const int32_t* wwt;
+    const int32_t* wrk;
+    const int32_t* scol;
+    const int32_t* swt;
+    const int32_t* srk;
+    const int64_t* orowptr;
+    const int32_t* ocol;
+    const int32_t* owt;
+    const int32_t* ork;
+};
+
+}  // namespace wtri
+
+struct wtri_graph {
+    wtri::DevGraph d;
+    cudaStream_t stream;
+    int device;
+    void* base;        // one allocation holding every array
+    int64_t bytes;
+};
+
+namespace wtri {
+
+// Build (wtri_build.cu).
+int build_graph(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int32_t* w,
+                int on_device, cudaStream_t stream, wtri_graph** out);
+
+// Exact top-k (wtri_topk.cu).  Writes device outputs; status (count or a
+// negative code) to d_count.  'retry_scale' enlarges the scratch buffers.
+int topk_device(const wtri_graph* g, int pcode, int32_t k, wtri_tri* d_tris, double* d_weight,
+                int32_t* d_count, cudaStream_t stream, int retry_scale);
+
+// Edge sampling (wtri_sample.cu).
+int sample_topk_device(const wtri_graph* g, int pcode, int32_t k, int64_t nsamples,
+                       uint64_t seed, wtri_tri* d_tris, double* d_weight, int32_t* d_count,
+                       cudaStream_t stream, int retry_scale);
+
+// Phase timers / launch counter (wtri_prof.cu).  'bytes' is the phase's
+// algorithmic traffic; 'launches' the number of kernels it launches.
+void prof_begin(const char* name, cudaStream_t s, double bytes, int launches);
+void prof_end(cudaStream_t s);
+
+struct ProfScope {
+    cudaStream_t s;
+    ProfScope(const char* name, cudaStream_t st, double bytes, int launches) : s(st) {
+        prof_begin(name, st, bytes, launches);
+    }
+    ~ProfScope() { prof_end(s); }
+};
+
+// Shared launch helpers.
+inline unsigned int ceil_div_u(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }
+int sm_count();
+
+// Device-wide exclusive scan of int32 counts into int64 offsets (n+1
+// outputs; out[n] = total).  Scratch is stream-ordered.
+int exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+
+}  // namespace wtri

@@ -1,0 +1,317 @@
+// Stable LSD radix sort passes (reduce-then-scan), 8-bit digits.
+//
+// One pass orders N records by digit (key >> shift) & mask, stably, where a
+// record is a 32-bit key plus NV 32-bit values.  Records come from a Loader
+// and go to a Storer, so a pass can read a virtual stream (e.g. two
+// adjacency entries per edge) and write final arrays without staging copies.
+//
+//   Loader: __device__ uint32_t key(int64_t i) const;
+//           __device__ uint32_t val(int q, int64_t i) const;   // q < NV
+//   Storer: __device__ void key(int64_t pos, uint32_t k) const;
+//           __device__ void val(int q, int64_t pos, uint32_t x) const;
+//
+// Three kernels per pass: per-chunk digit histograms (upsweep), a per-digit
+// scan over chunks, and the scatter (downsweep).  Within a tile the scatter
+// ranks records with warp match + per-warp counters (stable), stages them in
+// shared memory in digit order, and writes each digit's run contiguously.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wtri_internal.cuh"
+
+namespace wtri {
+namespace radix {
+
+constexpr int BITS = 8;
+constexpr int RADIX = 1 << BITS;
+constexpr int THREADS = 256;
+constexpr int WARPS = THREADS / 32;
+constexpr int ITEMS = 12;
+constexpr int TILE = THREADS * ITEMS;
+static_assert(THREADS == RADIX, "one thread per digit in the tile scan");
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Exclusive scan of one value per thread over a 256-thread block.
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_t* warp_tot,
+                                                             uint32_t* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < WARPS ? warp_tot[lane] : 0;
+        uint32_t ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        if (lane < WARPS) warp_tot[lane] = ti - t;
+        if (lane == WARPS - 1) *total = ti;
+    }
+    __syncthreads();
+    uint32_t r = warp_tot[w] + inc - x;
+    __syncthreads();
+    return r;
+}
+
+struct PassGeom {
+    int64_t n;        // records
+    int64_t chunk;    // records per chunk (multiple of TILE)
+    int chunks;       // G
+    int shift;
+    uint32_t mask;
+};
+
+template <class Loader>
+__global__ void __launch_bounds__(THREADS) k_upsweep(Loader ld, PassGeom g, uint32_t* counts) {
+    __shared__ uint32_t hist[WARPS][RADIX];
+    const int w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < WARPS * RADIX; i += THREADS) (&hist[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t beg = (int64_t)blockIdx.x * g.chunk;
+    const int64_t end = min(g.n, beg + g.chunk);
+    for (int64_t i = beg + threadIdx.x; i < end; i += THREADS) {
+        uint32_t d = (ld.key(i) >> g.shift) & g.mask;
+        atomicAdd(&hist[w][d], 1u);
+    }
+    __syncthreads();
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < WARPS; k++) s += hist[k][threadIdx.x];
+    counts[(int64_t)threadIdx.x * g.chunks + blockIdx.x] = s;
+}
+
+// Block d: exclusive scan of counts[d][0..G) in place; totals[d] = sum.
+__global__ void __launch_bounds__(THREADS) k_digit_scan(uint32_t* counts, int chunks,
+                                                        uint32_t* totals) {
+    __shared__ uint32_t warp_tot[WARPS];
+    __shared__ uint32_t tot;
+    uint32_t* c = counts + (int64_t)blockIdx.x * chunks;
+    uint32_t carry = 0;
+    for (int base = 0; base < chunks; base += THREADS) {
+        int i = base + threadIdx.x;
+        uint32_t x = i < chunks ? c[i] : 0;
+        uint32_t ex = block_exclusive_scan_256(x, warp_tot, &tot);
+        if (i < chunks) c[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+template <int NV>
+struct TileSmem {
+    uint32_t cnt[WARPS][RADIX];
+    uint32_t stage[TILE];
+    uint32_t stage_key[TILE];
+    uint32_t run[RADIX];         // global position of this chunk's next record per digit
+    uint32_t tile_start[RADIX];  // tile-local start of each digit
+    uint32_t tile_total[RADIX];
+    uint32_t warp_tot[WARPS];
+    uint32_t total;
+};
+
+template <int NV, class Loader, class Storer, bool STORE_KEY>
+__global__ void __launch_bounds__(THREADS) k_downsweep(Loader ld, Storer st, PassGeom g,
+                                                       const uint32_t* counts,
+                                                       const uint32_t* totals) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSmem<NV>& S = *reinterpret_cast<TileSmem<NV>*>(smem_raw);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+
+    {   // global base of each digit = exclusive scan of digit totals
+        uint32_t t = totals[threadIdx.x];
+        uint32_t base = block_exclusive_scan_256(t, S.warp_tot, &S.total);
+        S.run[threadIdx.x] = base + counts[(int64_t)threadIdx.x * g.chunks + blockIdx.x];
+    }
+    __syncthreads();
+
+    const int64_t beg = (int64_t)blockIdx.x * g.chunk;
+    const int64_t end = min(g.n, beg + g.chunk);
+    const uint32_t lt = lanemask_lt();
+
+    for (int64_t tbase = beg; tbase < end; tbase += TILE) {
+        const int tcount = (int)min((int64_t)TILE, end - tbase);
+        for (int i = threadIdx.x; i < WARPS * RADIX; i += THREADS) (&S.cnt[0][0])[i] = 0;
+        __syncthreads();
+
+        uint32_t key[ITEMS];
+        uint32_t rank[ITEMS];
+        uint32_t dig[ITEMS];
+#pragma unroll
+        for (int j = 0; j < ITEMS; j++) {
+            const int li = w * 32 * ITEMS + j * 32 + lane;
+            const bool valid = li < tcount;
+            key[j] = valid ? ld.key(tbase + li) : 0u;
+            dig[j] = valid ? ((key[j] >> g.shift) & g.mask) : (uint32_t)RADIX;
+        }
+#pragma unroll
+        for (int j = 0; j < ITEMS; j++) {
+            const uint32_t d = dig[j];
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const bool valid = d < (uint32_t)RADIX;
+            uint32_t base = valid ? S.cnt[w][d] : 0u;
+            rank[j] = base + __popc(peers & lt);
+            __syncwarp();
+            if (valid && (__ffs(peers) - 1) == lane) S.cnt[w][d] = base + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {   // per digit: warp offsets, tile totals, tile starts
+            const int d = threadIdx.x;
+            uint32_t s = 0;
+#pragma unroll
+            for (int k = 0; k < WARPS; k++) {
+                uint32_t c = S.cnt[k][d];
+                S.cnt[k][d] = s;
+                s += c;
+            }
+            S.tile_total[d] = s;
+            uint32_t st0 = block_exclusive_scan_256(s, S.warp_tot, &S.total);
+            S.tile_start[d] = st0;
+#pragma unroll
+            for (int k = 0; k < WARPS; k++) S.cnt[k][d] += st0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < ITEMS; j++) {
+            if (dig[j] < (uint32_t)RADIX) {
+                rank[j] += S.cnt[w][dig[j]];
+                S.stage_key[rank[j]] = key[j];
+            }
+        }
+        __syncthreads();
+        int64_t gpos[ITEMS];
+#pragma unroll
+        for (int i = 0; i < ITEMS; i++) {
+            const int p = i * THREADS + threadIdx.x;
+            gpos[i] = -1;
+            if (p < tcount) {
+                const uint32_t k = S.stage_key[p];
+                const uint32_t d = (k >> g.shift) & g.mask;
+                gpos[i] = (int64_t)S.run[d] + (p - (int64_t)S.tile_start[d]);
+                if (STORE_KEY) st.key(gpos[i], k);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < ITEMS; j++) {
+                if (dig[j] < (uint32_t)RADIX) {
+                    const int li = w * 32 * ITEMS + j * 32 + lane;
+                    S.stage[rank[j]] = ld.val(q, tbase + li);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < ITEMS; i++) {
+                const int p = i * THREADS + threadIdx.x;
+                if (p < tcount) st.val(q, gpos[i], S.stage[p]);
+            }
+        }
+        __syncthreads();
+        S.run[threadIdx.x] += S.tile_total[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// Record arrays (ping-pong buffers between passes).
+template <int NV>
+struct ArrLoader {
+    static constexpr double KEY_BYTES = 4.0;
+    static constexpr double REC_BYTES = 4.0 * (1 + NV);
+    const uint32_t* k;
+    const uint32_t* v[NV > 0 ? NV : 1];
+    __device__ __forceinline__ uint32_t key(int64_t i) const { return __ldg(k + i); }
+    __device__ __forceinline__ uint32_t val(int q, int64_t i) const { return __ldg(v[q] + i); }
+};
+
+template <int NV>
+struct ArrStorer {
+    __host__ __device__ double rec_bytes() const { return 4.0 * (1 + NV); }
+    uint32_t* k;
+    uint32_t* v[NV > 0 ? NV : 1];
+    __device__ __forceinline__ void key(int64_t p, uint32_t x) const { k[p] = x; }
+    __device__ __forceinline__ void val(int q, int64_t p, uint32_t x) const { v[q][p] = x; }
+};
+
+// Chunking: enough chunks to fill the GPU, each a whole number of tiles.
+inline PassGeom make_geom(int64_t n, int shift, int bits) {
+    PassGeom g;
+    g.n = n;
+    const int64_t tiles = (n + TILE - 1) / TILE;
+    int64_t want = (int64_t)sm_count() * 8;
+    if (want > tiles) want = tiles;
+    if (want < 1) want = 1;
+    const int64_t tiles_per = (tiles + want - 1) / want;
+    g.chunk = tiles_per * TILE;
+    g.chunks = (int)((n + g.chunk - 1) / g.chunk);
+    if (g.chunks < 1) g.chunks = 1;
+    g.shift = shift;
+    g.mask = (bits >= 32) ? 0xffffffffu : ((1u << bits) - 1u);
+    return g;
+}
+
+inline size_t downsweep_smem(int nv) {
+    (void)nv;
+    return sizeof(TileSmem<1>);
+}
+static_assert(sizeof(TileSmem<1>) <= 48 * 1024, "downsweep shared memory");
+
+// Scratch for counts: RADIX * chunks + RADIX totals (uint32).
+inline size_t scratch_words(int64_t n) {
+    PassGeom g = make_geom(n, 0, BITS);
+    return (size_t)RADIX * g.chunks + RADIX;
+}
+
+// One pass.  'scratch' holds scratch_words(n) uint32 (device).
+template <int NV, bool STORE_KEY, class Loader, class Storer>
+int run_pass(const Loader& ld, const Storer& st, int64_t n, int shift, int bits,
+             uint32_t* scratch, cudaStream_t s) {
+    if (n <= 0) return WTRI_OK;
+    PassGeom g = make_geom(n, shift, bits);
+    uint32_t* counts = scratch;
+    uint32_t* totals = scratch + (size_t)RADIX * g.chunks;
+    {
+        ProfScope ps("radix_upsweep", s, (double)n * Loader::KEY_BYTES + 4.0 * RADIX * g.chunks, 1);
+        k_upsweep<Loader><<<g.chunks, THREADS, 0, s>>>(ld, g, counts);
+    }
+    {
+        ProfScope ps("radix_digit_scan", s, 8.0 * RADIX * g.chunks, 1);
+        k_digit_scan<<<RADIX, THREADS, 0, s>>>(counts, g.chunks, totals);
+    }
+    const size_t smem = downsweep_smem(NV);  // < 48 KB: no opt-in attribute needed
+    {
+        ProfScope ps("radix_downsweep", s, (double)n * (Loader::REC_BYTES + st.rec_bytes()), 1);
+        k_downsweep<NV, Loader, Storer, STORE_KEY><<<g.chunks, THREADS, smem, s>>>(ld, st, g, counts,
+                                                                                  totals);
+    }
+    WTRI_CUDA(cudaGetLastError());
+    return WTRI_OK;
+}
+
+inline int bit_length(uint64_t x) {
+    int b = 0;
+    while (x) {
+        b++;
+        x >>= 1;
+    }
+    return b;
+}
+
+}  // namespace radix
+}  // namespace wtri

@@ -1,0 +1,222 @@
+"""ctypes binding of libwtri.so (argument marshalling only).
+
+Names follow the C ABI: ``build_csr`` -> wtri_build_csr, ``topk`` ->
+wtri_topk, ``topk_device`` -> wtri_topk_device, ``sample_topk`` ->
+wtri_sample_topk.  Host inputs are numpy arrays; device inputs and outputs
+are torch CUDA tensors (torch provides device memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libwtri.so")
+
+WTRI_OK = 0
+WTRI_PENDING = 1
+CODES = {
+    -1: "WTRI_EINVAL",
+    -2: "WTRI_ENOMEM",
+    -3: "WTRI_ECUDA",
+    -4: "WTRI_ETIMEOUT",
+    -5: "WTRI_EUNSUPPORTED",
+    -6: "WTRI_ENOTFOUND",
+}
+
+ARRAYS = {
+    "degree": (0, np.int32, "n"),
+    "rowptr": (1, np.int64, "n+1"),
+    "order_u": (2, np.int32, "m"),
+    "order_v": (3, np.int32, "m"),
+    "order_w": (4, np.int32, "m"),
+    "wcol": (5, np.int32, "2m"),
+    "wwt": (6, np.int32, "2m"),
+    "wrank": (7, np.int32, "2m"),
+    "scol": (8, np.int32, "2m"),
+    "swt": (9, np.int32, "2m"),
+    "srank": (10, np.int32, "2m"),
+    "orowptr": (11, np.int64, "n+1"),
+    "ocol": (12, np.int32, "m"),
+    "owt": (13, np.int32, "m"),
+    "orank": (14, np.int32, "m"),
+}
+
+
+class WtriUnavailable(RuntimeError):
+    """libwtri.so is missing or cannot be loaded: build it first
+    (``python -c "import __graft_entry__ as g; g.build()"``)."""
+
+
+class WtriError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Tri(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_int32), ("b", ctypes.c_int32), ("c", ctypes.c_int32)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("tris", ctypes.c_void_p), ("weight", ctypes.c_void_p),
+                ("capacity", ctypes.c_int32), ("count", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise WtriUnavailable(f"{_LIB_PATH} not built")
+    try:
+        L = ctypes.CDLL(_LIB_PATH)
+    except OSError as e:  # pragma: no cover
+        raise WtriUnavailable(str(e)) from e
+    vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.wtri_build_csr.argtypes = [i32, i64, vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)]
+    L.wtri_graph_free.argtypes = [vp]
+    L.wtri_graph_free.restype = None
+    L.wtri_graph_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                  ctypes.POINTER(i32), ctypes.POINTER(i64)]
+    L.wtri_topk.argtypes = [vp, f64, i32, ctypes.POINTER(_Result)]
+    L.wtri_topk_device.argtypes = [vp, f64, i32, vp, vp, vp, vp]
+    L.wtri_sample_topk.argtypes = [vp, f64, i32, i64, ctypes.c_uint64, ctypes.POINTER(_Result)]
+    L.wtri_graph_copy_array.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
+    L.wtri_last_error.restype = ctypes.c_char_p
+    L.wtri_last_error.argtypes = []
+    L.wtri_version.restype = ctypes.c_char_p
+    for f in (L.wtri_build_csr, L.wtri_graph_info, L.wtri_topk, L.wtri_topk_device,
+              L.wtri_sample_topk, L.wtri_graph_copy_array):
+        f.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != WTRI_OK:
+        raise WtriError(rc, lib().wtri_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _dev_ptr(t):
+    return ctypes.c_void_p(int(t.data_ptr()))
+
+
+class Graph:
+    """A device-resident graph built by wtri_build_csr."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().wtri_graph_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self):
+        n, m = ctypes.c_int32(), ctypes.c_int64()
+        md, mw, nb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().wtri_graph_info(self._h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(md),
+                                     ctypes.byref(mw), ctypes.byref(nb)))
+        return {"n": n.value, "m": m.value, "max_degree": md.value, "max_weight": mw.value,
+                "device_bytes": nb.value}
+
+    def array(self, name: str) -> np.ndarray:
+        which, dt, _ = ARRAYS[name]
+        nb = ctypes.c_int64()
+        _check(lib().wtri_graph_copy_array(self._h, which, None, 0, ctypes.byref(nb)))
+        out = np.empty(nb.value // np.dtype(dt).itemsize, dtype=dt)
+        _check(lib().wtri_graph_copy_array(self._h, which, out.ctypes.data_as(ctypes.c_void_p),
+                                           nb.value, ctypes.byref(nb)))
+        return out
+
+    def topk(self, p: float, k: int):
+        return topk(self, p, k)
+
+    def sample_topk(self, p: float, k: int, nsamples: int, seed: int):
+        return sample_topk(self, p, k, nsamples, seed)
+
+
+def build_csr(n: int, u, v, w, stream=None) -> Graph:
+    """u, v, w: int32 numpy arrays (host) or int32 torch CUDA tensors (device)."""
+    on_device = 0
+    keep = []
+    if hasattr(u, "is_cuda") and u.is_cuda:
+        for t in (u, v, w):
+            if not (hasattr(t, "is_cuda") and t.is_cuda) or str(t.dtype) != "torch.int32":
+                raise TypeError("device inputs must all be int32 CUDA tensors")
+            if not t.is_contiguous():
+                raise TypeError("device inputs must be contiguous")
+        ptrs = [_dev_ptr(t) for t in (u, v, w)]
+        m = int(u.shape[0])
+        on_device = 1
+    else:
+        arrs = [np.ascontiguousarray(x, dtype=np.int32) for x in (u, v, w)]
+        keep = arrs
+        ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in arrs]
+        m = int(arrs[0].shape[0])
+    h = ctypes.c_void_p()
+    rc = lib().wtri_build_csr(int(n), m, ptrs[0], ptrs[1], ptrs[2], on_device,
+                              _stream_ptr(stream), ctypes.byref(h))
+    del keep
+    _check(rc)
+    return Graph(h.value)
+
+
+def _host_query(fn, k):
+    tris = np.zeros((max(k, 1), 3), dtype=np.int32)
+    wts = np.zeros(max(k, 1), dtype=np.float64)
+    res = _Result(tris.ctypes.data, wts.ctypes.data, max(k, 1), 0)
+    _check(fn(ctypes.byref(res)))
+    c = res.count
+    return tris[:c].copy(), wts[:c].copy()
+
+
+def topk(g: Graph, p: float, k: int):
+    """Exact top-k: (tris int32 [count,3] ascending ids, weights float64)."""
+    return _host_query(lambda r: lib().wtri_topk(g.handle, float(p), int(k), r), int(k))
+
+
+def topk_device(g: Graph, p: float, k: int, out_tris, out_weight, out_count, stream=None):
+    """Stream-ordered query into torch CUDA tensors: out_tris int32 [k,3],
+    out_weight float64 [k], out_count int32 [1]."""
+    _check(lib().wtri_topk_device(g.handle, float(p), int(k), _dev_ptr(out_tris),
+                                  _dev_ptr(out_weight), _dev_ptr(out_count), _stream_ptr(stream)))
+
+
+def sample_topk(g: Graph, p: float, k: int, nsamples: int, seed: int):
+    return _host_query(lambda r: lib().wtri_sample_topk(g.handle, float(p), int(k), int(nsamples),
+                                                         ctypes.c_uint64(seed & (2**64 - 1)), r),
+                       int(k))
+
+
+def p_values():
+    return [-math.inf, 1.0, 2.0, math.inf]

@@ -1,0 +1,52 @@
+"""GPU parity at the full mid workload size (Chung-Lu n=1e6, m=2e7, exponent
+2.1, d_max 5e4, Zipf(2) weights capped at 1e6; k=1000 at all four p), the
+configuration bench.py times: every output element against the oracle."""
+import pytest
+
+import oracle
+import synth
+from wtri_testutil import PS, assert_topk_equal
+
+pytestmark = pytest.mark.gpu
+
+wt = pytest.importorskip("paper_1910_00692_gb300")
+
+
+@pytest.fixture(scope="module")
+def mid():
+    g = synth.mid_graph(1)
+    d = wt.build_csr(g.n, g.u, g.v, g.w)
+    yield g, d
+    d.free()
+
+
+@pytest.mark.parametrize("p", PS)
+def test_mid_full_k1000(mid, p):
+    g, d = mid
+    want = oracle.topk(g.n, g.u, g.v, g.w, p, 1000)
+    tris, wts = d.topk(p, 1000)
+    assert_topk_equal(tris, wts, want, p, f"mid p={p}")
+
+
+def test_mid_structure_sample(mid):
+    """Sampled checks of the device structures at full size (properties that
+    hold at any size, plus exact rows for a few vertices)."""
+    import numpy as np
+    g, d = mid
+    ow = d.array("order_w")
+    assert np.all(np.diff(ow) <= 0)
+    assert np.array_equal(np.sort(ow), np.sort(g.w))
+    rowptr = d.array("rowptr")
+    deg = np.bincount(np.concatenate([g.u, g.v]), minlength=g.n)
+    assert np.array_equal(np.diff(rowptr), deg)
+    scol, wwt, wrk = d.array("scol"), d.array("wwt"), d.array("wrank")
+    rng = np.random.default_rng(0)
+    for x in list(rng.integers(0, g.n, 200)) + [int(np.argmax(deg))]:
+        s, e = rowptr[x], rowptr[x + 1]
+        assert np.all(np.diff(scol[s:e]) > 0)
+        assert np.all(np.diff(wrk[s:e]) > 0)
+        assert np.all(np.diff(wwt[s:e]) <= 0)
+        nb = np.sort(np.concatenate([g.v[g.u == x], g.u[g.v == x]]))
+        assert np.array_equal(scol[s:e], nb)
+    orow = d.array("orowptr")
+    assert orow[-1] == g.m

@@ -1,0 +1,219 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Triangle sets and order are compared element by element (bit-exact ids);
+weights bit-exact for p in {-inf, 1, +inf} and within 1e-12 relative at
+p = 2.  Inputs are the seeded synthetic graphs of synth/.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from golden_io import P_OF, closed_form, load_all
+from wtri_testutil import PS, assert_topk_equal
+
+pytestmark = pytest.mark.gpu
+
+wt = pytest.importorskip("paper_1910_00692_gb300")
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return synth.tiny_graph(0)
+
+
+@pytest.fixture(scope="module")
+def tiny_dev(tiny):
+    g = wt.build_csr(tiny.n, tiny.u, tiny.v, tiny.w)
+    yield g
+    g.free()
+
+
+@pytest.mark.parametrize("fx", load_all(), ids=lambda d: d["name"])
+def test_golden(fx):
+    g = wt.build_csr(fx["n"], fx["u"], fx["v"], fx["w"])
+    try:
+        for pname, rows in fx["expected"].items():
+            tris, wts = g.topk(P_OF[pname], fx["k"])
+            assert tris.shape[0] == len(rows), pname
+            for i, row in enumerate(rows):
+                assert tuple(int(x) for x in tris[i]) == tuple(row[:3]), (pname, i)
+                want = closed_form(row[4])
+                assert abs(wts[i] - want) <= 1e-15 * max(1.0, abs(want)), (pname, i)
+    finally:
+        g.free()
+
+
+@pytest.mark.parametrize("p", PS)
+@pytest.mark.parametrize("k", [1, 100, 777, 20000])
+def test_tiny_vs_oracle(tiny, tiny_dev, p, k):
+    want = oracle.topk(tiny.n, tiny.u, tiny.v, tiny.w, p, k)
+    tris, wts = tiny_dev.topk(p, k)
+    assert_topk_equal(tris, wts, want, p, f"tiny p={p} k={k}")
+
+
+def test_tiny_structures(tiny, tiny_dev):
+    g, d = tiny, tiny_dev
+    perm = oracle.edge_order(g.w)
+    assert np.array_equal(d.array("order_w"), g.w[perm])
+    ou, ov = d.array("order_u"), d.array("order_v")
+    assert np.array_equal(ou, g.u[perm]) and np.array_equal(ov, g.v[perm])
+    rowptr, col, wtt, eid = oracle.sym_csr(g.n, g.u, g.v, g.w)
+    assert np.array_equal(d.array("rowptr"), rowptr)
+    assert np.array_equal(d.array("degree"), np.diff(rowptr).astype(np.int32))
+    assert np.array_equal(d.array("scol"), col)
+    assert np.array_equal(d.array("swt"), wtt)
+    rank = np.empty(g.m, np.int64)
+    rank[perm] = np.arange(g.m)
+    assert np.array_equal(d.array("srank"), rank[eid])
+    wrp, wcol, wwt, wrk = oracle.weight_sorted_rows(g.n, g.u, g.v, g.w)
+    assert np.array_equal(d.array("wcol"), wcol)
+    assert np.array_equal(d.array("wwt"), wwt)
+    assert np.array_equal(d.array("wrank"), wrk)
+    orow, ocol, owt, oeid = oracle.oriented_csr(g.n, g.u, g.v, g.w)
+    assert np.array_equal(d.array("orowptr"), orow)
+    assert np.array_equal(d.array("ocol"), ocol)
+    assert np.array_equal(d.array("owt"), owt)
+    assert np.array_equal(d.array("orank"), rank[oeid])
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_small_graphs(seed):
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(3, 80))
+    g = synth.random_small_graph(n, float(rng.uniform(0.05, 0.9)), int(rng.integers(1, 7)), seed)
+    if g.m == 0:
+        return
+    d = wt.build_csr(g.n, g.u, g.v, g.w)
+    try:
+        for p in PS:
+            for k in (1, 3, 50, 100000 // 2):
+                k = min(k, 65536)
+                want = oracle.topk(g.n, g.u, g.v, g.w, p, k)
+                tris, wts = d.topk(p, k)
+                assert_topk_equal(tris, wts, want, p, f"seed={seed} n={n} p={p} k={k}")
+    finally:
+        d.free()
+
+
+@pytest.mark.parametrize("n,m,seed", [(20000, 200000, 11), (100000, 1000000, 12)])
+def test_scaled_mid_vs_oracle(n, m, seed):
+    g = synth.scaled_mid_graph(n, m, seed=seed)
+    d = wt.build_csr(g.n, g.u, g.v, g.w)
+    try:
+        for p in PS:
+            for k in (10, 1000, 5000):
+                want = oracle.topk(g.n, g.u, g.v, g.w, p, k)
+                tris, wts = d.topk(p, k)
+                assert_topk_equal(tris, wts, want, p, f"n={n} p={p} k={k}")
+    finally:
+        d.free()
+
+
+def test_device_inputs_and_device_outputs(tiny):
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    u = torch.from_numpy(tiny.u).to(dev)
+    v = torch.from_numpy(tiny.v).to(dev)
+    w = torch.from_numpy(tiny.w).to(dev)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        d = wt.build_csr(tiny.n, u, v, w, stream=s)
+    try:
+        k = 500
+        for p in PS:
+            ot = torch.zeros((k, 3), dtype=torch.int32, device=dev)
+            ow = torch.zeros(k, dtype=torch.float64, device=dev)
+            oc = torch.zeros(1, dtype=torch.int32, device=dev)
+            wt.topk_device(d, p, k, ot, ow, oc, stream=s)
+            s.synchronize()
+            cnt = int(oc.item())
+            want = oracle.topk(tiny.n, tiny.u, tiny.v, tiny.w, p, k)
+            assert_topk_equal(ot[:cnt].cpu().numpy(), ow[:cnt].cpu().numpy(), want, p, f"device p={p}")
+    finally:
+        d.free()
+
+
+@pytest.mark.parametrize("bad", ["self_loop", "out_of_range", "zero_weight", "negative_weight", "duplicate",
+                                 "duplicate_flipped"])
+def test_invalid_inputs(bad):
+    u = np.array([0, 1, 2, 3], np.int32)
+    v = np.array([1, 2, 0, 0], np.int32)
+    w = np.array([1, 2, 3, 4], np.int32)
+    n = 4
+    if bad == "self_loop":
+        v[1] = 1
+    elif bad == "out_of_range":
+        v[1] = 4
+    elif bad == "zero_weight":
+        w[2] = 0
+    elif bad == "negative_weight":
+        w[2] = -1
+    elif bad == "duplicate":
+        u[3], v[3] = 1, 2
+    elif bad == "duplicate_flipped":
+        u[3], v[3] = 2, 1
+    with pytest.raises(wt.WtriError) as ei:
+        wt.build_csr(n, u, v, w)
+    assert ei.value.code == -1
+
+
+def test_bad_queries(tiny_dev):
+    with pytest.raises(wt.WtriError) as ei:
+        tiny_dev.topk(float("nan"), 10)
+    assert ei.value.code == -1
+    with pytest.raises(wt.WtriError) as ei:
+        tiny_dev.topk(0.5, 10)
+    assert ei.value.code == -5
+    with pytest.raises(wt.WtriError) as ei:
+        tiny_dev.topk(1.0, 0)
+    assert ei.value.code == -1
+
+
+def test_empty_and_degenerate():
+    d = wt.build_csr(5, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32))
+    try:
+        for p in PS:
+            tris, wts = d.topk(p, 10)
+            assert tris.shape[0] == 0
+    finally:
+        d.free()
+    # a single edge, a path: no triangle
+    d = wt.build_csr(3, np.array([0, 1], np.int32), np.array([1, 2], np.int32), np.array([5, 6], np.int32))
+    try:
+        assert d.topk(1.0, 3)[0].shape[0] == 0
+    finally:
+        d.free()
+    # maximum int32 weights at p = 2 (key 3 * (2^31-1)^2 must not wrap)
+    W = 2**31 - 1
+    d = wt.build_csr(4, np.array([0, 1, 0, 2], np.int32), np.array([1, 2, 2, 3], np.int32),
+                     np.array([W, W, W, 1], np.int32))
+    try:
+        for p in PS:
+            want = oracle.topk(4, np.array([0, 1, 0, 2], np.int32), np.array([1, 2, 2, 3], np.int32),
+                               np.array([W, W, W, 1], np.int32), p, 2)
+            tris, wts = d.topk(p, 2)
+            assert_topk_equal(tris, wts, want, p, "max weights")
+    finally:
+        d.free()
+
+
+def test_complete_graph_closed_form():
+    n = 40
+    iu, ju = np.triu_indices(n, 1)
+    u, v = iu.astype(np.int32), ju.astype(np.int32)
+    w = (iu + ju + 1).astype(np.int32)
+    d = wt.build_csr(n, u, v, w)
+    try:
+        N = n * (n - 1) * (n - 2) // 6
+        tris, wts = d.topk(1.0, N)
+        assert tris.shape[0] == N
+        sums = tris.sum(axis=1)
+        # p = 1 key is 2(a+b+c)+3: non-increasing sums, ties by triple
+        assert np.all(np.diff(sums) <= 0)
+        assert tuple(tris[0]) == (n - 3, n - 2, n - 1)
+        np.testing.assert_array_equal(wts, (2 * sums + 3) / 3.0)
+    finally:
+        d.free()
