@@ -137,6 +137,28 @@ WTRI_API int wtri_topk_device(const wtri_graph* g, double p, int32_t k, wtri_tri
                               double* d_weight, int32_t* d_count, void* stream);
 
 /*
+ * wtri_topk_device without any allocation.  The paper has no counterpart:
+ * this exists for callers that cannot allocate device memory while they
+ * run, such as a server that hands all device memory to its own caching
+ * allocator at start-up, or a latency-critical loop that must never block
+ * on cudaMalloc/cudaMallocAsync.  Arguments, outputs and results are those
+ * of wtri_topk_device.
+ *
+ * Scratch comes from one fixed array inside the library: about 26 MB
+ * (1,048,576 candidate triangles and 65,536 deferred scans) that every GPU
+ * loading the library keeps until the process exits.  k above 16384 is
+ * rejected with WTRI_EINVAL.  If a query produces more candidates than the
+ * array holds, d_count receives WTRI_ENOMEM; use wtri_topk_device then.
+ * All calls share the array (its status word is cleared at the start of
+ * each call), so calls that overlap on the GPU, on different streams or
+ * from different host threads, race: serialize them.  The first call on a
+ * device looks up the array's device address with that device current;
+ * make that first call before any stream capture.
+ */
+WTRI_API int wtri_topk_device_noalloc(const wtri_graph* g, double p, int32_t k, wtri_tri* d_tris,
+                                      double* d_weight, int32_t* d_count, void* stream);
+
+/*
  * Weighted edge sampling (Algorithm 3, Section 4.1): draws nsamples edges
  * with probability w_e^p / Z (Proposition 4.1), adds every triangle on each
  * sampled edge (the common neighbours N(a) ∩ N(b)) to a set, and returns the

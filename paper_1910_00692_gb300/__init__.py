@@ -19,7 +19,8 @@ from .wtri import (  # noqa: F401
     sample_topk,
     topk,
     topk_device,
+    topk_device_noalloc,
 )
 
 __all__ = ["ARRAYS", "Graph", "WtriError", "WtriUnavailable", "build_csr", "lib", "lib_path",
-           "sample_topk", "topk", "topk_device"]
+           "sample_topk", "topk", "topk_device", "topk_device_noalloc"]

@@ -108,6 +108,7 @@ int sample_topk_device(const wtri_graph* g, int pcode, int32_t k, int64_t nsampl
 // algorithmic traffic; 'launches' the number of kernels it launches.
 void prof_begin(const char* name, cudaStream_t s, double bytes, int launches);
 void prof_end(cudaStream_t s);
+void count_launches(int launches);  // launch counter only, no events
 
 struct ProfScope {
     cudaStream_t s;

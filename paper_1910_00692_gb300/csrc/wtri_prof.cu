@@ -85,6 +85,8 @@ void prof_begin(const char* name, cudaStream_t s, double bytes, int launches) {
     t_stack.push_back(p);
 }
 
+void count_launches(int launches) { g_launches.fetch_add(launches, std::memory_order_relaxed); }
+
 void prof_end(cudaStream_t s) {
     if (!g_enabled.load(std::memory_order_relaxed) || t_stack.empty()) return;
     Pending p = t_stack.back();

@@ -35,6 +35,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "wtri_internal.cuh"
 
@@ -689,3 +690,130 @@ int topk_device(const wtri_graph* g, int pcode, int32_t k, wtri_tri* d_tris, dou
 }
 
 }  // namespace wtri
+
+// ---------------------------------------------------------------------------
+// Query variant that allocates nothing.
+//
+// For callers that may not allocate device memory once they are running:
+// for example a server whose device memory is all handed to its own caching
+// allocator at start-up, or a latency-critical loop that must never wait on
+// the allocator.  The query's scratch (status word, candidate buffer,
+// deferred-scan list) lives in one fixed array compiled into the library.
+// Every GPU that loads the library keeps this array (NOALLOC_BYTES, about
+// 26 MB) until the process exits.  All calls share it: the status word is
+// cleared at the start of each call, and calls that overlap on the GPU (on
+// different streams, or from several host threads) race on it.
+// ---------------------------------------------------------------------------
+namespace wtri {
+namespace {
+
+constexpr uint32_t NOALLOC_CAP = 1u << 20;     // candidates
+constexpr uint32_t NOALLOC_LONG = 1u << 16;    // deferred scans
+constexpr int32_t NOALLOC_K_MAX = 16384;
+constexpr size_t NOALLOC_CAND_OFF = 256;
+constexpr size_t NOALLOC_TRI_OFF = NOALLOC_CAND_OFF + (size_t)NOALLOC_CAP * 8;
+constexpr size_t NOALLOC_LONG_OFF = NOALLOC_TRI_OFF + (size_t)NOALLOC_CAP * 16;
+constexpr size_t NOALLOC_BYTES = NOALLOC_LONG_OFF + (size_t)NOALLOC_LONG * sizeof(LongItem);
+static_assert(sizeof(QState) <= NOALLOC_CAND_OFF, "status word fits its slot");
+static_assert(NOALLOC_LONG_OFF % 256 == 0, "aligned deferred list");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the fixed array for the current device, looked up once
+// per device (with that device current).
+int noalloc_scratch(void** out) {
+    int dev = 0;
+    WTRI_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return set_error(WTRI_EUNSUPPORTED, "device index above 63");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return cuda_error(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                              "cudaGetSymbolAddress(static query scratch)", __FILE__, __LINE__);
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return WTRI_OK;
+}
+
+template <int P>
+int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight,
+                      int32_t* d_count, cudaStream_t s) {
+    const DevGraph& G = g->d;
+    const int64_t m = G.m;
+    void* base = nullptr;
+    WTRI_TRY(noalloc_scratch(&base));
+    char* p = (char*)base;
+    Query q;
+    q.st = (QState*)p;
+    q.ckey = (unsigned long long*)(p + NOALLOC_CAND_OFF);
+    q.ctri = (int4*)(p + NOALLOC_TRI_OFF);
+    q.longs = (LongItem*)(p + NOALLOC_LONG_OFF);
+    q.cap = NOALLOC_CAP;
+    q.long_cap = NOALLOC_LONG;
+    q.k = k;
+    // The array keeps the previous call's contents: reset the status word
+    // (counters, threshold, stop flag, error bits).
+    WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
+
+    const size_t lsmem = (size_t)STAGE_MAX * 4 + 16;
+    static bool attr_done[4] = {false, false, false, false};
+    if (!attr_done[P]) {
+        WTRI_CUDA(cudaFuncSetAttribute(k_long<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)lsmem));
+        attr_done[P] = true;
+    }
+    const int long_grid = sm_count() * 2;
+    int64_t lo = 0, size = FIRST_ROUND;
+    while (lo < m) {
+        const int64_t hi = std::min(m, lo + size);
+        k_round<P><<<ceil_div_u(hi - lo, RBLK), RBLK, 0, s>>>(G, q, lo, hi);
+        k_long<P><<<long_grid, LBLK, lsmem, s>>>(G, q);
+        k_select<<<1, SBLK, 0, s>>>(q);
+        count_launches(3);
+        lo = hi;
+        size *= ROUND_GROWTH;
+    }
+    k_final_select<<<1, SBLK, 0, s>>>(q);
+    k_rank_scatter<P><<<ceil_div_u(std::max(k, 1), 256), 256, 0, s>>>(q, d_tris, d_weight, d_count);
+    count_launches(2);
+    WTRI_CUDA(cudaGetLastError());
+    return WTRI_OK;
+}
+
+}  // namespace
+}  // namespace wtri
+
+extern "C" WTRI_API int wtri_topk_device_noalloc(const wtri_graph* g, double p, int32_t k,
+                                                 wtri_tri* d_tris, double* d_weight,
+                                                 int32_t* d_count, void* stream) {
+    using namespace wtri;
+    if (!g) return set_error(WTRI_EINVAL, "graph is NULL");
+    if (k <= 0) return set_error(WTRI_EINVAL, "k must be positive");
+    if (k > NOALLOC_K_MAX)
+        return set_error(WTRI_EINVAL, "k above 16384, the most the fixed query scratch supports");
+    int code = 0;
+    WTRI_TRY(p_to_code(p, &code));
+    if (!d_tris || !d_weight || !d_count) return set_error(WTRI_EINVAL, "output pointers are NULL");
+    cudaStream_t s = stream ? (cudaStream_t)stream : g->stream;
+    if (g->d.m == 0) {
+        WTRI_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int32_t), s));
+        return WTRI_OK;
+    }
+    switch (code) {
+        case P_MIN: return run_query_noalloc<P_MIN>(g, k, d_tris, d_weight, d_count, s);
+        case P_ONE: return run_query_noalloc<P_ONE>(g, k, d_tris, d_weight, d_count, s);
+        case P_TWO: return run_query_noalloc<P_TWO>(g, k, d_tris, d_weight, d_count, s);
+        default: return run_query_noalloc<P_MAX>(g, k, d_tris, d_weight, d_count, s);
+    }
+}
+

@@ -91,12 +91,14 @@ def lib():
                                   ctypes.POINTER(i32), ctypes.POINTER(i64)]
     L.wtri_topk.argtypes = [vp, f64, i32, ctypes.POINTER(_Result)]
     L.wtri_topk_device.argtypes = [vp, f64, i32, vp, vp, vp, vp]
+    L.wtri_topk_device_noalloc.argtypes = [vp, f64, i32, vp, vp, vp, vp]
     L.wtri_sample_topk.argtypes = [vp, f64, i32, i64, ctypes.c_uint64, ctypes.POINTER(_Result)]
     L.wtri_graph_copy_array.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
     L.wtri_last_error.restype = ctypes.c_char_p
     L.wtri_last_error.argtypes = []
     L.wtri_version.restype = ctypes.c_char_p
     for f in (L.wtri_build_csr, L.wtri_graph_info, L.wtri_topk, L.wtri_topk_device,
+              L.wtri_topk_device_noalloc,
               L.wtri_sample_topk, L.wtri_graph_copy_array):
         f.restype = ctypes.c_int
     _lib = L
@@ -210,6 +212,14 @@ def topk_device(g: Graph, p: float, k: int, out_tris, out_weight, out_count, str
     out_weight float64 [k], out_count int32 [1]."""
     _check(lib().wtri_topk_device(g.handle, float(p), int(k), _dev_ptr(out_tris),
                                   _dev_ptr(out_weight), _dev_ptr(out_count), _stream_ptr(stream)))
+
+
+def topk_device_noalloc(g: Graph, p: float, k: int, out_tris, out_weight, out_count, stream=None):
+    """wtri_topk_device_noalloc: the same query with scratch taken from the
+    library's fixed device array instead of any allocation (k <= 16384)."""
+    _check(lib().wtri_topk_device_noalloc(g.handle, float(p), int(k), _dev_ptr(out_tris),
+                                          _dev_ptr(out_weight), _dev_ptr(out_count),
+                                          _stream_ptr(stream)))
 
 
 def sample_topk(g: Graph, p: float, k: int, nsamples: int, seed: int):
