@@ -7,6 +7,7 @@
 
 #include <new>
 #include <string>
+#include <vector>
 
 #include "wtri_internal.cuh"
 
@@ -199,6 +200,7 @@ WTRI_API int wtri_graph_copy_array(const wtri_graph* g, int which, void* dst,
     const int64_t n = g->d.n, m = g->d.m;
     const void* src = nullptr;
     int64_t bytes = 0;
+    bool oriented = false;
     switch (which) {
         case WTRI_ARR_DEGREE: src = g->d.deg; bytes = 4 * n; break;
         case WTRI_ARR_ROWPTR: src = g->d.rowptr; bytes = 8 * (n + 1); break;
@@ -211,18 +213,44 @@ WTRI_API int wtri_graph_copy_array(const wtri_graph* g, int which, void* dst,
         case WTRI_ARR_SCOL: src = g->d.scol; bytes = 8 * m; break;
         case WTRI_ARR_SWT: src = g->d.swt; bytes = 8 * m; break;
         case WTRI_ARR_SRANK: src = g->d.srk; bytes = 8 * m; break;
-        case WTRI_ARR_OROWPTR: src = g->d.orowptr; bytes = 8 * (n + 1); break;
-        case WTRI_ARR_OCOL: src = g->d.ocol; bytes = 4 * m; break;
-        case WTRI_ARR_OWT: src = g->d.owt; bytes = 4 * m; break;
-        case WTRI_ARR_ORANK: src = g->d.ork; bytes = 4 * m; break;
+        case WTRI_ARR_OROWPTR: bytes = 8 * (n + 1); oriented = true; break;
+        case WTRI_ARR_OCOL: src = g->d.ocol; bytes = 4 * m; oriented = true; break;
+        case WTRI_ARR_OWT: src = g->d.owt; bytes = 4 * m; oriented = true; break;
+        case WTRI_ARR_ORANK: src = g->d.ork; bytes = 4 * m; oriented = true; break;
         default: return set_error(WTRI_EINVAL, "unknown array id");
     }
     if (bytes_out) *bytes_out = bytes;
     if (!dst) return WTRI_OK;
     if (bytes_capacity < bytes) return set_error(WTRI_EINVAL, "destination too small");
     if (bytes == 0) return WTRI_OK;
-    WTRI_CUDA(cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyDeviceToHost, g->stream));
+    if (!oriented) {
+        WTRI_CUDA(cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyDeviceToHost, g->stream));
+        WTRI_CUDA(cudaStreamSynchronize(g->stream));
+        return WTRI_OK;
+    }
+    // The device keeps oriented row x in the slots of symmetric row x; the
+    // exported form is the compact CSR (offsets n+1, entries m).
+    std::vector<int32_t> od((size_t)n);
+    std::vector<int64_t> rp((size_t)n + 1);
+    WTRI_CUDA(cudaMemcpyAsync(od.data(), g->d.odeg, 4 * (size_t)n, cudaMemcpyDeviceToHost, g->stream));
+    WTRI_CUDA(cudaMemcpyAsync(rp.data(), g->d.rowptr, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost,
+                              g->stream));
+    std::vector<int32_t> gap;
+    if (src) {
+        gap.resize((size_t)(2 * m));
+        WTRI_CUDA(cudaMemcpyAsync(gap.data(), src, 8 * (size_t)m, cudaMemcpyDeviceToHost, g->stream));
+    }
     WTRI_CUDA(cudaStreamSynchronize(g->stream));
+    if (!src) {
+        int64_t* o = (int64_t*)dst;
+        o[0] = 0;
+        for (int64_t x = 0; x < n; x++) o[x + 1] = o[x] + od[(size_t)x];
+        return WTRI_OK;
+    }
+    int32_t* o = (int32_t*)dst;
+    int64_t at = 0;
+    for (int64_t x = 0; x < n; x++)
+        for (int64_t j = 0; j < od[(size_t)x]; j++) o[at++] = gap[(size_t)(rp[(size_t)x] + j)];
     return WTRI_OK;
 }
 

@@ -6,16 +6,18 @@
 // 4), and the NodeIterator++ degree ordering (Section 5.2).
 //
 // Pipeline (one stream, inputs read once from HBM or host):
-//   1. k_validate_degree: rejects bad edges, counts degrees, max weight.
-//   2. rowptr = exclusive scan of degrees (+ max degree).
-//   3. Edge order: stable LSD radix sort of key (wmax - w) carrying (u, v).
-//   4. Weight-sorted lists: the virtual stream "two entries per edge, in edge
+//   1. k_validate: rejects bad edges, finds the max weight.
+//   2. Edge order: stable LSD radix sort of key (wmax - w) carrying (u, v).
+//   3. Weight-sorted lists: the virtual stream "two entries per edge, in edge
 //      order" is stably radix-sorted by row, so each row keeps edge order.
+//   4. Row offsets and degrees from the boundaries of the sorted rows (no
+//      atomics), plus the list of long rows.
 //   5. Id-sorted lists: the weight-sorted entries, read row by row (so the
 //      stream is ascending in its row x), are mirrored to (row c, col x) and
 //      stably sorted by row c, which leaves each row ascending in x.
-//   6. Repeated pairs show up as equal neighbours in an id-sorted row.
-//   7. Oriented lists: per row, keep neighbours of higher (degree, id) rank.
+//   6. Oriented lists: per row, keep neighbours of higher (degree, id) rank,
+//      in place of the row's own slots; repeated pairs show up in the same
+//      pass as equal neighbours next to each other.
 #include <cuda_runtime.h>
 #include <stdio.h>
 
@@ -39,15 +41,15 @@ struct BuildStatus {
     unsigned long long first_bad;  // smallest offending edge index
 };
 
-__global__ void k_validate_degree(int32_t n, int64_t m, const int32_t* __restrict__ u,
-                                  const int32_t* __restrict__ v, const int32_t* __restrict__ w,
-                                  int32_t* __restrict__ deg, BuildStatus* st) {
+__global__ void k_validate(int32_t n, int64_t m, const int32_t* __restrict__ u,
+                           const int32_t* __restrict__ v, const int32_t* __restrict__ w,
+                           BuildStatus* st) {
     int32_t wloc = 0;
     uint32_t eloc = 0;
     unsigned long long bad = ~0ull;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t a = u[i], b = v[i], x = w[i];
+        const int32_t a = __ldg(u + i), b = __ldg(v + i), x = __ldg(w + i);
         uint32_t e = 0;
         if (a < 0 || a >= n || b < 0 || b >= n) e |= DEV_ERR_RANGE;
         else if (a == b) e |= DEV_ERR_SELF_LOOP;
@@ -57,8 +59,6 @@ __global__ void k_validate_degree(int32_t n, int64_t m, const int32_t* __restric
             if ((unsigned long long)i < bad) bad = (unsigned long long)i;
             continue;
         }
-        atomicAdd(&deg[a], 1);
-        atomicAdd(&deg[b], 1);
         wloc = max(wloc, x);
     }
 #pragma unroll
@@ -296,21 +296,36 @@ __global__ void k_copy_identity_order(int64_t m, const int32_t* u, const int32_t
     }
 }
 
-// Repeated undirected pair = equal neighbours next to each other in one
-// id-sorted row.
-__global__ void k_find_duplicates(int64_t n2, const int32_t* __restrict__ srow,
-                                  const int32_t* __restrict__ scol, BuildStatus* st) {
-    unsigned long long bad = ~0ull;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n2;
+// Row offsets from the row-sorted entry stream: entry i starts row x for
+// every x in (row[i-1], row[i]]; rows past the last entry start at n2.
+__global__ void k_rowptr_from_rows(int32_t n, int64_t n2, const int32_t* __restrict__ row,
+                                   int64_t* __restrict__ rowptr) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2;
          i += (int64_t)gridDim.x * blockDim.x) {
-        if (srow[i] == srow[i - 1] && scol[i] == scol[i - 1]) {
-            if ((unsigned long long)i < bad) bad = (unsigned long long)i;
-        }
+        const int32_t cur = __ldg(row + i);
+        const int32_t prev = i == 0 ? -1 : __ldg(row + i - 1);
+        for (int32_t x = prev + 1; x <= cur; x++) rowptr[x] = i;
+        if (i == n2 - 1)
+            for (int64_t x = (int64_t)cur + 1; x <= n; x++) rowptr[x] = n2;
     }
-    if (bad != ~0ull) {
-        atomicOr(&st->err, DEV_ERR_DUPLICATE);
-        atomicMin(&st->first_bad, bad);  // entry index, not edge index
+}
+
+constexpr int LONG_ROW = 1024;
+
+// Degrees, the maximum degree, and the list of long rows (oriented by blocks).
+__global__ void k_degrees(int32_t n, const int64_t* __restrict__ rowptr, int32_t* __restrict__ deg,
+                          BuildStatus* st, int32_t* long_rows, int32_t* long_count) {
+    int32_t mx = 0;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = (int32_t)(rowptr[x + 1] - rowptr[x]);
+        deg[x] = d;
+        mx = max(mx, d);
+        if (d >= LONG_ROW) long_rows[atomicAdd(long_count, 1)] = (int32_t)x;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(&st->maxdeg, mx);
 }
 
 __device__ __forceinline__ bool rank_less(const int32_t* deg, int32_t a, int32_t b) {
@@ -318,78 +333,41 @@ __device__ __forceinline__ bool rank_less(const int32_t* deg, int32_t a, int32_t
     return da < db || (da == db && a < b);
 }
 
-// Out-degree in the orientation: the lower-ranked endpoint owns the edge.
-__global__ void k_out_degree(int64_t m, const int32_t* __restrict__ ou,
-                             const int32_t* __restrict__ ov, const int32_t* __restrict__ deg,
-                             int32_t* __restrict__ odeg) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t a = ou[r], b = ov[r];
-        atomicAdd(&odeg[rank_less(deg, a, b) ? a : b], 1);
-    }
-}
+constexpr int OBLK = 512;
 
-constexpr int LONG_ROW = 1024;
-
-// Warp per row (rows shorter than LONG_ROW); long rows are queued.
-__global__ void k_orient_rows(int32_t n, const int64_t* __restrict__ rowptr,
-                              const int32_t* __restrict__ scol, const int32_t* __restrict__ swt,
-                              const int32_t* __restrict__ srk, const int32_t* __restrict__ deg,
-                              const int64_t* __restrict__ orowptr, int32_t* __restrict__ ocol,
-                              int32_t* __restrict__ owt, int32_t* __restrict__ ork,
-                              int32_t* long_rows, int32_t* long_count) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t x = warp; x < n; x += nwarps) {
-        const int64_t s = rowptr[x], e = rowptr[x + 1];
-        if (e - s >= LONG_ROW) {
-            if (lane == 0) long_rows[atomicAdd(long_count, 1)] = (int32_t)x;
-            continue;
-        }
-        int64_t out = orowptr[x];
-        for (int64_t j0 = s; j0 < e; j0 += 32) {
-            const int64_t j = j0 + lane;
-            bool fwd = false;
-            int32_t c = 0;
-            if (j < e) {
-                c = scol[j];
-                fwd = rank_less(deg, (int32_t)x, c);
-            }
-            const uint32_t b = __ballot_sync(0xffffffffu, fwd);
-            if (fwd) {
-                const int64_t p = out + __popc(b & ((1u << lane) - 1u));
-                ocol[p] = c;
-                owt[p] = swt[j];
-                ork[p] = srk[j];
-            }
-            out += __popc(b);
-        }
-    }
-}
-
-// Block per long row.
-__global__ void k_orient_long_rows(const int32_t* __restrict__ long_rows,
-                                   const int32_t* __restrict__ long_count,
-                                   const int64_t* __restrict__ rowptr,
-                                   const int32_t* __restrict__ scol, const int32_t* __restrict__ swt,
-                                   const int32_t* __restrict__ srk, const int32_t* __restrict__ deg,
-                                   const int64_t* __restrict__ orowptr, int32_t* __restrict__ ocol,
-                                   int32_t* __restrict__ owt, int32_t* __restrict__ ork) {
-    __shared__ uint32_t warp_cnt[BLK / 32];
+// Degree orientation, in the slots of the symmetric rows: row x keeps its
+// neighbours of higher (degree, id) rank, in id order, at
+// [rowptr[x], rowptr[x] + odeg[x]).  The same pass finds repeated pairs
+// (equal neighbours next to each other in an id-sorted row).  Blocks first
+// take long rows from a queue, then warps take short rows.
+__global__ void __launch_bounds__(OBLK) k_orient(
+    int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ scol,
+    const int32_t* __restrict__ swt, const int32_t* __restrict__ srk, const int32_t* __restrict__ deg,
+    int32_t* __restrict__ ocol, int32_t* __restrict__ owt, int32_t* __restrict__ ork,
+    int32_t* __restrict__ odeg, const int32_t* __restrict__ long_rows,
+    const int32_t* __restrict__ long_count, int32_t* next_long, BuildStatus* st) {
+    __shared__ uint32_t warp_cnt[OBLK / 32];
     __shared__ uint32_t tot;
+    __shared__ int32_t item;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int cnt = *long_count;
-    for (int it = blockIdx.x; it < cnt; it += gridDim.x) {
+    unsigned long long dup = ~0ull;
+    const int nlong = *long_count;
+    for (;;) {
+        if (threadIdx.x == 0) item = atomicAdd(next_long, 1);
+        __syncthreads();
+        const int it = item;
+        __syncthreads();
+        if (it >= nlong) break;
         const int32_t x = long_rows[it];
         const int64_t s = rowptr[x], e = rowptr[x + 1];
-        int64_t out = orowptr[x];
-        for (int64_t j0 = s; j0 < e; j0 += BLK) {
+        int64_t out = s;
+        for (int64_t j0 = s; j0 < e; j0 += OBLK) {
             const int64_t j = j0 + threadIdx.x;
             bool fwd = false;
             int32_t c = 0;
             if (j < e) {
-                c = scol[j];
+                c = __ldg(scol + j);
+                if (j > s && __ldg(scol + j - 1) == c) dup = min(dup, (unsigned long long)j);
                 fwd = rank_less(deg, x, c);
             }
             const uint32_t b = __ballot_sync(0xffffffffu, fwd);
@@ -397,8 +375,8 @@ __global__ void k_orient_long_rows(const int32_t* __restrict__ long_rows,
             __syncthreads();
             if (threadIdx.x == 0) {
                 uint32_t acc = 0;
-                for (int k = 0; k < BLK / 32; k++) {
-                    uint32_t t = warp_cnt[k];
+                for (int k = 0; k < OBLK / 32; k++) {
+                    const uint32_t t = warp_cnt[k];
                     warp_cnt[k] = acc;
                     acc += t;
                 }
@@ -408,12 +386,43 @@ __global__ void k_orient_long_rows(const int32_t* __restrict__ long_rows,
             if (fwd) {
                 const int64_t p = out + warp_cnt[wid] + __popc(b & ((1u << lane) - 1u));
                 ocol[p] = c;
-                owt[p] = swt[j];
-                ork[p] = srk[j];
+                owt[p] = __ldg(swt + j);
+                ork[p] = __ldg(srk + j);
             }
             out += tot;
             __syncthreads();
         }
+        if (threadIdx.x == 0) odeg[x] = (int32_t)(out - s);
+    }
+    const int64_t warp = ((int64_t)blockIdx.x * OBLK + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * OBLK) >> 5;
+    for (int64_t x = warp; x < n; x += nwarps) {
+        const int64_t s = rowptr[x], e = rowptr[x + 1];
+        if (e - s >= LONG_ROW) continue;  // taken by a block above
+        int64_t out = s;
+        for (int64_t j0 = s; j0 < e; j0 += 32) {
+            const int64_t j = j0 + lane;
+            bool fwd = false;
+            int32_t c = 0;
+            if (j < e) {
+                c = __ldg(scol + j);
+                if (j > s && __ldg(scol + j - 1) == c) dup = min(dup, (unsigned long long)j);
+                fwd = rank_less(deg, (int32_t)x, c);
+            }
+            const uint32_t b = __ballot_sync(0xffffffffu, fwd);
+            if (fwd) {
+                const int64_t p = out + __popc(b & ((1u << lane) - 1u));
+                ocol[p] = c;
+                owt[p] = __ldg(swt + j);
+                ork[p] = __ldg(srk + j);
+            }
+            out += __popc(b);
+        }
+        if (lane == 0) odeg[x] = (int32_t)(out - s);
+    }
+    if (dup != ~0ull) {
+        atomicOr(&st->err, DEV_ERR_DUPLICATE);
+        atomicMin(&st->first_bad, dup);  // entry index of the repeat
     }
 }
 
@@ -455,19 +464,6 @@ int exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaSt
 
 namespace {
 
-int scan_with_max(const int32_t* in, int64_t* out, int64_t n, int32_t* d_max, cudaStream_t s) {
-    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-    int64_t* tile_sums = nullptr;
-    WTRI_CUDA(cudaMallocAsync((void**)&tile_sums, sizeof(int64_t) * (size_t)std::max<int64_t>(tiles, 1), s));
-    ProfScope ps("scan_offsets", s, 4.0 * n * 2 + 8.0 * (n + 1), 3);
-    k_scan_reduce<<<(unsigned)tiles, BLK, 0, s>>>(in, n, tile_sums, d_max);
-    k_scan_tiles<<<1, BLK, 0, s>>>(tile_sums, tiles, out + n);
-    k_scan_apply<<<(unsigned)tiles, BLK, 0, s>>>(in, n, tile_sums, out);
-    WTRI_CUDA(cudaGetLastError());
-    WTRI_CUDA(cudaFreeAsync(tile_sums, s));
-    return WTRI_OK;
-}
-
 struct Scratch {
     cudaStream_t s;
     void* p = nullptr;
@@ -497,6 +493,7 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
 
     int dev = 0;
     WTRI_CUDA(cudaGetDevice(&dev));
+    keep_pool_memory(dev);
 
     // Inputs on the device.
     Scratch in_buf(s);
@@ -521,13 +518,12 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         off = align_up(off + bytes + 16, 256);
         return o;
     };
-    const size_t o_deg = take(4 * N1);
+    const size_t o_deg = take(4 * N1), o_odeg = take(4 * N1);
     const size_t o_rowptr = take(8 * (N1 + 1));
-    const size_t o_orowptr = take(8 * (N1 + 1));
     const size_t o_ou = take(4 * M), o_ov = take(4 * M), o_ow = take(4 * M);
     const size_t o_wcol = take(4 * M2), o_wwt = take(4 * M2), o_wrk = take(4 * M2);
     const size_t o_scol = take(4 * M2), o_swt = take(4 * M2), o_srk = take(4 * M2);
-    const size_t o_ocol = take(4 * M), o_owt = take(4 * M), o_ork = take(4 * M);
+    const size_t o_ocol = take(4 * M2), o_owt = take(4 * M2), o_ork = take(4 * M2);
     const size_t total = off;
 
     wtri_graph* g = new (std::nothrow) wtri_graph();
@@ -535,7 +531,6 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     g->stream = s;
     g->device = dev;
     g->bytes = (int64_t)total;
-    keep_pool_memory(dev);
     cudaError_t e = cudaMallocAsync(&g->base, total, s);
     if (e != cudaSuccess) {
         delete g;
@@ -544,8 +539,8 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     }
     char* B = (char*)g->base;
     int32_t* deg = (int32_t*)(B + o_deg);
+    int32_t* odeg = (int32_t*)(B + o_odeg);
     int64_t* rowptr = (int64_t*)(B + o_rowptr);
-    int64_t* orowptr = (int64_t*)(B + o_orowptr);
     int32_t *ou = (int32_t*)(B + o_ou), *ov = (int32_t*)(B + o_ov), *ow = (int32_t*)(B + o_ow);
     int32_t *wcol = (int32_t*)(B + o_wcol), *wwt = (int32_t*)(B + o_wwt), *wrk = (int32_t*)(B + o_wrk);
     int32_t *scol = (int32_t*)(B + o_scol), *swt = (int32_t*)(B + o_swt), *srk = (int32_t*)(B + o_srk);
@@ -566,20 +561,14 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     d_st = (BuildStatus*)st_buf.p;
     {
         BuildStatus init = {0u, 0, 0, 0, ~0ull};
-        if (cudaMemcpyAsync(d_st, &init, sizeof(init), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemsetAsync(deg, 0, 4 * N1, s) != cudaSuccess)
-            return fail(cuda_error(cudaGetLastError(), "memset", __FILE__, __LINE__));
+        if (cudaMemcpyAsync(d_st, &init, sizeof(init), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "status init", __FILE__, __LINE__));
     }
 
-    // 1. validation + degrees
+    // 1. validation + max weight
     if (m > 0) {
-        ProfScope ps("validate_degree", s, 12.0 * m + 4.0 * n, 1);
-        k_validate_degree<<<grid_for(m), BLK, 0, s>>>(n, m, u, v, w, deg, d_st);
-    }
-    // 2. row offsets + max degree
-    {
-        int rc = scan_with_max(deg, rowptr, (int64_t)n, &d_st->maxdeg, s);
-        if (rc != WTRI_OK) return fail(rc);
+        ProfScope ps("validate", s, 12.0 * m, 1);
+        k_validate<<<grid_for(m), BLK, 0, s>>>(n, m, u, v, w, d_st);
     }
     if (cudaMemcpyAsync(&h_st, d_st, sizeof(h_st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
@@ -594,7 +583,7 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     g->d.n = n;
     g->d.m = m;
     g->d.wmax = h_st.wmax;
-    g->d.maxdeg = h_st.maxdeg;
+    g->d.maxdeg = 0;
 
     if (m > 0) {
         // Scratch: two ping-pong record buffers of (key + 3 values) x 2m, the
@@ -602,7 +591,7 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         const int64_t n2 = 2 * m;
         const size_t rec_words = 4 * (size_t)n2;
         const size_t cnt_words = radix::scratch_words(n2);
-        const size_t words = 2 * rec_words + cnt_words + 2 * (size_t)n2 + 2 * N1 + 8;
+        const size_t words = 2 * rec_words + cnt_words + (size_t)n2 + N1 + 8;
         Scratch tmp(s);
         if (cudaMallocAsync(&tmp.p, words * 4, s) != cudaSuccess) {
             cudaGetLastError();
@@ -612,12 +601,12 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         uint32_t* pp_b = pp_a + rec_words;
         uint32_t* counts = pp_b + rec_words;
         int32_t* wrow = (int32_t*)(counts + cnt_words);
-        int32_t* srow = wrow + n2;
-        int32_t* odeg = srow + n2;
-        int32_t* long_rows = odeg + n;
-        int32_t* long_count = long_rows + n;
+        int32_t* long_rows = wrow + n2;
+        int32_t* long_count = long_rows + n;  // [0] count, [1] next
+        if (cudaMemsetAsync(long_count, 0, 8, s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "memset", __FILE__, __LINE__));
 
-        // 3. edge order
+        // 2. edge order
         const int wbits = radix::bit_length((uint64_t)(h_st.wmax - 1));
         if (wbits == 0) {
             ProfScope ps("edge_order_copy", s, 24.0 * m, 1);
@@ -628,7 +617,7 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
             int rc = lsd_sort<2>(el, es, m, wbits, pp_a, pp_b, m, counts, s);
             if (rc != WTRI_OK) return fail(rc);
         }
-        // 4. weight-sorted rows (row key kept in wrow for step 5)
+        // 3. weight-sorted rows (row key kept in wrow)
         const int nbits = std::max(1, radix::bit_length((uint64_t)(n - 1)));
         {
             OrderEntryLoader ol{ou, ov, ow};
@@ -636,38 +625,27 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
             int rc = lsd_sort<3>(ol, rs, n2, nbits, pp_a, pp_b, n2, counts, s);
             if (rc != WTRI_OK) return fail(rc);
         }
-        // 5. id-sorted rows; the last pass also writes each entry's row
+        // 4. row offsets, degrees, long rows
+        {
+            ProfScope ps("row_offsets", s, 4.0 * n2 + 8.0 * (n + 1) + 4.0 * n, 2);
+            k_rowptr_from_rows<<<grid_for(n2), BLK, 0, s>>>(n, n2, wrow, rowptr);
+            k_degrees<<<grid_for(n), BLK, 0, s>>>(n, rowptr, deg, d_st, long_rows, long_count);
+        }
+        // 5. id-sorted rows
         {
             MirrorLoader ml{wrow, wcol, wwt, wrk};
-            RowsStorer rs{srow, scol, swt, srk};
+            RowsStorer rs{nullptr, scol, swt, srk};
             int rc = lsd_sort<3>(ml, rs, n2, nbits, pp_a, pp_b, n2, counts, s);
             if (rc != WTRI_OK) return fail(rc);
         }
-        // 6. repeated pairs
+        // 6. orientation + repeated pairs
         {
-            ProfScope ps("find_duplicates", s, 8.0 * n2, 1);
-            k_find_duplicates<<<grid_for(n2), BLK, 0, s>>>(n2, srow, scol, d_st);
-        }
-        // 7. orientation
-        if (cudaMemsetAsync(odeg, 0, 4 * N1, s) != cudaSuccess ||
-            cudaMemsetAsync(long_count, 0, 4, s) != cudaSuccess)
-            return fail(cuda_error(cudaGetLastError(), "memset", __FILE__, __LINE__));
-        {
-            ProfScope ps("out_degree", s, 8.0 * m + 8.0 * n, 1);
-            k_out_degree<<<grid_for(m), BLK, 0, s>>>(m, ou, ov, deg, odeg);
-        }
-        {
-            int rc = exclusive_scan_i32_to_i64(odeg, orowptr, (int64_t)n, s);
-            if (rc != WTRI_OK) return fail(rc);
-        }
-        {
-            // reads the id-sorted rows (col for every entry, weight and rank
-            // for the kept half), writes m oriented entries
-            ProfScope ps("orient_rows", s, 4.0 * n2 + 8.0 * m + 12.0 * m + 16.0 * n, 2);
-            k_orient_rows<<<grid_for((int64_t)n * 32), BLK, 0, s>>>(
-                n, rowptr, scol, swt, srk, deg, orowptr, ocol, owt, ork, long_rows, long_count);
-            k_orient_long_rows<<<sm_count() * 2, BLK, 0, s>>>(long_rows, long_count, rowptr, scol,
-                                                              swt, srk, deg, orowptr, ocol, owt, ork);
+            // reads every id-sorted neighbour, weight and rank of the kept
+            // half, writes m oriented entries and the out-degrees
+            ProfScope ps("orient", s, 4.0 * n2 + 8.0 * m + 12.0 * m + 8.0 * n + 8.0 * (n + 1), 1);
+            k_orient<<<sm_count() * 4, OBLK, 0, s>>>(n, rowptr, scol, swt, srk, deg, ocol, owt, ork,
+                                                     odeg, long_rows, long_count, long_count + 1,
+                                                     d_st);
         }
         if (cudaGetLastError() != cudaSuccess)
             return fail(set_error(WTRI_ECUDA, "build kernel launch failed"));
@@ -675,22 +653,25 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
             cudaStreamSynchronize(s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "build", __FILE__, __LINE__));
         if (h_st.err & DEV_ERR_DUPLICATE) {
-            int32_t pair[2] = {-1, -1};
+            int32_t col[2] = {-1, -1};
             const int64_t j = (int64_t)h_st.first_bad;
-            cudaMemcpyAsync(&pair[0], srow + j, 4, cudaMemcpyDeviceToHost, s);
-            cudaMemcpyAsync(&pair[1], scol + j, 4, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(&col[0], scol + j, 4, cudaMemcpyDeviceToHost, s);
             cudaStreamSynchronize(s);
-            return fail(set_error(WTRI_EINVAL, "repeated undirected pair (" +
-                                                   std::to_string(pair[0]) + ", " +
-                                                   std::to_string(pair[1]) + ")"));
+            return fail(set_error(WTRI_EINVAL, "repeated undirected pair: neighbour " +
+                                                   std::to_string(col[0]) +
+                                                   " appears twice in one row"));
         }
+        g->d.maxdeg = h_st.maxdeg;
     } else {
-        if (cudaMemsetAsync(orowptr, 0, 8 * (N1 + 1), s) != cudaSuccess ||
+        if (cudaMemsetAsync(rowptr, 0, 8 * (N1 + 1), s) != cudaSuccess ||
+            cudaMemsetAsync(deg, 0, 4 * N1, s) != cudaSuccess ||
+            cudaMemsetAsync(odeg, 0, 4 * N1, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "build", __FILE__, __LINE__));
     }
 
     g->d.deg = deg;
+    g->d.odeg = odeg;
     g->d.rowptr = rowptr;
     g->d.ord_u = ou;
     g->d.ord_v = ov;
@@ -701,7 +682,6 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     g->d.scol = scol;
     g->d.swt = swt;
     g->d.srk = srk;
-    g->d.orowptr = orowptr;
     g->d.ocol = ocol;
     g->d.owt = owt;
     g->d.ork = ork;

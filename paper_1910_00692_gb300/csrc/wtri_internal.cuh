@@ -53,8 +53,9 @@ int p_to_code(double p, int* code);
 //   rowptr[n+1]           offsets of both symmetric layouts
 //   wcol/wwt/wrk[2m]      per-vertex lists in edge order (weight-sorted)
 //   scol/swt/srk[2m]      per-vertex lists by neighbour id
-//   orowptr[n+1]          oriented offsets
-//   ocol/owt/ork[m]       oriented lists by neighbour id
+//   odeg[n]               oriented out-degree
+//   ocol/owt/ork[2m]      oriented lists by neighbour id: row x occupies
+//                         [rowptr[x], rowptr[x] + odeg[x]) (gaps after it)
 // ---------------------------------------------------------------------------
 struct DevGraph {
     int32_t n;
@@ -62,6 +63,7 @@ struct DevGraph {
     int32_t wmax;
     int32_t maxdeg;
     const int32_t* deg;
+    const int32_t* odeg;
     const int64_t* rowptr;
     const int32_t* ord_u;
     const int32_t* ord_v;
@@ -72,7 +74,6 @@ struct DevGraph {
     const int32_t* scol;
     const int32_t* swt;
     const int32_t* srk;
-    const int64_t* orowptr;
     const int32_t* ocol;
     const int32_t* owt;
     const int32_t* ork;

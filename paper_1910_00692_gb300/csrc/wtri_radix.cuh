@@ -18,6 +18,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "wtri_internal.cuh"
 
@@ -115,10 +116,9 @@ __global__ void __launch_bounds__(THREADS) k_digit_scan(uint32_t* counts, int ch
 template <int NV>
 struct TileSmem {
     uint32_t cnt[WARPS][RADIX];
-    uint32_t stage[TILE];
-    uint32_t stage_key[TILE];
-    uint32_t run[RADIX];         // global position of this chunk's next record per digit
-    uint32_t tile_start[RADIX];  // tile-local start of each digit
+    uint32_t stage[NV + 1][TILE];  // key, then values, in tile-sorted order
+    uint32_t run[RADIX];           // global position of this chunk's next record per digit
+    uint32_t tile_start[RADIX];    // tile-local start of each digit
     uint32_t tile_total[RADIX];
     uint32_t warp_tot[WARPS];
     uint32_t total;
@@ -146,23 +146,26 @@ __global__ void __launch_bounds__(THREADS) k_downsweep(Loader ld, Storer st, Pas
     for (int64_t tbase = beg; tbase < end; tbase += TILE) {
         const int tcount = (int)min((int64_t)TILE, end - tbase);
         for (int i = threadIdx.x; i < WARPS * RADIX; i += THREADS) (&S.cnt[0][0])[i] = 0;
-        __syncthreads();
 
+        // Every load of the tile is issued before any use (one round trip).
         uint32_t key[ITEMS];
+        uint32_t val[NV > 0 ? NV : 1][ITEMS];
         uint32_t rank[ITEMS];
-        uint32_t dig[ITEMS];
 #pragma unroll
         for (int j = 0; j < ITEMS; j++) {
             const int li = w * 32 * ITEMS + j * 32 + lane;
             const bool valid = li < tcount;
             key[j] = valid ? ld.key(tbase + li) : 0u;
-            dig[j] = valid ? ((key[j] >> g.shift) & g.mask) : (uint32_t)RADIX;
+#pragma unroll
+            for (int q = 0; q < NV; q++) val[q][j] = valid ? ld.val(q, tbase + li) : 0u;
         }
+        __syncthreads();  // counters cleared
 #pragma unroll
         for (int j = 0; j < ITEMS; j++) {
-            const uint32_t d = dig[j];
+            const int li = w * 32 * ITEMS + j * 32 + lane;
+            const bool valid = li < tcount;
+            const uint32_t d = valid ? ((key[j] >> g.shift) & g.mask) : (uint32_t)RADIX;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const bool valid = d < (uint32_t)RADIX;
             uint32_t base = valid ? S.cnt[w][d] : 0u;
             rank[j] = base + __popc(peers & lt);
             __syncwarp();
@@ -188,39 +191,27 @@ __global__ void __launch_bounds__(THREADS) k_downsweep(Loader ld, Storer st, Pas
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < ITEMS; j++) {
-            if (dig[j] < (uint32_t)RADIX) {
-                rank[j] += S.cnt[w][dig[j]];
-                S.stage_key[rank[j]] = key[j];
+            const int li = w * 32 * ITEMS + j * 32 + lane;
+            if (li < tcount) {
+                const uint32_t d = (key[j] >> g.shift) & g.mask;
+                const uint32_t pos = rank[j] + S.cnt[w][d];
+                S.stage[0][pos] = key[j];
+#pragma unroll
+                for (int q = 0; q < NV; q++) S.stage[q + 1][pos] = val[q][j];
             }
         }
         __syncthreads();
-        int64_t gpos[ITEMS];
+        // Consecutive threads write consecutive positions of one digit's run.
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
             const int p = i * THREADS + threadIdx.x;
-            gpos[i] = -1;
             if (p < tcount) {
-                const uint32_t k = S.stage_key[p];
+                const uint32_t k = S.stage[0][p];
                 const uint32_t d = (k >> g.shift) & g.mask;
-                gpos[i] = (int64_t)S.run[d] + (p - (int64_t)S.tile_start[d]);
-                if (STORE_KEY) st.key(gpos[i], k);
-            }
-        }
+                const int64_t gp = (int64_t)S.run[d] + (p - (int64_t)S.tile_start[d]);
+                if (STORE_KEY) st.key(gp, k);
 #pragma unroll
-        for (int q = 0; q < NV; q++) {
-            __syncthreads();
-#pragma unroll
-            for (int j = 0; j < ITEMS; j++) {
-                if (dig[j] < (uint32_t)RADIX) {
-                    const int li = w * 32 * ITEMS + j * 32 + lane;
-                    S.stage[rank[j]] = ld.val(q, tbase + li);
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < ITEMS; i++) {
-                const int p = i * THREADS + threadIdx.x;
-                if (p < tcount) st.val(q, gpos[i], S.stage[p]);
+                for (int q = 0; q < NV; q++) st.val(q, gp, S.stage[q + 1][p]);
             }
         }
         __syncthreads();
@@ -249,12 +240,26 @@ struct ArrStorer {
     __device__ __forceinline__ void val(int q, int64_t p, uint32_t x) const { v[q][p] = x; }
 };
 
+// Chunks per SM.  Each chunk keeps one partially written line per digit and
+// output array in L2 while it streams, so the chunk count is kept small
+// enough that those write fronts fit in L2 (WTRI_RADIX_CHUNKS_PER_SM
+// overrides the default of 2 for tuning).
+inline int chunks_per_sm() {
+    static int v = 0;
+    if (v == 0) {
+        const char* e = getenv("WTRI_RADIX_CHUNKS_PER_SM");
+        int x = e ? atoi(e) : 0;
+        v = (x >= 1 && x <= 64) ? x : 2;
+    }
+    return v;
+}
+
 // Chunking: enough chunks to fill the GPU, each a whole number of tiles.
 inline PassGeom make_geom(int64_t n, int shift, int bits) {
     PassGeom g;
     g.n = n;
     const int64_t tiles = (n + TILE - 1) / TILE;
-    int64_t want = (int64_t)sm_count() * 8;
+    int64_t want = (int64_t)sm_count() * chunks_per_sm();
     if (want > tiles) want = tiles;
     if (want < 1) want = 1;
     const int64_t tiles_per = (tiles + want - 1) / want;
@@ -266,11 +271,10 @@ inline PassGeom make_geom(int64_t n, int shift, int bits) {
     return g;
 }
 
-inline size_t downsweep_smem(int nv) {
-    (void)nv;
-    return sizeof(TileSmem<1>);
+template <int NV>
+inline size_t downsweep_smem() {
+    return sizeof(TileSmem<NV>);
 }
-static_assert(sizeof(TileSmem<1>) <= 48 * 1024, "downsweep shared memory");
 
 // Scratch for counts: RADIX * chunks + RADIX totals (uint32).
 inline size_t scratch_words(int64_t n) {
@@ -294,7 +298,13 @@ int run_pass(const Loader& ld, const Storer& st, int64_t n, int shift, int bits,
         ProfScope ps("radix_digit_scan", s, 8.0 * RADIX * g.chunks, 1);
         k_digit_scan<<<RADIX, THREADS, 0, s>>>(counts, g.chunks, totals);
     }
-    const size_t smem = downsweep_smem(NV);  // < 48 KB: no opt-in attribute needed
+    const size_t smem = downsweep_smem<NV>();
+    static bool attr_set = false;  // per instantiation; idempotent
+    if (!attr_set) {
+        WTRI_CUDA(cudaFuncSetAttribute(k_downsweep<NV, Loader, Storer, STORE_KEY>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
     {
         ProfScope ps("radix_downsweep", s, (double)n * (Loader::REC_BYTES + st.rec_bytes()), 1);
         k_downsweep<NV, Loader, Storer, STORE_KEY><<<g.chunks, THREADS, smem, s>>>(ld, st, g, counts,

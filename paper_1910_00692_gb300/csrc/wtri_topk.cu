@@ -52,10 +52,11 @@ constexpr int STAGE_MAX = 24576;   // ids of a y row staged in shared memory (96
 constexpr int64_t FIRST_ROUND = 2048;
 constexpr int ROUND_GROWTH = 4;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;  // bounded mbarrier polling
+constexpr uint32_t STOP_NONE = 0x7fffffffu; // edge positions are below 2^31
 
 struct QState {
     unsigned long long tau;   // keys below tau are pruned; 0 = no bound yet
-    int32_t stop;             // an edge's bound fell below tau
+    uint32_t stop_rev;        // STOP_NONE - (first edge whose bound fell below tau); 0 = none
     uint32_t err;             // DEV_ERR_* bits
     uint32_t count;           // candidates appended (may exceed capacity)
     uint32_t long_count;      // deferred scans
@@ -101,9 +102,6 @@ __device__ __forceinline__ void sort3(int32_t& a, int32_t& b, int32_t& c) {
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
     return *(volatile const unsigned long long*)p;
 }
-__device__ __forceinline__ int32_t ld_volatile_i32(const int32_t* p) {
-    return *(volatile const int32_t*)p;
-}
 
 // Position just after edge r's own entry in x's weight-sorted list.
 __device__ __forceinline__ int64_t suffix_start(const DevGraph& G, int32_t x, int32_t r,
@@ -123,13 +121,14 @@ __device__ __forceinline__ int64_t suffix_start(const DevGraph& G, int32_t x, in
 }
 
 // Closing edge (y, c) in the oriented lists: stored once, at the endpoint of
-// lower (degree, id) rank, rows ascending by id.
+// lower (degree, id) rank, rows ascending by id (row s starts at rowptr[s]
+// and holds odeg[s] entries).
 __device__ __forceinline__ bool probe_oriented(const DevGraph& G, int32_t y, int32_t dy, int32_t c,
                                                int32_t& wyc, int32_t& ryc) {
     const int32_t dc = __ldg(G.deg + c);
     const bool ylow = dy < dc || (dy == dc && y < c);
     const int32_t s = ylow ? y : c, t = ylow ? c : y;
-    int64_t lo = __ldg(G.orowptr + s), hi = __ldg(G.orowptr + s + 1);
+    int64_t lo = __ldg(G.rowptr + s), hi = lo + __ldg(G.odeg + s);
     const int64_t end = hi;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
@@ -164,14 +163,20 @@ __device__ __forceinline__ void append(const Query& q, unsigned long long key, i
 // ---------------------------------------------------------------------------
 template <int P>
 __global__ void __launch_bounds__(RBLK) k_round(DevGraph G, Query q, int64_t lo, int64_t hi) {
-    if (ld_volatile_i32(&q.st->stop)) return;
+    // A round whose first edge lies at or past the first failing edge of an
+    // earlier round has nothing to do.  (Within a round, blocks run in any
+    // order, so the stop point only ever skips whole later rounds; each edge
+    // of the current round is decided by its own bound.)
+    const uint32_t stop_at = STOP_NONE - *(volatile const uint32_t*)&q.st->stop_rev;
+    if (lo >= (int64_t)stop_at) return;
     const unsigned long long tau = ld_volatile_u64(&q.st->tau);
     const int64_t r64 = lo + (int64_t)blockIdx.x * RBLK + threadIdx.x;
     if (r64 >= hi) return;
     const int32_t r = (int32_t)r64;
     const uint32_t w = (uint32_t)__ldg(G.ord_w + r);
     if (keyof<P>(w, w, w) < tau) {
-        q.st->stop = 1;  // every later edge has a bound no larger
+        // every later edge has a bound no larger: record the first such edge
+        atomicMax(&q.st->stop_rev, STOP_NONE - (uint32_t)r);
         return;
     }
     const int32_t u = __ldg(G.ord_u + r), v = __ldg(G.ord_v + r);

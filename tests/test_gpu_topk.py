@@ -54,8 +54,7 @@ def test_tiny_vs_oracle(tiny, tiny_dev, p, k):
     assert_topk_equal(tris, wts, want, p, f"tiny p={p} k={k}")
 
 
-def test_tiny_structures(tiny, tiny_dev):
-    g, d = tiny, tiny_dev
+def _check_structures(g, d):
     perm = oracle.edge_order(g.w)
     assert np.array_equal(d.array("order_w"), g.w[perm])
     ou, ov = d.array("order_u"), d.array("order_v")
@@ -77,6 +76,21 @@ def test_tiny_structures(tiny, tiny_dev):
     assert np.array_equal(d.array("ocol"), ocol)
     assert np.array_equal(d.array("owt"), owt)
     assert np.array_equal(d.array("orank"), rank[oeid])
+
+
+def test_tiny_structures(tiny, tiny_dev):
+    _check_structures(tiny, tiny_dev)
+
+
+@pytest.mark.parametrize("n,m,seed", [(20000, 200000, 11), (100000, 1000000, 12)])
+def test_scaled_structures(n, m, seed):
+    """Graphs with rows longer than the block-orientation threshold."""
+    g = synth.scaled_mid_graph(n, m, seed=seed)
+    d = wt.build_csr(g.n, g.u, g.v, g.w)
+    try:
+        _check_structures(g, d)
+    finally:
+        d.free()
 
 
 @pytest.mark.parametrize("seed", range(24))
