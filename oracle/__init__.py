@@ -71,8 +71,18 @@ def lib():
         L.or_topk.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, ctypes.c_int,
                               ctypes.c_int64, ctypes.c_int, i32p, u64p, f64p, I64P, I64P]
         L.or_count_triangles.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, I64P]
+        u64p_ = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+        u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+        L.or_philox4x64_10.argtypes = [u64p_, u64p_, u64p_]
+        L.or_philox4x64_10.restype = None
+        L.or_sample_edges.argtypes = [ctypes.c_int64, i32p, i64p, ctypes.c_int, ctypes.c_int64,
+                                      ctypes.c_uint64, i64p]
+        L.or_topk_of_sampled.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, u8p,
+                                         ctypes.c_int, ctypes.c_int64, ctypes.c_int, i32p, u64p, f64p,
+                                         I64P, I64P]
         for f in (L.or_validate, L.or_sym_csr, L.or_edge_order, L.or_oriented_csr,
-                  L.or_score, L.or_topk, L.or_count_triangles):
+                  L.or_score, L.or_topk, L.or_count_triangles, L.or_sample_edges,
+                  L.or_topk_of_sampled):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -180,6 +190,62 @@ def topk(n, u, v, w, p, k, nthreads=0):
     c = int(cnt.value)
     return {"tri": tri[: 3 * c].reshape(c, 3), "key": key[:c], "value": val[:c],
             "count": c, "ntri": int(ntri.value)}
+
+
+def philox4x64_10(counter, key):
+    """One Philox4x64-10 block: counter (4 uint64), key (2 uint64) -> 4 uint64."""
+    c = np.ascontiguousarray(np.array(counter, dtype=np.uint64).reshape(4))
+    k = np.ascontiguousarray(np.array(key, dtype=np.uint64).reshape(2))
+    out = np.zeros(4, np.uint64)
+    lib().or_philox4x64_10(c, k, out)
+    return out
+
+
+def sample_edges(w, p, nsamples, seed):
+    """Algorithm 3's edge draws (probability w^p / Z), p in {1, 2}.  Returns
+    (perm, hits): hits[r] counts draws of the r-th edge of edge_order()."""
+    w = _arr(w)
+    perm = edge_order(w)
+    hits = np.zeros(max(w.shape[0], 1), np.int64)
+    rc = lib().or_sample_edges(w.shape[0], w, perm, pcode(p), int(nsamples),
+                               ctypes.c_uint64(int(seed) & (2**64 - 1)), hits)
+    if rc != 0:
+        raise OracleError(f"or_sample_edges failed (rc={rc})")
+    return perm, hits[: w.shape[0]]
+
+
+def topk_of_marked(n, u, v, w, mark, p, k, nthreads=0):
+    """Top-k of the triangles that have at least one marked edge (mark[i] != 0
+    for input edge i): the triangle set T of Algorithm 3 for a given draw."""
+    u, v, w = _arr(u), _arr(v), _arr(w)
+    m = u.shape[0]
+    mark = np.ascontiguousarray(mark, dtype=np.uint8)
+    k = int(k)
+    tri = np.zeros(3 * max(k, 1), np.int32)
+    key = np.zeros(max(k, 1), np.uint64)
+    val = np.zeros(max(k, 1), np.float64)
+    cnt = ctypes.c_int64(0)
+    ntri = ctypes.c_int64(0)
+    rc = lib().or_topk_of_sampled(n, m, u, v, w, mark, pcode(p), k, int(nthreads), tri, key, val,
+                                  ctypes.byref(cnt), ctypes.byref(ntri))
+    if rc != 0:
+        raise OracleError(f"or_topk_of_sampled failed (rc={rc})")
+    c = int(cnt.value)
+    return {"tri": tri[: 3 * c].reshape(c, 3), "key": key[:c], "value": val[:c], "count": c,
+            "ntri": int(ntri.value)}
+
+
+def sample_topk(n, u, v, w, p, k, nsamples, seed, nthreads=0):
+    """Top-k of Algorithm 3's triangle set T (every triangle with at least one
+    drawn edge).  Returns the topk() dict plus 'sampled_edges'."""
+    u, v, w = _arr(u), _arr(v), _arr(w)
+    m = u.shape[0]
+    perm, hits = sample_edges(w, p, nsamples, seed)
+    mark = np.zeros(max(m, 1), np.uint8)
+    mark[perm[hits > 0]] = 1
+    r = topk_of_marked(n, u, v, w, mark[:m], p, k, nthreads)
+    r["sampled_edges"] = int((hits > 0).sum())
+    return r
 
 
 def count_triangles(n, u, v, w=None):

@@ -493,3 +493,195 @@ int or_count_triangles(int32_t n, int64_t m, const int32_t* u, const int32_t* v,
     free(eid);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Weighted edge sampling (Algorithm 3, Section 4.1).                       */
+/* ------------------------------------------------------------------------ */
+
+/* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As
+ * Easy as 1, 2, 3", SC'11): ten rounds of two 64x64->128 multiplies with
+ * the published multipliers and Weyl key increments.  Written from that
+ * description; pinned against numpy's Philox bit generator in the tests. */
+void or_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint64_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; r++) {
+        unsigned __int128 p0 = (unsigned __int128)M0 * c0;
+        unsigned __int128 p1 = (unsigned __int128)M1 * c2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/*
+ * Draws nsamples edges with probability w_e^p / Z, Z = sum_e w_e^p (the
+ * first step of Algorithm 3; Proposition 4.1), p in {1, 2}.
+ *
+ * Definition used on both sides: with the edges in the edge order
+ * perm[0..m) (weight desc, index asc) and C[r] = sum_{j<=r} w_{perm[j]}^p
+ * (exact, 128-bit), sample s takes x = word 0 of
+ * Philox4x64-10(counter = (s, 0, 0, 0), key = (seed, 0)), t = floor(x * Z /
+ * 2^64), and returns the first r with C[r] > t.
+ *
+ * hits[r] receives how many times the r-th edge of the order was drawn.
+ */
+int or_sample_edges(int64_t m, const int32_t* w, const int64_t* perm, int pcode, int64_t nsamples,
+                    uint64_t seed, int64_t* hits) {
+    if (pcode != 1 && pcode != 2) return OR_EINVAL;
+    unsigned __int128* C = (unsigned __int128*)malloc(sizeof(unsigned __int128) * (size_t)(m + 1));
+    if (!C) return OR_ENOMEM;
+    unsigned __int128 acc = 0;
+    for (int64_t r = 0; r < m; r++) {
+        unsigned __int128 x = (unsigned __int128)(uint64_t)w[perm[r]];
+        acc += pcode == 1 ? x : x * x;
+        C[r] = acc;
+        hits[r] = 0;
+    }
+    const unsigned __int128 Z = acc;
+    const uint64_t key[2] = {seed, 0};
+    for (int64_t s = 0; s < nsamples && m > 0; s++) {
+        uint64_t ctr[4] = {(uint64_t)s, 0, 0, 0}, out[4];
+        or_philox4x64_10(ctr, key, out);
+        /* t = floor(x * Z / 2^64), with Z < 2^128 split in two halves */
+        const uint64_t zl = (uint64_t)Z, zh = (uint64_t)(Z >> 64);
+        unsigned __int128 t = (unsigned __int128)out[0] * zh +
+                              (((unsigned __int128)out[0] * zl) >> 64);
+        int64_t lo = 0, hi = m;  /* first r with C[r] > t */
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (C[mid] > t) hi = mid;
+            else lo = mid + 1;
+        }
+        hits[lo]++;
+    }
+    free(C);
+    return OR_OK;
+}
+
+/*
+ * Top-k of the triangle set T of Algorithm 3: T holds every triangle that
+ * has at least one sampled edge (a triangle is added when any of its edges
+ * is drawn).  Enumerated by brute force over all triangles (NodeIterator++),
+ * keeping those with a sampled edge; ranked like or_topk.
+ * edge_sampled[i] != 0 marks input edge i.
+ */
+int or_topk_of_sampled(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int32_t* w,
+                       const uint8_t* edge_sampled, int pcode, int64_t k, int nthreads,
+                       int32_t* tri, uint64_t* key, double* value, int64_t* count, int64_t* ntri) {
+    *count = 0;
+    *ntri = 0;
+    if (pcode < 0 || pcode > 3 || k <= 0) return OR_EINVAL;
+    int64_t* orow = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    int32_t* ocol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    int32_t* owt = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    int64_t* oeid = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m + 1));
+    if (!orow || !ocol || !owt || !oeid) {
+        free(orow); free(ocol); free(owt); free(oeid);
+        return OR_ENOMEM;
+    }
+    int rc = or_oriented_csr(n, m, u, v, w, orow, ocol, owt, oeid);
+    if (rc != OR_OK) {
+        free(orow); free(ocol); free(owt); free(oeid);
+        return rc;
+    }
+    int nt = 1;
+#ifdef _OPENMP
+    nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#endif
+    or_heap* heaps = (or_heap*)calloc((size_t)nt, sizeof(or_heap));
+    int64_t* counts = (int64_t*)calloc((size_t)nt, sizeof(int64_t));
+    int alloc_fail = 0;
+    for (int t = 0; t < nt; t++) {
+        heaps[t].cap = k;
+        heaps[t].h = (or_tri*)malloc(sizeof(or_tri) * (size_t)k);
+        if (!heaps[t].h) alloc_fail = 1;
+    }
+    if (!alloc_fail) {
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+        {
+            int tid = 0;
+#ifdef _OPENMP
+            tid = omp_get_thread_num();
+#endif
+            or_heap* hp = &heaps[tid];
+            int64_t local = 0;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+            for (int32_t a = 0; a < n; a++) {
+                for (int64_t i = orow[a]; i < orow[a + 1]; i++) {
+                    int32_t b = ocol[i];
+                    int64_t p = orow[a], pe = orow[a + 1];
+                    int64_t q = orow[b], qe = orow[b + 1];
+                    while (p < pe && q < qe) {
+                        if (ocol[p] < ocol[q]) {
+                            p++;
+                        } else if (ocol[p] > ocol[q]) {
+                            q++;
+                        } else {
+                            if (edge_sampled[oeid[i]] || edge_sampled[oeid[p]] || edge_sampled[oeid[q]]) {
+                                or_tri x;
+                                x.key = tri_key(pcode, owt[i], owt[p], owt[q]);
+                                x.t[0] = a;
+                                x.t[1] = b;
+                                x.t[2] = ocol[p];
+                                sort3(x.t);
+                                heap_offer(hp, &x);
+                                local++;
+                            }
+                            p++;
+                            q++;
+                        }
+                    }
+                }
+            }
+            counts[tid] = local;
+        }
+        int64_t total = 0, pooled = 0;
+        for (int t = 0; t < nt; t++) {
+            total += counts[t];
+            pooled += heaps[t].size;
+        }
+        or_tri* all = (or_tri*)malloc(sizeof(or_tri) * (size_t)(pooled + 1));
+        if (!all) {
+            rc = OR_ENOMEM;
+        } else {
+            int64_t at = 0;
+            for (int t = 0; t < nt; t++) {
+                memcpy(all + at, heaps[t].h, sizeof(or_tri) * (size_t)heaps[t].size);
+                at += heaps[t].size;
+            }
+            qsort(all, (size_t)pooled, sizeof(or_tri), cmp_tri);
+            int64_t out = pooled < k ? pooled : k;
+            for (int64_t i = 0; i < out; i++) {
+                tri[3 * i + 0] = all[i].t[0];
+                tri[3 * i + 1] = all[i].t[1];
+                tri[3 * i + 2] = all[i].t[2];
+                key[i] = all[i].key;
+                value[i] = tri_value(pcode, all[i].key);
+            }
+            *count = out;
+            *ntri = total;
+            free(all);
+        }
+    } else {
+        rc = OR_ENOMEM;
+    }
+    for (int t = 0; t < nt; t++) free(heaps[t].h);
+    free(heaps);
+    free(counts);
+    free(orow);
+    free(ocol);
+    free(owt);
+    free(oeid);
+    return rc;
+}
