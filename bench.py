@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wtri", choices=["wtri", "reference"])
     ap.add_argument("--k", type=int, default=1000)
-    ap.add_argument("--small", action="store_true", help="tiny workload (smoke/profiling)")
+    ap.add_argument("--workload", default="mid", choices=["mid", "quarter", "tiny"],
+                    help="mid: the bench workload; quarter: n=1e6 m=5e6 (profiling captures); "
+                         "tiny: n=2000 m=20000")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -59,10 +61,13 @@ def dist_env():
     return world, rank, local
 
 
-def workload(small: bool):
+def workload(name: str):
     import synth
-    if small:
+    if name == "tiny":
         return synth.tiny_graph(0), "chung-lu n=2000 m=20000 gamma=2.1 (tiny)"
+    if name == "quarter":
+        return (synth.scaled_mid_graph(1_000_000, 5_000_000, seed=1),
+                "chung-lu n=1e6 m=5e6 gamma=2.1 zipf(2,1e6) (profiling size)")
     return synth.mid_graph(1), WORKLOAD
 
 
@@ -166,7 +171,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     import oracle
-    g, wl = workload(args.small)
+    g, wl = workload(args.workload)
     times = []
     nthreads = os.cpu_count() or 1
     for step in range(args.warmup + args.steps):
@@ -224,7 +229,7 @@ def main():
                                  ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_double)]
 
-    g, wl = workload(args.small)
+    g, wl = workload(args.workload)
     m = g.m
     k = args.k
     stream = torch.cuda.Stream(device=dev)

@@ -49,8 +49,8 @@ constexpr int LBLK = 256;          // k_long block
 constexpr int SBLK = 1024;         // k_select block
 constexpr int T_SHORT = 32;        // wedges a thread scans before deferring
 constexpr int STAGE_MAX = 24576;   // ids of a y row staged in shared memory (96 KB)
-constexpr int64_t FIRST_ROUND = 2048;
-constexpr int ROUND_GROWTH = 4;
+constexpr int64_t FIRST_ROUND = 64;
+constexpr int ROUND_GROWTH = 8;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;  // bounded mbarrier polling
 constexpr uint32_t STOP_NONE = 0x7fffffffu; // edge positions are below 2^31
 
@@ -159,47 +159,18 @@ __device__ __forceinline__ void append(const Query& q, unsigned long long key, i
 }
 
 // ---------------------------------------------------------------------------
-// Round: one thread per edge of [lo, hi).
+// Round: threads stride over the edges of [lo, hi).
 // ---------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(RBLK) k_round(DevGraph G, Query q, int64_t lo, int64_t hi) {
-    // A round whose first edge lies at or past the first failing edge of an
-    // earlier round has nothing to do.  (Within a round, blocks run in any
-    // order, so the stop point only ever skips whole later rounds; each edge
-    // of the current round is decided by its own bound.)
-    const uint32_t stop_at = STOP_NONE - *(volatile const uint32_t*)&q.st->stop_rev;
-    if (lo >= (int64_t)stop_at) return;
-    const unsigned long long tau = ld_volatile_u64(&q.st->tau);
-    const int64_t r64 = lo + (int64_t)blockIdx.x * RBLK + threadIdx.x;
-    if (r64 >= hi) return;
-    const int32_t r = (int32_t)r64;
-    const uint32_t w = (uint32_t)__ldg(G.ord_w + r);
-    if (keyof<P>(w, w, w) < tau) {
-        // every later edge has a bound no larger: record the first such edge
-        atomicMax(&q.st->stop_rev, STOP_NONE - (uint32_t)r);
-        return;
-    }
-    const int32_t u = __ldg(G.ord_u + r), v = __ldg(G.ord_v + r);
-    const int64_t su = suffix_start(G, u, r, &q.st->err);
-    const int64_t sv = suffix_start(G, v, r, &q.st->err);
-    const int64_t eu = __ldg(G.rowptr + u + 1), ev = __ldg(G.rowptr + v + 1);
-    if (su >= eu || sv >= ev) return;  // no edge after r on one side: owns nothing
-    const uint32_t umax = (uint32_t)__ldg(G.wwt + su), vmax = (uint32_t)__ldg(G.wwt + sv);
-    if (keyof<P>(w, umax, vmax) < tau) return;  // edge bound
-    // Scan the shorter suffix; probe the other endpoint.
-    const bool xu = (eu - su) <= (ev - sv);
-    const int32_t x = xu ? u : v, y = xu ? v : u;
-    const int64_t sx = xu ? su : sv, ex = xu ? eu : ev;
-    const uint32_t ymax = xu ? vmax : umax;
-    const int32_t dy = __ldg(G.deg + y);
-    int64_t j = sx;
-    const int64_t jstop = min(ex, sx + (int64_t)T_SHORT);
-    bool done = false;
+__device__ __forceinline__ void scan_wedges(const DevGraph& G, const Query& q,
+                                            unsigned long long tau, int32_t r, uint32_t w,
+                                            int32_t x, int32_t y, int32_t dy, uint32_t ymax,
+                                            int64_t& j, int64_t jstop, bool& done) {
     for (; j < jstop; j++) {
         const uint32_t wxc = (uint32_t)__ldg(G.wwt + j);
         if (keyof<P>(w, wxc, ymax) < tau) {  // wedge bound, non-increasing along the list
             done = true;
-            break;
+            return;
         }
         const int32_t c = __ldg(G.wcol + j);
         int32_t wyc, ryc;
@@ -212,6 +183,35 @@ __global__ void __launch_bounds__(RBLK) k_round(DevGraph G, Query q, int64_t lo,
             }
         }
     }
+}
+
+// Returns false once this edge's bound is below tau (and so is every later
+// edge's).
+template <int P>
+__device__ __forceinline__ bool process_edge(const DevGraph& G, const Query& q,
+                                             unsigned long long tau, int32_t r) {
+    const uint32_t w = (uint32_t)__ldg(G.ord_w + r);
+    if (keyof<P>(w, w, w) < tau) {
+        // every later edge has a bound no larger: record the first such edge
+        atomicMax(&q.st->stop_rev, STOP_NONE - (uint32_t)r);
+        return false;
+    }
+    const int32_t u = __ldg(G.ord_u + r), v = __ldg(G.ord_v + r);
+    const int64_t su = suffix_start(G, u, r, &q.st->err);
+    const int64_t sv = suffix_start(G, v, r, &q.st->err);
+    const int64_t eu = __ldg(G.rowptr + u + 1), ev = __ldg(G.rowptr + v + 1);
+    if (su >= eu || sv >= ev) return true;  // no edge after r on one side: owns nothing
+    const uint32_t umax = (uint32_t)__ldg(G.wwt + su), vmax = (uint32_t)__ldg(G.wwt + sv);
+    if (keyof<P>(w, umax, vmax) < tau) return true;  // edge bound
+    // Scan the shorter suffix; probe the other endpoint.
+    const bool xu = (eu - su) <= (ev - sv);
+    const int32_t x = xu ? u : v, y = xu ? v : u;
+    const int64_t sx = xu ? su : sv, ex = xu ? eu : ev;
+    const uint32_t ymax = xu ? vmax : umax;
+    const int32_t dy = __ldg(G.deg + y);
+    int64_t j = sx;
+    bool done = false;
+    scan_wedges<P>(G, q, tau, r, w, x, y, dy, ymax, j, min(ex, sx + (int64_t)T_SHORT), done);
     if (!done && j < ex) {
         const uint32_t slot = atomicAdd(&q.st->long_count, 1u);
         if (slot < q.long_cap) {
@@ -227,22 +227,30 @@ __global__ void __launch_bounds__(RBLK) k_round(DevGraph G, Query q, int64_t lo,
             q.longs[slot] = it;
         } else {
             // Deferred list full: finish the scan here.
-            for (; j < ex; j++) {
-                const uint32_t wxc = (uint32_t)__ldg(G.wwt + j);
-                if (keyof<P>(w, wxc, ymax) < tau) break;
-                const int32_t c = __ldg(G.wcol + j);
-                int32_t wyc, ryc;
-                if (probe_oriented(G, y, dy, c, wyc, ryc) && ryc > r) {
-                    const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc);
-                    if (key >= tau) {
-                        int32_t a = x, b = y, cc = c;
-                        sort3(a, b, cc);
-                        append(q, key, a, b, cc);
-                    }
-                }
-            }
+            scan_wedges<P>(G, q, tau, r, w, x, y, dy, ymax, j, ex, done);
         }
     }
+    return true;
+}
+
+template <int P>
+__global__ void __launch_bounds__(RBLK) k_round(DevGraph G, Query q, int64_t lo, int64_t hi) {
+    // Blocks run in any order, so an edge is skipped only once an edge at or
+    // before it has failed its bound (all later edges have no larger bound).
+    const volatile uint32_t* stop_rev = &q.st->stop_rev;
+    if (lo >= (int64_t)(STOP_NONE - *stop_rev)) return;
+    const unsigned long long tau = ld_volatile_u64(&q.st->tau);
+    const int64_t stride = (int64_t)gridDim.x * RBLK;
+    for (int64_t r64 = lo + (int64_t)blockIdx.x * RBLK + threadIdx.x; r64 < hi; r64 += stride) {
+        if (r64 >= (int64_t)(STOP_NONE - *stop_rev)) break;
+        if (!process_edge<P>(G, q, tau, (int32_t)r64)) break;
+    }
+}
+
+// Grid of a round: a few resident blocks per SM, striding over the range.
+inline unsigned round_grid(int64_t edges) {
+    const int64_t cap = (int64_t)sm_count() * 8;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cap, (edges + RBLK - 1) / RBLK));
 }
 
 // ---------------------------------------------------------------------------
@@ -419,6 +427,9 @@ __device__ __forceinline__ int cmp_prefix(unsigned long long key, int4 t, const 
 }
 
 struct SelectSmem {
+    unsigned long long prefix;   // key-only select: chosen high bytes
+    unsigned long long maxkey;
+    uint32_t need;               // key-only select: remaining rank
     uint32_t hist[256];
     uint32_t pw[5];
     uint32_t below;   // candidates strictly better than the prefix
@@ -528,23 +539,126 @@ __device__ uint32_t select_and_compact(unsigned long long* ckey, int4* ctri, uin
     return out;
 }
 
+// The K-th largest key among n candidates (one block, MSB-first over the
+// significant bytes only).
+__device__ unsigned long long kth_key(const unsigned long long* ckey, uint32_t n, uint32_t K,
+                                      SelectSmem& S) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    unsigned long long mx = 0;
+    for (uint32_t i = tid; i < n; i += SBLK) mx = max(mx, ckey[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if (tid == 0) {
+        S.prefix = 0;
+        S.maxkey = 0;
+        S.need = K;
+    }
+    __syncthreads();
+    if (lane == 0) atomicMax(&S.maxkey, mx);
+    __syncthreads();
+    int nbytes = 0;
+    for (unsigned long long t = S.maxkey; t; t >>= 8) nbytes++;
+    for (int byte = nbytes - 1; byte >= 0; byte--) {
+        const int shift = 8 * byte;
+        const unsigned long long hi_mask = (shift + 8 >= 64) ? 0ull : (~0ull << (shift + 8));
+        for (int i = tid; i < 256; i += SBLK) S.hist[i] = 0;
+        __syncthreads();
+        const unsigned long long prefix = S.prefix;
+        for (uint32_t base = 0; base < n; base += SBLK) {
+            const uint32_t i = base + tid;
+            uint32_t d = 256;
+            if (i < n) {
+                const unsigned long long kk = ckey[i];
+                if ((kk & hi_mask) == (prefix & hi_mask)) d = (uint32_t)(kk >> shift) & 255u;
+            }
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (d < 256 && (__ffs(peers) - 1) == lane) atomicAdd(&S.hist[d], __popc(peers));
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const uint32_t need = S.need;
+            uint32_t acc = 0;
+            int dsel = 0;
+            for (int d = 255; d >= 0; d--) {
+                const uint32_t h = S.hist[d];
+                if (acc + h >= need) {
+                    dsel = d;
+                    break;
+                }
+                acc += h;
+            }
+            S.need = need - acc;
+            S.prefix = prefix | ((unsigned long long)dsel << shift);
+        }
+        __syncthreads();
+    }
+    const unsigned long long T = S.prefix;
+    __syncthreads();
+    return T;
+}
+
+// Keeps candidates with key >= T at the front (in place); returns how many.
+__device__ uint32_t compact_ge(unsigned long long* ckey, int4* ctri, uint32_t n,
+                               unsigned long long T, SelectSmem& S) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    uint32_t out = 0;
+    for (uint32_t base = 0; base < n; base += SBLK) {
+        const uint32_t i = base + tid;
+        bool keep = false;
+        unsigned long long kk = 0;
+        int4 t = make_int4(0, 0, 0, 0);
+        if (i < n) {
+            kk = ckey[i];
+            keep = kk >= T;
+            if (keep) t = ctri[i];
+        }
+        const uint32_t b = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) S.warp_cnt[wid] = __popc(b);
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t acc = 0;
+            for (int wv = 0; wv < SBLK / 32; wv++) {
+                const uint32_t c = S.warp_cnt[wv];
+                S.warp_cnt[wv] = acc;
+                acc += c;
+            }
+            S.kept = acc;
+        }
+        __syncthreads();
+        if (keep) {
+            const uint32_t p = out + S.warp_cnt[wid] + __popc(b & ((1u << lane) - 1u));
+            ckey[p] = kk;  // p <= i: writes never overtake unread entries
+            ctri[p] = t;
+        }
+        out += S.kept;
+        __syncthreads();
+    }
+    return out;
+}
+
+// After each round: tau = the k-th largest key among the candidates (a
+// lower bound on the final k-th key, since they are k distinct triangles),
+// and candidates below tau are dropped.  Ties with tau stay; the final step
+// resolves them by the vertex triple.
 __global__ void __launch_bounds__(SBLK) k_select(Query q) {
     __shared__ SelectSmem S;
     const uint32_t err = *(volatile uint32_t*)&q.st->err;
     if (err) return;
     const uint32_t n = min(*(volatile uint32_t*)&q.st->count, q.cap);
-    if (n == q.st->selected) {
-        // nothing new; still clear the deferred list
+    if (n == q.st->selected || n < (uint32_t)q.k) {
         if (threadIdx.x == 0) q.st->long_count = 0;
         return;
     }
-    unsigned long long mk;
-    const uint32_t kept = select_and_compact(q.ckey, q.ctri, n, (uint32_t)q.k, S, &mk);
+    const unsigned long long T = kth_key(q.ckey, n, (uint32_t)q.k, S);
+    const uint32_t kept = compact_ge(q.ckey, q.ctri, n, T, S);
     if (threadIdx.x == 0) {
         q.st->count = kept;
         q.st->selected = kept;
         q.st->long_count = 0;
-        if (kept >= (uint32_t)q.k && mk > q.st->tau) q.st->tau = mk;
+        if (T > q.st->tau) q.st->tau = T;
     }
 }
 
@@ -558,9 +672,8 @@ __device__ __forceinline__ bool before(unsigned long long ka, int4 a, unsigned l
 }
 
 template <int P>
-__global__ void k_rank_scatter(Query q, wtri_tri* out_tri, double* out_w, int32_t* out_count) {
-    __shared__ unsigned long long skey[256];
-    __shared__ int4 stri[256];
+__global__ void __launch_bounds__(256) k_rank_scatter(Query q, wtri_tri* out_tri, double* out_w,
+                                                      int32_t* out_count) {
     const uint32_t err = *(volatile uint32_t*)&q.st->err;
     const uint32_t n = min(*(volatile uint32_t*)&q.st->count, q.cap);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -571,26 +684,18 @@ __global__ void k_rank_scatter(Query q, wtri_tri* out_tri, double* out_w, int32_
         *out_count = status;
     }
     if (err) return;
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long ki = 0;
-    int4 ti = make_int4(0, 0, 0, 0);
-    if (i < n) {
-        ki = q.ckey[i];
-        ti = q.ctri[i];
-    }
+    // One warp per kept candidate: its rank is the number of kept candidates
+    // before it in the total order.
+    const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const unsigned long long ki = q.ckey[i];
+    const int4 ti = q.ctri[i];
     uint32_t rank = 0;
-    for (uint32_t base = 0; base < n; base += 256) {
-        __syncthreads();
-        if (base + threadIdx.x < n) {
-            skey[threadIdx.x] = q.ckey[base + threadIdx.x];
-            stri[threadIdx.x] = q.ctri[base + threadIdx.x];
-        }
-        __syncthreads();
-        const uint32_t lim = min(256u, n - base);
-        if (i < n)
-            for (uint32_t j = 0; j < lim; j++) rank += before(skey[j], stri[j], ki, ti) ? 1u : 0u;
-    }
-    if (i < n) {
+    for (uint32_t j = lane; j < n; j += 32) rank += before(q.ckey[j], q.ctri[j], ki, ti) ? 1u : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    if (lane == 0) {
         out_tri[rank].a = ti.x;
         out_tri[rank].b = ti.y;
         out_tri[rank].c = ti.z;
@@ -658,7 +763,7 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
         const int64_t hi = std::min(m, lo + size);
         {
             ProfScope ps("topk_round", s, 0.0, 1);
-            k_round<P><<<ceil_div_u(hi - lo, RBLK), RBLK, 0, s>>>(G, q, lo, hi);
+            k_round<P><<<round_grid(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
         }
         {
             ProfScope ps("topk_long", s, 0.0, 1);
@@ -674,8 +779,7 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
     {
         ProfScope ps("topk_final", s, 0.0, 2);
         k_final_select<<<1, SBLK, 0, s>>>(q);
-        k_rank_scatter<P><<<ceil_div_u(std::max(k, 1), 256), 256, 0, s>>>(q, d_tris, d_weight,
-                                                                          d_count);
+        k_rank_scatter<P><<<ceil_div_u(std::max(k, 1), 8), 256, 0, s>>>(q, d_tris, d_weight, d_count);
     }
     WTRI_CUDA(cudaGetLastError());
     WTRI_CUDA(cudaFreeAsync(buf, s));
@@ -781,7 +885,7 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
     int64_t lo = 0, size = FIRST_ROUND;
     while (lo < m) {
         const int64_t hi = std::min(m, lo + size);
-        k_round<P><<<ceil_div_u(hi - lo, RBLK), RBLK, 0, s>>>(G, q, lo, hi);
+        k_round<P><<<round_grid(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
         k_long<P><<<long_grid, LBLK, lsmem, s>>>(G, q);
         k_select<<<1, SBLK, 0, s>>>(q);
         count_launches(3);
@@ -789,7 +893,7 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
         size *= ROUND_GROWTH;
     }
     k_final_select<<<1, SBLK, 0, s>>>(q);
-    k_rank_scatter<P><<<ceil_div_u(std::max(k, 1), 256), 256, 0, s>>>(q, d_tris, d_weight, d_count);
+    k_rank_scatter<P><<<ceil_div_u(std::max(k, 1), 8), 256, 0, s>>>(q, d_tris, d_weight, d_count);
     count_launches(2);
     WTRI_CUDA(cudaGetLastError());
     return WTRI_OK;
