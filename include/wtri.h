@@ -175,6 +175,16 @@ WTRI_API int wtri_sample_topk(const wtri_graph* g, double p, int32_t k, int64_t 
                               uint64_t seed, wtri_result* out);
 
 /*
+ * Only the draws of wtri_sample_topk (the first step of Algorithm 3): bit r
+ * of mark_words (word r/32, bit r%32) is set iff the r-th edge of the edge
+ * order (weight desc, input index asc) was drawn at least once.  Host
+ * output of ceil(m/32) words (words_capacity at least that).  Exists so
+ * that the draws can be compared bit for bit with another implementation.
+ */
+WTRI_API int wtri_sample_edges(const wtri_graph* g, double p, int64_t nsamples, uint64_t seed,
+                               uint32_t* mark_words, int64_t words_capacity);
+
+/*
  * Copies one internal array of a built graph to host memory, for tests that
  * compare the device structures with an independent construction.
  * which: one of the WTRI_ARR_* values.  dst must hold bytes_capacity bytes;

@@ -16,6 +16,7 @@ from .wtri import (  # noqa: F401
     build_csr,
     lib,
     lib_path,
+    sample_edges,
     sample_topk,
     topk,
     topk_device,
@@ -23,4 +24,4 @@ from .wtri import (  # noqa: F401
 )
 
 __all__ = ["ARRAYS", "Graph", "WtriError", "WtriUnavailable", "build_csr", "lib", "lib_path",
-           "sample_topk", "topk", "topk_device", "topk_device_noalloc"]
+           "sample_edges", "sample_topk", "topk", "topk_device", "topk_device_noalloc"]

@@ -194,6 +194,37 @@ WTRI_API int wtri_sample_topk(const wtri_graph* g, double p, int32_t k, int64_t 
                              });
 }
 
+WTRI_API int wtri_sample_edges(const wtri_graph* g, double p, int64_t nsamples, uint64_t seed,
+                               uint32_t* mark_words, int64_t words_capacity) {
+    if (!g) return set_error(WTRI_EINVAL, "graph is NULL");
+    int code = 0;
+    WTRI_TRY(p_to_code(p, &code));
+    if (code != P_ONE && code != P_TWO)
+        return set_error(WTRI_EUNSUPPORTED, "edge sampling needs p = 1 or 2");
+    if (nsamples < 0) return set_error(WTRI_EINVAL, "nsamples must be non-negative");
+    const int64_t words = (g->d.m + 31) / 32;
+    if (!mark_words || words_capacity < words)
+        return set_error(WTRI_EINVAL, "mark array smaller than ceil(m/32) words");
+    if (words == 0) return WTRI_OK;
+    cudaStream_t s = g->stream;
+    void* d = nullptr;
+    WTRI_CUDA(cudaMallocAsync(&d, 4 * (size_t)words, s));
+    int rc = WTRI_OK;
+    if (nsamples == 0) {
+        if (cudaMemsetAsync(d, 0, 4 * (size_t)words, s) != cudaSuccess)
+            rc = cuda_error(cudaGetLastError(), "memset", __FILE__, __LINE__);
+    } else {
+        rc = sample_edges_device(g, code, nsamples, seed, (uint32_t*)d, s);
+    }
+    if (rc == WTRI_OK) {
+        cudaError_t e = cudaMemcpyAsync(mark_words, d, 4 * (size_t)words, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_error(e, "mark copy", __FILE__, __LINE__);
+    }
+    cudaFreeAsync(d, s);
+    return rc;
+}
+
 WTRI_API int wtri_graph_copy_array(const wtri_graph* g, int which, void* dst,
                                    int64_t bytes_capacity, int64_t* bytes_out) {
     if (!g) return set_error(WTRI_EINVAL, "graph is NULL");

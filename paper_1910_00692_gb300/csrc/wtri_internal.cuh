@@ -100,10 +100,13 @@ int build_graph(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const 
 int topk_device(const wtri_graph* g, int pcode, int32_t k, wtri_tri* d_tris, double* d_weight,
                 int32_t* d_count, cudaStream_t stream, int retry_scale);
 
-// Edge sampling (wtri_sample.cu).
+// Edge sampling (wtri_topk.cu).
 int sample_topk_device(const wtri_graph* g, int pcode, int32_t k, int64_t nsamples,
                        uint64_t seed, wtri_tri* d_tris, double* d_weight, int32_t* d_count,
                        cudaStream_t stream, int retry_scale);
+// Only the draws: bitmap over edge-order positions (ceil(m/32) words).
+int sample_edges_device(const wtri_graph* g, int pcode, int64_t nsamples, uint64_t seed,
+                        uint32_t* d_mark, cudaStream_t stream);
 
 // Phase timers / launch counter (wtri_prof.cu).  'bytes' is the phase's
 // algorithmic traffic; 'launches' the number of kernels it launches.

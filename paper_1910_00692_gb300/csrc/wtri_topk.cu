@@ -81,7 +81,25 @@ struct Query {
     LongItem* longs;
     uint32_t long_cap;
     int32_t k;
+    // Sampled mode (edge sampling): bitmap of drawn edges by edge-order
+    // position, and the drawn positions in ascending order.
+    const uint32_t* smark;
+    const int32_t* slist;
 };
+
+__device__ __forceinline__ bool drawn(const Query& q, int32_t r) {
+    return (__ldg(q.smark + (r >> 5)) >> (r & 31)) & 1u;
+}
+
+// Ownership.  Exact mode: a triangle belongs to its first edge in the edge
+// order, so the edge at position r owns (x, y, c) iff both other edges come
+// later.  Sampled mode (Algorithm 3's set T): a triangle belongs to its
+// first DRAWN edge, so each triangle with a drawn edge is reported once.
+template <bool SAMPLED>
+__device__ __forceinline__ bool owns(const Query& q, int32_t r, int32_t rxc, int32_t ryc) {
+    if (!SAMPLED) return rxc > r && ryc > r;
+    return !(rxc < r && drawn(q, rxc)) && !(ryc < r && drawn(q, ryc));
+}
 
 template <int P>
 __device__ __forceinline__ unsigned long long keyof(uint32_t a, uint32_t b, uint32_t c) {
@@ -161,7 +179,7 @@ __device__ __forceinline__ void append(const Query& q, unsigned long long key, i
 // ---------------------------------------------------------------------------
 // Round: threads stride over the edges of [lo, hi).
 // ---------------------------------------------------------------------------
-template <int P>
+template <int P, bool SAMPLED>
 __device__ __forceinline__ void scan_wedges(const DevGraph& G, const Query& q,
                                             unsigned long long tau, int32_t r, uint32_t w,
                                             int32_t x, int32_t y, int32_t dy, uint32_t ymax,
@@ -173,8 +191,10 @@ __device__ __forceinline__ void scan_wedges(const DevGraph& G, const Query& q,
             return;
         }
         const int32_t c = __ldg(G.wcol + j);
+        if (SAMPLED && c == y) continue;  // the edge itself (full rows in sampled mode)
         int32_t wyc, ryc;
-        if (probe_oriented(G, y, dy, c, wyc, ryc) && ryc > r) {
+        if (probe_oriented(G, y, dy, c, wyc, ryc) &&
+            owns<SAMPLED>(q, r, __ldg(G.wrk + j), ryc)) {
             const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc);
             if (key >= tau) {
                 int32_t a = x, b = y, cc = c;
@@ -187,18 +207,21 @@ __device__ __forceinline__ void scan_wedges(const DevGraph& G, const Query& q,
 
 // Returns false once this edge's bound is below tau (and so is every later
 // edge's).
-template <int P>
+template <int P, bool SAMPLED>
 __device__ __forceinline__ bool process_edge(const DevGraph& G, const Query& q,
-                                             unsigned long long tau, int32_t r) {
+                                             unsigned long long tau, int32_t idx) {
+    const int32_t r = SAMPLED ? __ldg(q.slist + idx) : idx;
     const uint32_t w = (uint32_t)__ldg(G.ord_w + r);
-    if (keyof<P>(w, w, w) < tau) {
+    if (!SAMPLED && keyof<P>(w, w, w) < tau) {
         // every later edge has a bound no larger: record the first such edge
         atomicMax(&q.st->stop_rev, STOP_NONE - (uint32_t)r);
         return false;
     }
     const int32_t u = __ldg(G.ord_u + r), v = __ldg(G.ord_v + r);
-    const int64_t su = suffix_start(G, u, r, &q.st->err);
-    const int64_t sv = suffix_start(G, v, r, &q.st->err);
+    // Exact mode scans what comes after r in each list; sampled mode scans
+    // whole lists (the other two edges may be heavier than a drawn edge).
+    const int64_t su = SAMPLED ? __ldg(G.rowptr + u) : suffix_start(G, u, r, &q.st->err);
+    const int64_t sv = SAMPLED ? __ldg(G.rowptr + v) : suffix_start(G, v, r, &q.st->err);
     const int64_t eu = __ldg(G.rowptr + u + 1), ev = __ldg(G.rowptr + v + 1);
     if (su >= eu || sv >= ev) return true;  // no edge after r on one side: owns nothing
     const uint32_t umax = (uint32_t)__ldg(G.wwt + su), vmax = (uint32_t)__ldg(G.wwt + sv);
@@ -211,7 +234,8 @@ __device__ __forceinline__ bool process_edge(const DevGraph& G, const Query& q,
     const int32_t dy = __ldg(G.deg + y);
     int64_t j = sx;
     bool done = false;
-    scan_wedges<P>(G, q, tau, r, w, x, y, dy, ymax, j, min(ex, sx + (int64_t)T_SHORT), done);
+    scan_wedges<P, SAMPLED>(G, q, tau, r, w, x, y, dy, ymax, j, min(ex, sx + (int64_t)T_SHORT),
+                            done);
     if (!done && j < ex) {
         const uint32_t slot = atomicAdd(&q.st->long_count, 1u);
         if (slot < q.long_cap) {
@@ -227,13 +251,13 @@ __device__ __forceinline__ bool process_edge(const DevGraph& G, const Query& q,
             q.longs[slot] = it;
         } else {
             // Deferred list full: finish the scan here.
-            scan_wedges<P>(G, q, tau, r, w, x, y, dy, ymax, j, ex, done);
+            scan_wedges<P, SAMPLED>(G, q, tau, r, w, x, y, dy, ymax, j, ex, done);
         }
     }
     return true;
 }
 
-template <int P>
+template <int P, bool SAMPLED = false>
 __global__ void __launch_bounds__(RBLK) k_round(DevGraph G, Query q, int64_t lo, int64_t hi) {
     // Blocks run in any order, so an edge is skipped only once an edge at or
     // before it has failed its bound (all later edges have no larger bound).
@@ -243,7 +267,7 @@ __global__ void __launch_bounds__(RBLK) k_round(DevGraph G, Query q, int64_t lo,
     const int64_t stride = (int64_t)gridDim.x * RBLK;
     for (int64_t r64 = lo + (int64_t)blockIdx.x * RBLK + threadIdx.x; r64 < hi; r64 += stride) {
         if (r64 >= (int64_t)(STOP_NONE - *stop_rev)) break;
-        if (!process_edge<P>(G, q, tau, (int32_t)r64)) break;
+        if (!process_edge<P, SAMPLED>(G, q, tau, (int32_t)r64)) break;
     }
 }
 
@@ -292,7 +316,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
     return ok != 0;
 }
 
-template <int P>
+template <int P, bool SAMPLED = false>
 __global__ void __launch_bounds__(LBLK) k_long(DevGraph G, Query q) {
     extern __shared__ __align__(128) unsigned char lsm[];
     int32_t* srow = reinterpret_cast<int32_t*>(lsm);
@@ -360,6 +384,10 @@ __global__ void __launch_bounds__(LBLK) k_long(DevGraph G, Query q) {
             if (__ballot_sync(0xffffffffu, live) == 0) break;
             if (live) {
                 const int32_t c = __ldg(G.wcol + j);
+                if (SAMPLED && c == y) live = false;  // the edge itself
+            }
+            if (live) {
+                const int32_t c = __ldg(G.wcol + j);
                 int32_t wyc = 0, ryc = -1;
                 bool found = false;
                 if (staged) {
@@ -377,7 +405,7 @@ __global__ void __launch_bounds__(LBLK) k_long(DevGraph G, Query q) {
                 } else {
                     found = probe_oriented(G, y, dy, c, wyc, ryc);
                 }
-                if (found && ryc > r) {
+                if (found && owns<SAMPLED>(q, r, __ldg(G.wrk + j), ryc)) {
                     const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc);
                     if (key >= tau) {
                         int32_t a = x, b = y, cc = c;
@@ -746,6 +774,8 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
     q.cap = cap;
     q.long_cap = long_cap;
     q.k = k;
+    q.smark = nullptr;
+    q.slist = nullptr;
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
 
     const size_t lsmem = (size_t)STAGE_MAX * 4 + 16;
@@ -768,6 +798,281 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
         {
             ProfScope ps("topk_long", s, 0.0, 1);
             k_long<P><<<long_grid, LBLK, lsmem, s>>>(G, q);
+        }
+        {
+            ProfScope ps("topk_select", s, 0.0, 1);
+            k_select<<<1, SBLK, 0, s>>>(q);
+        }
+        lo = hi;
+        size *= ROUND_GROWTH;
+    }
+    {
+        ProfScope ps("topk_final", s, 0.0, 2);
+        k_final_select<<<1, SBLK, 0, s>>>(q);
+        k_rank_scatter<P><<<ceil_div_u(std::max(k, 1), 8), 256, 0, s>>>(q, d_tris, d_weight, d_count);
+    }
+    WTRI_CUDA(cudaGetLastError());
+    WTRI_CUDA(cudaFreeAsync(buf, s));
+    return WTRI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Weighted edge sampling (Algorithm 3, Proposition 4.1, Section 4.1).
+//
+// Draw: with the edges in the edge order and C[r] = sum_{j<=r} w_j^p (exact
+// integers), sample s takes x = word 0 of Philox4x64-10(counter (s,0,0,0),
+// key (seed,0)), t = floor(x * Z / 2^64), and the edge is the first r with
+// C[r] > t.  Equal weights are contiguous in the edge order (Section 4.1's
+// weight classes), so the search runs over the class table (start, weight,
+// cumulative mass) and the position inside the class is (t - C_prev) /
+// w^p.  Drawn edges are marked in a bitmap; the marked positions, in
+// ascending order, are then swept like the exact query (heaviest first) in
+// sampled-ownership mode.
+// ---------------------------------------------------------------------------
+typedef unsigned __int128 u128;
+
+// Philox4x64-10 (Salmon et al., SC'11), first output word only.
+__device__ __forceinline__ uint64_t philox_word0(uint64_t c0, uint64_t k0) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t c1 = 0, c2 = 0, c3 = 0, k1 = 0;
+#pragma unroll
+    for (int i = 0; i < 10; i++) {
+        const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c1 = lo1;
+        c3 = lo0;
+        c0 = n0;
+        c2 = n2;
+        k0 += W0;
+        k1 += W1;
+    }
+    return c0;
+}
+
+// Class starts: position r starts a class when its weight differs from r-1.
+__global__ void k_class_flags(int64_t m, const int32_t* __restrict__ ow, int32_t* __restrict__ flag) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m;
+         r += (int64_t)gridDim.x * blockDim.x)
+        flag[r] = (r == 0 || __ldg(ow + r) != __ldg(ow + r - 1)) ? 1 : 0;
+}
+
+__global__ void k_class_starts(int64_t m, const int32_t* __restrict__ flag,
+                               const int64_t* __restrict__ cls, int64_t* __restrict__ cstart) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m;
+         r += (int64_t)gridDim.x * blockDim.x)
+        if (flag[r]) cstart[cls[r]] = r;
+    if (blockIdx.x == 0 && threadIdx.x == 0) cstart[cls[m]] = m;  // sentinel
+}
+
+// Inclusive prefix of class masses count * w^p, one block (classes are few:
+// one per distinct weight).
+template <int P>
+__global__ void __launch_bounds__(1024) k_class_mass(const int64_t* __restrict__ cls_total,
+                                                     const int64_t* __restrict__ cstart,
+                                                     const int32_t* __restrict__ ow,
+                                                     u128* __restrict__ cmass) {
+    __shared__ u128 warp_sum[32];
+    __shared__ u128 carry;
+    const int64_t nc = *cls_total;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t base = 0; base < nc; base += 1024) {
+        const int64_t c = base + threadIdx.x;
+        u128 x = 0;
+        if (c < nc) {
+            const u128 wv = (u128)(uint64_t)__ldg(ow + cstart[c]);
+            x = (u128)(uint64_t)(cstart[c + 1] - cstart[c]) * (P == P_TWO ? wv * wv : wv);
+        }
+        u128 inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t lo = __shfl_up_sync(0xffffffffu, (uint64_t)inc, o);
+            const uint64_t hi = __shfl_up_sync(0xffffffffu, (uint64_t)(inc >> 64), o);
+            if (lane >= o) inc += ((u128)hi << 64) | lo;
+        }
+        if (lane == 31) warp_sum[wid] = inc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            u128 acc = carry;
+            for (int k = 0; k < 32; k++) {
+                const u128 t = warp_sum[k];
+                warp_sum[k] = acc;
+                acc += t;
+            }
+            carry = acc;
+        }
+        __syncthreads();
+        if (c < nc) cmass[c] = warp_sum[wid] + inc;
+        __syncthreads();
+    }
+}
+
+template <int P>
+__global__ void k_draw(int64_t nsamples, uint64_t seed, const int64_t* __restrict__ cls_total,
+                       const int64_t* __restrict__ cstart, const int32_t* __restrict__ ow,
+                       const u128* __restrict__ cmass, uint32_t* __restrict__ mark) {
+    const int64_t nc = *cls_total;
+    const u128 Z = cmass[nc - 1];
+    const uint64_t zl = (uint64_t)Z, zh = (uint64_t)(Z >> 64);
+    for (int64_t sidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sidx < nsamples;
+         sidx += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = philox_word0((uint64_t)sidx, seed);
+        const u128 t = (u128)x * zh + (u128)__umul64hi(x, zl);  // floor(x * Z / 2^64)
+        int64_t lo = 0, hi = nc;                                   // first class with mass > t
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (cmass[mid] > t) hi = mid;
+            else lo = mid + 1;
+        }
+        const u128 prev = lo > 0 ? cmass[lo - 1] : (u128)0;
+        const u128 wv = (u128)(uint64_t)__ldg(ow + cstart[lo]);
+        const u128 wp = P == P_TWO ? wv * wv : wv;
+        const int64_t r = cstart[lo] + (int64_t)((t - prev) / wp);
+        atomicOr(mark + (r >> 5), 1u << (r & 31));
+    }
+}
+
+__global__ void k_mark_popc(int64_t words, const uint32_t* __restrict__ mark, int32_t* __restrict__ pc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+         i += (int64_t)gridDim.x * blockDim.x)
+        pc[i] = __popc(mark[i]);
+}
+
+__global__ void k_mark_list(int64_t words, const uint32_t* __restrict__ mark,
+                            const int64_t* __restrict__ off, int32_t* __restrict__ list) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t b = mark[i];
+        int64_t o = off[i];
+        while (b) {
+            const int bit = __ffs(b) - 1;
+            list[o++] = (int32_t)(i * 32 + bit);
+            b &= b - 1;
+        }
+    }
+}
+
+inline unsigned grid_of(int64_t work) {
+    const int64_t cap = (int64_t)sm_count() * 16;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cap, (work + 255) / 256));
+}
+
+// Draws the samples into a bitmap over edge-order positions (words =
+// ceil(m/32), zeroed here).  Scratch: cls (m+1 int64), cstart (m+1 int64),
+// cmass (m u128), flags (m int32).
+template <int P>
+int draw_samples(const wtri_graph* g, int64_t nsamples, uint64_t seed, uint32_t* mark,
+                 cudaStream_t s) {
+    const DevGraph& G = g->d;
+    const int64_t m = G.m, words = (m + 31) / 32;
+    const size_t bytes = 8 * (size_t)(m + 1) * 2 + 16 * (size_t)m + 4 * (size_t)m + 256;
+    void* buf = nullptr;
+    if (cudaMallocAsync(&buf, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(WTRI_ENOMEM, "sampling scratch allocation failed");
+    }
+    char* p = (char*)buf;
+    int64_t* cls = (int64_t*)p;
+    p += 8 * (size_t)(m + 1);
+    int64_t* cstart = (int64_t*)p;
+    p += 8 * (size_t)(m + 1);
+    u128* cmass = (u128*)p;
+    p += 16 * (size_t)m;
+    int32_t* flag = (int32_t*)p;
+    WTRI_CUDA(cudaMemsetAsync(mark, 0, 4 * (size_t)words, s));
+    {
+        ProfScope ps("sample_classes", s, 4.0 * m + 4.0 * m, 1);
+        k_class_flags<<<grid_of(m), 256, 0, s>>>(m, G.ord_w, flag);
+    }
+    WTRI_TRY(exclusive_scan_i32_to_i64(flag, cls, m, s));  // cls[m] = number of classes
+    {
+        ProfScope ps("sample_class_table", s, 12.0 * m, 2);
+        k_class_starts<<<grid_of(m), 256, 0, s>>>(m, flag, cls, cstart);
+        k_class_mass<P><<<1, 1024, 0, s>>>(cls + m, cstart, G.ord_w, cmass);
+    }
+    {
+        ProfScope ps("sample_draw", s, 0.0, 1);
+        k_draw<P><<<grid_of(nsamples), 256, 0, s>>>(nsamples, seed, cls + m, cstart, G.ord_w, cmass,
+                                                    mark);
+    }
+    WTRI_CUDA(cudaGetLastError());
+    WTRI_CUDA(cudaFreeAsync(buf, s));
+    return WTRI_OK;
+}
+
+template <int P>
+int run_sample(const wtri_graph* g, int32_t k, int64_t nsamples, uint64_t seed, wtri_tri* d_tris,
+               double* d_weight, int32_t* d_count, cudaStream_t s, int scale) {
+    const DevGraph& G = g->d;
+    const int64_t m = G.m, words = (m + 31) / 32;
+    const uint32_t cap = (uint32_t)std::min<int64_t>(
+        (int64_t(1) << 20) * scale + 16 * (int64_t)k, (int64_t(1) << 31) - 1);
+    const uint32_t long_cap = (uint32_t)((1u << 16) * scale);
+    const size_t qbytes = 256 + (size_t)cap * 24 + 256 + (size_t)long_cap * sizeof(LongItem) + 256;
+    const size_t sbytes = 4 * (size_t)words + 8 * (size_t)(words + 1) + 4 * (size_t)words + 4 * (size_t)m + 256;
+    void* buf = nullptr;
+    if (cudaMallocAsync(&buf, qbytes + sbytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(WTRI_ENOMEM, "sampling query scratch allocation failed");
+    }
+    char* p = (char*)buf;
+    Query q;
+    q.st = (QState*)p;
+    p += 256;
+    q.ckey = (unsigned long long*)p;
+    p += (size_t)cap * 8;
+    q.ctri = (int4*)p;
+    p += (size_t)cap * 16;
+    p = (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+    q.longs = (LongItem*)p;
+    p += (size_t)long_cap * sizeof(LongItem);
+    p = (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+    uint32_t* mark = (uint32_t*)p;
+    p += 4 * (size_t)words;
+    p = (char*)(((uintptr_t)p + 7) & ~(uintptr_t)7);
+    int64_t* off = (int64_t*)p;
+    p += 8 * (size_t)(words + 1);
+    int32_t* pc = (int32_t*)p;
+    p += 4 * (size_t)words;
+    int32_t* list = (int32_t*)p;
+    q.cap = cap;
+    q.long_cap = long_cap;
+    q.k = k;
+    q.smark = mark;
+    q.slist = list;
+    WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
+    ProfScope whole(P == P_ONE ? "sample_p=1" : "sample_p=2", s, 0.0, 0);
+    WTRI_TRY(draw_samples<P>(g, nsamples, seed, mark, s));
+    {
+        ProfScope ps("sample_compact", s, 8.0 * words, 2);
+        k_mark_popc<<<grid_of(words), 256, 0, s>>>(words, mark, pc);
+        WTRI_TRY(exclusive_scan_i32_to_i64(pc, off, words, s));
+        k_mark_list<<<grid_of(words), 256, 0, s>>>(words, mark, off, list);
+    }
+    int64_t nlist = 0;
+    WTRI_CUDA(cudaMemcpyAsync(&nlist, off + words, 8, cudaMemcpyDeviceToHost, s));
+    WTRI_CUDA(cudaStreamSynchronize(s));
+    const size_t lsmem = (size_t)STAGE_MAX * 4 + 16;
+    static bool attr_done[4] = {false, false, false, false};
+    if (!attr_done[P]) {
+        WTRI_CUDA(cudaFuncSetAttribute(k_long<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)lsmem));
+        attr_done[P] = true;
+    }
+    const int long_grid = sm_count() * 2;
+    int64_t lo = 0, size = FIRST_ROUND;
+    while (lo < nlist) {
+        const int64_t hi = std::min(nlist, lo + size);
+        {
+            ProfScope ps("sample_round", s, 0.0, 1);
+            k_round<P, true><<<round_grid(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
+        }
+        {
+            ProfScope ps("sample_long", s, 0.0, 1);
+            k_long<P, true><<<long_grid, LBLK, lsmem, s>>>(G, q);
         }
         {
             ProfScope ps("topk_select", s, 0.0, 1);
@@ -870,6 +1175,8 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
     q.cap = NOALLOC_CAP;
     q.long_cap = NOALLOC_LONG;
     q.k = k;
+    q.smark = nullptr;
+    q.slist = nullptr;
     // The array keeps the previous call's contents: reset the status word
     // (counters, threshold, stop flag, error bits).
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
@@ -900,6 +1207,20 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
 }
 
 }  // namespace
+int sample_topk_device(const wtri_graph* g, int pcode, int32_t k, int64_t nsamples, uint64_t seed,
+                       wtri_tri* d_tris, double* d_weight, int32_t* d_count, cudaStream_t stream,
+                       int retry_scale) {
+    if (pcode == P_ONE)
+        return run_sample<P_ONE>(g, k, nsamples, seed, d_tris, d_weight, d_count, stream, retry_scale);
+    return run_sample<P_TWO>(g, k, nsamples, seed, d_tris, d_weight, d_count, stream, retry_scale);
+}
+
+int sample_edges_device(const wtri_graph* g, int pcode, int64_t nsamples, uint64_t seed,
+                        uint32_t* d_mark, cudaStream_t stream) {
+    if (pcode == P_ONE) return draw_samples<P_ONE>(g, nsamples, seed, d_mark, stream);
+    return draw_samples<P_TWO>(g, nsamples, seed, d_mark, stream);
+}
+
 }  // namespace wtri
 
 extern "C" WTRI_API int wtri_topk_device_noalloc(const wtri_graph* g, double p, int32_t k,

@@ -94,12 +94,13 @@ def lib():
     L.wtri_topk_device_noalloc.argtypes = [vp, f64, i32, vp, vp, vp, vp]
     L.wtri_sample_topk.argtypes = [vp, f64, i32, i64, ctypes.c_uint64, ctypes.POINTER(_Result)]
     L.wtri_graph_copy_array.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
+    L.wtri_sample_edges.argtypes = [vp, f64, i64, ctypes.c_uint64, vp, i64]
     L.wtri_last_error.restype = ctypes.c_char_p
     L.wtri_last_error.argtypes = []
     L.wtri_version.restype = ctypes.c_char_p
     for f in (L.wtri_build_csr, L.wtri_graph_info, L.wtri_topk, L.wtri_topk_device,
               L.wtri_topk_device_noalloc,
-              L.wtri_sample_topk, L.wtri_graph_copy_array):
+              L.wtri_sample_topk, L.wtri_graph_copy_array, L.wtri_sample_edges):
         f.restype = ctypes.c_int
     _lib = L
     return L
@@ -226,6 +227,19 @@ def sample_topk(g: Graph, p: float, k: int, nsamples: int, seed: int):
     return _host_query(lambda r: lib().wtri_sample_topk(g.handle, float(p), int(k), int(nsamples),
                                                          ctypes.c_uint64(seed & (2**64 - 1)), r),
                        int(k))
+
+
+def sample_edges(g: Graph, p: float, nsamples: int, seed: int) -> np.ndarray:
+    """wtri_sample_edges: boolean mask over edge-order positions of the edges
+    drawn by Algorithm 3 (probability w^p / Z per draw)."""
+    m = g.info()["m"]
+    words = (m + 31) // 32
+    out = np.zeros(max(words, 1), dtype=np.uint32)
+    _check(lib().wtri_sample_edges(g.handle, float(p), int(nsamples),
+                                   ctypes.c_uint64(int(seed) & (2**64 - 1)),
+                                   out.ctypes.data_as(ctypes.c_void_p), words))
+    bits = np.unpackbits(out.view(np.uint8), bitorder="little")
+    return bits[:m].astype(bool)
 
 
 def p_values():
