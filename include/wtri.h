@@ -159,6 +159,18 @@ WTRI_API int wtri_topk_device_noalloc(const wtri_graph* g, double p, int32_t k, 
                                       double* d_weight, int32_t* d_count, void* stream);
 
 /*
+ * Batched exact top-k: query i asks for the top-k[i] triangles of gs[i] at
+ * p[i] (same problem and result format as wtri_topk, results in outs[i]).
+ * All queries run in one launch sequence captured in a CUDA graph on the
+ * first graph's stream: each phase kernel covers every query at once, and
+ * each query keeps its own threshold and candidate buffer.  Graphs must be
+ * on one device.  Returns after all results are in the host arrays.  No
+ * counterpart in the paper (whose algorithms answer one query at a time).
+ */
+WTRI_API int wtri_topk_batch(const wtri_graph* const* gs, const double* p, const int32_t* k,
+                             int32_t nq, wtri_result* outs);
+
+/*
  * Weighted edge sampling (Algorithm 3, Section 4.1): draws nsamples edges
  * with probability w_e^p / Z (Proposition 4.1), adds every triangle on each
  * sampled edge (the common neighbours N(a) ∩ N(b)) to a set, and returns the

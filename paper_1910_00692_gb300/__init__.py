@@ -19,9 +19,10 @@ from .wtri import (  # noqa: F401
     sample_edges,
     sample_topk,
     topk,
+    topk_batch,
     topk_device,
     topk_device_noalloc,
 )
 
 __all__ = ["ARRAYS", "Graph", "WtriError", "WtriUnavailable", "build_csr", "lib", "lib_path",
-           "sample_edges", "sample_topk", "topk", "topk_device", "topk_device_noalloc"]
+           "sample_edges", "sample_topk", "topk", "topk_batch", "topk_device", "topk_device_noalloc"]

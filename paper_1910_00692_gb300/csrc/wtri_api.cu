@@ -194,6 +194,30 @@ WTRI_API int wtri_sample_topk(const wtri_graph* g, double p, int32_t k, int64_t 
                              });
 }
 
+WTRI_API int wtri_topk_batch(const wtri_graph* const* gs, const double* p, const int32_t* k,
+                             int32_t nq, wtri_result* outs) {
+    if (nq < 0) return set_error(WTRI_EINVAL, "nq must be non-negative");
+    if (nq == 0) return WTRI_OK;
+    if (!gs || !p || !k || !outs) return set_error(WTRI_EINVAL, "NULL batch arrays");
+    std::vector<int32_t> codes((size_t)nq);
+    for (int32_t i = 0; i < nq; i++) outs[i].count = 0;
+    int dev = -1;
+    for (int32_t i = 0; i < nq; i++) {
+        if (!gs[i]) return set_error(WTRI_EINVAL, "graph " + std::to_string(i) + " is NULL");
+        if (dev < 0) dev = gs[i]->device;
+        if (gs[i]->device != dev) return set_error(WTRI_EINVAL, "batch graphs on different devices");
+        int c = 0;
+        int rc = p_to_code(p[i], &c);
+        if (rc != WTRI_OK) return rc;
+        codes[(size_t)i] = c;
+        rc = check_query(gs[i], k[i]);
+        if (rc != WTRI_OK) return rc;
+        if (!outs[i].tris || !outs[i].weight || outs[i].capacity < k[i])
+            return set_error(WTRI_EINVAL, "result " + std::to_string(i) + " arrays NULL or too small");
+    }
+    return topk_batch(gs, codes.data(), k, nq, outs, gs[0]->stream, 1);
+}
+
 WTRI_API int wtri_sample_edges(const wtri_graph* g, double p, int64_t nsamples, uint64_t seed,
                                uint32_t* mark_words, int64_t words_capacity) {
     if (!g) return set_error(WTRI_EINVAL, "graph is NULL");

@@ -108,6 +108,10 @@ int sample_topk_device(const wtri_graph* g, int pcode, int32_t k, int64_t nsampl
 int sample_edges_device(const wtri_graph* g, int pcode, int64_t nsamples, uint64_t seed,
                         uint32_t* d_mark, cudaStream_t stream);
 
+// Batched top-k (wtri_batch.cu): host results, optional CUDA-graph capture.
+int topk_batch(const wtri_graph* const* gs, const int32_t* pcodes, const int32_t* ks, int32_t nq,
+               wtri_result* outs, cudaStream_t s, int use_graph);
+
 // Phase timers / launch counter (wtri_prof.cu).  'bytes' is the phase's
 // algorithmic traffic; 'launches' the number of kernels it launches.
 void prof_begin(const char* name, cudaStream_t s, double bytes, int launches);

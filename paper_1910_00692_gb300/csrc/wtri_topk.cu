@@ -1,749 +1,11 @@
-// Exact top-k weighted triangles: heavy-first enumeration with a running
-// threshold.
-//
-// Method (the exactness argument of Algorithm 2 and Section 3.2, re-derived
-// for a parallel schedule):
-//  * Edges are visited in the edge order (weight desc, input index asc); r is
-//    an edge's position.  Each triangle is owned by its first edge in that
-//    order, so edge r owns triangle {x, y, c} iff both (x,c) and (y,c) come
-//    after r.  Every triangle is enumerated exactly once.
-//  * Every triangle owned by r has all edge weights <= w_r, and m_p is
-//    monotone in each argument with m_p <= max, so its key is at most
-//    K(w_r, w_r, w_r).  Once that bound is below the threshold tau, no later
-//    edge can contribute: the sweep stops.  This is the paper's heavy-first
-//    threshold argument with one monotone cursor in place of two pointers.
-//  * Per edge, the entries of x and y after r are suffixes of their
-//    weight-sorted lists; their first entries bound the other two weights
-//    (edge bound), and scanning x's suffix in weight order gives a wedge bound
-//    K(w_r, w_xc, max_y) that only decreases, so the scan stops at the first
-//    wedge below tau.  The closing edge (y, c) is found by binary search in
-//    the oriented (degree-ordered) lists.
-//  * tau is the key of the k-th best of k distinct triangles found so far, a
-//    valid lower bound on the true k-th key; pruning is strict (< tau), so
-//    triangles tied with the k-th key are still enumerated and the triple
-//    tie-break decides them.
-//
-// Schedule: the edge order is processed in rounds of geometrically growing
-// ranges [lo, hi).  Each round is three launches: k_round (thread per edge,
-// short scans inline, long scans deferred), k_long (block per deferred scan,
-// the closing-edge lookups go to the y row staged in shared memory by a bulk
-// copy), and k_select (one block: radix select of the k-th candidate under
-// the total order, in-place compaction, new tau).  Rounds after the stop
-// return at once, so the launch sequence depends only on (m, k) and can be
-// captured in a CUDA graph.
-#include <cooperative_groups.h>
-#include <cuda_runtime.h>
+// Exact top-k query, weighted edge sampling and the allocation-free query:
+// host orchestration of the kernels in wtri_query.cuh.
+#include "wtri_query.cuh"
 
-#include <algorithm>
 #include <mutex>
-
-#include "wtri_internal.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace wtri {
 namespace {
-
-constexpr int RBLK = 256;          // k_round block
-constexpr int LBLK = 256;          // k_long block
-constexpr int SBLK = 1024;         // k_select block
-constexpr int T_SHORT = 32;        // wedges a thread scans before deferring
-constexpr int STAGE_MAX = 24576;   // ids of a y row staged in shared memory (96 KB)
-constexpr int64_t FIRST_ROUND = 64;
-constexpr int ROUND_GROWTH = 8;
-constexpr uint32_t WAIT_LIMIT = 1u << 24;  // bounded mbarrier polling
-constexpr uint32_t STOP_NONE = 0x7fffffffu; // edge positions are below 2^31
-
-struct QState {
-    unsigned long long tau;   // keys below tau are pruned; 0 = no bound yet
-    uint32_t stop_rev;        // STOP_NONE - (first edge whose bound fell below tau); 0 = none
-    uint32_t err;             // DEV_ERR_* bits
-    uint32_t count;           // candidates appended (may exceed capacity)
-    uint32_t long_count;      // deferred scans
-    uint32_t selected;        // count right after the last compaction
-    uint32_t pad[3];
-};
-
-struct LongItem {
-    int32_t r;      // owning edge (position in the edge order)
-    int32_t x, y;   // scanned endpoint, probed endpoint
-    int32_t w;      // w_r
-    int32_t ymax;   // first weight of y's suffix
-    int32_t pad;
-    int64_t j0, j1; // remaining suffix of x's weight-sorted list
-};
-
-struct Query {
-    QState* st;
-    unsigned long long* ckey;
-    int4* ctri;
-    uint32_t cap;
-    LongItem* longs;
-    uint32_t long_cap;
-    int32_t k;
-    // Sampled mode (edge sampling): bitmap of drawn edges by edge-order
-    // position, and the drawn positions in ascending order.
-    const uint32_t* smark;
-    const int32_t* slist;
-};
-
-__device__ __forceinline__ bool drawn(const Query& q, int32_t r) {
-    return (__ldg(q.smark + (r >> 5)) >> (r & 31)) & 1u;
-}
-
-// Ownership.  Exact mode: a triangle belongs to its first edge in the edge
-// order, so the edge at position r owns (x, y, c) iff both other edges come
-// later.  Sampled mode (Algorithm 3's set T): a triangle belongs to its
-// first DRAWN edge, so each triangle with a drawn edge is reported once.
-template <bool SAMPLED>
-__device__ __forceinline__ bool owns(const Query& q, int32_t r, int32_t rxc, int32_t ryc) {
-    if (!SAMPLED) return rxc > r && ryc > r;
-    return !(rxc < r && drawn(q, rxc)) && !(ryc < r && drawn(q, ryc));
-}
-
-template <int P>
-__device__ __forceinline__ unsigned long long keyof(uint32_t a, uint32_t b, uint32_t c) {
-    if (P == P_ONE) return (unsigned long long)a + b + c;
-    if (P == P_TWO)
-        return (unsigned long long)a * a + (unsigned long long)b * b + (unsigned long long)c * c;
-    if (P == P_MAX) return (unsigned long long)max(a, max(b, c));
-    return (unsigned long long)min(a, min(b, c));
-}
-
-__device__ __forceinline__ void sort3(int32_t& a, int32_t& b, int32_t& c) {
-    int32_t t;
-    if (a > b) { t = a; a = b; b = t; }
-    if (b > c) { t = b; b = c; c = t; }
-    if (a > b) { t = a; a = b; b = t; }
-}
-
-__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
-    return *(volatile const unsigned long long*)p;
-}
-
-// Position just after edge r's own entry in x's weight-sorted list.
-__device__ __forceinline__ int64_t suffix_start(const DevGraph& G, int32_t x, int32_t r,
-                                                uint32_t* err) {
-    int64_t lo = G.rowptr[x], hi = G.rowptr[x + 1];
-    const int64_t end = hi;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (__ldg(G.wrk + mid) < r) lo = mid + 1;
-        else hi = mid;
-    }
-    if (lo >= end || __ldg(G.wrk + lo) != r) {
-        atomicOr(err, DEV_ERR_INTERNAL);
-        return end;
-    }
-    return lo + 1;
-}
-
-// Closing edge (y, c) in the oriented lists: stored once, at the endpoint of
-// lower (degree, id) rank, rows ascending by id (row s starts at rowptr[s]
-// and holds odeg[s] entries).
-__device__ __forceinline__ bool probe_oriented(const DevGraph& G, int32_t y, int32_t dy, int32_t c,
-                                               int32_t& wyc, int32_t& ryc) {
-    const int32_t dc = __ldg(G.deg + c);
-    const bool ylow = dy < dc || (dy == dc && y < c);
-    const int32_t s = ylow ? y : c, t = ylow ? c : y;
-    int64_t lo = __ldg(G.rowptr + s), hi = lo + __ldg(G.odeg + s);
-    const int64_t end = hi;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (__ldg(G.ocol + mid) < t) lo = mid + 1;
-        else hi = mid;
-    }
-    if (lo < end && __ldg(G.ocol + lo) == t) {
-        wyc = __ldg(G.owt + lo);
-        ryc = __ldg(G.ork + lo);
-        return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void append(const Query& q, unsigned long long key, int32_t a, int32_t b,
-                                       int32_t c) {
-    cg::coalesced_group g = cg::coalesced_threads();
-    uint32_t base = 0;
-    if (g.thread_rank() == 0) base = atomicAdd(&q.st->count, (uint32_t)g.size());
-    base = g.shfl(base, 0);
-    const uint32_t idx = base + g.thread_rank();
-    if (idx < q.cap) {
-        q.ckey[idx] = key;
-        q.ctri[idx] = make_int4(a, b, c, 0);
-    } else {
-        atomicOr(&q.st->err, DEV_ERR_OVERFLOW);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Round: threads stride over the edges of [lo, hi).
-// ---------------------------------------------------------------------------
-template <int P, bool SAMPLED>
-__device__ __forceinline__ void scan_wedges(const DevGraph& G, const Query& q,
-                                            unsigned long long tau, int32_t r, uint32_t w,
-                                            int32_t x, int32_t y, int32_t dy, uint32_t ymax,
-                                            int64_t& j, int64_t jstop, bool& done) {
-    for (; j < jstop; j++) {
-        const uint32_t wxc = (uint32_t)__ldg(G.wwt + j);
-        if (keyof<P>(w, wxc, ymax) < tau) {  // wedge bound, non-increasing along the list
-            done = true;
-            return;
-        }
-        const int32_t c = __ldg(G.wcol + j);
-        if (SAMPLED && c == y) continue;  // the edge itself (full rows in sampled mode)
-        int32_t wyc, ryc;
-        if (probe_oriented(G, y, dy, c, wyc, ryc) &&
-            owns<SAMPLED>(q, r, __ldg(G.wrk + j), ryc)) {
-            const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc);
-            if (key >= tau) {
-                int32_t a = x, b = y, cc = c;
-                sort3(a, b, cc);
-                append(q, key, a, b, cc);
-            }
-        }
-    }
-}
-
-// Returns false once this edge's bound is below tau (and so is every later
-// edge's).
-template <int P, bool SAMPLED>
-__device__ __forceinline__ bool process_edge(const DevGraph& G, const Query& q,
-                                             unsigned long long tau, int32_t idx) {
-    const int32_t r = SAMPLED ? __ldg(q.slist + idx) : idx;
-    const uint32_t w = (uint32_t)__ldg(G.ord_w + r);
-    if (!SAMPLED && keyof<P>(w, w, w) < tau) {
-        // every later edge has a bound no larger: record the first such edge
-        atomicMax(&q.st->stop_rev, STOP_NONE - (uint32_t)r);
-        return false;
-    }
-    const int32_t u = __ldg(G.ord_u + r), v = __ldg(G.ord_v + r);
-    // Exact mode scans what comes after r in each list; sampled mode scans
-    // whole lists (the other two edges may be heavier than a drawn edge).
-    const int64_t su = SAMPLED ? __ldg(G.rowptr + u) : suffix_start(G, u, r, &q.st->err);
-    const int64_t sv = SAMPLED ? __ldg(G.rowptr + v) : suffix_start(G, v, r, &q.st->err);
-    const int64_t eu = __ldg(G.rowptr + u + 1), ev = __ldg(G.rowptr + v + 1);
-    if (su >= eu || sv >= ev) return true;  // no edge after r on one side: owns nothing
-    const uint32_t umax = (uint32_t)__ldg(G.wwt + su), vmax = (uint32_t)__ldg(G.wwt + sv);
-    if (keyof<P>(w, umax, vmax) < tau) return true;  // edge bound
-    // Scan the shorter suffix; probe the other endpoint.
-    const bool xu = (eu - su) <= (ev - sv);
-    const int32_t x = xu ? u : v, y = xu ? v : u;
-    const int64_t sx = xu ? su : sv, ex = xu ? eu : ev;
-    const uint32_t ymax = xu ? vmax : umax;
-    const int32_t dy = __ldg(G.deg + y);
-    int64_t j = sx;
-    bool done = false;
-    scan_wedges<P, SAMPLED>(G, q, tau, r, w, x, y, dy, ymax, j, min(ex, sx + (int64_t)T_SHORT),
-                            done);
-    if (!done && j < ex) {
-        const uint32_t slot = atomicAdd(&q.st->long_count, 1u);
-        if (slot < q.long_cap) {
-            LongItem it;
-            it.r = r;
-            it.x = x;
-            it.y = y;
-            it.w = (int32_t)w;
-            it.ymax = (int32_t)ymax;
-            it.pad = 0;
-            it.j0 = j;
-            it.j1 = ex;
-            q.longs[slot] = it;
-        } else {
-            // Deferred list full: finish the scan here.
-            scan_wedges<P, SAMPLED>(G, q, tau, r, w, x, y, dy, ymax, j, ex, done);
-        }
-    }
-    return true;
-}
-
-template <int P, bool SAMPLED = false>
-__global__ void __launch_bounds__(RBLK) k_round(DevGraph G, Query q, int64_t lo, int64_t hi) {
-    // Blocks run in any order, so an edge is skipped only once an edge at or
-    // before it has failed its bound (all later edges have no larger bound).
-    const volatile uint32_t* stop_rev = &q.st->stop_rev;
-    if (lo >= (int64_t)(STOP_NONE - *stop_rev)) return;
-    const unsigned long long tau = ld_volatile_u64(&q.st->tau);
-    const int64_t stride = (int64_t)gridDim.x * RBLK;
-    for (int64_t r64 = lo + (int64_t)blockIdx.x * RBLK + threadIdx.x; r64 < hi; r64 += stride) {
-        if (r64 >= (int64_t)(STOP_NONE - *stop_rev)) break;
-        if (!process_edge<P, SAMPLED>(G, q, tau, (int32_t)r64)) break;
-    }
-}
-
-// Grid of a round: a few resident blocks per SM, striding over the range.
-inline unsigned round_grid(int64_t edges) {
-    const int64_t cap = (int64_t)sm_count() * 8;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cap, (edges + RBLK - 1) / RBLK));
-}
-
-// ---------------------------------------------------------------------------
-// Deferred long scans: one block per item.  The y row (ids) is staged in
-// shared memory with a bulk async copy completed on an mbarrier; lookups of
-// the closing edge are binary searches there.  Rows longer than STAGE_MAX
-// fall back to the oriented lists in global memory.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-
-template <int P, bool SAMPLED = false>
-__global__ void __launch_bounds__(LBLK) k_long(DevGraph G, Query q) {
-    extern __shared__ __align__(128) unsigned char lsm[];
-    int32_t* srow = reinterpret_cast<int32_t*>(lsm);
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ int timed_out;
-    const uint32_t n_items = min(*(volatile const uint32_t*)&q.st->long_count, q.long_cap);
-    if (blockIdx.x >= n_items) return;
-    const unsigned long long tau = ld_volatile_u64(&q.st->tau);
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        timed_out = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    uint32_t phase = 0;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const LongItem item = q.longs[it];
-        const int64_t ybeg = __ldg(G.rowptr + item.y), yend = __ldg(G.rowptr + item.y + 1);
-        const int32_t dy = (int32_t)(yend - ybeg);
-        const bool staged = dy <= STAGE_MAX;
-        int32_t off = 0;
-        if (staged) {
-            // 16-byte aligned source: round the start down, the size up (the
-            // id array has 16 bytes of slack after its end).
-            const int64_t a0 = ybeg & ~int64_t(3);
-            off = (int32_t)(ybeg - a0);
-            const uint32_t bytes = (uint32_t)(((off + dy) * 4 + 15) & ~15);
-            if (threadIdx.x == 0) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&bar, bytes);
-                bulk_g2s(srow, G.scol + a0, bytes, &bar);
-            }
-            // Every thread waits (bounded).
-            uint32_t spins = 0;
-            while (!mbar_try_wait(&bar, phase)) {
-                if (++spins >= WAIT_LIMIT) {
-                    atomicOr(&q.st->err, DEV_ERR_TIMEOUT);
-                    timed_out = 1;
-                    break;
-                }
-            }
-            phase ^= 1u;
-            __syncthreads();
-            if (timed_out) {
-                // Give the copy a second bounded chance to land before exit.
-                uint32_t s2 = 0;
-                while (!mbar_try_wait(&bar, phase ^ 1u) && ++s2 < WAIT_LIMIT) {
-                }
-                return;
-            }
-        }
-        const uint32_t w = (uint32_t)item.w, ymax = (uint32_t)item.ymax;
-        const int32_t x = item.x, y = item.y, r = item.r;
-        // Warps take 32-entry chunks in order; the wedge bound only decreases
-        // along the list, so a warp whose chunk fails entirely stops.
-        for (int64_t base = item.j0 + (int64_t)wid * 32; base < item.j1; base += LBLK) {
-            const int64_t j = base + lane;
-            bool live = false;
-            uint32_t wxc = 0;
-            if (j < item.j1) {
-                wxc = (uint32_t)__ldg(G.wwt + j);
-                live = keyof<P>(w, wxc, ymax) >= tau;
-            }
-            if (__ballot_sync(0xffffffffu, live) == 0) break;
-            if (live) {
-                const int32_t c = __ldg(G.wcol + j);
-                if (SAMPLED && c == y) live = false;  // the edge itself
-            }
-            if (live) {
-                const int32_t c = __ldg(G.wcol + j);
-                int32_t wyc = 0, ryc = -1;
-                bool found = false;
-                if (staged) {
-                    int lo = 0, hi = dy;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (srow[off + mid] < c) lo = mid + 1;
-                        else hi = mid;
-                    }
-                    if (lo < dy && srow[off + lo] == c) {
-                        found = true;
-                        wyc = __ldg(G.swt + ybeg + lo);
-                        ryc = __ldg(G.srk + ybeg + lo);
-                    }
-                } else {
-                    found = probe_oriented(G, y, dy, c, wyc, ryc);
-                }
-                if (found && owns<SAMPLED>(q, r, __ldg(G.wrk + j), ryc)) {
-                    const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc);
-                    if (key >= tau) {
-                        int32_t a = x, b = y, cc = c;
-                        sort3(a, b, cc);
-                        append(q, key, a, b, cc);
-                    }
-                }
-            }
-        }
-        __syncthreads();  // the staged row is reused by the next item
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Selection under the total order (key desc, a asc, b asc, c asc).
-// Each candidate maps to a 5-word tuple where smaller is better:
-//   (~key_hi, ~key_lo, a, b, c).  An MSB-first radix select over its 20
-// bytes finds the prefix P such that exactly K candidates have tuple
-// prefix <= P; those are kept (compacted in place).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t tuple_word(unsigned long long key, int4 t, int wi) {
-    switch (wi) {
-        case 0: return ~(uint32_t)(key >> 32);
-        case 1: return ~(uint32_t)key;
-        case 2: return (uint32_t)t.x;
-        case 3: return (uint32_t)t.y;
-        default: return (uint32_t)t.z;
-    }
-}
-
-// Compare the first 'depth' bytes of a candidate's tuple with the prefix
-// (pw = prefix words).  Returns <0, 0, >0.
-__device__ __forceinline__ int cmp_prefix(unsigned long long key, int4 t, const uint32_t* pw,
-                                          int depth) {
-    const int full = depth >> 2, rem = depth & 3;
-    for (int wi = 0; wi < full; wi++) {
-        const uint32_t a = tuple_word(key, t, wi);
-        if (a != pw[wi]) return a < pw[wi] ? -1 : 1;
-    }
-    if (rem) {
-        const uint32_t mask = 0xffffffffu << (32 - 8 * rem);
-        const uint32_t a = tuple_word(key, t, full) & mask;
-        const uint32_t b = pw[full] & mask;
-        if (a != b) return a < b ? -1 : 1;
-    }
-    return 0;
-}
-
-struct SelectSmem {
-    unsigned long long prefix;   // key-only select: chosen high bytes
-    unsigned long long maxkey;
-    uint32_t need;               // key-only select: remaining rank
-    uint32_t hist[256];
-    uint32_t pw[5];
-    uint32_t below;   // candidates strictly better than the prefix
-    uint32_t eq;      // candidates equal to the prefix
-    uint32_t done;
-    uint32_t warp_cnt[SBLK / 32];
-    uint32_t kept;
-    unsigned long long minkey;
-};
-
-// Keeps exactly K = min(K_want, n) best candidates at the front; returns the
-// kept count and sets *minkey_out to their smallest key.
-__device__ uint32_t select_and_compact(unsigned long long* ckey, int4* ctri, uint32_t n,
-                                       uint32_t K, SelectSmem& S,
-                                       unsigned long long* minkey_out) {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid < 5) S.pw[tid] = 0;
-    if (tid == 0) {
-        S.below = 0;
-        S.eq = n;
-        S.done = (n <= K) ? 1u : 0u;
-        S.minkey = ~0ull;
-    }
-    __syncthreads();
-    int depth = 0;  // bytes fixed in the prefix
-    while (!S.done && depth < 20) {
-        for (int i = tid; i < 256; i += SBLK) S.hist[i] = 0;
-        __syncthreads();
-        const int wi = depth >> 2, sh = 24 - 8 * (depth & 3);
-        for (uint32_t base = 0; base < n; base += SBLK) {
-            const uint32_t i = base + tid;
-            uint32_t d = 256;
-            if (i < n) {
-                const unsigned long long kk = ckey[i];
-                const int4 t = ctri[i];
-                if (cmp_prefix(kk, t, S.pw, depth) == 0) d = (tuple_word(kk, t, wi) >> sh) & 255u;
-            }
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            if (d < 256 && (__ffs(peers) - 1) == lane) atomicAdd(&S.hist[d], __popc(peers));
-        }
-        __syncthreads();
-        if (tid == 0) {
-            // Need the K-th overall: K - below among the prefix-equal ones.
-            const uint32_t need = K - S.below;
-            uint32_t acc = 0, dsel = 0;
-            for (uint32_t d = 0; d < 256; d++) {
-                const uint32_t h = S.hist[d];
-                if (acc + h >= need) {
-                    dsel = d;
-                    break;
-                }
-                acc += h;
-            }
-            S.below += acc;
-            S.eq = S.hist[dsel];
-            S.pw[wi] |= dsel << sh;
-            if (S.below + S.eq == K) S.done = 1;
-        }
-        __syncthreads();
-        depth++;
-    }
-    const int final_depth = depth;
-    // Compact in place: keep tuple prefix <= P (or everything if n <= K).
-    const bool keep_all = (n <= K);
-    uint32_t out = 0;
-    unsigned long long mk = ~0ull;
-    for (uint32_t base = 0; base < n; base += SBLK) {
-        const uint32_t i = base + tid;
-        bool keep = false;
-        unsigned long long kk = 0;
-        int4 t = make_int4(0, 0, 0, 0);
-        if (i < n) {
-            kk = ckey[i];
-            t = ctri[i];
-            keep = keep_all || cmp_prefix(kk, t, S.pw, final_depth) <= 0;
-        }
-        const uint32_t b = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) S.warp_cnt[wid] = __popc(b);
-        __syncthreads();
-        if (tid == 0) {
-            uint32_t acc = 0;
-            for (int wv = 0; wv < SBLK / 32; wv++) {
-                const uint32_t c = S.warp_cnt[wv];
-                S.warp_cnt[wv] = acc;
-                acc += c;
-            }
-            S.kept = acc;
-        }
-        __syncthreads();
-        if (keep) {
-            const uint32_t p = out + S.warp_cnt[wid] + __popc(b & ((1u << lane) - 1u));
-            ckey[p] = kk;  // p <= i: writes never overtake unread entries
-            ctri[p] = t;
-            mk = kk < mk ? kk : mk;
-        }
-        out += S.kept;
-        __syncthreads();
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mk, o);
-        mk = y < mk ? y : mk;
-    }
-    if (lane == 0) atomicMin(&S.minkey, mk);
-    __syncthreads();
-    *minkey_out = S.minkey;
-    return out;
-}
-
-// The K-th largest key among n candidates (one block, MSB-first over the
-// significant bytes only).
-__device__ unsigned long long kth_key(const unsigned long long* ckey, uint32_t n, uint32_t K,
-                                      SelectSmem& S) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    unsigned long long mx = 0;
-    for (uint32_t i = tid; i < n; i += SBLK) mx = max(mx, ckey[i]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
-        mx = y > mx ? y : mx;
-    }
-    if (tid == 0) {
-        S.prefix = 0;
-        S.maxkey = 0;
-        S.need = K;
-    }
-    __syncthreads();
-    if (lane == 0) atomicMax(&S.maxkey, mx);
-    __syncthreads();
-    int nbytes = 0;
-    for (unsigned long long t = S.maxkey; t; t >>= 8) nbytes++;
-    for (int byte = nbytes - 1; byte >= 0; byte--) {
-        const int shift = 8 * byte;
-        const unsigned long long hi_mask = (shift + 8 >= 64) ? 0ull : (~0ull << (shift + 8));
-        for (int i = tid; i < 256; i += SBLK) S.hist[i] = 0;
-        __syncthreads();
-        const unsigned long long prefix = S.prefix;
-        for (uint32_t base = 0; base < n; base += SBLK) {
-            const uint32_t i = base + tid;
-            uint32_t d = 256;
-            if (i < n) {
-                const unsigned long long kk = ckey[i];
-                if ((kk & hi_mask) == (prefix & hi_mask)) d = (uint32_t)(kk >> shift) & 255u;
-            }
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            if (d < 256 && (__ffs(peers) - 1) == lane) atomicAdd(&S.hist[d], __popc(peers));
-        }
-        __syncthreads();
-        if (tid == 0) {
-            const uint32_t need = S.need;
-            uint32_t acc = 0;
-            int dsel = 0;
-            for (int d = 255; d >= 0; d--) {
-                const uint32_t h = S.hist[d];
-                if (acc + h >= need) {
-                    dsel = d;
-                    break;
-                }
-                acc += h;
-            }
-            S.need = need - acc;
-            S.prefix = prefix | ((unsigned long long)dsel << shift);
-        }
-        __syncthreads();
-    }
-    const unsigned long long T = S.prefix;
-    __syncthreads();
-    return T;
-}
-
-// Keeps candidates with key >= T at the front (in place); returns how many.
-__device__ uint32_t compact_ge(unsigned long long* ckey, int4* ctri, uint32_t n,
-                               unsigned long long T, SelectSmem& S) {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    uint32_t out = 0;
-    for (uint32_t base = 0; base < n; base += SBLK) {
-        const uint32_t i = base + tid;
-        bool keep = false;
-        unsigned long long kk = 0;
-        int4 t = make_int4(0, 0, 0, 0);
-        if (i < n) {
-            kk = ckey[i];
-            keep = kk >= T;
-            if (keep) t = ctri[i];
-        }
-        const uint32_t b = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) S.warp_cnt[wid] = __popc(b);
-        __syncthreads();
-        if (tid == 0) {
-            uint32_t acc = 0;
-            for (int wv = 0; wv < SBLK / 32; wv++) {
-                const uint32_t c = S.warp_cnt[wv];
-                S.warp_cnt[wv] = acc;
-                acc += c;
-            }
-            S.kept = acc;
-        }
-        __syncthreads();
-        if (keep) {
-            const uint32_t p = out + S.warp_cnt[wid] + __popc(b & ((1u << lane) - 1u));
-            ckey[p] = kk;  // p <= i: writes never overtake unread entries
-            ctri[p] = t;
-        }
-        out += S.kept;
-        __syncthreads();
-    }
-    return out;
-}
-
-// After each round: tau = the k-th largest key among the candidates (a
-// lower bound on the final k-th key, since they are k distinct triangles),
-// and candidates below tau are dropped.  Ties with tau stay; the final step
-// resolves them by the vertex triple.
-__global__ void __launch_bounds__(SBLK) k_select(Query q) {
-    __shared__ SelectSmem S;
-    const uint32_t err = *(volatile uint32_t*)&q.st->err;
-    if (err) return;
-    const uint32_t n = min(*(volatile uint32_t*)&q.st->count, q.cap);
-    if (n == q.st->selected || n < (uint32_t)q.k) {
-        if (threadIdx.x == 0) q.st->long_count = 0;
-        return;
-    }
-    const unsigned long long T = kth_key(q.ckey, n, (uint32_t)q.k, S);
-    const uint32_t kept = compact_ge(q.ckey, q.ctri, n, T, S);
-    if (threadIdx.x == 0) {
-        q.st->count = kept;
-        q.st->selected = kept;
-        q.st->long_count = 0;
-        if (T > q.st->tau) q.st->tau = T;
-    }
-}
-
-// Final ranking: candidate i's rank is the number of kept candidates before
-// it in the total order.
-__device__ __forceinline__ bool before(unsigned long long ka, int4 a, unsigned long long kb, int4 b) {
-    if (ka != kb) return ka > kb;
-    if (a.x != b.x) return a.x < b.x;
-    if (a.y != b.y) return a.y < b.y;
-    return a.z < b.z;
-}
-
-template <int P>
-__global__ void __launch_bounds__(256) k_rank_scatter(Query q, wtri_tri* out_tri, double* out_w,
-                                                      int32_t* out_count) {
-    const uint32_t err = *(volatile uint32_t*)&q.st->err;
-    const uint32_t n = min(*(volatile uint32_t*)&q.st->count, q.cap);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        int32_t status = (int32_t)n;
-        if (err & DEV_ERR_OVERFLOW) status = WTRI_ENOMEM;
-        else if (err & DEV_ERR_TIMEOUT) status = WTRI_ETIMEOUT;
-        else if (err) status = WTRI_ECUDA;
-        *out_count = status;
-    }
-    if (err) return;
-    // One warp per kept candidate: its rank is the number of kept candidates
-    // before it in the total order.
-    const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (i >= n) return;
-    const unsigned long long ki = q.ckey[i];
-    const int4 ti = q.ctri[i];
-    uint32_t rank = 0;
-    for (uint32_t j = lane; j < n; j += 32) rank += before(q.ckey[j], q.ctri[j], ki, ti) ? 1u : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
-    if (lane == 0) {
-        out_tri[rank].a = ti.x;
-        out_tri[rank].b = ti.y;
-        out_tri[rank].c = ti.z;
-        double val;
-        if (P == P_ONE) val = (double)ki / 3.0;
-        else if (P == P_TWO) val = sqrt((double)ki / 3.0);
-        else val = (double)ki;
-        out_w[rank] = val;
-    }
-}
-
-__global__ void k_final_select(Query q) {
-    __shared__ SelectSmem S;
-    const uint32_t err = *(volatile uint32_t*)&q.st->err;
-    if (err) return;
-    const uint32_t n = min(*(volatile uint32_t*)&q.st->count, q.cap);
-    unsigned long long mk;
-    const uint32_t kept = select_and_compact(q.ckey, q.ctri, n, (uint32_t)q.k, S, &mk);
-    if (threadIdx.x == 0) q.st->count = kept;
-}
 
 template <int P>
 int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight, int32_t* d_count,
@@ -776,6 +38,8 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
     q.k = k;
     q.smark = nullptr;
     q.slist = nullptr;
+    q.long_count = &q.st->long_count;
+    q.qid = 0;
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
 
     const size_t lsmem = (size_t)STAGE_MAX * 4 + 16;
@@ -1043,6 +307,8 @@ int run_sample(const wtri_graph* g, int32_t k, int64_t nsamples, uint64_t seed, 
     q.k = k;
     q.smark = mark;
     q.slist = list;
+    q.long_count = &q.st->long_count;
+    q.qid = 0;
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
     ProfScope whole(P == P_ONE ? "sample_p=1" : "sample_p=2", s, 0.0, 0);
     WTRI_TRY(draw_samples<P>(g, nsamples, seed, mark, s));
@@ -1177,6 +443,8 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
     q.k = k;
     q.smark = nullptr;
     q.slist = nullptr;
+    q.long_count = &q.st->long_count;
+    q.qid = 0;
     // The array keeps the previous call's contents: reset the status word
     // (counters, threshold, stop flag, error bits).
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));

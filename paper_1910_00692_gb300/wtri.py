@@ -95,12 +95,14 @@ def lib():
     L.wtri_sample_topk.argtypes = [vp, f64, i32, i64, ctypes.c_uint64, ctypes.POINTER(_Result)]
     L.wtri_graph_copy_array.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
     L.wtri_sample_edges.argtypes = [vp, f64, i64, ctypes.c_uint64, vp, i64]
+    L.wtri_topk_batch.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_Result)]
     L.wtri_last_error.restype = ctypes.c_char_p
     L.wtri_last_error.argtypes = []
     L.wtri_version.restype = ctypes.c_char_p
     for f in (L.wtri_build_csr, L.wtri_graph_info, L.wtri_topk, L.wtri_topk_device,
               L.wtri_topk_device_noalloc,
-              L.wtri_sample_topk, L.wtri_graph_copy_array, L.wtri_sample_edges):
+              L.wtri_sample_topk, L.wtri_graph_copy_array, L.wtri_sample_edges,
+              L.wtri_topk_batch):
         f.restype = ctypes.c_int
     _lib = L
     return L
@@ -227,6 +229,29 @@ def sample_topk(g: Graph, p: float, k: int, nsamples: int, seed: int):
     return _host_query(lambda r: lib().wtri_sample_topk(g.handle, float(p), int(k), int(nsamples),
                                                          ctypes.c_uint64(seed & (2**64 - 1)), r),
                        int(k))
+
+
+def topk_batch(graphs, ps, ks):
+    """wtri_topk_batch: one batched launch for query i = (graphs[i], ps[i],
+    ks[i]).  Returns a list of (tris, weights) like topk()."""
+    nq = len(graphs)
+    if nq == 0:
+        return []
+    handles = (ctypes.c_void_p * nq)(*[g.handle.value for g in graphs])
+    p_arr = np.ascontiguousarray(ps, dtype=np.float64)
+    k_arr = np.ascontiguousarray(ks, dtype=np.int32)
+    tris = [np.zeros((max(int(k), 1), 3), dtype=np.int32) for k in k_arr]
+    wts = [np.zeros(max(int(k), 1), dtype=np.float64) for k in k_arr]
+    res = (_Result * nq)()
+    for i in range(nq):
+        res[i].tris = tris[i].ctypes.data
+        res[i].weight = wts[i].ctypes.data
+        res[i].capacity = int(max(int(k_arr[i]), 1))
+        res[i].count = 0
+    _check(lib().wtri_topk_batch(ctypes.cast(handles, ctypes.c_void_p),
+                                 p_arr.ctypes.data_as(ctypes.c_void_p),
+                                 k_arr.ctypes.data_as(ctypes.c_void_p), nq, res))
+    return [(tris[i][:res[i].count].copy(), wts[i][:res[i].count].copy()) for i in range(nq)]
 
 
 def sample_edges(g: Graph, p: float, nsamples: int, seed: int) -> np.ndarray:

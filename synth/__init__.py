@@ -38,6 +38,7 @@ __all__ = [
     "tiny_graph",
     "mid_graph",
     "batch_graph",
+    "batch_queries",
     "scaled_mid_graph",
     "random_small_graph",
 ]
@@ -182,16 +183,26 @@ def scaled_mid_graph(n: int, m: int, seed: int = 1, gamma: float = 2.1,
     return Graph(n, u, v, w, name=f"chung-lu n={n} m={m} g={gamma} zipf({s},{cap})")
 
 
-def batch_graph(g: int, seed: int = 3) -> Graph:
-    """Graph ``g`` of the 4,096-graph batch: n log-uniform in [100, 2e5], m = 10 n,
-    exponent 2.2, Zipf(2) weights capped at 1e6."""
+def batch_graph(g: int, seed: int = 3, n_hi: int = 200_000) -> Graph:
+    """Graph ``g`` of the 4,096-graph batch: n log-uniform in [100, n_hi]
+    (2e5 for the batch workload), m = 10 n, exponent 2.2, Zipf(2) weights
+    capped at 1e6."""
     rng = _rng(seed, 10, g)
-    n = int(round(math.exp(rng.uniform(math.log(100), math.log(200_000)))))
+    n = int(round(math.exp(rng.uniform(math.log(100), math.log(n_hi)))))
     m = min(10 * n, n * (n - 1) // 2)
     d_max = min(n - 1, math.sqrt(2 * m))
     u, v = chung_lu(n, m, 2.2, d_max, seed, substream=(11, g))
     w = zipf_weights(m, 2.0, 1_000_000, _rng(seed, 12, g))
     return Graph(n, u, v, w, name=f"batch[{g}] n={n} m={m}")
+
+
+def batch_queries(count: int, seed: int = 3):
+    """Per-graph query parameters of the batch: k uniform in [10, 1000], p
+    uniform over {-inf, 1, 2, +inf}."""
+    rng = _rng(seed, 13)
+    ks = rng.integers(10, 1001, size=count).astype(np.int32)
+    ps = np.array([-math.inf, 1.0, 2.0, math.inf])[rng.integers(0, 4, size=count)]
+    return ps, ks
 
 
 def random_small_graph(n: int, p_edge: float, wmax: int, seed) -> Graph:
