@@ -171,6 +171,41 @@ WTRI_API int wtri_topk_batch(const wtri_graph* const* gs, const double* p, const
                              int32_t nq, wtri_result* outs);
 
 /*
+ * Serving with continuous batching (no counterpart in the paper).
+ *
+ * wtri_server_create: a server with an HBM budget (bytes: resident graphs
+ *   plus the scratch of every request in flight) and at most max_slots
+ *   requests running at once.  A scheduler thread admits waiting requests,
+ *   oldest first, as slots and budget free up, and launches them as
+ *   micro-batches on its own worker streams (several overlap on the
+ *   device).  The server uses the device current at creation.
+ * wtri_server_add_graph: registers a built graph (borrowed: it must outlive
+ *   the server); its device bytes count against the budget (WTRI_ENOMEM if
+ *   it does not fit).  *graph_id receives its id.
+ * wtri_submit: queues the query (graph_id, p, k) and returns at once with a
+ *   ticket.  WTRI_ENOTFOUND for an unknown graph, WTRI_ENOMEM if the
+ *   request could never fit the budget, p and k as in wtri_topk.
+ * wtri_poll: WTRI_PENDING while the request waits or runs; otherwise copies
+ *   the result (as wtri_topk would return it) to out and retires the ticket
+ *   (WTRI_OK), or returns the request's error.  Reads host state only.
+ *   WTRI_ENOTFOUND for an unknown or retired ticket.
+ * wtri_poll_timed: wtri_poll that also returns the seconds from submission
+ *   to completion.
+ * wtri_server_stats: micro-batches launched, requests admitted, requests
+ *   waiting and running, scratch bytes in flight (any pointer may be NULL).
+ * wtri_server_free: finishes every queued request, stops the scheduler and
+ *   frees the server (not the graphs).
+ */
+WTRI_API int wtri_server_create(uint64_t hbm_budget_bytes, int32_t max_slots, wtri_server** out);
+WTRI_API int wtri_server_add_graph(wtri_server* s, wtri_graph* g, int32_t* graph_id);
+WTRI_API int wtri_submit(wtri_server* s, int32_t graph_id, double p, int32_t k, uint64_t* ticket);
+WTRI_API int wtri_poll(wtri_server* s, uint64_t ticket, wtri_result* out);
+WTRI_API int wtri_poll_timed(wtri_server* s, uint64_t ticket, wtri_result* out, double* latency_s);
+WTRI_API int wtri_server_stats(wtri_server* s, uint64_t* batches, uint64_t* admitted, int32_t* waiting,
+                               int32_t* running, uint64_t* scratch_bytes);
+WTRI_API void wtri_server_free(wtri_server* s);
+
+/*
  * Weighted edge sampling (Algorithm 3, Section 4.1): draws nsamples edges
  * with probability w_e^p / Z (Proposition 4.1), adds every triangle on each
  * sampled edge (the common neighbours N(a) ∩ N(b)) to a set, and returns the

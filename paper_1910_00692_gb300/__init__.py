@@ -11,6 +11,7 @@ from __future__ import annotations
 from .wtri import (  # noqa: F401
     ARRAYS,
     Graph,
+    Server,
     WtriError,
     WtriUnavailable,
     build_csr,
@@ -24,5 +25,5 @@ from .wtri import (  # noqa: F401
     topk_device_noalloc,
 )
 
-__all__ = ["ARRAYS", "Graph", "WtriError", "WtriUnavailable", "build_csr", "lib", "lib_path",
+__all__ = ["ARRAYS", "Graph", "Server", "WtriError", "WtriUnavailable", "build_csr", "lib", "lib_path",
            "sample_edges", "sample_topk", "topk", "topk_batch", "topk_device", "topk_device_noalloc"]

@@ -129,38 +129,49 @@ size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
-// Runs nq queries; results to caller host arrays.  Queries whose bounded
-// buffers overflowed are re-run one by one with larger buffers.
-int topk_batch(const wtri_graph* const* gs, const int32_t* pcodes, const int32_t* ks, int32_t nq,
-               wtri_result* outs, cudaStream_t user_stream, int use_graph) {
-    // The batch runs on a stream of its own (the legacy default stream cannot
-    // be captured), ordered after the work already queued on the caller's.
-    static thread_local cudaStream_t own[64] = {};
-    int dev = 0;
-    WTRI_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return set_error(WTRI_EUNSUPPORTED, "device index above 63");
-    if (!own[dev]) WTRI_CUDA(cudaStreamCreateWithFlags(&own[dev], cudaStreamNonBlocking));
-    cudaStream_t s = own[dev];
-    {
-        cudaEvent_t ev;
-        WTRI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        cudaError_t e = cudaEventRecord(ev, user_stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
-        cudaEventDestroy(ev);
-        WTRI_CUDA(e);
-    }
-    std::vector<DevGraph> hg((size_t)nq);
-    std::vector<Query> hq((size_t)nq);
-    std::vector<int64_t> koffs((size_t)nq + 1, 0);
-    int64_t mmax = 0;
+}  // namespace wtri
+
+// ---------------------------------------------------------------------------
+// Host side: a batch plan (schedule, buffer layout, descriptors), launching
+// it on a stream into one device scratch block, and collecting results.
+// Used by wtri_topk_batch and by the serving loop.
+// ---------------------------------------------------------------------------
+struct wtri_batch_plan {
+    int32_t nq = 0;
+    int R = 0;
+    std::vector<wtri::DevGraph> hg;
+    std::vector<int32_t> pcodes, ks;
+    std::vector<uint32_t> caps;
+    std::vector<int64_t> offs, los, totals, koffs;
+    std::vector<unsigned char> hq;  // Query descriptors (filled at launch)
     size_t cand_total = 0;
-    std::vector<uint32_t> caps((size_t)nq);
+    uint32_t long_cap = 1u << 18;
+    size_t o_st, o_key, o_tri, o_long, o_lcnt, o_g, o_q, o_pc, o_offs, o_los, o_koffs, o_otri, o_ow,
+        o_stat, bytes;
+    std::vector<int32_t> stat;
+    std::vector<wtri_tri> otri;
+    std::vector<double> ow;
+};
+
+namespace wtri {
+
+BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes, const int32_t* ks,
+                             int32_t nq) {
+    BatchPlan* P = new (std::nothrow) BatchPlan();
+    if (!P) return nullptr;
+    P->nq = nq;
+    P->hg.resize((size_t)nq);
+    P->pcodes.assign(pcodes, pcodes + nq);
+    P->ks.assign(ks, ks + nq);
+    P->caps.resize((size_t)nq);
+    P->koffs.assign((size_t)nq + 1, 0);
+    int64_t mmax = 0;
     for (int i = 0; i < nq; i++) {
-        hg[(size_t)i] = gs[i]->d;
+        P->hg[(size_t)i] = gs[i]->d;
         mmax = std::max<int64_t>(mmax, gs[i]->d.m);
-        koffs[(size_t)i + 1] = koffs[(size_t)i] + ks[i];
-        caps[(size_t)i] = (uint32_t)std::max<int64_t>(16384, 16 * (int64_t)ks[i]);
-        cand_total += caps[(size_t)i];
+        P->koffs[(size_t)i + 1] = P->koffs[(size_t)i] + ks[i];
+        P->caps[(size_t)i] = (uint32_t)std::max<int64_t>(16384, 16 * (int64_t)ks[i]);
+        P->cand_total += P->caps[(size_t)i];
     }
     // Round schedule (same as a single query), per query clipped to its m.
     std::vector<int64_t> r_lo, r_hi;
@@ -169,187 +180,250 @@ int topk_batch(const wtri_graph* const* gs, const int32_t* pcodes, const int32_t
         r_hi.push_back(std::min(mmax, lo + size));
     }
     const int R = (int)r_lo.size();
-    std::vector<int64_t> offs((size_t)R * (nq + 1)), los((size_t)R * nq);
-    std::vector<int64_t> totals((size_t)R);
+    P->R = R;
+    P->offs.resize((size_t)R * (nq + 1));
+    P->los.resize((size_t)R * nq);
+    P->totals.resize((size_t)R);
     for (int r = 0; r < R; r++) {
         int64_t acc = 0;
         for (int i = 0; i < nq; i++) {
             const int64_t m = gs[i]->d.m;
             const int64_t a = std::min(m, r_lo[(size_t)r]), b = std::min(m, r_hi[(size_t)r]);
-            offs[(size_t)r * (nq + 1) + i] = acc;
-            los[(size_t)r * nq + i] = a;
+            P->offs[(size_t)r * (nq + 1) + i] = acc;
+            P->los[(size_t)r * nq + i] = a;
             acc += b - a;
         }
-        offs[(size_t)r * (nq + 1) + nq] = acc;
-        totals[(size_t)r] = acc;
+        P->offs[(size_t)r * (nq + 1) + nq] = acc;
+        P->totals[(size_t)r] = acc;
     }
-    const uint32_t long_cap = 1u << 18;
-    // Device scratch: states, candidates, deferred list, descriptors, outputs.
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
         off = al256(off + bytes);
         return o;
     };
-    const size_t o_st = take(sizeof(QState) * (size_t)nq);
-    const size_t o_key = take(8 * cand_total);
-    const size_t o_tri = take(16 * cand_total);
-    const size_t o_long = take(sizeof(LongItem) * (size_t)long_cap);
-    const size_t o_lcnt = take(64);
-    const size_t o_g = take(sizeof(DevGraph) * (size_t)nq);
-    const size_t o_q = take(sizeof(Query) * (size_t)nq);
-    const size_t o_pc = take(4 * (size_t)nq);
-    const size_t o_offs = take(8 * offs.size());
-    const size_t o_los = take(8 * std::max<size_t>(los.size(), 1));
-    const size_t o_koffs = take(8 * koffs.size());
-    const size_t o_otri = take(sizeof(wtri_tri) * (size_t)koffs[(size_t)nq]);
-    const size_t o_ow = take(8 * (size_t)koffs[(size_t)nq]);
-    const size_t o_stat = take(4 * (size_t)nq);
-    void* buf = nullptr;
-    if (cudaMallocAsync(&buf, off, s) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(WTRI_ENOMEM, "batch scratch allocation failed");
-    }
-    char* B0 = (char*)buf;
-    QState* st = (QState*)(B0 + o_st);
-    unsigned long long* ckey = (unsigned long long*)(B0 + o_key);
-    int4* ctri = (int4*)(B0 + o_tri);
-    LongItem* longs = (LongItem*)(B0 + o_long);
-    uint32_t* lcnt = (uint32_t*)(B0 + o_lcnt);
+    P->o_st = take(sizeof(QState) * (size_t)nq);
+    P->o_key = take(8 * P->cand_total);
+    P->o_tri = take(16 * P->cand_total);
+    P->o_long = take(sizeof(LongItem) * (size_t)P->long_cap);
+    P->o_lcnt = take(64);
+    P->o_g = take(sizeof(DevGraph) * (size_t)nq);
+    P->o_q = take(sizeof(Query) * (size_t)nq);
+    P->o_pc = take(4 * (size_t)nq);
+    P->o_offs = take(8 * std::max<size_t>(P->offs.size(), 1));
+    P->o_los = take(8 * std::max<size_t>(P->los.size(), 1));
+    P->o_koffs = take(8 * P->koffs.size());
+    P->o_otri = take(sizeof(wtri_tri) * (size_t)P->koffs[(size_t)nq]);
+    P->o_ow = take(8 * (size_t)P->koffs[(size_t)nq]);
+    P->o_stat = take(4 * (size_t)nq);
+    P->bytes = off;
+    return P;
+}
+
+size_t batch_plan_bytes(const BatchPlan* P) { return P->bytes; }
+
+void batch_plan_destroy(BatchPlan* P) { delete P; }
+
+// Uploads the descriptors (small, from pageable memory: the call returns
+// once they are staged) and enqueues every kernel of the batch on s.
+int batch_plan_launch(BatchPlan* P, void* dbuf, cudaStream_t s, int use_graph) {
+    const int nq = P->nq;
+    char* B0 = (char*)dbuf;
+    QState* st = (QState*)(B0 + P->o_st);
+    unsigned long long* ckey = (unsigned long long*)(B0 + P->o_key);
+    int4* ctri = (int4*)(B0 + P->o_tri);
+    LongItem* longs = (LongItem*)(B0 + P->o_long);
+    uint32_t* lcnt = (uint32_t*)(B0 + P->o_lcnt);
+    std::vector<Query> hq((size_t)nq);
     size_t c0 = 0;
     for (int i = 0; i < nq; i++) {
         Query& q = hq[(size_t)i];
         q.st = st + i;
         q.ckey = ckey + c0;
         q.ctri = ctri + c0;
-        q.cap = caps[(size_t)i];
+        q.cap = P->caps[(size_t)i];
         q.longs = longs;
-        q.long_cap = long_cap;
-        q.k = ks[i];
+        q.long_cap = P->long_cap;
+        q.k = P->ks[(size_t)i];
         q.smark = nullptr;
         q.slist = nullptr;
         q.long_count = lcnt;
         q.qid = i;
-        c0 += caps[(size_t)i];
+        c0 += P->caps[(size_t)i];
     }
     BatchDev Bd;
-    Bd.graphs = (const DevGraph*)(B0 + o_g);
-    Bd.queries = (const Query*)(B0 + o_q);
-    Bd.pcodes = (const int32_t*)(B0 + o_pc);
+    Bd.graphs = (const DevGraph*)(B0 + P->o_g);
+    Bd.queries = (const Query*)(B0 + P->o_q);
+    Bd.pcodes = (const int32_t*)(B0 + P->o_pc);
     Bd.nq = nq;
-    int64_t* d_offs = (int64_t*)(B0 + o_offs);
-    int64_t* d_los = (int64_t*)(B0 + o_los);
-    int64_t* d_koffs = (int64_t*)(B0 + o_koffs);
-    wtri_tri* d_otri = (wtri_tri*)(B0 + o_otri);
-    double* d_ow = (double*)(B0 + o_ow);
-    int32_t* d_stat = (int32_t*)(B0 + o_stat);
-    int rc = WTRI_OK;
-    auto cu = [&](cudaError_t e, const char* what) {
-        if (e != cudaSuccess && rc == WTRI_OK) rc = cuda_error(e, what, __FILE__, __LINE__);
-    };
-    cu(cudaMemcpyAsync((void*)Bd.graphs, hg.data(), sizeof(DevGraph) * nq, cudaMemcpyHostToDevice, s), "upload");
-    cu(cudaMemcpyAsync((void*)Bd.queries, hq.data(), sizeof(Query) * nq, cudaMemcpyHostToDevice, s), "upload");
-    cu(cudaMemcpyAsync((void*)Bd.pcodes, pcodes, 4 * (size_t)nq, cudaMemcpyHostToDevice, s), "upload");
-    cu(cudaMemcpyAsync(d_offs, offs.data(), 8 * offs.size(), cudaMemcpyHostToDevice, s), "upload");
-    if (!los.empty())
-        cu(cudaMemcpyAsync(d_los, los.data(), 8 * los.size(), cudaMemcpyHostToDevice, s), "upload");
-    cu(cudaMemcpyAsync(d_koffs, koffs.data(), 8 * koffs.size(), cudaMemcpyHostToDevice, s), "upload");
-    // Uploads come from pageable memory: finish them before the capture.
-    cu(cudaStreamSynchronize(s), "upload");
+    int64_t* d_offs = (int64_t*)(B0 + P->o_offs);
+    int64_t* d_los = (int64_t*)(B0 + P->o_los);
+    int64_t* d_koffs = (int64_t*)(B0 + P->o_koffs);
+    wtri_tri* d_otri = (wtri_tri*)(B0 + P->o_otri);
+    double* d_ow = (double*)(B0 + P->o_ow);
+    int32_t* d_stat = (int32_t*)(B0 + P->o_stat);
+    WTRI_CUDA(cudaMemcpyAsync((void*)Bd.graphs, P->hg.data(), sizeof(DevGraph) * nq, cudaMemcpyHostToDevice, s));
+    WTRI_CUDA(cudaMemcpyAsync((void*)Bd.queries, hq.data(), sizeof(Query) * nq, cudaMemcpyHostToDevice, s));
+    WTRI_CUDA(cudaMemcpyAsync((void*)Bd.pcodes, P->pcodes.data(), 4 * (size_t)nq, cudaMemcpyHostToDevice, s));
+    WTRI_CUDA(cudaMemcpyAsync(d_offs, P->offs.data(), 8 * P->offs.size(), cudaMemcpyHostToDevice, s));
+    if (!P->los.empty())
+        WTRI_CUDA(cudaMemcpyAsync(d_los, P->los.data(), 8 * P->los.size(), cudaMemcpyHostToDevice, s));
+    WTRI_CUDA(cudaMemcpyAsync(d_koffs, P->koffs.data(), 8 * P->koffs.size(), cudaMemcpyHostToDevice, s));
 
     const size_t lsmem = (size_t)STAGE_MAX * 4 + 16;
-    static bool attr_done = false;
-    if (!attr_done && rc == WTRI_OK) {
-        cu(cudaFuncSetAttribute(k_long_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem),
-           "attribute");
+    static bool attr_done = false;  // idempotent
+    if (!attr_done) {
+        WTRI_CUDA(cudaFuncSetAttribute(k_long_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)lsmem));
         attr_done = true;
     }
     const int long_grid = sm_count() * 2;
+    const int R = P->R;
     auto launch_all = [&]() {
         cudaMemsetAsync(st, 0, sizeof(QState) * (size_t)nq, s);
         cudaMemsetAsync(lcnt, 0, 64, s);
         for (int r = 0; r < R; r++) {
-            k_round_batch<<<round_grid(totals[(size_t)r]), RBLK, 0, s>>>(
+            k_round_batch<<<round_grid(P->totals[(size_t)r]), RBLK, 0, s>>>(
                 Bd, d_offs + (size_t)r * (nq + 1), d_los + (size_t)r * nq);
-            k_long_batch<<<long_grid, LBLK, lsmem, s>>>(Bd, longs, lcnt, long_cap);
+            k_long_batch<<<long_grid, LBLK, lsmem, s>>>(Bd, longs, lcnt, P->long_cap);
             k_select_batch<<<nq, SBLK, 0, s>>>(Bd);
         }
         k_final_batch<<<nq, SBLK, 0, s>>>(Bd);
-        const int64_t warps = koffs[(size_t)nq];
+        const int64_t warps = P->koffs[(size_t)nq];
         k_rank_batch<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8,
                                                                         sm_count() * 16)),
                        256, 0, s>>>(Bd, d_koffs, d_otri, d_ow, d_stat);
     };
-    if (rc == WTRI_OK) {
-        ProfScope ps("topk_batch", s, 0.0, 3 * R + 2);
-        if (use_graph) {
-            cudaGraph_t graph = nullptr;
-            cudaGraphExec_t exec = nullptr;
-            const cudaError_t eb = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-            cu(eb, "begin capture");
-            if (eb == cudaSuccess) {
-                launch_all();
-                // always leave capture mode, even if a launch failed
-                cu(cudaStreamEndCapture(s, &graph), "end capture");
-            }
-            if (rc == WTRI_OK) cu(cudaGraphInstantiate(&exec, graph, 0), "instantiate");
-            if (rc == WTRI_OK) cu(cudaGraphLaunch(exec, s), "graph launch");
-            if (exec) cudaGraphExecDestroy(exec);
-            if (graph) cudaGraphDestroy(graph);
-        } else {
+    int rc = WTRI_OK;
+    ProfScope ps("topk_batch", s, 0.0, 3 * R + 2);
+    if (use_graph) {
+        // The descriptors must have landed before the captured work refers
+        // to them only through device pointers: that holds, the copies are
+        // ordered on s before the graph launch.
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
             launch_all();
-            cu(cudaGetLastError(), "batch launch");
+            e = cudaStreamEndCapture(s, &graph);  // always leave capture mode
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) rc = cuda_error(e, "batch graph", __FILE__, __LINE__);
+    } else {
+        launch_all();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_error(e, "batch launch", __FILE__, __LINE__);
+    }
+    return rc;
+}
+
+// Copies statuses and results to the plan's host vectors (synchronizes s).
+int batch_plan_collect(BatchPlan* P, void* dbuf, cudaStream_t s) {
+    const int nq = P->nq;
+    char* B0 = (char*)dbuf;
+    P->stat.assign((size_t)nq, 0);
+    P->otri.resize((size_t)P->koffs[(size_t)nq]);
+    P->ow.resize((size_t)P->koffs[(size_t)nq]);
+    WTRI_CUDA(cudaMemcpyAsync(P->stat.data(), B0 + P->o_stat, 4 * (size_t)nq, cudaMemcpyDeviceToHost, s));
+    WTRI_CUDA(cudaMemcpyAsync(P->otri.data(), B0 + P->o_otri, sizeof(wtri_tri) * P->otri.size(),
+                              cudaMemcpyDeviceToHost, s));
+    WTRI_CUDA(cudaMemcpyAsync(P->ow.data(), B0 + P->o_ow, 8 * P->ow.size(), cudaMemcpyDeviceToHost, s));
+    WTRI_CUDA(cudaStreamSynchronize(s));
+    return WTRI_OK;
+}
+
+int32_t batch_plan_status(const BatchPlan* P, int i) { return P->stat[(size_t)i]; }
+const wtri_tri* batch_plan_tris(const BatchPlan* P, int i) { return P->otri.data() + P->koffs[(size_t)i]; }
+const double* batch_plan_weights(const BatchPlan* P, int i) { return P->ow.data() + P->koffs[(size_t)i]; }
+
+// One query with larger bounded buffers (for queries that overflowed a
+// batch's); results to host arrays.
+int topk_retry_host(const wtri_graph* g, int pcode, int32_t k, cudaStream_t s, wtri_tri* htri,
+                    double* hw, int32_t* count) {
+    void* dbuf = nullptr;
+    WTRI_CUDA(cudaMallocAsync(&dbuf, (sizeof(wtri_tri) + 8) * (size_t)k + 64, s));
+    wtri_tri* dt = (wtri_tri*)dbuf;
+    double* dw = (double*)((char*)dbuf + ((sizeof(wtri_tri) * (size_t)k + 15) & ~size_t(15)));
+    int32_t* dc = (int32_t*)(dw + k);
+    int32_t cnt = WTRI_ENOMEM;
+    int rc = WTRI_OK;
+    for (int scale = 8; scale <= 64 && cnt == WTRI_ENOMEM && rc == WTRI_OK; scale *= 8) {
+        rc = topk_device(g, pcode, k, dt, dw, dc, s, scale);
+        if (rc == WTRI_OK) {
+            cudaError_t e = cudaMemcpyAsync(&cnt, dc, 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = cuda_error(e, "retry", __FILE__, __LINE__);
         }
     }
-    std::vector<int32_t> stat((size_t)nq, 0);
-    std::vector<wtri_tri> otri((size_t)koffs[(size_t)nq]);
-    std::vector<double> ow((size_t)koffs[(size_t)nq]);
-    if (rc == WTRI_OK) {
-        cu(cudaMemcpyAsync(stat.data(), d_stat, 4 * (size_t)nq, cudaMemcpyDeviceToHost, s), "status");
-        cu(cudaMemcpyAsync(otri.data(), d_otri, sizeof(wtri_tri) * otri.size(), cudaMemcpyDeviceToHost, s),
-           "results");
-        cu(cudaMemcpyAsync(ow.data(), d_ow, 8 * ow.size(), cudaMemcpyDeviceToHost, s), "results");
-        cu(cudaStreamSynchronize(s), "results");
+    if (rc == WTRI_OK && cnt < 0) rc = set_error(cnt, "query failed on retry with larger buffers");
+    if (rc == WTRI_OK && cnt > 0) {
+        cudaError_t e = cudaMemcpyAsync(htri, dt, sizeof(wtri_tri) * (size_t)cnt, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hw, dw, 8 * (size_t)cnt, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_error(e, "retry copy", __FILE__, __LINE__);
     }
+    cudaFreeAsync(dbuf, s);
+    if (rc == WTRI_OK) *count = cnt;
+    return rc;
+}
+
+cudaStream_t own_stream() {
+    static thread_local cudaStream_t own[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!own[dev] && cudaStreamCreateWithFlags(&own[dev], cudaStreamNonBlocking) != cudaSuccess)
+        return nullptr;
+    return own[dev];
+}
+
+// Runs nq queries; results to caller host arrays.  Queries whose bounded
+// buffers overflowed are re-run one by one with larger buffers.
+int topk_batch(const wtri_graph* const* gs, const int32_t* pcodes, const int32_t* ks, int32_t nq,
+               wtri_result* outs, cudaStream_t user_stream, int use_graph) {
+    // The batch runs on a stream of its own (the legacy default stream cannot
+    // be captured), ordered after the work already queued on the caller's.
+    cudaStream_t s = own_stream();
+    if (!s) return set_error(WTRI_ECUDA, "could not create the batch stream");
+    {
+        cudaEvent_t ev;
+        WTRI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, user_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+        cudaEventDestroy(ev);
+        WTRI_CUDA(e);
+    }
+    BatchPlan* P = batch_plan_create(gs, pcodes, ks, nq);
+    if (!P) return set_error(WTRI_ENOMEM, "host allocation failed");
+    void* buf = nullptr;
+    if (cudaMallocAsync(&buf, P->bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        batch_plan_destroy(P);
+        return set_error(WTRI_ENOMEM, "batch scratch allocation failed");
+    }
+    int rc = batch_plan_launch(P, buf, s, use_graph);
+    if (rc == WTRI_OK) rc = batch_plan_collect(P, buf, s);
     cudaFreeAsync(buf, s);
-    if (rc != WTRI_OK) return rc;
-    std::vector<int> redo;
-    for (int i = 0; i < nq; i++) {
-        const int32_t c = stat[(size_t)i];
+    for (int i = 0; i < nq && rc == WTRI_OK; i++) {
+        const int32_t c = P->stat[(size_t)i];
         if (c == WTRI_ENOMEM) {
-            redo.push_back(i);
+            rc = topk_retry_host(gs[i], pcodes[i], ks[i], s, outs[i].tris, outs[i].weight, &outs[i].count);
             continue;
         }
-        if (c < 0) return set_error(c, "device-side error in batched query " + std::to_string(i));
-        std::copy(otri.begin() + koffs[(size_t)i], otri.begin() + koffs[(size_t)i] + c, outs[i].tris);
-        std::copy(ow.begin() + koffs[(size_t)i], ow.begin() + koffs[(size_t)i] + c, outs[i].weight);
+        if (c < 0) {
+            rc = set_error(c, "device-side error in batched query " + std::to_string(i));
+            break;
+        }
+        std::copy(P->otri.begin() + P->koffs[(size_t)i], P->otri.begin() + P->koffs[(size_t)i] + c,
+                  outs[i].tris);
+        std::copy(P->ow.begin() + P->koffs[(size_t)i], P->ow.begin() + P->koffs[(size_t)i] + c,
+                  outs[i].weight);
         outs[i].count = c;
     }
-    for (int i : redo) {
-        // Larger bounded buffers, one query at a time.
-        const int32_t k = ks[i];
-        void* dbuf = nullptr;
-        WTRI_CUDA(cudaMallocAsync(&dbuf, (sizeof(wtri_tri) + 8) * (size_t)k + 64, s));
-        wtri_tri* dt = (wtri_tri*)dbuf;
-        double* dw = (double*)((char*)dbuf + ((sizeof(wtri_tri) * (size_t)k + 15) & ~size_t(15)));
-        int32_t* dc = (int32_t*)(dw + k);
-        int32_t cnt = WTRI_ENOMEM;
-        for (int scale = 8; scale <= 64 && cnt == WTRI_ENOMEM; scale *= 8) {
-            WTRI_TRY(topk_device(gs[i], pcodes[i], k, dt, dw, dc, s, scale));
-            WTRI_CUDA(cudaMemcpyAsync(&cnt, dc, 4, cudaMemcpyDeviceToHost, s));
-            WTRI_CUDA(cudaStreamSynchronize(s));
-        }
-        if (cnt < 0) {
-            cudaFreeAsync(dbuf, s);
-            return set_error(cnt, "batched query " + std::to_string(i) + " failed on retry");
-        }
-        WTRI_CUDA(cudaMemcpyAsync(outs[i].tris, dt, sizeof(wtri_tri) * (size_t)cnt, cudaMemcpyDeviceToHost, s));
-        WTRI_CUDA(cudaMemcpyAsync(outs[i].weight, dw, 8 * (size_t)cnt, cudaMemcpyDeviceToHost, s));
-        WTRI_CUDA(cudaStreamSynchronize(s));
-        cudaFreeAsync(dbuf, s);
-        outs[i].count = cnt;
-    }
-    return WTRI_OK;
+    batch_plan_destroy(P);
+    return rc;
 }
 
 }  // namespace wtri

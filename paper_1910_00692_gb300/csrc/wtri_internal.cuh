@@ -81,6 +81,8 @@ struct DevGraph {
 
 }  // namespace wtri
 
+struct wtri_batch_plan;  // defined in wtri_batch.cu
+
 struct wtri_graph {
     wtri::DevGraph d;
     cudaStream_t stream;
@@ -111,6 +113,20 @@ int sample_edges_device(const wtri_graph* g, int pcode, int64_t nsamples, uint64
 // Batched top-k (wtri_batch.cu): host results, optional CUDA-graph capture.
 int topk_batch(const wtri_graph* const* gs, const int32_t* pcodes, const int32_t* ks, int32_t nq,
                wtri_result* outs, cudaStream_t s, int use_graph);
+// Pieces of a batch for the serving loop: plan (host), launch into one device
+// scratch block (bytes from batch_plan_bytes), collect (synchronizes).
+typedef ::wtri_batch_plan BatchPlan;
+BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes, const int32_t* ks,
+                             int32_t nq);
+size_t batch_plan_bytes(const BatchPlan* P);
+int batch_plan_launch(BatchPlan* P, void* dbuf, cudaStream_t s, int use_graph);
+int batch_plan_collect(BatchPlan* P, void* dbuf, cudaStream_t s);
+int32_t batch_plan_status(const BatchPlan* P, int i);
+const wtri_tri* batch_plan_tris(const BatchPlan* P, int i);
+const double* batch_plan_weights(const BatchPlan* P, int i);
+void batch_plan_destroy(BatchPlan* P);
+int topk_retry_host(const wtri_graph* g, int pcode, int32_t k, cudaStream_t s, wtri_tri* htri,
+                    double* hw, int32_t* count);
 
 // Phase timers / launch counter (wtri_prof.cu).  'bytes' is the phase's
 // algorithmic traffic; 'launches' the number of kernels it launches.

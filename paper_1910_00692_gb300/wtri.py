@@ -96,13 +96,24 @@ def lib():
     L.wtri_graph_copy_array.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
     L.wtri_sample_edges.argtypes = [vp, f64, i64, ctypes.c_uint64, vp, i64]
     L.wtri_topk_batch.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_Result)]
+    u64 = ctypes.c_uint64
+    L.wtri_server_create.argtypes = [u64, i32, ctypes.POINTER(vp)]
+    L.wtri_server_add_graph.argtypes = [vp, vp, ctypes.POINTER(i32)]
+    L.wtri_submit.argtypes = [vp, i32, f64, i32, ctypes.POINTER(u64)]
+    L.wtri_poll.argtypes = [vp, u64, ctypes.POINTER(_Result)]
+    L.wtri_poll_timed.argtypes = [vp, u64, ctypes.POINTER(_Result), ctypes.POINTER(f64)]
+    L.wtri_server_stats.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(i32),
+                                    ctypes.POINTER(i32), ctypes.POINTER(u64)]
+    L.wtri_server_free.argtypes = [vp]
+    L.wtri_server_free.restype = None
     L.wtri_last_error.restype = ctypes.c_char_p
     L.wtri_last_error.argtypes = []
     L.wtri_version.restype = ctypes.c_char_p
     for f in (L.wtri_build_csr, L.wtri_graph_info, L.wtri_topk, L.wtri_topk_device,
               L.wtri_topk_device_noalloc,
               L.wtri_sample_topk, L.wtri_graph_copy_array, L.wtri_sample_edges,
-              L.wtri_topk_batch):
+              L.wtri_topk_batch, L.wtri_server_create, L.wtri_server_add_graph, L.wtri_submit,
+              L.wtri_poll, L.wtri_poll_timed, L.wtri_server_stats):
         f.restype = ctypes.c_int
     _lib = L
     return L
@@ -252,6 +263,61 @@ def topk_batch(graphs, ps, ks):
                                  p_arr.ctypes.data_as(ctypes.c_void_p),
                                  k_arr.ctypes.data_as(ctypes.c_void_p), nq, res))
     return [(tris[i][:res[i].count].copy(), wts[i][:res[i].count].copy()) for i in range(nq)]
+
+
+class Server:
+    """wtri_server_*: continuous-batching server over resident graphs."""
+
+    PENDING = WTRI_PENDING
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int):
+        h = ctypes.c_void_p()
+        _check(lib().wtri_server_create(ctypes.c_uint64(int(hbm_budget_bytes)), int(max_slots),
+                                        ctypes.byref(h)))
+        self._h = h
+        self._graphs = []
+
+    def add_graph(self, g: Graph) -> int:
+        gid = ctypes.c_int32()
+        _check(lib().wtri_server_add_graph(self._h, g.handle, ctypes.byref(gid)))
+        self._graphs.append(g)
+        return gid.value
+
+    def submit(self, graph_id: int, p: float, k: int) -> int:
+        t = ctypes.c_uint64()
+        _check(lib().wtri_submit(self._h, int(graph_id), float(p), int(k), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, k: int):
+        """None while pending, else (tris, weights, latency_s)."""
+        tris = np.zeros((max(k, 1), 3), dtype=np.int32)
+        wts = np.zeros(max(k, 1), dtype=np.float64)
+        res = _Result(tris.ctypes.data, wts.ctypes.data, max(k, 1), 0)
+        lat = ctypes.c_double()
+        rc = lib().wtri_poll_timed(self._h, ctypes.c_uint64(ticket), ctypes.byref(res), ctypes.byref(lat))
+        if rc == WTRI_PENDING:
+            return None
+        _check(rc)
+        return tris[:res.count].copy(), wts[:res.count].copy(), lat.value
+
+    def stats(self):
+        b, a, sc = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        wq, rn = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().wtri_server_stats(self._h, ctypes.byref(b), ctypes.byref(a), ctypes.byref(wq),
+                                       ctypes.byref(rn), ctypes.byref(sc)))
+        return {"batches": b.value, "admitted": a.value, "waiting": wq.value, "running": rn.value,
+                "scratch_bytes": sc.value}
+
+    def free(self):
+        if self._h:
+            lib().wtri_server_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def sample_edges(g: Graph, p: float, nsamples: int, seed: int) -> np.ndarray:
