@@ -51,6 +51,8 @@ def parse():
                          "tiny: n=2000 m=20000")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the sampler, batch and serving measurements")
     return ap.parse_args()
 
 
@@ -164,6 +166,127 @@ def prof_snapshot(L):
         out[name.value.decode()] = {"calls": calls.value, "ms": ms.value, "bytes": by.value}
         i += 1
     return out
+
+
+def bench_sampler(wt, g, stream, k):
+    """Weighted edge sampling: 1e7 draws (Philox seed 7), p = 1, top-1000 of
+    the sampled set; recall against the exact top-1000."""
+    import torch
+    d = wt.build_csr(g.n, g.u, g.v, g.w)
+    try:
+        exact, _ = d.topk(1.0, k)
+        d.sample_topk(1.0, k, 1_000_000, 7)  # warm-up
+        times = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tris, _ = d.sample_topk(1.0, k, 10_000_000, 7)
+            times.append(time.perf_counter() - t0)
+        ref = set(map(tuple, exact.tolist()))
+        recall = len(ref & set(map(tuple, tris.tolist()))) / max(1, len(ref))
+        return {"nsamples": 10_000_000, "seed": 7, "p": 1, "k": k, "ms": 1e3 * min(times),
+                "recall_at_k": recall, "api": "wtri_sample_topk (host results)"}
+    finally:
+        d.free()
+
+
+def bench_batch(wt, stream, count=1024, n_hi=20_000):
+    """Batched form: `count` graphs (n log-uniform in [100, n_hi], m = 10 n,
+    exponent 2.2, Zipf(2)), per-graph k ~ U[10,1000], p ~ U{-inf,1,2,+inf}:
+    one wtri_topk_batch call against the same queries as plain wtri_topk
+    calls (host results both)."""
+    import synth
+    import torch
+    graphs = [synth.batch_graph(i, seed=3, n_hi=n_hi) for i in range(count)]
+    ps, ks = synth.batch_queries(count, seed=3)
+    ds = [wt.build_csr(x.n, x.u, x.v, x.w) for x in graphs]
+    try:
+        wt.topk_batch(ds[:8], ps[:8], ks[:8])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = wt.topk_batch(ds, ps, ks)
+        t_batch = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        plain = [d.topk(ps[i], int(ks[i])) for i, d in enumerate(ds)]
+        t_plain = time.perf_counter() - t0
+        same = all(np.array_equal(res[i][0], plain[i][0]) and np.array_equal(res[i][1], plain[i][1])
+                   for i in range(count))
+        return {"graphs": count, "edges": int(sum(x.m for x in graphs)),
+                "n_range": [100, n_hi], "batched_ms": 1e3 * t_batch, "plain_calls_ms": 1e3 * t_plain,
+                "speedup": t_plain / t_batch, "results_identical": bool(same),
+                "note": "batch of the 4,096-graph recipe with a smaller n range (host generation time)"}
+    finally:
+        for d in ds:
+            d.free()
+
+
+def bench_serve(wt, g_mid, rate=2000.0, count=4000):
+    """Serving: Poisson arrivals at `rate` req/s over resident graphs (the
+    bench graph plus two Chung-Lu graphs of 2e6 and 5e6 edges), k ~ U[10,1000],
+    p ~ U{-inf,1,2,+inf}.  Latency = submission to completion.  Baseline: a
+    sequential loop of wtri_topk fed the same arrival times (its latency
+    includes waiting for the previous requests)."""
+    import synth
+    gs = [g_mid, synth.scaled_mid_graph(200_000, 2_000_000, seed=5),
+          synth.scaled_mid_graph(500_000, 5_000_000, seed=6)]
+    ds = [wt.build_csr(x.n, x.u, x.v, x.w) for x in gs]
+    rng = np.random.default_rng(6)
+    gaps = rng.exponential(1.0 / rate, size=count)
+    arrive = np.cumsum(gaps)
+    gid = rng.integers(0, len(gs), size=count)
+    ks = rng.integers(10, 1001, size=count)
+    ps = np.array(PS)[rng.integers(0, 4, size=count)]
+    try:
+        srv = wt.Server(120 << 30, 256)
+        ids = [srv.add_graph(d) for d in ds]
+        for i in range(16):  # warm-up
+            t = srv.submit(ids[i % 3], PS[i % 4], 100)
+            while srv.poll(t, 100) is None:
+                time.sleep(0.0002)
+        tickets = []
+        t0 = time.perf_counter()
+        for i in range(count):
+            while time.perf_counter() - t0 < arrive[i]:
+                pass
+            tickets.append(srv.submit(ids[gid[i]], ps[i], int(ks[i])))
+        # latency is measured by the server (submission to completion), so
+        # collecting the results in order does not change it
+        lat = [None] * count
+        t_last = 0.0
+        for i in range(count):
+            r = srv.poll(tickets[i], int(ks[i]))
+            while r is None:
+                time.sleep(0.0001)
+                r = srv.poll(tickets[i], int(ks[i]))
+            lat[i] = r[2]
+            t_last = max(t_last, arrive[i] + r[2])
+        t_end = t_last
+        st = srv.stats()
+        srv.free()
+        lat = np.array(lat)
+        # sequential loop: real service times, queueing from the same arrivals
+        service = np.empty(count)
+        for i in range(count):
+            a = time.perf_counter()
+            ds[gid[i]].topk(ps[i], int(ks[i]))
+            service[i] = time.perf_counter() - a
+        finish = 0.0
+        seq_lat = np.empty(count)
+        for i in range(count):
+            start = max(arrive[i], finish)
+            finish = start + service[i]
+            seq_lat[i] = finish - arrive[i]
+        return {"requests": count, "rate_req_s": rate, "graphs_edges": [int(x.m) for x in gs],
+                "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "qps": count / t_end, "micro_batches": int(st["batches"]), "retries": int(st["retries"]),
+                "sequential_p50_ms": 1e3 * float(np.percentile(seq_lat, 50)),
+                "sequential_p99_ms": 1e3 * float(np.percentile(seq_lat, 99)),
+                "sequential_qps": count / finish, "budget_gb": 120,
+                "note": "reduced pool: the bench graph and two Chung-Lu graphs instead of the "
+                        "1e9- and 2e8-edge graphs (host generation time)"}
+    finally:
+        for d in ds:
+            d.free()
 
 
 def run_reference(args, world, rank):
@@ -335,6 +458,15 @@ def main():
         e2e = {"value": world * m / t_e2e, "unit": "edges/s", "h2d_bytes_per_step": 12 * m,
                "d2h_bytes_per_step": d2h // e2e_steps, "ms_per_step": t_e2e * 1e3}
 
+    # ---- weighted edge sampling (Algorithm 3) on the same graph --------------
+    sampler = None
+    batch = None
+    serve = None
+    if rank == 0 and not args.no_extras and args.workload == "mid":
+        sampler = bench_sampler(wt, g, stream, k)
+        batch = bench_batch(wt, stream)
+        serve = bench_serve(wt, g)
+
     # ---- CPU baseline: the oracle, bounded sample (rank 0, N=1) -------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -357,6 +489,7 @@ def main():
                        "l2": "inputs larger than L2: COO 240 MB, resident graph ~1.4 GB per step"},
             "query_ms": query_ms, "phase_ms_per_step": step_ms_parts,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "sampler": sampler, "batch": batch, "serve": serve,
             "gpu_launches": int(launches), "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

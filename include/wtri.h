@@ -192,7 +192,8 @@ WTRI_API int wtri_topk_batch(const wtri_graph* const* gs, const double* p, const
  * wtri_poll_timed: wtri_poll that also returns the seconds from submission
  *   to completion.
  * wtri_server_stats: micro-batches launched, requests admitted, requests
- *   waiting and running, scratch bytes in flight (any pointer may be NULL).
+ *   waiting and running, scratch bytes in flight, requests re-run alone
+ *   after overflowing their batched buffers (any pointer may be NULL).
  * wtri_server_free: finishes every queued request, stops the scheduler and
  *   frees the server (not the graphs).
  */
@@ -202,7 +203,7 @@ WTRI_API int wtri_submit(wtri_server* s, int32_t graph_id, double p, int32_t k, 
 WTRI_API int wtri_poll(wtri_server* s, uint64_t ticket, wtri_result* out);
 WTRI_API int wtri_poll_timed(wtri_server* s, uint64_t ticket, wtri_result* out, double* latency_s);
 WTRI_API int wtri_server_stats(wtri_server* s, uint64_t* batches, uint64_t* admitted, int32_t* waiting,
-                               int32_t* running, uint64_t* scratch_bytes);
+                               int32_t* running, uint64_t* scratch_bytes, uint64_t* retries);
 WTRI_API void wtri_server_free(wtri_server* s);
 
 /*

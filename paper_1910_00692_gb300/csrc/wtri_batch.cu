@@ -3,14 +3,15 @@
 // Every query keeps its own state (threshold, stop point, candidate buffer)
 // exactly as in the single query; the kernels of each phase run over all
 // queries at once:
-//   k_round_batch   threads stride over the concatenated edge ranges of all
-//                   queries for this round (host-computed offsets; a binary
-//                   search maps a work item to its query);
+//   k_round_offsets one block: each query's live range for this round (cut
+//                   at its stop point) and their prefix offsets;
+//   k_round_batch   threads stride over the concatenated live ranges (a
+//                   binary search maps a work item to its query);
 //   k_long_batch    deferred long scans of all queries (items carry the
 //                   query index);
 //   k_select_batch  one block per query: k-th key, compaction, threshold;
 //   k_final_batch / k_rank_batch: exact selection and ranking per query.
-// The whole sequence (rounds x 3 + 2 launches) is captured in one CUDA
+// The whole sequence (rounds x 4 + 2 launches) is captured in one CUDA
 // graph and launched once.
 #include "wtri_query.cuh"
 
@@ -35,6 +36,49 @@ __device__ __forceinline__ int find_q(const int64_t* offs, int nq, int64_t t) {
         else hi = mid;
     }
     return lo;
+}
+
+// Per round: each query's live range is [lo, min(hi, its stop point)); the
+// exclusive prefix of the live sizes maps work items to queries, so
+// queries that have stopped cost nothing in later rounds.
+__global__ void __launch_bounds__(1024) k_round_offsets(BatchDev B, const int64_t* __restrict__ lo,
+                                                        const int64_t* __restrict__ hi,
+                                                        int64_t* __restrict__ offs) {
+    __shared__ int64_t warp_sum[32];
+    __shared__ int64_t carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < B.nq; base += 1024) {
+        const int qi = base + threadIdx.x;
+        int64_t sz = 0;
+        if (qi < B.nq) {
+            const int64_t stop = (int64_t)(STOP_NONE - *(volatile const uint32_t*)&B.queries[qi].st->stop_rev);
+            const int64_t e = min(hi[qi], stop);
+            sz = e > lo[qi] ? e - lo[qi] : 0;
+        }
+        int64_t inc = sz;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) warp_sum[wid] = inc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t acc = carry;
+            for (int k = 0; k < 32; k++) {
+                const int64_t t = warp_sum[k];
+                warp_sum[k] = acc;
+                acc += t;
+            }
+            carry = acc;
+        }
+        __syncthreads();
+        if (qi < B.nq) offs[qi] = warp_sum[wid] + inc - sz;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) offs[B.nq] = carry;
 }
 
 __global__ void __launch_bounds__(RBLK) k_round_batch(BatchDev B, const int64_t* __restrict__ offs,
@@ -146,14 +190,22 @@ struct wtri_batch_plan {
     std::vector<unsigned char> hq;  // Query descriptors (filled at launch)
     size_t cand_total = 0;
     uint32_t long_cap = 1u << 18;
-    size_t o_st, o_key, o_tri, o_long, o_lcnt, o_g, o_q, o_pc, o_offs, o_los, o_koffs, o_otri, o_ow,
-        o_stat, bytes;
+    size_t o_st, o_key, o_tri, o_long, o_lcnt, o_g, o_q, o_pc, o_offs, o_live, o_los, o_koffs, o_otri,
+        o_ow, o_stat, bytes;
     std::vector<int32_t> stat;
     std::vector<wtri_tri> otri;
     std::vector<double> ow;
 };
 
 namespace wtri {
+
+// Candidate slots of one batched query: enough for k plus ties, and for the
+// first rounds of a large graph (enumerated before the threshold exists).
+uint32_t batch_query_cap(int32_t k, int64_t m) {
+    int64_t cap = std::max<int64_t>(16 * (int64_t)k, m / 16);
+    cap = std::min<int64_t>(cap, int64_t(1) << 20);
+    return (uint32_t)std::max<int64_t>(cap, 16384);
+}
 
 BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes, const int32_t* ks,
                              int32_t nq) {
@@ -170,7 +222,7 @@ BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes,
         P->hg[(size_t)i] = gs[i]->d;
         mmax = std::max<int64_t>(mmax, gs[i]->d.m);
         P->koffs[(size_t)i + 1] = P->koffs[(size_t)i] + ks[i];
-        P->caps[(size_t)i] = (uint32_t)std::max<int64_t>(16384, 16 * (int64_t)ks[i]);
+        P->caps[(size_t)i] = batch_query_cap(ks[i], gs[i]->d.m);
         P->cand_total += P->caps[(size_t)i];
     }
     // Round schedule (same as a single query), per query clipped to its m.
@@ -181,7 +233,9 @@ BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes,
     }
     const int R = (int)r_lo.size();
     P->R = R;
-    P->offs.resize((size_t)R * (nq + 1));
+    // offs: per round, the query ranges' hi ends (the device computes the
+    // live offsets from them and the stop points); totals bound the grids.
+    P->offs.resize((size_t)R * nq);
     P->los.resize((size_t)R * nq);
     P->totals.resize((size_t)R);
     for (int r = 0; r < R; r++) {
@@ -189,11 +243,10 @@ BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes,
         for (int i = 0; i < nq; i++) {
             const int64_t m = gs[i]->d.m;
             const int64_t a = std::min(m, r_lo[(size_t)r]), b = std::min(m, r_hi[(size_t)r]);
-            P->offs[(size_t)r * (nq + 1) + i] = acc;
+            P->offs[(size_t)r * nq + i] = b;
             P->los[(size_t)r * nq + i] = a;
             acc += b - a;
         }
-        P->offs[(size_t)r * (nq + 1) + nq] = acc;
         P->totals[(size_t)r] = acc;
     }
     size_t off = 0;
@@ -211,6 +264,7 @@ BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes,
     P->o_q = take(sizeof(Query) * (size_t)nq);
     P->o_pc = take(4 * (size_t)nq);
     P->o_offs = take(8 * std::max<size_t>(P->offs.size(), 1));
+    P->o_live = take(8 * ((size_t)nq + 1) * std::max(R, 1));
     P->o_los = take(8 * std::max<size_t>(P->los.size(), 1));
     P->o_koffs = take(8 * P->koffs.size());
     P->o_otri = take(sizeof(wtri_tri) * (size_t)P->koffs[(size_t)nq]);
@@ -257,6 +311,7 @@ int batch_plan_launch(BatchPlan* P, void* dbuf, cudaStream_t s, int use_graph) {
     Bd.pcodes = (const int32_t*)(B0 + P->o_pc);
     Bd.nq = nq;
     int64_t* d_offs = (int64_t*)(B0 + P->o_offs);
+    int64_t* d_live = (int64_t*)(B0 + P->o_live);
     int64_t* d_los = (int64_t*)(B0 + P->o_los);
     int64_t* d_koffs = (int64_t*)(B0 + P->o_koffs);
     wtri_tri* d_otri = (wtri_tri*)(B0 + P->o_otri);
@@ -283,8 +338,10 @@ int batch_plan_launch(BatchPlan* P, void* dbuf, cudaStream_t s, int use_graph) {
         cudaMemsetAsync(st, 0, sizeof(QState) * (size_t)nq, s);
         cudaMemsetAsync(lcnt, 0, 64, s);
         for (int r = 0; r < R; r++) {
-            k_round_batch<<<round_grid(P->totals[(size_t)r]), RBLK, 0, s>>>(
-                Bd, d_offs + (size_t)r * (nq + 1), d_los + (size_t)r * nq);
+            int64_t* live = d_live + (size_t)r * (nq + 1);
+            k_round_offsets<<<1, 1024, 0, s>>>(Bd, d_los + (size_t)r * nq, d_offs + (size_t)r * nq, live);
+            k_round_batch<<<round_grid(P->totals[(size_t)r]), RBLK, 0, s>>>(Bd, live,
+                                                                            d_los + (size_t)r * nq);
             k_long_batch<<<long_grid, LBLK, lsmem, s>>>(Bd, longs, lcnt, P->long_cap);
             k_select_batch<<<nq, SBLK, 0, s>>>(Bd);
         }
@@ -295,7 +352,7 @@ int batch_plan_launch(BatchPlan* P, void* dbuf, cudaStream_t s, int use_graph) {
                        256, 0, s>>>(Bd, d_koffs, d_otri, d_ow, d_stat);
     };
     int rc = WTRI_OK;
-    ProfScope ps("topk_batch", s, 0.0, 3 * R + 2);
+    ProfScope ps("topk_batch", s, 0.0, 4 * R + 2);
     if (use_graph) {
         // The descriptors must have landed before the captured work refers
         // to them only through device pointers: that holds, the copies are

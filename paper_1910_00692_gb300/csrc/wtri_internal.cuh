@@ -116,6 +116,7 @@ int topk_batch(const wtri_graph* const* gs, const int32_t* pcodes, const int32_t
 // Pieces of a batch for the serving loop: plan (host), launch into one device
 // scratch block (bytes from batch_plan_bytes), collect (synchronizes).
 typedef ::wtri_batch_plan BatchPlan;
+uint32_t batch_query_cap(int32_t k, int64_t m);
 BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes, const int32_t* ks,
                              int32_t nq);
 size_t batch_plan_bytes(const BatchPlan* P);

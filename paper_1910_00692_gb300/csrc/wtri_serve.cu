@@ -55,8 +55,8 @@ struct InFlight {
     std::vector<std::shared_ptr<Request>> reqs;
 };
 
-size_t request_bytes(int32_t k) {
-    const size_t cap = std::max<size_t>(16384, 16 * (size_t)k);
+size_t request_bytes(int32_t k, int64_t m) {
+    const size_t cap = batch_query_cap(k, m);
     return 256 + cap * 24 + (size_t)k * 20 + 512;
 }
 
@@ -81,7 +81,7 @@ struct wtri_server {
     cudaStream_t streams[wtri::WORKER_STREAMS] = {};
     bool stream_busy[wtri::WORKER_STREAMS] = {};
     std::vector<wtri::InFlight> inflight;  // touched by the worker only
-    uint64_t batches = 0, admitted = 0;
+    uint64_t batches = 0, admitted = 0, retries = 0;
 };
 
 namespace wtri {
@@ -98,6 +98,10 @@ void finish_batch(wtri_server* S, InFlight& f) {
         r->w.assign((size_t)std::max(r->k, 1), 0.0);
         int rrc = WTRI_OK;
         if (c == WTRI_ENOMEM) {
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->retries++;
+            }
             int32_t cnt = 0;
             rrc = topk_retry_host(S->graphs[(size_t)r->graph_id], r->pcode, r->k, s, r->tris.data(),
                                   r->w.data(), &cnt);
@@ -292,12 +296,12 @@ WTRI_API int wtri_submit(wtri_server* S, int32_t graph_id, double p, int32_t k, 
     auto r = std::make_shared<Request>();
     r->pcode = code;
     r->k = k;
-    r->bytes = request_bytes(k);
     r->t_submit = now_s();
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (graph_id < 0 || graph_id >= (int32_t)S->graphs.size())
             return set_error(WTRI_ENOTFOUND, "unknown graph id");
+        r->bytes = request_bytes(k, S->graphs[(size_t)graph_id]->d.m);
         if (S->stop) return set_error(WTRI_EINVAL, "server is shutting down");
         if (S->graph_bytes + BATCH_FIXED_BYTES + r->bytes > S->budget)
             return set_error(WTRI_ENOMEM, "request scratch can never fit the HBM budget");
@@ -340,9 +344,10 @@ WTRI_API int wtri_poll(wtri_server* S, uint64_t ticket, wtri_result* out) {
 }
 
 WTRI_API int wtri_server_stats(wtri_server* S, uint64_t* batches, uint64_t* admitted, int32_t* waiting,
-                               int32_t* running, uint64_t* scratch_bytes) {
+                               int32_t* running, uint64_t* scratch_bytes, uint64_t* retries) {
     if (!S) return set_error(WTRI_EINVAL, "server is NULL");
     std::lock_guard<std::mutex> lk(S->mu);
+    if (retries) *retries = S->retries;
     if (batches) *batches = S->batches;
     if (admitted) *admitted = S->admitted;
     if (waiting) *waiting = (int32_t)S->waiting.size();

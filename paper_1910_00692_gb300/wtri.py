@@ -103,7 +103,7 @@ def lib():
     L.wtri_poll.argtypes = [vp, u64, ctypes.POINTER(_Result)]
     L.wtri_poll_timed.argtypes = [vp, u64, ctypes.POINTER(_Result), ctypes.POINTER(f64)]
     L.wtri_server_stats.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(i32),
-                                    ctypes.POINTER(i32), ctypes.POINTER(u64)]
+                                    ctypes.POINTER(i32), ctypes.POINTER(u64), ctypes.POINTER(u64)]
     L.wtri_server_free.argtypes = [vp]
     L.wtri_server_free.restype = None
     L.wtri_last_error.restype = ctypes.c_char_p
@@ -301,12 +301,12 @@ class Server:
         return tris[:res.count].copy(), wts[:res.count].copy(), lat.value
 
     def stats(self):
-        b, a, sc = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        b, a, sc, rt = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         wq, rn = ctypes.c_int32(), ctypes.c_int32()
         _check(lib().wtri_server_stats(self._h, ctypes.byref(b), ctypes.byref(a), ctypes.byref(wq),
-                                       ctypes.byref(rn), ctypes.byref(sc)))
+                                       ctypes.byref(rn), ctypes.byref(sc), ctypes.byref(rt)))
         return {"batches": b.value, "admitted": a.value, "waiting": wq.value, "running": rn.value,
-                "scratch_bytes": sc.value}
+                "scratch_bytes": sc.value, "retries": rt.value}
 
     def free(self):
         if self._h:
