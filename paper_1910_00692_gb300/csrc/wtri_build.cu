@@ -173,6 +173,8 @@ __global__ void k_scan_apply(const int32_t* __restrict__ in, int64_t n,
 struct EdgeLoader {
     static constexpr double KEY_BYTES = 4.0;   // w
     static constexpr double REC_BYTES = 12.0;  // u, v, w
+    static constexpr int NARR = 3;             // TMA source arrays: w, u, v
+    static constexpr uint32_t TILE_ELEMS = radix::TILE;
     const int32_t* u;
     const int32_t* v;
     const int32_t* w;
@@ -182,6 +184,18 @@ struct EdgeLoader {
     }
     __device__ __forceinline__ uint32_t val(int q, int64_t i) const {
         return (uint32_t)__ldg((q == 0 ? u : v) + i);
+    }
+    __device__ __forceinline__ const void* tile_src(int a, int64_t tbase) const {
+        return (a == 0 ? w : (a == 1 ? u : v)) + tbase;
+    }
+    __device__ __forceinline__ uint32_t skey(const uint32_t* in, int li, int64_t) const {
+        return (uint32_t)(wmax - (int32_t)in[li]);
+    }
+    __device__ __forceinline__ uint32_t sval(const uint32_t* in, int q, int li, int64_t) const {
+        return in[(q + 1) * radix::TILE + li];
+    }
+    bool tma_ok() const {
+        return (((uintptr_t)u | (uintptr_t)v | (uintptr_t)w) & 15) == 0;
     }
 };
 
@@ -204,9 +218,25 @@ struct EdgeOrderStorer {
 struct OrderEntryLoader {
     static constexpr double KEY_BYTES = 4.0;  // u or v: 8 bytes per edge, two entries
     static constexpr double REC_BYTES = 6.0;  // u, v, w: 12 bytes per edge, two entries
+    static constexpr int NARR = 3;            // TMA source arrays: ou, ov, ow (half a tile each)
+    static constexpr uint32_t TILE_ELEMS = radix::TILE / 2;
     const int32_t* ou;
     const int32_t* ov;
     const int32_t* ow;
+    __device__ __forceinline__ const void* tile_src(int a, int64_t tbase) const {
+        return (a == 0 ? ou : (a == 1 ? ov : ow)) + (tbase >> 1);
+    }
+    __device__ __forceinline__ uint32_t skey(const uint32_t* in, int li, int64_t) const {
+        return in[((li & 1) ? radix::TILE : 0) + (li >> 1)];
+    }
+    __device__ __forceinline__ uint32_t sval(const uint32_t* in, int q, int li, int64_t tbase) const {
+        if (q == 0) return in[((li & 1) ? 0 : radix::TILE) + (li >> 1)];
+        if (q == 1) return in[2 * radix::TILE + (li >> 1)];
+        return (uint32_t)((tbase >> 1) + (li >> 1));
+    }
+    bool tma_ok() const {
+        return (((uintptr_t)ou | (uintptr_t)ov | (uintptr_t)ow) & 15) == 0;
+    }
     __device__ __forceinline__ uint32_t key(int64_t i) const {
         const int64_t r = i >> 1;
         return (uint32_t)__ldg(((i & 1) ? ov : ou) + r);
@@ -224,10 +254,22 @@ struct OrderEntryLoader {
 struct MirrorLoader {
     static constexpr double KEY_BYTES = 4.0;   // wcol
     static constexpr double REC_BYTES = 16.0;  // wcol, wrow, wwt, wrk
+    static constexpr int NARR = 4;             // TMA source arrays: wcol, wrow, wwt, wrk
+    static constexpr uint32_t TILE_ELEMS = radix::TILE;
     const int32_t* wrow;
     const int32_t* wcol;
     const int32_t* wwt;
     const int32_t* wrk;
+    __device__ __forceinline__ const void* tile_src(int a, int64_t tbase) const {
+        return (a == 0 ? wcol : (a == 1 ? wrow : (a == 2 ? wwt : wrk))) + tbase;
+    }
+    __device__ __forceinline__ uint32_t skey(const uint32_t* in, int li, int64_t) const { return in[li]; }
+    __device__ __forceinline__ uint32_t sval(const uint32_t* in, int q, int li, int64_t) const {
+        return in[(q + 1) * radix::TILE + li];
+    }
+    bool tma_ok() const {
+        return (((uintptr_t)wrow | (uintptr_t)wcol | (uintptr_t)wwt | (uintptr_t)wrk) & 15) == 0;
+    }
     __device__ __forceinline__ uint32_t key(int64_t i) const { return (uint32_t)__ldg(wcol + i); }
     __device__ __forceinline__ uint32_t val(int q, int64_t i) const {
         return (uint32_t)__ldg((q == 0 ? wrow : (q == 1 ? wwt : wrk)) + i);
@@ -253,7 +295,7 @@ struct RowsStorer {
 // middle passes through ping-pong arrays, last pass into 'last'.
 template <int NV, class First, class Last>
 int lsd_sort(const First& first, const Last& last, int64_t n, int bits, uint32_t* pp_a,
-             uint32_t* pp_b, int64_t cap, uint32_t* scratch, cudaStream_t s) {
+             uint32_t* pp_b, int64_t cap, uint32_t* scratch, cudaStream_t s, uint32_t* err) {
     using namespace radix;
     const int passes = (bits + BITS - 1) / BITS;
     (void)cap;
@@ -267,19 +309,20 @@ int lsd_sort(const First& first, const Last& last, int64_t n, int bits, uint32_t
         ArrStorer<NV> as;
         al.k = cur;
         as.k = nxt;
+        const size_t stride = ((size_t)n + 3) & ~size_t(3);  // 16-byte aligned arrays
         for (int q = 0; q < NV; q++) {
-            al.v[q] = cur + (size_t)(q + 1) * n;
-            as.v[q] = nxt + (size_t)(q + 1) * n;
+            al.v[q] = cur + (size_t)(q + 1) * stride;
+            as.v[q] = nxt + (size_t)(q + 1) * stride;
         }
         if (p == 0 && p == passes - 1) {
-            WTRI_TRY((run_pass<NV, true>(first, last, n, shift, pb, scratch, s)));
+            WTRI_TRY((run_pass<NV, true>(first, last, n, shift, pb, scratch, s, err)));
         } else if (p == 0) {
-            WTRI_TRY((run_pass<NV, true>(first, as, n, shift, pb, scratch, s)));
+            WTRI_TRY((run_pass<NV, true>(first, as, n, shift, pb, scratch, s, err)));
             std::swap(cur, nxt);
         } else if (p == passes - 1) {
-            WTRI_TRY((run_pass<NV, true>(al, last, n, shift, pb, scratch, s)));
+            WTRI_TRY((run_pass<NV, true>(al, last, n, shift, pb, scratch, s, err)));
         } else {
-            WTRI_TRY((run_pass<NV, true>(al, as, n, shift, pb, scratch, s)));
+            WTRI_TRY((run_pass<NV, true>(al, as, n, shift, pb, scratch, s, err)));
             std::swap(cur, nxt);
         }
     }
@@ -589,7 +632,7 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         // Scratch: two ping-pong record buffers of (key + 3 values) x 2m, the
         // radix counts, the row keys of the weight-sorted layout, long rows.
         const int64_t n2 = 2 * m;
-        const size_t rec_words = 4 * (size_t)n2;
+        const size_t rec_words = 4 * ((((size_t)n2) + 3) & ~size_t(3)) + 4;
         const size_t cnt_words = radix::scratch_words(n2);
         const size_t words = 2 * rec_words + cnt_words + (size_t)n2 + N1 + 8;
         Scratch tmp(s);
@@ -614,7 +657,7 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         } else {
             EdgeLoader el{u, v, w, h_st.wmax};
             EdgeOrderStorer es{ou, ov, ow, h_st.wmax};
-            int rc = lsd_sort<2>(el, es, m, wbits, pp_a, pp_b, m, counts, s);
+            int rc = lsd_sort<2>(el, es, m, wbits, pp_a, pp_b, m, counts, s, &d_st->err);
             if (rc != WTRI_OK) return fail(rc);
         }
         // 3. weight-sorted rows (row key kept in wrow)
@@ -622,7 +665,7 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         {
             OrderEntryLoader ol{ou, ov, ow};
             RowsStorer rs{wrow, wcol, wwt, wrk};
-            int rc = lsd_sort<3>(ol, rs, n2, nbits, pp_a, pp_b, n2, counts, s);
+            int rc = lsd_sort<3>(ol, rs, n2, nbits, pp_a, pp_b, n2, counts, s, &d_st->err);
             if (rc != WTRI_OK) return fail(rc);
         }
         // 4. row offsets, degrees, long rows
@@ -635,7 +678,7 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         {
             MirrorLoader ml{wrow, wcol, wwt, wrk};
             RowsStorer rs{nullptr, scol, swt, srk};
-            int rc = lsd_sort<3>(ml, rs, n2, nbits, pp_a, pp_b, n2, counts, s);
+            int rc = lsd_sort<3>(ml, rs, n2, nbits, pp_a, pp_b, n2, counts, s, &d_st->err);
             if (rc != WTRI_OK) return fail(rc);
         }
         // 6. orientation + repeated pairs
@@ -652,6 +695,8 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         if (cudaMemcpyAsync(&h_st, d_st, sizeof(h_st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "build", __FILE__, __LINE__));
+        if (h_st.err & DEV_ERR_TIMEOUT)
+            return fail(set_error(WTRI_ETIMEOUT, "a bounded wait in the radix sort ran out"));
         if (h_st.err & DEV_ERR_DUPLICATE) {
             int32_t col[2] = {-1, -1};
             const int64_t j = (int64_t)h_st.first_bad;

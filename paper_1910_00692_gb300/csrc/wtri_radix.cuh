@@ -76,14 +76,22 @@ struct PassGeom {
     uint32_t mask;
 };
 
+// Digit histogram of each chunk.  UP_SPLIT blocks share a chunk (each a
+// slice of it) and add their counts into the zeroed per-chunk histogram.
+constexpr int UP_SPLIT = 8;
+
 template <class Loader>
 __global__ void __launch_bounds__(THREADS) k_upsweep(Loader ld, PassGeom g, uint32_t* counts) {
     __shared__ uint32_t hist[WARPS][RADIX];
     const int w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < WARPS * RADIX; i += THREADS) (&hist[0][0])[i] = 0;
     __syncthreads();
-    const int64_t beg = (int64_t)blockIdx.x * g.chunk;
-    const int64_t end = min(g.n, beg + g.chunk);
+    const int chunk = blockIdx.x / UP_SPLIT, part = blockIdx.x % UP_SPLIT;
+    const int64_t cbeg = (int64_t)chunk * g.chunk;
+    const int64_t cend = min(g.n, cbeg + g.chunk);
+    const int64_t slice = (g.chunk + UP_SPLIT - 1) / UP_SPLIT;
+    const int64_t beg = cbeg + part * slice;
+    const int64_t end = min(cend, beg + slice);
     for (int64_t i = beg + threadIdx.x; i < end; i += THREADS) {
         uint32_t d = (ld.key(i) >> g.shift) & g.mask;
         atomicAdd(&hist[w][d], 1u);
@@ -92,7 +100,7 @@ __global__ void __launch_bounds__(THREADS) k_upsweep(Loader ld, PassGeom g, uint
     uint32_t s = 0;
 #pragma unroll
     for (int k = 0; k < WARPS; k++) s += hist[k][threadIdx.x];
-    counts[(int64_t)threadIdx.x * g.chunks + blockIdx.x] = s;
+    if (s) atomicAdd(&counts[(int64_t)threadIdx.x * g.chunks + chunk], s);
 }
 
 // Block d: exclusive scan of counts[d][0..G) in place; totals[d] = sum.
@@ -220,15 +228,241 @@ __global__ void __launch_bounds__(THREADS) k_downsweep(Loader ld, Storer st, Pas
     }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-fed scatter.  One CTA per SM streams its chunk tile by tile; while a
+// tile is ranked and scattered, the next tile's source arrays arrive in the
+// other half of a double buffer by bulk async copies (cp.async.bulk) that
+// complete on one mbarrier per buffer.  Waits are bounded: on timeout the
+// pass records DEV_ERR_TIMEOUT and the CTA returns.  Only whole tiles go
+// through TMA; a chunk's last partial tile is loaded with plain loads.
+// ---------------------------------------------------------------------------
+constexpr int TMA_ARRS = 4;                 // source arrays per loader, at most
+constexpr uint32_t TMA_WAIT_LIMIT = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void tma_bar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void tma_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool tma_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+template <int NV>
+struct TmaSmem {
+    uint32_t in[2][TMA_ARRS][TILE];  // source arrays of the current / next tile
+    uint32_t stage[NV + 1][TILE];
+    uint32_t cnt[WARPS][RADIX];
+    uint32_t run[RADIX];
+    uint32_t tile_start[RADIX];
+    uint32_t tile_total[RADIX];
+    uint32_t warp_tot[WARPS];
+    uint32_t total;
+    int timed_out;
+    uint64_t bar[2];
+};
+
+// Records of the current tile from the TMA buffer.
+template <class Loader>
+struct SmemSrc {
+    const Loader& ld;
+    const uint32_t* in;  // in[b][0]; array a at in + a * TILE
+    int64_t tbase;
+    __device__ __forceinline__ uint32_t key(int li) const { return ld.skey(in, li, tbase); }
+    __device__ __forceinline__ uint32_t val(int q, int li) const { return ld.sval(in, q, li, tbase); }
+};
+
+// Records of a tile straight from global memory.
+template <class Loader>
+struct GlobalSrc {
+    const Loader& ld;
+    int64_t tbase;
+    __device__ __forceinline__ uint32_t key(int li) const { return ld.key(tbase + li); }
+    __device__ __forceinline__ uint32_t val(int q, int li) const { return ld.val(q, tbase + li); }
+};
+
+// Rank, stage and scatter one tile of tcount records (all threads).
+template <int NV, bool STORE_KEY, class Src, class Storer, class Smem>
+__device__ __forceinline__ void scatter_tile(const Src& src, const Storer& st, const PassGeom& g,
+                                             int tcount, Smem& S) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    for (int i = threadIdx.x; i < WARPS * RADIX; i += THREADS) (&S.cnt[0][0])[i] = 0;
+    __syncthreads();
+    uint32_t key[ITEMS];
+    uint32_t rank[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        const int li = w * 32 * ITEMS + j * 32 + lane;
+        key[j] = li < tcount ? src.key(li) : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        const int li = w * 32 * ITEMS + j * 32 + lane;
+        const bool valid = li < tcount;
+        const uint32_t d = valid ? ((key[j] >> g.shift) & g.mask) : (uint32_t)RADIX;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t base = valid ? S.cnt[w][d] : 0u;
+        rank[j] = base + __popc(peers & lt);
+        __syncwarp();
+        if (valid && (__ffs(peers) - 1) == lane) S.cnt[w][d] = base + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;
+        uint32_t s = 0;
+#pragma unroll
+        for (int k = 0; k < WARPS; k++) {
+            uint32_t c = S.cnt[k][d];
+            S.cnt[k][d] = s;
+            s += c;
+        }
+        S.tile_total[d] = s;
+        uint32_t st0 = block_exclusive_scan_256(s, S.warp_tot, &S.total);
+        S.tile_start[d] = st0;
+#pragma unroll
+        for (int k = 0; k < WARPS; k++) S.cnt[k][d] += st0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        const int li = w * 32 * ITEMS + j * 32 + lane;
+        if (li < tcount) {
+            const uint32_t d = (key[j] >> g.shift) & g.mask;
+            const uint32_t pos = rank[j] + S.cnt[w][d];
+            S.stage[0][pos] = key[j];
+#pragma unroll
+            for (int q = 0; q < NV; q++) S.stage[q + 1][pos] = src.val(q, li);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+        const int p = i * THREADS + threadIdx.x;
+        if (p < tcount) {
+            const uint32_t k = S.stage[0][p];
+            const uint32_t d = (k >> g.shift) & g.mask;
+            const int64_t gp = (int64_t)S.run[d] + (p - (int64_t)S.tile_start[d]);
+            if (STORE_KEY) st.key(gp, k);
+#pragma unroll
+            for (int q = 0; q < NV; q++) st.val(q, gp, S.stage[q + 1][p]);
+        }
+    }
+    __syncthreads();
+    S.run[threadIdx.x] += S.tile_total[threadIdx.x];
+    __syncthreads();
+}
+
+template <int NV, class Loader, class Storer, bool STORE_KEY>
+__global__ void __launch_bounds__(THREADS) k_downsweep_tma(Loader ld, Storer st, PassGeom g,
+                                                           const uint32_t* counts,
+                                                           const uint32_t* totals, uint32_t* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TmaSmem<NV>& S = *reinterpret_cast<TmaSmem<NV>*>(smem_raw);
+    {
+        uint32_t t = totals[threadIdx.x];
+        uint32_t base = block_exclusive_scan_256(t, S.warp_tot, &S.total);
+        S.run[threadIdx.x] = base + counts[(int64_t)threadIdx.x * g.chunks + blockIdx.x];
+    }
+    const int64_t beg = (int64_t)blockIdx.x * g.chunk;
+    const int64_t end = min(g.n, beg + g.chunk);
+    const int64_t nfull = end > beg ? (end - beg) / TILE : 0;
+    const uint32_t arr_bytes = Loader::TILE_ELEMS * 4u;
+    if (threadIdx.x == 0) {
+        tma_bar_init(&S.bar[0]);
+        tma_bar_init(&S.bar[1]);
+        S.timed_out = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int64_t t, int b) {
+        const int64_t tbase = beg + t * TILE;
+        tma_expect(&S.bar[b], arr_bytes * Loader::NARR);
+#pragma unroll
+        for (int a = 0; a < Loader::NARR; a++)
+            tma_load_1d(&S.in[b][a][0], ld.tile_src(a, tbase), arr_bytes, &S.bar[b]);
+    };
+    if (threadIdx.x == 0 && nfull > 0) issue(0, 0);
+    for (int64_t t = 0; t < nfull; t++) {
+        const int b = (int)(t & 1);
+        if (threadIdx.x == 0 && t + 1 < nfull) {
+            // the other buffer was last read by tile t-1, finished at its
+            // closing barrier; order those reads before the async writes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(t + 1, b ^ 1);
+        }
+        const uint32_t parity = (uint32_t)((t >> 1) & 1);
+        uint32_t spins = 0;
+        while (!tma_try_wait(&S.bar[b], parity)) {
+            if (++spins >= TMA_WAIT_LIMIT) {
+                S.timed_out = 1;
+                break;
+            }
+        }
+        __syncthreads();
+        if (S.timed_out) {
+            if (threadIdx.x == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+            // give copies still in flight a bounded chance to land
+            for (int bb = 0; bb < 2; bb++) {
+                uint32_t s2 = 0;
+                while (!tma_try_wait(&S.bar[bb], parity) && ++s2 < TMA_WAIT_LIMIT) {
+                }
+            }
+            return;
+        }
+        SmemSrc<Loader> src{ld, &S.in[b][0][0], beg + t * TILE};
+        scatter_tile<NV, STORE_KEY>(src, st, g, TILE, S);
+    }
+    const int64_t tail = beg + nfull * TILE;
+    if (tail < end) {
+        GlobalSrc<Loader> src{ld, tail};
+        scatter_tile<NV, STORE_KEY>(src, st, g, (int)(end - tail), S);
+    }
+}
+
 // Record arrays (ping-pong buffers between passes).
 template <int NV>
 struct ArrLoader {
     static constexpr double KEY_BYTES = 4.0;
     static constexpr double REC_BYTES = 4.0 * (1 + NV);
+    static constexpr int NARR = 1 + NV;
+    static constexpr uint32_t TILE_ELEMS = TILE;
     const uint32_t* k;
     const uint32_t* v[NV > 0 ? NV : 1];
     __device__ __forceinline__ uint32_t key(int64_t i) const { return __ldg(k + i); }
     __device__ __forceinline__ uint32_t val(int q, int64_t i) const { return __ldg(v[q] + i); }
+    __device__ __forceinline__ const void* tile_src(int a, int64_t tbase) const {
+        return (a == 0 ? k : v[a - 1]) + tbase;
+    }
+    __device__ __forceinline__ uint32_t skey(const uint32_t* in, int li, int64_t) const { return in[li]; }
+    __device__ __forceinline__ uint32_t sval(const uint32_t* in, int q, int li, int64_t) const {
+        return in[(q + 1) * TILE + li];
+    }
+    bool tma_ok() const {
+        bool ok = ((uintptr_t)k & 15) == 0;
+        for (int q = 0; q < NV; q++) ok = ok && ((uintptr_t)v[q] & 15) == 0;
+        return ok;
+    }
 };
 
 template <int NV>
@@ -255,11 +489,11 @@ inline int chunks_per_sm() {
 }
 
 // Chunking: enough chunks to fill the GPU, each a whole number of tiles.
-inline PassGeom make_geom(int64_t n, int shift, int bits) {
+inline PassGeom make_geom(int64_t n, int shift, int bits, int per_sm = 0) {
     PassGeom g;
     g.n = n;
     const int64_t tiles = (n + TILE - 1) / TILE;
-    int64_t want = (int64_t)sm_count() * chunks_per_sm();
+    int64_t want = (int64_t)sm_count() * (per_sm > 0 ? per_sm : chunks_per_sm());
     if (want > tiles) want = tiles;
     if (want < 1) want = 1;
     const int64_t tiles_per = (tiles + want - 1) / want;
@@ -283,29 +517,52 @@ inline size_t scratch_words(int64_t n) {
 }
 
 // One pass.  'scratch' holds scratch_words(n) uint32 (device).
+// Whether the TMA-fed scatter is used (WTRI_RADIX_TMA=0 turns it off).
+inline bool tma_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("WTRI_RADIX_TMA");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 template <int NV, bool STORE_KEY, class Loader, class Storer>
 int run_pass(const Loader& ld, const Storer& st, int64_t n, int shift, int bits,
-             uint32_t* scratch, cudaStream_t s) {
+             uint32_t* scratch, cudaStream_t s, uint32_t* err) {
     if (n <= 0) return WTRI_OK;
-    PassGeom g = make_geom(n, shift, bits);
+    const bool use_tma = tma_enabled() && err != nullptr && ld.tma_ok();
+    PassGeom g = make_geom(n, shift, bits, use_tma ? 1 : 0);
     uint32_t* counts = scratch;
     uint32_t* totals = scratch + (size_t)RADIX * g.chunks;
     {
         ProfScope ps("radix_upsweep", s, (double)n * Loader::KEY_BYTES + 4.0 * RADIX * g.chunks, 1);
-        k_upsweep<Loader><<<g.chunks, THREADS, 0, s>>>(ld, g, counts);
+        WTRI_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * RADIX * (size_t)g.chunks, s));
+        k_upsweep<Loader><<<g.chunks * UP_SPLIT, THREADS, 0, s>>>(ld, g, counts);
     }
     {
         ProfScope ps("radix_digit_scan", s, 8.0 * RADIX * g.chunks, 1);
         k_digit_scan<<<RADIX, THREADS, 0, s>>>(counts, g.chunks, totals);
     }
-    const size_t smem = downsweep_smem<NV>();
-    static bool attr_set = false;  // per instantiation; idempotent
-    if (!attr_set) {
-        WTRI_CUDA(cudaFuncSetAttribute(k_downsweep<NV, Loader, Storer, STORE_KEY>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
-    {
+    if (use_tma) {
+        const size_t smem = sizeof(TmaSmem<NV>);
+        static bool attr_tma = false;  // per instantiation; idempotent
+        if (!attr_tma) {
+            WTRI_CUDA(cudaFuncSetAttribute(k_downsweep_tma<NV, Loader, Storer, STORE_KEY>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_tma = true;
+        }
+        ProfScope ps("radix_downsweep", s, (double)n * (Loader::REC_BYTES + st.rec_bytes()), 1);
+        k_downsweep_tma<NV, Loader, Storer, STORE_KEY><<<g.chunks, THREADS, smem, s>>>(
+            ld, st, g, counts, totals, err);
+    } else {
+        const size_t smem = downsweep_smem<NV>();
+        static bool attr_set = false;  // per instantiation; idempotent
+        if (!attr_set) {
+            WTRI_CUDA(cudaFuncSetAttribute(k_downsweep<NV, Loader, Storer, STORE_KEY>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_set = true;
+        }
         ProfScope ps("radix_downsweep", s, (double)n * (Loader::REC_BYTES + st.rec_bytes()), 1);
         k_downsweep<NV, Loader, Storer, STORE_KEY><<<g.chunks, THREADS, smem, s>>>(ld, st, g, counts,
                                                                                   totals);
