@@ -159,6 +159,31 @@ WTRI_API int wtri_topk_device_noalloc(const wtri_graph* g, double p, int32_t k, 
                                       double* d_weight, int32_t* d_count, void* stream);
 
 /*
+ * One shard of a query split across GPUs (Section 2 of the paper discusses
+ * partitioned triangle enumeration; the split here is this library's).
+ * Every triangle belongs to its first edge in the edge order; the edges are
+ * dealt to nshards shards in chunks of 1024 consecutive positions,
+ * round-robin.  Returns the exact top-k of the triangles whose first edge
+ * belongs to `shard` (results as wtri_topk) and their integer ranking keys
+ * (a+b+c, a^2+b^2+c^2, max or min) in keys[0..count).  The union of all
+ * shards' results holds the global top-k: merge them with wtri_merge_topk.
+ * 0 <= shard < nshards; keys has room for k entries.
+ */
+WTRI_API int wtri_topk_shard(const wtri_graph* g, double p, int32_t k, int32_t shard,
+                             int32_t nshards, wtri_result* out, uint64_t* keys);
+
+/*
+ * Host-side merge of per-shard results: the k best of all parts under the
+ * total order (key desc, triple asc), with their weights and (if out_keys
+ * is not NULL) keys.  Part i has counts[i] entries in tris[i], weights[i],
+ * keys[i].  Parts must be disjoint (WTRI_EINVAL if a triangle repeats).
+ * Pure host code: no device needed.
+ */
+WTRI_API int wtri_merge_topk(int32_t nparts, const int32_t* counts, const wtri_tri* const* tris,
+                             const double* const* weights, const uint64_t* const* keys, int32_t k,
+                             wtri_result* out, uint64_t* out_keys);
+
+/*
  * Batched exact top-k: query i asks for the top-k[i] triangles of gs[i] at
  * p[i] (same problem and result format as wtri_topk, results in outs[i]).
  * All queries run in one launch sequence captured in a CUDA graph on the

@@ -80,9 +80,12 @@ def lib():
         L.or_topk_of_sampled.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, u8p,
                                          ctypes.c_int, ctypes.c_int64, ctypes.c_int, i32p, u64p, f64p,
                                          I64P, I64P]
+        L.or_topk_shard.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, i64p, ctypes.c_int,
+                                    ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, i32p,
+                                    u64p, f64p, I64P, I64P]
         for f in (L.or_validate, L.or_sym_csr, L.or_edge_order, L.or_oriented_csr,
                   L.or_score, L.or_topk, L.or_count_triangles, L.or_sample_edges,
-                  L.or_topk_of_sampled):
+                  L.or_topk_of_sampled, L.or_topk_shard):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -246,6 +249,30 @@ def sample_topk(n, u, v, w, p, k, nsamples, seed, nthreads=0):
     r = topk_of_marked(n, u, v, w, mark[:m], p, k, nthreads)
     r["sampled_edges"] = int((hits > 0).sum())
     return r
+
+
+def topk_shard(n, u, v, w, p, k, shard, nshards, chunk_shift=10):
+    """Top-k of the triangles whose first edge in the edge order falls in
+    shard `shard` (edge positions dealt in chunks of 2^chunk_shift,
+    round-robin over nshards)."""
+    u, v, w = _arr(u), _arr(v), _arr(w)
+    m = u.shape[0]
+    perm = edge_order(w)
+    rank = np.empty(max(m, 1), np.int64)
+    rank[perm] = np.arange(m, dtype=np.int64)
+    k = int(k)
+    tri = np.zeros(3 * max(k, 1), np.int32)
+    key = np.zeros(max(k, 1), np.uint64)
+    val = np.zeros(max(k, 1), np.float64)
+    cnt = ctypes.c_int64(0)
+    ntri = ctypes.c_int64(0)
+    rc = lib().or_topk_shard(n, m, u, v, w, rank, pcode(p), k, int(shard), int(nshards), int(chunk_shift),
+                             tri, key, val, ctypes.byref(cnt), ctypes.byref(ntri))
+    if rc != 0:
+        raise OracleError(f"or_topk_shard failed (rc={rc})")
+    c = int(cnt.value)
+    return {"tri": tri[: 3 * c].reshape(c, 3), "key": key[:c], "value": val[:c], "count": c,
+            "ntri": int(ntri.value)}
 
 
 def count_triangles(n, u, v, w=None):

@@ -685,3 +685,87 @@ int or_topk_of_sampled(int32_t n, int64_t m, const int32_t* u, const int32_t* v,
     free(oeid);
     return rc;
 }
+
+/*
+ * Top-k of the triangles whose first edge in the edge order (weight desc,
+ * index asc) lies in shard `shard` of `nshards`, the edges being dealt to
+ * shards in chunks of 2^chunk_shift consecutive positions, round-robin.
+ * rank[i] is input edge i's position in the edge order.  Brute force over
+ * every triangle (NodeIterator++), like or_topk.
+ */
+int or_topk_shard(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int32_t* w,
+                  const int64_t* rank, int pcode, int64_t k, int32_t shard, int32_t nshards,
+                  int chunk_shift, int32_t* tri, uint64_t* key, double* value, int64_t* count,
+                  int64_t* ntri) {
+    *count = 0;
+    *ntri = 0;
+    if (pcode < 0 || pcode > 3 || k <= 0 || nshards < 1 || shard < 0 || shard >= nshards)
+        return OR_EINVAL;
+    int64_t* orow = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    int32_t* ocol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    int32_t* owt = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    int64_t* oeid = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m + 1));
+    if (!orow || !ocol || !owt || !oeid) {
+        free(orow); free(ocol); free(owt); free(oeid);
+        return OR_ENOMEM;
+    }
+    int rc = or_oriented_csr(n, m, u, v, w, orow, ocol, owt, oeid);
+    if (rc != OR_OK) {
+        free(orow); free(ocol); free(owt); free(oeid);
+        return rc;
+    }
+    or_heap hp;
+    hp.cap = k;
+    hp.size = 0;
+    hp.h = (or_tri*)malloc(sizeof(or_tri) * (size_t)k);
+    int64_t total = 0;
+    if (!hp.h) rc = OR_ENOMEM;
+    for (int32_t a = 0; a < n && rc == OR_OK; a++) {
+        for (int64_t i = orow[a]; i < orow[a + 1]; i++) {
+            int32_t b = ocol[i];
+            int64_t p = orow[a], pe = orow[a + 1];
+            int64_t q = orow[b], qe = orow[b + 1];
+            while (p < pe && q < qe) {
+                if (ocol[p] < ocol[q]) {
+                    p++;
+                } else if (ocol[p] > ocol[q]) {
+                    q++;
+                } else {
+                    int64_t r0 = rank[oeid[i]], r1 = rank[oeid[p]], r2 = rank[oeid[q]];
+                    int64_t own = r0 < r1 ? r0 : r1;
+                    own = own < r2 ? own : r2;
+                    if ((int32_t)((own >> chunk_shift) % nshards) == shard) {
+                        or_tri x;
+                        x.key = tri_key(pcode, owt[i], owt[p], owt[q]);
+                        x.t[0] = a;
+                        x.t[1] = b;
+                        x.t[2] = ocol[p];
+                        sort3(x.t);
+                        heap_offer(&hp, &x);
+                        total++;
+                    }
+                    p++;
+                    q++;
+                }
+            }
+        }
+    }
+    if (rc == OR_OK) {
+        qsort(hp.h, (size_t)hp.size, sizeof(or_tri), cmp_tri);
+        for (int64_t i = 0; i < hp.size; i++) {
+            tri[3 * i + 0] = hp.h[i].t[0];
+            tri[3 * i + 1] = hp.h[i].t[1];
+            tri[3 * i + 2] = hp.h[i].t[2];
+            key[i] = hp.h[i].key;
+            value[i] = tri_value(pcode, hp.h[i].key);
+        }
+        *count = hp.size;
+        *ntri = total;
+    }
+    free(hp.h);
+    free(orow);
+    free(ocol);
+    free(owt);
+    free(oeid);
+    return rc;
+}

@@ -17,13 +17,15 @@ from .wtri import (  # noqa: F401
     build_csr,
     lib,
     lib_path,
+    merge_topk,
     sample_edges,
     sample_topk,
     topk,
     topk_batch,
     topk_device,
     topk_device_noalloc,
+    topk_shard,
 )
 
-__all__ = ["ARRAYS", "Graph", "Server", "WtriError", "WtriUnavailable", "build_csr", "lib", "lib_path",
+__all__ = ["ARRAYS", "Graph", "Server", "WtriError", "WtriUnavailable", "build_csr", "lib", "lib_path", "merge_topk", "topk_shard",
            "sample_edges", "sample_topk", "topk", "topk_batch", "topk_device", "topk_device_noalloc"]

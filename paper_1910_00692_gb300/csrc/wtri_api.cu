@@ -7,6 +7,7 @@
 
 #include <new>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "wtri_internal.cuh"
@@ -64,19 +65,21 @@ int check_query(const wtri_graph* g, int32_t k) {
 // Runs a device query into scratch outputs, copies them to the caller's host
 // result, retrying with larger device buffers if a bounded buffer filled.
 template <class Launch>
-int host_result_query(const wtri_graph* g, int32_t k, wtri_result* out, Launch launch) {
+int host_result_query(const wtri_graph* g, int32_t k, wtri_result* out, Launch launch,
+                      uint64_t* hkeys = nullptr) {
     cudaStream_t s = g->stream;
     const size_t tri_bytes = sizeof(wtri_tri) * (size_t)k;
     const size_t w_bytes = sizeof(double) * (size_t)k;
     void* buf = nullptr;
-    WTRI_CUDA(cudaMallocAsync(&buf, tri_bytes + w_bytes + 64, s));
+    WTRI_CUDA(cudaMallocAsync(&buf, tri_bytes + 2 * w_bytes + 64, s));
     wtri_tri* d_tri = (wtri_tri*)buf;
     double* d_w = (double*)((char*)buf + ((tri_bytes + 15) & ~size_t(15)));
-    int32_t* d_cnt = (int32_t*)((char*)d_w + w_bytes);
+    unsigned long long* d_key = (unsigned long long*)((char*)d_w + w_bytes);
+    int32_t* d_cnt = (int32_t*)((char*)d_key + w_bytes);
     int rc = WTRI_OK;
     int32_t status = 0;
     for (int scale = 1; scale <= 64; scale *= 8) {
-        rc = launch(d_tri, d_w, d_cnt, s, scale);
+        rc = launch(d_tri, d_w, d_cnt, s, scale, hkeys ? d_key : nullptr);
         if (rc != WTRI_OK) break;
         cudaError_t e = cudaMemcpyAsync(&status, d_cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -98,6 +101,8 @@ int host_result_query(const wtri_graph* g, int32_t k, wtri_result* out, Launch l
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(out->weight, d_w, sizeof(double) * (size_t)status,
                                 cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && hkeys)
+            e = cudaMemcpyAsync(hkeys, d_key, 8 * (size_t)status, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_error(e, "result copy", __FILE__, __LINE__);
     }
@@ -155,9 +160,70 @@ WTRI_API int wtri_topk(const wtri_graph* g, double p, int32_t k, wtri_result* ou
     if (out->capacity < k) return set_error(WTRI_EINVAL, "result capacity below k");
     if (g->d.m == 0) return WTRI_OK;
     return host_result_query(g, k, out,
-                             [&](wtri_tri* t, double* wv, int32_t* c, cudaStream_t s, int scale) {
+                             [&](wtri_tri* t, double* wv, int32_t* c, cudaStream_t s, int scale,
+                                 unsigned long long*) {
                                  return topk_device(g, code, k, t, wv, c, s, scale);
                              });
+}
+
+WTRI_API int wtri_topk_shard(const wtri_graph* g, double p, int32_t k, int32_t shard,
+                             int32_t nshards, wtri_result* out, uint64_t* keys) {
+    if (!out) return set_error(WTRI_EINVAL, "out is NULL");
+    out->count = 0;
+    int code = 0;
+    WTRI_TRY(check_query(g, k));
+    WTRI_TRY(p_to_code(p, &code));
+    if (nshards < 1 || shard < 0 || shard >= nshards)
+        return set_error(WTRI_EINVAL, "need 0 <= shard < nshards");
+    if (!out->tris || !out->weight || !keys) return set_error(WTRI_EINVAL, "result arrays are NULL");
+    if (out->capacity < k) return set_error(WTRI_EINVAL, "result capacity below k");
+    if (g->d.m == 0) return WTRI_OK;
+    return host_result_query(g, k, out,
+                             [&](wtri_tri* t, double* wv, int32_t* c, cudaStream_t s, int scale,
+                                 unsigned long long* dk) {
+                                 return topk_device(g, code, k, t, wv, c, s, scale, shard, nshards, dk);
+                             },
+                             keys);
+}
+
+WTRI_API int wtri_merge_topk(int32_t nparts, const int32_t* counts, const wtri_tri* const* tris,
+                             const double* const* weights, const uint64_t* const* keys, int32_t k,
+                             wtri_result* out, uint64_t* out_keys) {
+    if (!out) return set_error(WTRI_EINVAL, "out is NULL");
+    out->count = 0;
+    if (nparts < 0 || k <= 0) return set_error(WTRI_EINVAL, "need nparts >= 0 and k > 0");
+    if (nparts > 0 && (!counts || !tris || !weights || !keys))
+        return set_error(WTRI_EINVAL, "NULL part arrays");
+    if (!out->tris || !out->weight || out->capacity < k)
+        return set_error(WTRI_EINVAL, "result arrays NULL or too small");
+    struct Ent {
+        uint64_t key;
+        wtri_tri t;
+        double w;
+    };
+    std::vector<Ent> all;
+    for (int32_t i = 0; i < nparts; i++) {
+        if (counts[i] < 0) return set_error(WTRI_EINVAL, "negative part count");
+        for (int32_t j = 0; j < counts[i]; j++) all.push_back({keys[i][j], tris[i][j], weights[i][j]});
+    }
+    auto before = [](const Ent& x, const Ent& y) {
+        if (x.key != y.key) return x.key > y.key;
+        if (x.t.a != y.t.a) return x.t.a < y.t.a;
+        if (x.t.b != y.t.b) return x.t.b < y.t.b;
+        return x.t.c < y.t.c;
+    };
+    const size_t keep = std::min<size_t>(all.size(), (size_t)k);
+    std::partial_sort(all.begin(), all.begin() + (long)keep, all.end(), before);
+    for (size_t i = 1; i < keep; i++)
+        if (!before(all[i - 1], all[i]))
+            return set_error(WTRI_EINVAL, "the parts share a triangle (shards must be disjoint)");
+    for (size_t i = 0; i < keep; i++) {
+        out->tris[i] = all[i].t;
+        out->weight[i] = all[i].w;
+        if (out_keys) out_keys[i] = all[i].key;
+    }
+    out->count = (int32_t)keep;
+    return WTRI_OK;
 }
 
 WTRI_API int wtri_topk_device(const wtri_graph* g, double p, int32_t k, wtri_tri* d_tris,
@@ -188,7 +254,8 @@ WTRI_API int wtri_sample_topk(const wtri_graph* g, double p, int32_t k, int64_t 
     if (out->capacity < k) return set_error(WTRI_EINVAL, "result capacity below k");
     if (g->d.m == 0 || nsamples == 0) return WTRI_OK;
     return host_result_query(g, k, out,
-                             [&](wtri_tri* t, double* wv, int32_t* c, cudaStream_t s, int scale) {
+                             [&](wtri_tri* t, double* wv, int32_t* c, cudaStream_t s, int scale,
+                                 unsigned long long*) {
                                  return sample_topk_device(g, code, k, nsamples, seed, t, wv, c, s,
                                                            scale);
                              });

@@ -303,6 +303,8 @@ int batch_plan_launch(BatchPlan* P, void* dbuf, cudaStream_t s, int use_graph) {
         q.slist = nullptr;
         q.long_count = lcnt;
         q.qid = i;
+        q.shard = 0;
+        q.nshards = 1;
         c0 += P->caps[(size_t)i];
     }
     BatchDev Bd;

@@ -100,7 +100,8 @@ int build_graph(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const 
 // Exact top-k (wtri_topk.cu).  Writes device outputs; status (count or a
 // negative code) to d_count.  'retry_scale' enlarges the scratch buffers.
 int topk_device(const wtri_graph* g, int pcode, int32_t k, wtri_tri* d_tris, double* d_weight,
-                int32_t* d_count, cudaStream_t stream, int retry_scale);
+                int32_t* d_count, cudaStream_t stream, int retry_scale, int shard = 0,
+                int nshards = 1, unsigned long long* d_keys = nullptr);
 
 // Edge sampling (wtri_topk.cu).
 int sample_topk_device(const wtri_graph* g, int pcode, int32_t k, int64_t nsamples,

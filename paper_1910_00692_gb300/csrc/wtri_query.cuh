@@ -91,7 +91,14 @@ struct Query {
     // and the query's index in a batch (stored in deferred items).
     uint32_t* long_count;
     int32_t qid;
+    // Sharding (multi-GPU split of one query): this query owns the edges
+    // whose chunk (position >> SHARD_SHIFT) is congruent to shard modulo
+    // nshards; nshards <= 1 means every edge.
+    int32_t shard;
+    int32_t nshards;
 };
+
+constexpr int SHARD_SHIFT = 10;  // 1024-edge chunks of the edge order, dealt round-robin
 
 __device__ __forceinline__ bool drawn(const Query& q, int32_t r) {
     return (__ldg(q.smark + (r >> 5)) >> (r & 31)) & 1u;
@@ -228,6 +235,9 @@ __device__ __forceinline__ bool process_edge(const DevGraph& G, const Query& q,
         atomicMax(&q.st->stop_rev, STOP_NONE - (uint32_t)r);
         return false;
     }
+    if (!SAMPLED && q.nshards > 1 &&
+        (int32_t)(((uint32_t)r >> SHARD_SHIFT) % (uint32_t)q.nshards) != q.shard)
+        return true;  // owned by another shard
     const int32_t u = __ldg(G.ord_u + r), v = __ldg(G.ord_v + r);
     // Exact mode scans what comes after r in each list; sampled mode scans
     // whole lists (the other two edges may be heavier than a drawn edge).
@@ -737,7 +747,8 @@ __device__ __forceinline__ bool before(unsigned long long ka, int4 a, unsigned l
 // total order; one warp per candidate.  Also writes the status word.
 template <int P>
 __device__ __forceinline__ void rank_one(const Query& q, uint32_t i, wtri_tri* out_tri,
-                                         double* out_w, int32_t* out_count) {
+                                         double* out_w, int32_t* out_count,
+                                         unsigned long long* out_key = nullptr) {
     const uint32_t err = *(volatile uint32_t*)&q.st->err;
     const uint32_t n = min(*(volatile uint32_t*)&q.st->count, q.cap);
     const int lane = threadIdx.x & 31;
@@ -764,15 +775,17 @@ __device__ __forceinline__ void rank_one(const Query& q, uint32_t i, wtri_tri* o
         else if (P == P_TWO) val = sqrt((double)ki / 3.0);
         else val = (double)ki;
         out_w[rank] = val;
+        if (out_key) out_key[rank] = ki;
     }
 }
 
 template <int P>
 __global__ void __launch_bounds__(256) k_rank_scatter(Query q, wtri_tri* out_tri, double* out_w,
-                                                      int32_t* out_count) {
+                                                      int32_t* out_count,
+                                                      unsigned long long* out_key) {
     const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= (uint32_t)max(q.k, 1)) return;
-    rank_one<P>(q, i, out_tri, out_w, out_count);
+    rank_one<P>(q, i, out_tri, out_w, out_count, out_key);
 }
 
 __device__ void final_select(const Query& q, SelectSmem& S) {

@@ -68,6 +68,37 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_
     return r;
 }
 
+// Exclusive scan of one value per thread over an NT-thread block (NT <= 1024).
+template <int NT>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* warp_tot,
+                                                         uint32_t* total) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < NW ? warp_tot[lane] : 0;
+        uint32_t ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        if (lane < NW) warp_tot[lane] = ti - t;
+        if (lane == NW - 1) *total = ti;
+    }
+    __syncthreads();
+    uint32_t r = warp_tot[w] + inc - x;
+    __syncthreads();
+    return r;
+}
+
 struct PassGeom {
     int64_t n;        // records
     int64_t chunk;    // records per chunk (multiple of TILE)
@@ -267,15 +298,20 @@ __device__ __forceinline__ bool tma_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+constexpr int TMA_THREADS = 256;  // one CTA per SM holds the whole pipeline (512 measured slower)
+constexpr int TMA_WARPS = TMA_THREADS / 32;
+constexpr int TMA_ITEMS = TILE / TMA_THREADS;
+static_assert(TMA_ITEMS * TMA_THREADS == TILE, "TMA tile matches the plain tile");
+
 template <int NV>
 struct TmaSmem {
     uint32_t in[2][TMA_ARRS][TILE];  // source arrays of the current / next tile
     uint32_t stage[NV + 1][TILE];
-    uint32_t cnt[WARPS][RADIX];
+    uint32_t cnt[TMA_WARPS][RADIX];
     uint32_t run[RADIX];
     uint32_t tile_start[RADIX];
     uint32_t tile_total[RADIX];
-    uint32_t warp_tot[WARPS];
+    uint32_t warp_tot[32];
     uint32_t total;
     int timed_out;
     uint64_t bar[2];
@@ -300,24 +336,25 @@ struct GlobalSrc {
     __device__ __forceinline__ uint32_t val(int q, int li) const { return ld.val(q, tbase + li); }
 };
 
-// Rank, stage and scatter one tile of tcount records (all threads).
-template <int NV, bool STORE_KEY, class Src, class Storer, class Smem>
+// Rank, stage and scatter one tile of tcount records (all NT threads).
+template <int NT, int NV, bool STORE_KEY, class Src, class Storer, class Smem>
 __device__ __forceinline__ void scatter_tile(const Src& src, const Storer& st, const PassGeom& g,
                                              int tcount, Smem& S) {
+    constexpr int NW = NT / 32, IT = TILE / NT;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
-    for (int i = threadIdx.x; i < WARPS * RADIX; i += THREADS) (&S.cnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < NW * RADIX; i += NT) (&S.cnt[0][0])[i] = 0;
     __syncthreads();
-    uint32_t key[ITEMS];
-    uint32_t rank[ITEMS];
+    uint32_t key[IT];
+    uint32_t rank[IT];
 #pragma unroll
-    for (int j = 0; j < ITEMS; j++) {
-        const int li = w * 32 * ITEMS + j * 32 + lane;
+    for (int j = 0; j < IT; j++) {
+        const int li = w * 32 * IT + j * 32 + lane;
         key[j] = li < tcount ? src.key(li) : 0u;
     }
 #pragma unroll
-    for (int j = 0; j < ITEMS; j++) {
-        const int li = w * 32 * ITEMS + j * 32 + lane;
+    for (int j = 0; j < IT; j++) {
+        const int li = w * 32 * IT + j * 32 + lane;
         const bool valid = li < tcount;
         const uint32_t d = valid ? ((key[j] >> g.shift) & g.mask) : (uint32_t)RADIX;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
@@ -328,25 +365,29 @@ __device__ __forceinline__ void scatter_tile(const Src& src, const Storer& st, c
         __syncwarp();
     }
     __syncthreads();
-    {
+    {   // per digit (first RADIX threads): warp offsets, tile totals and starts
         const int d = threadIdx.x;
         uint32_t s = 0;
+        if (d < RADIX) {
 #pragma unroll
-        for (int k = 0; k < WARPS; k++) {
-            uint32_t c = S.cnt[k][d];
-            S.cnt[k][d] = s;
-            s += c;
+            for (int k = 0; k < NW; k++) {
+                uint32_t c = S.cnt[k][d];
+                S.cnt[k][d] = s;
+                s += c;
+            }
+            S.tile_total[d] = s;
         }
-        S.tile_total[d] = s;
-        uint32_t st0 = block_exclusive_scan_256(s, S.warp_tot, &S.total);
-        S.tile_start[d] = st0;
+        const uint32_t st0 = block_exclusive_scan<NT>(d < RADIX ? s : 0u, S.warp_tot, &S.total);
+        if (d < RADIX) {
+            S.tile_start[d] = st0;
 #pragma unroll
-        for (int k = 0; k < WARPS; k++) S.cnt[k][d] += st0;
+            for (int k = 0; k < NW; k++) S.cnt[k][d] += st0;
+        }
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < ITEMS; j++) {
-        const int li = w * 32 * ITEMS + j * 32 + lane;
+    for (int j = 0; j < IT; j++) {
+        const int li = w * 32 * IT + j * 32 + lane;
         if (li < tcount) {
             const uint32_t d = (key[j] >> g.shift) & g.mask;
             const uint32_t pos = rank[j] + S.cnt[w][d];
@@ -357,8 +398,8 @@ __device__ __forceinline__ void scatter_tile(const Src& src, const Storer& st, c
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < ITEMS; i++) {
-        const int p = i * THREADS + threadIdx.x;
+    for (int i = 0; i < IT; i++) {
+        const int p = i * NT + threadIdx.x;
         if (p < tcount) {
             const uint32_t k = S.stage[0][p];
             const uint32_t d = (k >> g.shift) & g.mask;
@@ -369,20 +410,21 @@ __device__ __forceinline__ void scatter_tile(const Src& src, const Storer& st, c
         }
     }
     __syncthreads();
-    S.run[threadIdx.x] += S.tile_total[threadIdx.x];
+    if (threadIdx.x < RADIX) S.run[threadIdx.x] += S.tile_total[threadIdx.x];
     __syncthreads();
 }
 
 template <int NV, class Loader, class Storer, bool STORE_KEY>
-__global__ void __launch_bounds__(THREADS) k_downsweep_tma(Loader ld, Storer st, PassGeom g,
-                                                           const uint32_t* counts,
-                                                           const uint32_t* totals, uint32_t* err) {
+__global__ void __launch_bounds__(TMA_THREADS) k_downsweep_tma(Loader ld, Storer st, PassGeom g,
+                                                               const uint32_t* counts,
+                                                               const uint32_t* totals, uint32_t* err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TmaSmem<NV>& S = *reinterpret_cast<TmaSmem<NV>*>(smem_raw);
     {
-        uint32_t t = totals[threadIdx.x];
-        uint32_t base = block_exclusive_scan_256(t, S.warp_tot, &S.total);
-        S.run[threadIdx.x] = base + counts[(int64_t)threadIdx.x * g.chunks + blockIdx.x];
+        const int d = threadIdx.x;
+        const uint32_t t = d < RADIX ? totals[d] : 0u;
+        const uint32_t base = block_exclusive_scan<TMA_THREADS>(t, S.warp_tot, &S.total);
+        if (d < RADIX) S.run[d] = base + counts[(int64_t)d * g.chunks + blockIdx.x];
     }
     const int64_t beg = (int64_t)blockIdx.x * g.chunk;
     const int64_t end = min(g.n, beg + g.chunk);
@@ -431,12 +473,12 @@ __global__ void __launch_bounds__(THREADS) k_downsweep_tma(Loader ld, Storer st,
             return;
         }
         SmemSrc<Loader> src{ld, &S.in[b][0][0], beg + t * TILE};
-        scatter_tile<NV, STORE_KEY>(src, st, g, TILE, S);
+        scatter_tile<TMA_THREADS, NV, STORE_KEY>(src, st, g, TILE, S);
     }
     const int64_t tail = beg + nfull * TILE;
     if (tail < end) {
         GlobalSrc<Loader> src{ld, tail};
-        scatter_tile<NV, STORE_KEY>(src, st, g, (int)(end - tail), S);
+        scatter_tile<TMA_THREADS, NV, STORE_KEY>(src, st, g, (int)(end - tail), S);
     }
 }
 
@@ -553,7 +595,7 @@ int run_pass(const Loader& ld, const Storer& st, int64_t n, int shift, int bits,
             attr_tma = true;
         }
         ProfScope ps("radix_downsweep", s, (double)n * (Loader::REC_BYTES + st.rec_bytes()), 1);
-        k_downsweep_tma<NV, Loader, Storer, STORE_KEY><<<g.chunks, THREADS, smem, s>>>(
+        k_downsweep_tma<NV, Loader, Storer, STORE_KEY><<<g.chunks, TMA_THREADS, smem, s>>>(
             ld, st, g, counts, totals, err);
     } else {
         const size_t smem = downsweep_smem<NV>();

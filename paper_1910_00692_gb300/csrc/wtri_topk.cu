@@ -9,7 +9,7 @@ namespace {
 
 template <int P>
 int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight, int32_t* d_count,
-              cudaStream_t s, int scale) {
+              cudaStream_t s, int scale, int shard, int nshards, unsigned long long* d_keys) {
     const DevGraph& G = g->d;
     const int64_t m = G.m;
     const uint32_t cap = (uint32_t)std::min<int64_t>(
@@ -40,6 +40,8 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
     q.slist = nullptr;
     q.long_count = &q.st->long_count;
     q.qid = 0;
+    q.shard = shard;
+    q.nshards = nshards;
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
 
     const size_t lsmem = (size_t)STAGE_MAX * 4 + 16;
@@ -73,7 +75,8 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
     {
         ProfScope ps("topk_final", s, 0.0, 2);
         k_final_select<<<1, SBLK, 0, s>>>(q);
-        k_rank_scatter<P><<<ceil_div_u(std::max(k, 1), 8), 256, 0, s>>>(q, d_tris, d_weight, d_count);
+        k_rank_scatter<P><<<ceil_div_u(std::max(k, 1), 8), 256, 0, s>>>(q, d_tris, d_weight, d_count,
+                                                                        d_keys);
     }
     WTRI_CUDA(cudaGetLastError());
     WTRI_CUDA(cudaFreeAsync(buf, s));
@@ -309,6 +312,8 @@ int run_sample(const wtri_graph* g, int32_t k, int64_t nsamples, uint64_t seed, 
     q.slist = list;
     q.long_count = &q.st->long_count;
     q.qid = 0;
+    q.shard = 0;
+    q.nshards = 1;
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
     ProfScope whole(P == P_ONE ? "sample_p=1" : "sample_p=2", s, 0.0, 0);
     WTRI_TRY(draw_samples<P>(g, nsamples, seed, mark, s));
@@ -350,7 +355,8 @@ int run_sample(const wtri_graph* g, int32_t k, int64_t nsamples, uint64_t seed, 
     {
         ProfScope ps("topk_final", s, 0.0, 2);
         k_final_select<<<1, SBLK, 0, s>>>(q);
-        k_rank_scatter<P><<<ceil_div_u(std::max(k, 1), 8), 256, 0, s>>>(q, d_tris, d_weight, d_count);
+        k_rank_scatter<P><<<ceil_div_u(std::max(k, 1), 8), 256, 0, s>>>(q, d_tris, d_weight, d_count,
+                                                                    nullptr);
     }
     WTRI_CUDA(cudaGetLastError());
     WTRI_CUDA(cudaFreeAsync(buf, s));
@@ -360,12 +366,17 @@ int run_sample(const wtri_graph* g, int32_t k, int64_t nsamples, uint64_t seed, 
 }  // namespace
 
 int topk_device(const wtri_graph* g, int pcode, int32_t k, wtri_tri* d_tris, double* d_weight,
-                int32_t* d_count, cudaStream_t stream, int retry_scale) {
+                int32_t* d_count, cudaStream_t stream, int retry_scale, int shard, int nshards,
+                unsigned long long* d_keys) {
     switch (pcode) {
-        case P_MIN: return run_query<P_MIN>(g, k, d_tris, d_weight, d_count, stream, retry_scale);
-        case P_ONE: return run_query<P_ONE>(g, k, d_tris, d_weight, d_count, stream, retry_scale);
-        case P_TWO: return run_query<P_TWO>(g, k, d_tris, d_weight, d_count, stream, retry_scale);
-        default: return run_query<P_MAX>(g, k, d_tris, d_weight, d_count, stream, retry_scale);
+        case P_MIN:
+            return run_query<P_MIN>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys);
+        case P_ONE:
+            return run_query<P_ONE>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys);
+        case P_TWO:
+            return run_query<P_TWO>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys);
+        default:
+            return run_query<P_MAX>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys);
     }
 }
 
@@ -445,6 +456,8 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
     q.slist = nullptr;
     q.long_count = &q.st->long_count;
     q.qid = 0;
+    q.shard = 0;
+    q.nshards = 1;
     // The array keeps the previous call's contents: reset the status word
     // (counters, threshold, stop flag, error bits).
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
@@ -468,7 +481,8 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
         size *= ROUND_GROWTH;
     }
     k_final_select<<<1, SBLK, 0, s>>>(q);
-    k_rank_scatter<P><<<ceil_div_u(std::max(k, 1), 8), 256, 0, s>>>(q, d_tris, d_weight, d_count);
+    k_rank_scatter<P><<<ceil_div_u(std::max(k, 1), 8), 256, 0, s>>>(q, d_tris, d_weight, d_count,
+                                                                    nullptr);
     count_launches(2);
     WTRI_CUDA(cudaGetLastError());
     return WTRI_OK;

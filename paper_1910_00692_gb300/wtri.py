@@ -96,6 +96,8 @@ def lib():
     L.wtri_graph_copy_array.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
     L.wtri_sample_edges.argtypes = [vp, f64, i64, ctypes.c_uint64, vp, i64]
     L.wtri_topk_batch.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_Result)]
+    L.wtri_topk_shard.argtypes = [vp, f64, i32, i32, i32, ctypes.POINTER(_Result), vp]
+    L.wtri_merge_topk.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(_Result), vp]
     u64 = ctypes.c_uint64
     L.wtri_server_create.argtypes = [u64, i32, ctypes.POINTER(vp)]
     L.wtri_server_add_graph.argtypes = [vp, vp, ctypes.POINTER(i32)]
@@ -113,7 +115,8 @@ def lib():
               L.wtri_topk_device_noalloc,
               L.wtri_sample_topk, L.wtri_graph_copy_array, L.wtri_sample_edges,
               L.wtri_topk_batch, L.wtri_server_create, L.wtri_server_add_graph, L.wtri_submit,
-              L.wtri_poll, L.wtri_poll_timed, L.wtri_server_stats):
+              L.wtri_poll, L.wtri_poll_timed, L.wtri_server_stats, L.wtri_topk_shard,
+              L.wtri_merge_topk):
         f.restype = ctypes.c_int
     _lib = L
     return L
@@ -240,6 +243,41 @@ def sample_topk(g: Graph, p: float, k: int, nsamples: int, seed: int):
     return _host_query(lambda r: lib().wtri_sample_topk(g.handle, float(p), int(k), int(nsamples),
                                                          ctypes.c_uint64(seed & (2**64 - 1)), r),
                        int(k))
+
+
+def topk_shard(g: Graph, p: float, k: int, shard: int, nshards: int):
+    """wtri_topk_shard: exact top-k of the triangles owned by one shard.
+    Returns (tris, weights, keys)."""
+    tris = np.zeros((max(k, 1), 3), dtype=np.int32)
+    wts = np.zeros(max(k, 1), dtype=np.float64)
+    keys = np.zeros(max(k, 1), dtype=np.uint64)
+    res = _Result(tris.ctypes.data, wts.ctypes.data, max(k, 1), 0)
+    _check(lib().wtri_topk_shard(g.handle, float(p), int(k), int(shard), int(nshards), ctypes.byref(res),
+                                 keys.ctypes.data_as(ctypes.c_void_p)))
+    c = res.count
+    return tris[:c].copy(), wts[:c].copy(), keys[:c].copy()
+
+
+def merge_topk(parts, k: int):
+    """wtri_merge_topk (host code, no device): parts = [(tris, weights,
+    keys), ...] -> the k best (tris, weights, keys)."""
+    n = len(parts)
+    prepared = [(np.ascontiguousarray(t, dtype=np.int32).reshape(-1, 3),
+                 np.ascontiguousarray(w, dtype=np.float64),
+                 np.ascontiguousarray(kk, dtype=np.uint64)) for t, w, kk in parts]
+    counts = np.array([p_[0].shape[0] for p_ in prepared], dtype=np.int32)
+    tp = (ctypes.c_void_p * max(n, 1))(*[p_[0].ctypes.data for p_ in prepared])
+    wp = (ctypes.c_void_p * max(n, 1))(*[p_[1].ctypes.data for p_ in prepared])
+    kp = (ctypes.c_void_p * max(n, 1))(*[p_[2].ctypes.data for p_ in prepared])
+    tris = np.zeros((max(k, 1), 3), dtype=np.int32)
+    wts = np.zeros(max(k, 1), dtype=np.float64)
+    keys = np.zeros(max(k, 1), dtype=np.uint64)
+    res = _Result(tris.ctypes.data, wts.ctypes.data, max(k, 1), 0)
+    _check(lib().wtri_merge_topk(n, counts.ctypes.data_as(ctypes.c_void_p), ctypes.cast(tp, ctypes.c_void_p),
+                                 ctypes.cast(wp, ctypes.c_void_p), ctypes.cast(kp, ctypes.c_void_p), int(k),
+                                 ctypes.byref(res), keys.ctypes.data_as(ctypes.c_void_p)))
+    c = res.count
+    return tris[:c].copy(), wts[:c].copy(), keys[:c].copy()
 
 
 def topk_batch(graphs, ps, ks):
