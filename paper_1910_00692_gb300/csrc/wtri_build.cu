@@ -174,7 +174,7 @@ struct EdgeLoader {
     static constexpr double KEY_BYTES = 4.0;   // w
     static constexpr double REC_BYTES = 12.0;  // u, v, w
     static constexpr int NARR = 3;             // TMA source arrays: w, u, v
-    static constexpr uint32_t TILE_ELEMS = radix::TILE;
+    static constexpr uint32_t TILE_ELEMS = radix::TT;
     const int32_t* u;
     const int32_t* v;
     const int32_t* w;
@@ -192,7 +192,7 @@ struct EdgeLoader {
         return (uint32_t)(wmax - (int32_t)in[li]);
     }
     __device__ __forceinline__ uint32_t sval(const uint32_t* in, int q, int li, int64_t) const {
-        return in[(q + 1) * radix::TILE + li];
+        return in[(q + 1) * radix::TT + li];
     }
     bool tma_ok() const {
         return (((uintptr_t)u | (uintptr_t)v | (uintptr_t)w) & 15) == 0;
@@ -219,7 +219,7 @@ struct OrderEntryLoader {
     static constexpr double KEY_BYTES = 4.0;  // u or v: 8 bytes per edge, two entries
     static constexpr double REC_BYTES = 6.0;  // u, v, w: 12 bytes per edge, two entries
     static constexpr int NARR = 3;            // TMA source arrays: ou, ov, ow (half a tile each)
-    static constexpr uint32_t TILE_ELEMS = radix::TILE / 2;
+    static constexpr uint32_t TILE_ELEMS = radix::TT / 2;
     const int32_t* ou;
     const int32_t* ov;
     const int32_t* ow;
@@ -227,11 +227,11 @@ struct OrderEntryLoader {
         return (a == 0 ? ou : (a == 1 ? ov : ow)) + (tbase >> 1);
     }
     __device__ __forceinline__ uint32_t skey(const uint32_t* in, int li, int64_t) const {
-        return in[((li & 1) ? radix::TILE : 0) + (li >> 1)];
+        return in[((li & 1) ? radix::TT : 0) + (li >> 1)];
     }
     __device__ __forceinline__ uint32_t sval(const uint32_t* in, int q, int li, int64_t tbase) const {
-        if (q == 0) return in[((li & 1) ? 0 : radix::TILE) + (li >> 1)];
-        if (q == 1) return in[2 * radix::TILE + (li >> 1)];
+        if (q == 0) return in[((li & 1) ? 0 : radix::TT) + (li >> 1)];
+        if (q == 1) return in[2 * radix::TT + (li >> 1)];
         return (uint32_t)((tbase >> 1) + (li >> 1));
     }
     bool tma_ok() const {
@@ -255,7 +255,7 @@ struct MirrorLoader {
     static constexpr double KEY_BYTES = 4.0;   // wcol
     static constexpr double REC_BYTES = 16.0;  // wcol, wrow, wwt, wrk
     static constexpr int NARR = 4;             // TMA source arrays: wcol, wrow, wwt, wrk
-    static constexpr uint32_t TILE_ELEMS = radix::TILE;
+    static constexpr uint32_t TILE_ELEMS = radix::TT;
     const int32_t* wrow;
     const int32_t* wcol;
     const int32_t* wwt;
@@ -265,7 +265,7 @@ struct MirrorLoader {
     }
     __device__ __forceinline__ uint32_t skey(const uint32_t* in, int li, int64_t) const { return in[li]; }
     __device__ __forceinline__ uint32_t sval(const uint32_t* in, int q, int li, int64_t) const {
-        return in[(q + 1) * radix::TILE + li];
+        return in[(q + 1) * radix::TT + li];
     }
     bool tma_ok() const {
         return (((uintptr_t)wrow | (uintptr_t)wcol | (uintptr_t)wwt | (uintptr_t)wrk) & 15) == 0;

@@ -298,15 +298,20 @@ __device__ __forceinline__ bool tma_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-constexpr int TMA_THREADS = 256;  // one CTA per SM holds the whole pipeline (512 measured slower)
+// One CTA per SM with full 3,072-record tiles: on the mid build this beat
+// half tiles at two CTAs per SM (3.40 vs 4.16 ms) and 512-thread CTAs (3.57
+// ms), longer per-digit write runs mattering more than overlap.
+constexpr int TMA_THREADS = 256;
 constexpr int TMA_WARPS = TMA_THREADS / 32;
-constexpr int TMA_ITEMS = TILE / TMA_THREADS;
-static_assert(TMA_ITEMS * TMA_THREADS == TILE, "TMA tile matches the plain tile");
+constexpr int TMA_ITEMS = 12;
+constexpr int TT = TMA_THREADS * TMA_ITEMS;  // records per TMA tile
+constexpr int TMA_CTAS_PER_SM = 1;
+static_assert(TILE % TT == 0, "chunks of whole plain tiles are whole TMA tiles");
 
 template <int NV>
 struct TmaSmem {
-    uint32_t in[2][TMA_ARRS][TILE];  // source arrays of the current / next tile
-    uint32_t stage[NV + 1][TILE];
+    uint32_t in[2][TMA_ARRS][TT];  // source arrays of the current / next tile
+    uint32_t stage[NV + 1][TT];
     uint32_t cnt[TMA_WARPS][RADIX];
     uint32_t run[RADIX];
     uint32_t tile_start[RADIX];
@@ -336,11 +341,11 @@ struct GlobalSrc {
     __device__ __forceinline__ uint32_t val(int q, int li) const { return ld.val(q, tbase + li); }
 };
 
-// Rank, stage and scatter one tile of tcount records (all NT threads).
-template <int NT, int NV, bool STORE_KEY, class Src, class Storer, class Smem>
+// Rank, stage and scatter one tile of tcount <= TL records (all NT threads).
+template <int NT, int TL, int NV, bool STORE_KEY, class Src, class Storer, class Smem>
 __device__ __forceinline__ void scatter_tile(const Src& src, const Storer& st, const PassGeom& g,
                                              int tcount, Smem& S) {
-    constexpr int NW = NT / 32, IT = TILE / NT;
+    constexpr int NW = NT / 32, IT = TL / NT;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
     for (int i = threadIdx.x; i < NW * RADIX; i += NT) (&S.cnt[0][0])[i] = 0;
@@ -415,7 +420,7 @@ __device__ __forceinline__ void scatter_tile(const Src& src, const Storer& st, c
 }
 
 template <int NV, class Loader, class Storer, bool STORE_KEY>
-__global__ void __launch_bounds__(TMA_THREADS) k_downsweep_tma(Loader ld, Storer st, PassGeom g,
+__global__ void __launch_bounds__(TMA_THREADS, TMA_CTAS_PER_SM) k_downsweep_tma(Loader ld, Storer st, PassGeom g,
                                                                const uint32_t* counts,
                                                                const uint32_t* totals, uint32_t* err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -428,7 +433,7 @@ __global__ void __launch_bounds__(TMA_THREADS) k_downsweep_tma(Loader ld, Storer
     }
     const int64_t beg = (int64_t)blockIdx.x * g.chunk;
     const int64_t end = min(g.n, beg + g.chunk);
-    const int64_t nfull = end > beg ? (end - beg) / TILE : 0;
+    const int64_t nfull = end > beg ? (end - beg) / TT : 0;
     const uint32_t arr_bytes = Loader::TILE_ELEMS * 4u;
     if (threadIdx.x == 0) {
         tma_bar_init(&S.bar[0]);
@@ -438,7 +443,7 @@ __global__ void __launch_bounds__(TMA_THREADS) k_downsweep_tma(Loader ld, Storer
     }
     __syncthreads();
     auto issue = [&](int64_t t, int b) {
-        const int64_t tbase = beg + t * TILE;
+        const int64_t tbase = beg + t * TT;
         tma_expect(&S.bar[b], arr_bytes * Loader::NARR);
 #pragma unroll
         for (int a = 0; a < Loader::NARR; a++)
@@ -472,13 +477,13 @@ __global__ void __launch_bounds__(TMA_THREADS) k_downsweep_tma(Loader ld, Storer
             }
             return;
         }
-        SmemSrc<Loader> src{ld, &S.in[b][0][0], beg + t * TILE};
-        scatter_tile<TMA_THREADS, NV, STORE_KEY>(src, st, g, TILE, S);
+        SmemSrc<Loader> src{ld, &S.in[b][0][0], beg + t * TT};
+        scatter_tile<TMA_THREADS, TT, NV, STORE_KEY>(src, st, g, TT, S);
     }
-    const int64_t tail = beg + nfull * TILE;
+    const int64_t tail = beg + nfull * TT;
     if (tail < end) {
         GlobalSrc<Loader> src{ld, tail};
-        scatter_tile<TMA_THREADS, NV, STORE_KEY>(src, st, g, (int)(end - tail), S);
+        scatter_tile<TMA_THREADS, TT, NV, STORE_KEY>(src, st, g, (int)(end - tail), S);
     }
 }
 
@@ -488,7 +493,7 @@ struct ArrLoader {
     static constexpr double KEY_BYTES = 4.0;
     static constexpr double REC_BYTES = 4.0 * (1 + NV);
     static constexpr int NARR = 1 + NV;
-    static constexpr uint32_t TILE_ELEMS = TILE;
+    static constexpr uint32_t TILE_ELEMS = TT;
     const uint32_t* k;
     const uint32_t* v[NV > 0 ? NV : 1];
     __device__ __forceinline__ uint32_t key(int64_t i) const { return __ldg(k + i); }
@@ -498,7 +503,7 @@ struct ArrLoader {
     }
     __device__ __forceinline__ uint32_t skey(const uint32_t* in, int li, int64_t) const { return in[li]; }
     __device__ __forceinline__ uint32_t sval(const uint32_t* in, int q, int li, int64_t) const {
-        return in[(q + 1) * TILE + li];
+        return in[(q + 1) * TT + li];
     }
     bool tma_ok() const {
         bool ok = ((uintptr_t)k & 15) == 0;
@@ -574,7 +579,7 @@ int run_pass(const Loader& ld, const Storer& st, int64_t n, int shift, int bits,
              uint32_t* scratch, cudaStream_t s, uint32_t* err) {
     if (n <= 0) return WTRI_OK;
     const bool use_tma = tma_enabled() && err != nullptr && ld.tma_ok();
-    PassGeom g = make_geom(n, shift, bits, use_tma ? 1 : 0);
+    PassGeom g = make_geom(n, shift, bits, use_tma ? TMA_CTAS_PER_SM : 0);
     uint32_t* counts = scratch;
     uint32_t* totals = scratch + (size_t)RADIX * g.chunks;
     {
