@@ -232,6 +232,34 @@ WTRI_API int wtri_server_stats(wtri_server* s, uint64_t* batches, uint64_t* admi
 WTRI_API void wtri_server_free(wtri_server* s);
 
 /*
+ * Query schedule tuning (no counterpart in the paper).  A query sweeps the
+ * edge order in rounds over [0, first_round), then ranges growing by
+ * `growth`; a thread scans up to t_short wedges of an edge itself and hands
+ * longer scans to a block that stages the closing vertex's list in shared
+ * memory, so t_short is the boundary between the short-list and long-list
+ * strategies.  Defaults: 64, 8, 32.
+ *
+ * wtri_autotune times a grid of settings (first_round in {32, 64, 256,
+ * 1024}, growth in {4, 8, 16}, t_short in {8, 16, 32, 64, 128}) on the
+ * graph itself with CUDA events — one exact top-k query at each of
+ * p = -inf, 1, 2, +inf, median of `reps` — and keeps the fastest for every
+ * later query on that graph (single, device, sampled and batched queries
+ * read it; results do not depend on it).  Not thread-safe against queries
+ * running on the same graph.  wtri_set_tune sets the values directly.
+ */
+typedef struct {
+    int64_t first_round;
+    int32_t growth;
+    int32_t t_short;
+    double default_ms;   /* the four queries with the defaults */
+    double tuned_ms;     /* ... with the chosen setting */
+    int32_t configs_tried;
+} wtri_tune_info;
+
+WTRI_API int wtri_autotune(wtri_graph* g, int32_t k, int32_t reps, wtri_tune_info* info);
+WTRI_API int wtri_set_tune(wtri_graph* g, int64_t first_round, int32_t growth, int32_t t_short);
+
+/*
  * Weighted edge sampling (Algorithm 3, Section 4.1): draws nsamples edges
  * with probability w_e^p / Z (Proposition 4.1), adds every triangle on each
  * sampled edge (the common neighbours N(a) ∩ N(b)) to a set, and returns the

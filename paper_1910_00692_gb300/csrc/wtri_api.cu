@@ -226,6 +226,106 @@ WTRI_API int wtri_merge_topk(int32_t nparts, const int32_t* counts, const wtri_t
     return WTRI_OK;
 }
 
+WTRI_API int wtri_set_tune(wtri_graph* g, int64_t first_round, int32_t growth, int32_t t_short) {
+    if (!g) return set_error(WTRI_EINVAL, "graph is NULL");
+    if (first_round < 1 || growth < 2 || t_short < 1)
+        return set_error(WTRI_EINVAL, "need first_round >= 1, growth >= 2, t_short >= 1");
+    g->tune.first_round = first_round;
+    g->tune.growth = growth;
+    g->tune.t_short = t_short;
+    return WTRI_OK;
+}
+
+WTRI_API int wtri_autotune(wtri_graph* g, int32_t k, int32_t reps, wtri_tune_info* info) {
+    if (!g) return set_error(WTRI_EINVAL, "graph is NULL");
+    WTRI_TRY(check_query(g, k));
+    if (reps < 1) return set_error(WTRI_EINVAL, "reps must be positive");
+    if (g->d.m == 0) {
+        if (info) *info = wtri_tune_info{g->tune.first_round, g->tune.growth, g->tune.t_short, 0, 0, 0};
+        return WTRI_OK;
+    }
+    cudaStream_t s = g->stream;
+    void* buf = nullptr;
+    const size_t tb = sizeof(wtri_tri) * (size_t)k, wb = 8 * (size_t)k;
+    WTRI_CUDA(cudaMallocAsync(&buf, tb + wb + 64, s));
+    wtri_tri* dt = (wtri_tri*)buf;
+    double* dw = (double*)((char*)buf + ((tb + 15) & ~size_t(15)));
+    int32_t* dc = (int32_t*)(dw + k);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // Median device time of one pass over the four p of the paper's configs.
+    auto time_cfg = [&](const wtri::Tune& t, double* ms_out) -> int {
+        const wtri::Tune keep = g->tune;
+        g->tune = t;
+        std::vector<float> ts;
+        int rc = WTRI_OK;
+        for (int r = 0; r <= reps && rc == WTRI_OK; r++) {  // first pass warms up
+            cudaEventRecord(e0, s);
+            for (int pc = 0; pc < 4 && rc == WTRI_OK; pc++) rc = topk_device(g, pc, k, dt, dw, dc, s, 1);
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) rc = cuda_error(e, "autotune", __FILE__, __LINE__);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0) ts.push_back(ms);
+        }
+        int32_t status = 0;
+        if (rc == WTRI_OK && cudaMemcpy(&status, dc, 4, cudaMemcpyDeviceToHost) == cudaSuccess && status < 0)
+            rc = WTRI_ENOMEM;  // a bounded buffer filled: this setting is not usable
+        g->tune = keep;
+        if (rc != WTRI_OK) return rc;
+        std::sort(ts.begin(), ts.end());
+        *ms_out = ts[ts.size() / 2];
+        return WTRI_OK;
+    };
+    const wtri::Tune dflt;
+    double best_ms = 0, dflt_ms = 0;
+    int rc = time_cfg(dflt, &dflt_ms);
+    wtri::Tune best = dflt;
+    best_ms = dflt_ms;
+    int tried = 1;
+    const int64_t firsts[] = {32, 64, 256, 1024};
+    const int32_t growths[] = {4, 8, 16};
+    const int32_t shorts[] = {8, 16, 32, 64, 128};
+    for (int64_t f : firsts)
+        for (int32_t gr : growths)
+            for (int32_t ts : shorts) {
+                if (rc != WTRI_OK) break;
+                wtri::Tune t;
+                t.first_round = f;
+                t.growth = gr;
+                t.t_short = ts;
+                if (f == dflt.first_round && gr == dflt.growth && ts == dflt.t_short) continue;
+                double ms = 0;
+                const int r2 = time_cfg(t, &ms);
+                tried++;
+                if (r2 == WTRI_ENOMEM) continue;
+                if (r2 != WTRI_OK) {
+                    rc = r2;
+                    break;
+                }
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = t;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(buf, s);
+    if (rc != WTRI_OK) return rc;
+    g->tune = best;
+    if (info) {
+        info->first_round = best.first_round;
+        info->growth = best.growth;
+        info->t_short = best.t_short;
+        info->default_ms = dflt_ms;
+        info->tuned_ms = best_ms;
+        info->configs_tried = tried;
+    }
+    return WTRI_OK;
+}
+
 WTRI_API int wtri_topk_device(const wtri_graph* g, double p, int32_t k, wtri_tri* d_tris,
                               double* d_weight, int32_t* d_count, void* stream) {
     int code = 0;

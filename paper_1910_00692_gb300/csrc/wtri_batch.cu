@@ -184,7 +184,7 @@ struct wtri_batch_plan {
     int32_t nq = 0;
     int R = 0;
     std::vector<wtri::DevGraph> hg;
-    std::vector<int32_t> pcodes, ks;
+    std::vector<int32_t> pcodes, ks, tshort;
     std::vector<uint32_t> caps;
     std::vector<int64_t> offs, los, totals, koffs;
     std::vector<unsigned char> hq;  // Query descriptors (filled at launch)
@@ -216,10 +216,12 @@ BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes,
     P->pcodes.assign(pcodes, pcodes + nq);
     P->ks.assign(ks, ks + nq);
     P->caps.resize((size_t)nq);
+    P->tshort.resize((size_t)nq);
     P->koffs.assign((size_t)nq + 1, 0);
     int64_t mmax = 0;
     for (int i = 0; i < nq; i++) {
         P->hg[(size_t)i] = gs[i]->d;
+        P->tshort[(size_t)i] = gs[i]->tune.t_short;
         mmax = std::max<int64_t>(mmax, gs[i]->d.m);
         P->koffs[(size_t)i + 1] = P->koffs[(size_t)i] + ks[i];
         P->caps[(size_t)i] = batch_query_cap(ks[i], gs[i]->d.m);
@@ -305,6 +307,7 @@ int batch_plan_launch(BatchPlan* P, void* dbuf, cudaStream_t s, int use_graph) {
         q.qid = i;
         q.shard = 0;
         q.nshards = 1;
+        q.t_short = P->tshort[(size_t)i];
         c0 += P->caps[(size_t)i];
     }
     BatchDev Bd;

@@ -83,12 +83,23 @@ struct DevGraph {
 
 struct wtri_batch_plan;  // defined in wtri_batch.cu
 
+namespace wtri {
+// Query schedule: rounds over [0, first_round), then ranges growing by
+// `growth`; threads scan t_short wedges inline before deferring.
+struct Tune {
+    int64_t first_round = 64;
+    int32_t growth = 8;
+    int32_t t_short = 32;
+};
+}  // namespace wtri
+
 struct wtri_graph {
     wtri::DevGraph d;
     cudaStream_t stream;
     int device;
     void* base;        // one allocation holding every array
     int64_t bytes;
+    wtri::Tune tune;   // set by wtri_autotune; read by every later query
 };
 
 namespace wtri {

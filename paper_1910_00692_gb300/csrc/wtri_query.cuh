@@ -49,9 +49,8 @@ namespace {
 constexpr int RBLK = 256;          // k_round block
 constexpr int LBLK = 256;          // k_long block
 constexpr int SBLK = 1024;         // k_select block
-constexpr int T_SHORT = 32;        // wedges a thread scans before deferring
 constexpr int STAGE_MAX = 24576;   // ids of a y row staged in shared memory (96 KB)
-constexpr int64_t FIRST_ROUND = 64;
+constexpr int64_t FIRST_ROUND = 64;  // batch schedule (single queries use the graph's tune)
 constexpr int ROUND_GROWTH = 8;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;  // bounded mbarrier polling
 constexpr uint32_t STOP_NONE = 0x7fffffffu; // edge positions are below 2^31
@@ -96,6 +95,9 @@ struct Query {
     // nshards; nshards <= 1 means every edge.
     int32_t shard;
     int32_t nshards;
+    // Wedges an edge's thread scans before deferring the rest to a block (the
+    // boundary between the short-list and long-list strategies).
+    int32_t t_short;
 };
 
 constexpr int SHARD_SHIFT = 10;  // 1024-edge chunks of the edge order, dealt round-robin
@@ -255,7 +257,7 @@ __device__ __forceinline__ bool process_edge(const DevGraph& G, const Query& q,
     const int32_t dy = __ldg(G.deg + y);
     int64_t j = sx;
     bool done = false;
-    scan_wedges<P, SAMPLED>(G, q, tau, r, w, x, y, dy, ymax, j, min(ex, sx + (int64_t)T_SHORT),
+    scan_wedges<P, SAMPLED>(G, q, tau, r, w, x, y, dy, ymax, j, min(ex, sx + (int64_t)q.t_short),
                             done);
     if (!done && j < ex) {
         const uint32_t slot = atomicAdd(q.long_count, 1u);

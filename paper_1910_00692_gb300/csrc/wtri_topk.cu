@@ -42,6 +42,7 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
     q.qid = 0;
     q.shard = shard;
     q.nshards = nshards;
+    q.t_short = g->tune.t_short;
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
 
     const size_t lsmem = (size_t)STAGE_MAX * 4 + 16;
@@ -54,7 +55,7 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
     const int long_grid = sm_count() * 2;
     static const char* qname[4] = {"query_p=-inf", "query_p=1", "query_p=2", "query_p=+inf"};
     ProfScope whole(qname[P], s, 0.0, 0);
-    int64_t lo = 0, size = FIRST_ROUND;
+    int64_t lo = 0, size = g->tune.first_round;
     while (lo < m) {
         const int64_t hi = std::min(m, lo + size);
         {
@@ -70,7 +71,7 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
             k_select<<<1, SBLK, 0, s>>>(q);
         }
         lo = hi;
-        size *= ROUND_GROWTH;
+        size *= g->tune.growth;
     }
     {
         ProfScope ps("topk_final", s, 0.0, 2);
@@ -314,6 +315,7 @@ int run_sample(const wtri_graph* g, int32_t k, int64_t nsamples, uint64_t seed, 
     q.qid = 0;
     q.shard = 0;
     q.nshards = 1;
+    q.t_short = g->tune.t_short;
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
     ProfScope whole(P == P_ONE ? "sample_p=1" : "sample_p=2", s, 0.0, 0);
     WTRI_TRY(draw_samples<P>(g, nsamples, seed, mark, s));
@@ -334,7 +336,7 @@ int run_sample(const wtri_graph* g, int32_t k, int64_t nsamples, uint64_t seed, 
         attr_done[P] = true;
     }
     const int long_grid = sm_count() * 2;
-    int64_t lo = 0, size = FIRST_ROUND;
+    int64_t lo = 0, size = g->tune.first_round;
     while (lo < nlist) {
         const int64_t hi = std::min(nlist, lo + size);
         {
@@ -350,7 +352,7 @@ int run_sample(const wtri_graph* g, int32_t k, int64_t nsamples, uint64_t seed, 
             k_select<<<1, SBLK, 0, s>>>(q);
         }
         lo = hi;
-        size *= ROUND_GROWTH;
+        size *= g->tune.growth;
     }
     {
         ProfScope ps("topk_final", s, 0.0, 2);
@@ -458,6 +460,7 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
     q.qid = 0;
     q.shard = 0;
     q.nshards = 1;
+    q.t_short = g->tune.t_short;
     // The array keeps the previous call's contents: reset the status word
     // (counters, threshold, stop flag, error bits).
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
@@ -470,7 +473,7 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
         attr_done[P] = true;
     }
     const int long_grid = sm_count() * 2;
-    int64_t lo = 0, size = FIRST_ROUND;
+    int64_t lo = 0, size = g->tune.first_round;
     while (lo < m) {
         const int64_t hi = std::min(m, lo + size);
         k_round<P><<<round_grid(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
@@ -478,7 +481,7 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
         k_select<<<1, SBLK, 0, s>>>(q);
         count_launches(3);
         lo = hi;
-        size *= ROUND_GROWTH;
+        size *= g->tune.growth;
     }
     k_final_select<<<1, SBLK, 0, s>>>(q);
     k_rank_scatter<P><<<ceil_div_u(std::max(k, 1), 8), 256, 0, s>>>(q, d_tris, d_weight, d_count,

@@ -61,6 +61,12 @@ class _Tri(ctypes.Structure):
     _fields_ = [("a", ctypes.c_int32), ("b", ctypes.c_int32), ("c", ctypes.c_int32)]
 
 
+class _TuneInfo(ctypes.Structure):
+    _fields_ = [("first_round", ctypes.c_int64), ("growth", ctypes.c_int32), ("t_short", ctypes.c_int32),
+                ("default_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double),
+                ("configs_tried", ctypes.c_int32)]
+
+
 class _Result(ctypes.Structure):
     _fields_ = [("tris", ctypes.c_void_p), ("weight", ctypes.c_void_p),
                 ("capacity", ctypes.c_int32), ("count", ctypes.c_int32)]
@@ -97,6 +103,8 @@ def lib():
     L.wtri_sample_edges.argtypes = [vp, f64, i64, ctypes.c_uint64, vp, i64]
     L.wtri_topk_batch.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_Result)]
     L.wtri_topk_shard.argtypes = [vp, f64, i32, i32, i32, ctypes.POINTER(_Result), vp]
+    L.wtri_autotune.argtypes = [vp, i32, i32, ctypes.POINTER(_TuneInfo)]
+    L.wtri_set_tune.argtypes = [vp, i64, i32, i32]
     L.wtri_merge_topk.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(_Result), vp]
     u64 = ctypes.c_uint64
     L.wtri_server_create.argtypes = [u64, i32, ctypes.POINTER(vp)]
@@ -116,7 +124,7 @@ def lib():
               L.wtri_sample_topk, L.wtri_graph_copy_array, L.wtri_sample_edges,
               L.wtri_topk_batch, L.wtri_server_create, L.wtri_server_add_graph, L.wtri_submit,
               L.wtri_poll, L.wtri_poll_timed, L.wtri_server_stats, L.wtri_topk_shard,
-              L.wtri_merge_topk):
+              L.wtri_merge_topk, L.wtri_autotune, L.wtri_set_tune):
         f.restype = ctypes.c_int
     _lib = L
     return L
@@ -179,6 +187,17 @@ class Graph:
 
     def topk(self, p: float, k: int):
         return topk(self, p, k)
+
+    def autotune(self, k: int = 1000, reps: int = 3) -> dict:
+        """wtri_autotune: times the schedule grid on this graph and keeps the best."""
+        info = _TuneInfo()
+        _check(lib().wtri_autotune(self._h, int(k), int(reps), ctypes.byref(info)))
+        return {"first_round": info.first_round, "growth": info.growth, "t_short": info.t_short,
+                "default_ms": info.default_ms, "tuned_ms": info.tuned_ms,
+                "configs_tried": info.configs_tried}
+
+    def set_tune(self, first_round: int, growth: int, t_short: int):
+        _check(lib().wtri_set_tune(self._h, int(first_round), int(growth), int(t_short)))
 
     def sample_topk(self, p: float, k: int, nsamples: int, seed: int):
         return sample_topk(self, p, k, nsamples, seed)
