@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default query schedule")
+    ap.add_argument("--tune", default=None,
+                    help="first_round,growth,t_short: use this schedule instead of running the tuner")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sampler, batch and serving measurements")
     return ap.parse_args()
@@ -97,6 +99,30 @@ def measured_peak():
         except Exception:
             pass
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def ncu_traffic():
+    """DRAM bytes per radix-scatter launch at the bench size, from the committed
+    ncu capture, if the kernel sources are unchanged since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "radix_downsweep_traffic_quarter.txt")
+    if not os.path.exists(path):
+        return None, "no capture"
+    fields = {}
+    for line in open(path):
+        if ":" in line:
+            k_, v_ = line.split(":", 1)
+            fields[k_.strip()] = v_.strip()
+    srcs = fields.get("sources", "").split()
+    h = hashlib.sha256()
+    for f in srcs:
+        fp = os.path.join(ROOT, f)
+        if not os.path.exists(fp):
+            return None, "capture sources missing"
+        h.update(open(fp, "rb").read())
+    if not srcs or h.hexdigest() != fields.get("source_sha256"):
+        return None, "kernel changed since the capture"
+    return float(fields["dram_bytes_per_launch_mid"]), "ncu capture of the quarter workload scaled x4"
 
 
 class ClockSampler:
@@ -369,7 +395,10 @@ def main():
     # autotuner times a grid of settings on a built graph); every step then
     # applies the chosen setting to its freshly built graph.
     tune = None
-    if not args.no_tune:
+    if args.tune:
+        f, gr, ts = (int(x) for x in args.tune.split(","))
+        tune = {"first_round": f, "growth": gr, "t_short": ts, "source": "--tune"}
+    elif not args.no_tune:
         d0 = wt.build_csr(g.n, du, dv, dw, stream=stream)
         tune = d0.autotune(k=k, reps=3)
         d0.free()
@@ -430,9 +459,12 @@ def main():
         per_launch_ms = d0["ms"] / max(1, d0["calls"])
         per_launch_bytes = d0["bytes"] / max(1, d0["calls"])
         achieved = (per_launch_bytes / 1e9) / (per_launch_ms / 1e3) if per_launch_ms > 0 else 0.0
+        traffic, traffic_src = (ncu_traffic() if name == "radix_downsweep" and args.workload == "mid"
+                                else (None, "no capture for this kernel/workload"))
         roofline = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
                     "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": None, "launch_ms": per_launch_ms, "algorithmic_bytes": per_launch_bytes}
+                    "traffic": traffic, "traffic_source": traffic_src,
+                    "launch_ms": per_launch_ms, "algorithmic_bytes": per_launch_bytes}
     step_ms_parts = {n_: v["ms"] / args.steps for n_, v in prof.items()}
     query_ms = {P_NAMES[p]: step_ms_parts.get(f"query_p={P_NAMES[p]}", None) for p in PS}
 
