@@ -1,18 +1,22 @@
 #!/usr/bin/env python3
-"""Benchmark: exact top-k weighted triangles on the mid workload.
+"""Benchmark: exact top-k weighted triangles.
 
-Workload: Chung-Lu n=1e6, m=2e7, exponent 2.1, d_max 5e4, Zipf(2) int32
-weights capped at 1e6 (seed 1).  One step = one pass of the whole path on
-one graph: wtri_build_csr from device-resident COO (validation, degrees,
-edge order, weight-sorted / id-sorted / oriented lists) followed by the
-exact top-1000 query at p = -inf, 1, 2 and +inf.  The metric is edges of the
-graph pushed through that step per second (whole job: all ranks' edges over
+Default workload (mid): Chung-Lu n=1e6, m=2e7, exponent 2.1, d_max 5e4,
+Zipf(2) int32 weights capped at 1e6 (seed 1).  One step = one pass of the
+whole path on one graph: wtri_build_csr from device-resident COO
+(validation, degrees, edge order, weight-sorted / id-sorted / oriented
+lists) followed by the exact top-1000 query at p = -inf, 1, 2 and +inf.
+--workload large: Chung-Lu n=5e7, m=1e9, exponent 2.0 drawn on the device,
+one step = build + the exact top-1000 query at p = 1, plus 1e7 weighted edge
+draws (Philox seed 7) reported with their recall.  The value is edges of the
+graph pushed through a step per second (whole job: all ranks' edges over
 the max-over-ranks time).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wtri|reference]
+                  [--workload mid|large|quarter|tiny]
 
 --impl reference times the CPU oracle (brute force, all host cores) on a
-bounded sample of the same workload: one of the four queries per step.
+bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -34,8 +38,11 @@ import numpy as np  # noqa: E402
 
 PS = [-math.inf, 1.0, 2.0, math.inf]
 P_NAMES = {-math.inf: "-inf", 1.0: "1", 2.0: "2", math.inf: "+inf"}
-METRIC = "oriented-edges/s through build + exact top-k (k=1000, p in {-inf,1,2,+inf})"
+METRIC = "top-k query latency & oriented-edges/sec (HBM GB/s vs peak), batched/served vs plain"
 WORKLOAD = "chung-lu n=1e6 m=2e7 gamma=2.1 dmax=5e4 zipf(2,1e6) int32 weights, k=1000, p in {-inf,1,2,+inf}"
+WORKLOAD_LARGE = ("chung-lu n=5e7 m=1e9 gamma=2.0 dmax=5e4 zipf(2,1e6) int32 weights (drawn on the "
+                  "device, seed 2), k=1000, p=1")
+STEP_DEF = "wtri_build_csr from device COO + exact top-k queries at the workload's p values"
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -46,9 +53,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wtri", choices=["wtri", "reference"])
     ap.add_argument("--k", type=int, default=1000)
-    ap.add_argument("--workload", default="mid", choices=["mid", "quarter", "tiny"],
-                    help="mid: the bench workload; quarter: n=1e6 m=5e6 (profiling captures); "
-                         "tiny: n=2000 m=20000")
+    ap.add_argument("--workload", default="mid", choices=["mid", "large", "quarter", "tiny"],
+                    help="mid: the bench workload; large: n=5e7 m=1e9 (device-generated); "
+                         "quarter: n=1e6 m=5e6 (profiling captures); tiny: n=2000 m=20000")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default query schedule")
@@ -67,7 +74,11 @@ def dist_env():
 
 
 def workload(name: str):
+    """(graph, description).  mid/quarter/tiny: numpy arrays on the host;
+    large: torch tensors on the current device."""
     import synth
+    if name == "large":
+        return synth.large_graph_device(2), WORKLOAD_LARGE
     if name == "tiny":
         return synth.tiny_graph(0), "chung-lu n=2000 m=20000 gamma=2.1 (tiny)"
     if name == "quarter":
@@ -316,33 +327,58 @@ def bench_serve(wt, g_mid, rate=2000.0, count=4000):
             d.free()
 
 
+def host_arrays(g, limit=None):
+    """(u, v, w) as numpy arrays on the host; at most `limit` edges (the
+    large workload's edge list is shuffled, so a prefix is a uniform
+    sample)."""
+    if isinstance(g.u, np.ndarray):
+        return (g.u, g.v, g.w) if limit is None else (g.u[:limit], g.v[:limit], g.w[:limit])
+    sl = slice(0, limit if limit is not None else g.m)
+    return tuple(x[sl].cpu().numpy() for x in (g.u, g.v, g.w))
+
+
+LARGE_CPU_SAMPLE = 20_000_000
+
+
 def run_reference(args, world, rank):
     """The oracle as it stands, on the host cores, bounded sample."""
     if rank != 0:
         return
     import oracle
+    if args.workload == "large":
+        import torch
+        if not torch.cuda.is_available():
+            print(json.dumps({"impl": "reference", "unavailable": "the large workload is drawn on the GPU"}))
+            return
     g, wl = workload(args.workload)
+    large = args.workload == "large"
+    hu, hv, hw = host_arrays(g, LARGE_CPU_SAMPLE if large else None)
+    ps = [1.0] if large else PS
     times = []
     nthreads = os.cpu_count() or 1
     for step in range(args.warmup + args.steps):
-        p = PS[step % 4]
+        p = ps[step % len(ps)]
         t0 = time.perf_counter()
-        oracle.topk(g.n, g.u, g.v, g.w, p, args.k)
+        oracle.topk(g.n, hu, hv, hw, p, args.k)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
-    # one query of the four per step: a full step is four of them
-    step_s = 4.0 * statistics.mean(times)
-    value = g.m / step_s
+    # one query of the step's len(ps) per timed iteration
+    step_s = len(ps) * statistics.mean(times)
+    value = hu.shape[0] / step_s
+    sample = ("one brute-force query per step (p cycling -inf,1,2,+inf) on the full graph, oracle "
+              "CSR build included; step time = 4 x mean") if not large else (
+              f"one brute-force p=1 top-{args.k} query per step on a uniform sample of "
+              f"{hu.shape[0]} of the {g.m} edges (a prefix of the shuffled edge list), oracle "
+              "CSR build included; value = sampled edges / time")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": wl, "global_batch": 1, "k": args.k},
+        "config": {"workload": wl, "global_batch": 1, "k": args.k, "step": STEP_DEF},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": nthreads, "kind": "oracle",
-                         "sample": "one brute-force query per step (p cycling -inf,1,2,+inf) on the "
-                                   "full graph, oracle CSR build included; step time = 4 x mean"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -380,12 +416,17 @@ def main():
                                  ctypes.POINTER(ctypes.c_double)]
 
     g, wl = workload(args.workload)
+    large = args.workload == "large"
+    ps_step = [1.0] if large else PS
     m = g.m
     k = args.k
     stream = torch.cuda.Stream(device=dev)
-    du = torch.from_numpy(g.u).to(dev)
-    dv = torch.from_numpy(g.v).to(dev)
-    dw = torch.from_numpy(g.w).to(dev)
+    if isinstance(g.u, np.ndarray):
+        du = torch.from_numpy(g.u).to(dev)
+        dv = torch.from_numpy(g.v).to(dev)
+        dw = torch.from_numpy(g.w).to(dev)
+    else:
+        du, dv, dw = g.u, g.v, g.w
     out_t = torch.zeros((k, 3), dtype=torch.int32, device=dev)
     out_w = torch.zeros(k, dtype=torch.float64, device=dev)
     out_c = torch.zeros(4, dtype=torch.int32, device=dev)
@@ -408,14 +449,14 @@ def main():
             d = wt.build_csr(g.n, du, dv, dw, stream=stream)
             if tune:
                 d.set_tune(tune["first_round"], tune["growth"], tune["t_short"])
-            for i, p in enumerate(PS):
+            for i, p in enumerate(ps_step):
                 wt.topk_device(d, p, k, out_t, out_w, out_c[i:i + 1], stream=stream)
             d.free()
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    counts = out_c.cpu().tolist()
+    counts = out_c[:len(ps_step)].cpu().tolist()
     if any(c < 0 for c in counts):
         raise SystemExit(f"device reported an error status: {counts}")
 
@@ -466,24 +507,28 @@ def main():
                     "traffic": traffic, "traffic_source": traffic_src,
                     "launch_ms": per_launch_ms, "algorithmic_bytes": per_launch_bytes}
     step_ms_parts = {n_: v["ms"] / args.steps for n_, v in prof.items()}
-    query_ms = {P_NAMES[p]: step_ms_parts.get(f"query_p={P_NAMES[p]}", None) for p in PS}
+    query_ms = {P_NAMES[p]: step_ms_parts.get(f"query_p={P_NAMES[p]}", None) for p in ps_step}
+    # whole-step HBM figure: algorithmic bytes of every phase over the step time
+    step_bytes = sum(v["bytes"] for v in prof.values()) / args.steps
+    step_hbm = {"algorithmic_bytes_per_step": step_bytes,
+                "achieved_gbs": step_bytes / 1e9 / (ms / 1e3),
+                "frac": step_bytes / 1e9 / (ms / 1e3) / measured_peak()[0],
+                "note": "query phases count no bytes (their reads are data dependent)"}
 
     # ---- end to end through the C ABI with host buffers --------------------
     e2e = None
     if not args.no_e2e:
-        hu = torch.from_numpy(g.u).pin_memory()
-        hv = torch.from_numpy(g.v).pin_memory()
-        hw = torch.from_numpy(g.w).pin_memory()
+        hu, hv, hw = (torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in host_arrays(g))
         hub, hvb, hwb = (x.numpy() for x in (hu, hv, hw))
         d2h = 0
-        e2e_steps = max(3, min(args.steps, 20))
+        e2e_steps = max(3, min(args.steps, 5 if large else 20))
 
         def e2e_step():
             nonlocal d2h
             d = wt.build_csr(g.n, hub, hvb, hwb, stream=stream)
             if tune:
                 d.set_tune(tune["first_round"], tune["growth"], tune["t_short"])
-            for p in PS:
+            for p in ps_step:
                 tris, wts = d.topk(p, k)
                 d2h += tris.nbytes + wts.nbytes + 4
             d.free()
@@ -508,21 +553,30 @@ def main():
     sampler = None
     batch = None
     serve = None
-    if rank == 0 and not args.no_extras and args.workload == "mid":
+    if rank == 0 and not args.no_extras and args.workload in ("mid", "large"):
         sampler = bench_sampler(wt, g, stream, k)
-        batch = bench_batch(wt, stream)
-        serve = bench_serve(wt, g)
+        if not large:
+            batch = bench_batch(wt, stream)
+            serve = bench_serve(wt, g)
 
     # ---- CPU baseline: the oracle, bounded sample (rank 0, N=1) -------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
+        cu, cv, cw = host_arrays(g, LARGE_CPU_SAMPLE if large else None)
         t0 = time.perf_counter()
-        oracle.topk(g.n, g.u, g.v, g.w, 1.0, k)
+        oracle.topk(g.n, cu, cv, cw, 1.0, k)
         t_q = time.perf_counter() - t0
-        cpu = {"value": m / (4 * t_q), "unit": "edges/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "one brute-force top-1000 query (p=1) on the full graph including the oracle's "
-                         f"own CSR build, {t_q:.2f} s; a step is four such queries"}
+        if large:
+            cpu = {"value": cu.shape[0] / t_q, "unit": "edges/s", "cores": os.cpu_count(),
+                   "kind": "oracle",
+                   "sample": f"one brute-force top-{k} query (p=1) on a uniform sample of {cu.shape[0]} "
+                             f"of the {m} edges, oracle CSR build included, {t_q:.2f} s; "
+                             "value = sampled edges / time"}
+        else:
+            cpu = {"value": m / (4 * t_q), "unit": "edges/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": "one brute-force top-1000 query (p=1) on the full graph including the "
+                             f"oracle's own CSR build, {t_q:.2f} s; a step is four such queries"}
 
     if rank == 0:
         line = {
@@ -531,9 +585,12 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic",
             "config": {"workload": wl, "global_batch": world, "seq_len": None, "k": k,
+                       "step": STEP_DEF,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
-                       "l2": "inputs larger than L2: COO 240 MB, resident graph ~1.4 GB per step"},
-            "query_ms": query_ms, "phase_ms_per_step": step_ms_parts, "tune": tune,
+                       "l2": (f"inputs larger than L2: COO {12 * m / 1e9:.2f} GB, resident graph "
+                              f"{84 * m / 1e9:.1f} GB per step")},
+            "query_ms": query_ms, "phase_ms_per_step": step_ms_parts, "step_hbm": step_hbm,
+            "tune": tune,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "sampler": sampler, "batch": batch, "serve": serve,
             "gpu_launches": int(launches), "clocks": clocks,

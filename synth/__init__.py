@@ -220,3 +220,128 @@ def random_small_graph(n: int, p_edge: float, wmax: int, seed) -> Graph:
     v2 = np.where(flip, u, v).astype(np.int32)
     w = rng.integers(1, wmax + 1, size=u.shape[0]).astype(np.int32)
     return Graph(n, u2, v2, w, name=f"gnp n={n} p={p_edge} w<={wmax}")
+
+
+# ---------------------------------------------------------------------------
+# Device-side generation for sizes numpy cannot draw in reasonable time (the
+# billion-edge workload).  Same recipe as chung_lu/zipf_weights (erased
+# Chung-Lu with the same expected-degree profile, truncated Zipf weights),
+# drawn with torch's seeded CUDA generator; torch serves only to draw the
+# inputs.  Everything stays on the device.
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class DeviceGraph:
+    n: int
+    m: int
+    u: "object"         # int32 [m], shuffled edge order, random endpoint order
+    v: "object"         # int32 [m]
+    w: "object"         # int32 [m], w[i] is the weight of edge (u[i], v[i])
+    keys: "object"      # int64 [m], min*n+max of every edge, ascending
+    w_by_key: "object"  # int32 [m], weight of the edge keys[j]
+    name: str = ""
+
+
+def _expected_degrees_torch(n, m, gamma, d_max, device):
+    import torch
+    a = 1.0 / (gamma - 1.0)
+    idx = torch.arange(n, dtype=torch.float64, device=device)
+    target = 2.0 * m
+
+    def total(i0):
+        return float(torch.sum(d_max * i0 ** a * (idx + i0) ** (-a)).item())
+
+    lo, hi = 1e-9, 1e12
+    if total(hi) < target:
+        return torch.full((n,), target / n, dtype=torch.float64, device=device)
+    for _ in range(200):
+        mid = math.sqrt(lo * hi)
+        if total(mid) < target:
+            lo = mid
+        else:
+            hi = mid
+        if hi / lo < 1 + 1e-12:
+            break
+    return d_max * hi ** a * (idx + hi) ** (-a)
+
+
+def chung_lu_device(n: int, m: int, gamma: float, d_max: float, seed: int, device="cuda"):
+    """Erased Chung-Lu graph drawn on the device.  Returns (u, v, keys, order):
+    u, v int32 in shuffled order, keys the ascending edge keys min*n+max, and
+    order (int64) with key(u[i], v[i]) == keys[order[i]]."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 1_000_003 + 17)
+    theta = _expected_degrees_torch(n, m, gamma, d_max, device)
+    cdf = torch.cumsum(theta, 0)
+    cdf /= cdf[-1].clone()
+    del theta
+    keys = torch.empty(0, dtype=torch.int64, device=device)
+    rounds = 0
+    while keys.numel() < m:
+        need = m - keys.numel()
+        draw = int(need * 1.15) + 1024
+        parts = [keys]
+        for start in range(0, draw, 1 << 28):
+            cnt = min(1 << 28, draw - start)
+            a = torch.searchsorted(cdf, torch.rand(cnt, dtype=torch.float64, device=device,
+                                                   generator=gen), right=True).clamp_(max=n - 1)
+            b = torch.searchsorted(cdf, torch.rand(cnt, dtype=torch.float64, device=device,
+                                                   generator=gen), right=True).clamp_(max=n - 1)
+            ok = a != b
+            a, b = a[ok], b[ok]
+            parts.append(torch.minimum(a, b) * n + torch.maximum(a, b))
+            del a, b, ok
+        keys = torch.unique(torch.cat(parts))
+        del parts
+        rounds += 1
+        if rounds > 100:
+            raise RuntimeError("Chung-Lu top-up did not converge")
+    if keys.numel() > m:
+        pick = torch.randperm(keys.numel(), device=device, generator=gen)[:m]
+        keys = keys[torch.sort(pick).values]
+        del pick
+    del cdf
+    order = torch.randperm(m, device=device, generator=gen)
+    shuffled = keys[order]
+    a = (shuffled // n).to(torch.int32)
+    b = (shuffled % n).to(torch.int32)
+    del shuffled
+    flip = torch.rand(m, device=device, generator=gen) < 0.5
+    u = torch.where(flip, b, a)
+    v = torch.where(flip, a, b)
+    del flip, a, b
+    return u, v, keys, order
+
+
+def zipf_weights_device(m: int, s: float, cap: int, seed: int, device="cuda"):
+    """m i.i.d. weights P(w) proportional to w^-s on 1..cap (int32, device)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 1_000_003 + 29)
+    x = torch.arange(1, cap + 1, dtype=torch.float64, device=device)
+    cdf = torch.cumsum(x ** (-s), 0)
+    cdf /= cdf[-1].clone()
+    out = torch.empty(m, dtype=torch.int32, device=device)
+    for start in range(0, m, 1 << 28):
+        cnt = min(1 << 28, m - start)
+        w = torch.searchsorted(cdf, torch.rand(cnt, dtype=torch.float64, device=device,
+                                               generator=gen), right=True) + 1
+        out[start:start + cnt] = w.clamp_(max=cap).to(torch.int32)
+    return out
+
+
+def large_graph_device(seed: int = 2, n: int = 50_000_000, m: int = 1_000_000_000,
+                       device="cuda") -> DeviceGraph:
+    """The billion-edge workload: Chung-Lu n=5e7, m=1e9, exponent 2.0,
+    d_max 5e4, Zipf(2) int32 weights capped at 1e6, drawn on the device
+    (about 36 GB of device memory for the result).  Smaller n, m give the
+    same recipe at reduced size."""
+    import torch
+    u, v, keys, order = chung_lu_device(n, m, 2.0, 50_000.0, seed, device)
+    w = zipf_weights_device(m, 2.0, 1_000_000, seed, device)
+    w_by_key = torch.empty_like(w)
+    w_by_key[order] = w
+    del order
+    torch.cuda.empty_cache()
+    return DeviceGraph(n, m, u, v, w, keys, w_by_key,
+                       f"chung-lu n={n} m={m} gamma=2.0 dmax=5e4 zipf(2,1e6) seed={seed} (device)")
