@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--workload", default="mid", choices=["mid", "large", "quarter", "tiny"],
                     help="mid: the bench workload; large: n=5e7 m=1e9 (device-generated); "
                          "quarter: n=1e6 m=5e6 (profiling captures); tiny: n=2000 m=20000")
+    ap.add_argument("--large-size", default=None,
+                    help="n,m: the large workload's recipe at another size (profiling captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default query schedule")
@@ -73,11 +75,15 @@ def dist_env():
     return world, rank, local
 
 
-def workload(name: str):
+def workload(name: str, large_size=None):
     """(graph, description).  mid/quarter/tiny: numpy arrays on the host;
     large: torch tensors on the current device."""
     import synth
     if name == "large":
+        if large_size:
+            n, m = (int(float(x)) for x in large_size.split(","))
+            return (synth.large_graph_device(2, n=n, m=m),
+                    f"chung-lu n={n} m={m} gamma=2.0 dmax=5e4 zipf(2,1e6) (device, profiling size)")
         return synth.large_graph_device(2), WORKLOAD_LARGE
     if name == "tiny":
         return synth.tiny_graph(0), "chung-lu n=2000 m=20000 gamma=2.1 (tiny)"
@@ -350,7 +356,7 @@ def run_reference(args, world, rank):
         if not torch.cuda.is_available():
             print(json.dumps({"impl": "reference", "unavailable": "the large workload is drawn on the GPU"}))
             return
-    g, wl = workload(args.workload)
+    g, wl = workload(args.workload, args.large_size)
     large = args.workload == "large"
     hu, hv, hw = host_arrays(g, LARGE_CPU_SAMPLE if large else None)
     ps = [1.0] if large else PS
@@ -415,7 +421,7 @@ def main():
                                  ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_double)]
 
-    g, wl = workload(args.workload)
+    g, wl = workload(args.workload, args.large_size)
     large = args.workload == "large"
     ps_step = [1.0] if large else PS
     m = g.m

@@ -168,35 +168,30 @@ __global__ void k_scan_apply(const int32_t* __restrict__ in, int64_t n,
 }
 
 // ---- radix loaders / storers for the build ---------------------------------
+// A record is (key, v0, v1, v2); copied tiles hold each source array at a
+// stride of radix::TT words.
+using radix::TT;
 
-// Pass input for the edge order: key = wmax - w, values (u, v).
+// Edge order input: key = wmax - w, values (u, v).
 struct EdgeLoader {
-    static constexpr double KEY_BYTES = 4.0;   // w
     static constexpr double REC_BYTES = 12.0;  // u, v, w
-    static constexpr int NARR = 3;             // TMA source arrays: w, u, v
-    static constexpr uint32_t TILE_ELEMS = radix::TT;
+    static constexpr int NARR = 3;             // w, u, v
+    static constexpr uint32_t TILE_WORDS = TT;
     const int32_t* u;
     const int32_t* v;
     const int32_t* w;
     int32_t wmax;
-    __device__ __forceinline__ uint32_t key(int64_t i) const {
-        return (uint32_t)(wmax - __ldg(w + i));
-    }
-    __device__ __forceinline__ uint32_t val(int q, int64_t i) const {
-        return (uint32_t)__ldg((q == 0 ? u : v) + i);
-    }
+    __device__ __forceinline__ uint32_t key(int64_t i) const { return (uint32_t)(wmax - __ldg(w + i)); }
     __device__ __forceinline__ const void* tile_src(int a, int64_t tbase) const {
         return (a == 0 ? w : (a == 1 ? u : v)) + tbase;
     }
-    __device__ __forceinline__ uint32_t skey(const uint32_t* in, int li, int64_t) const {
-        return (uint32_t)(wmax - (int32_t)in[li]);
+    __device__ __forceinline__ uint4 srec(const uint32_t* in, int li, int64_t) const {
+        return make_uint4((uint32_t)(wmax - (int32_t)in[li]), in[TT + li], in[2 * TT + li], 0u);
     }
-    __device__ __forceinline__ uint32_t sval(const uint32_t* in, int q, int li, int64_t) const {
-        return in[(q + 1) * radix::TT + li];
+    __device__ __forceinline__ uint4 grec(int64_t i) const {
+        return make_uint4(key(i), (uint32_t)__ldg(u + i), (uint32_t)__ldg(v + i), 0u);
     }
-    bool tma_ok() const {
-        return (((uintptr_t)u | (uintptr_t)v | (uintptr_t)w) & 15) == 0;
-    }
+    bool tma_ok() const { return (((uintptr_t)u | (uintptr_t)v | (uintptr_t)w) & 15) == 0; }
 };
 
 // Final edge-order output.
@@ -206,56 +201,49 @@ struct EdgeOrderStorer {
     int32_t* ov;
     int32_t* ow;
     int32_t wmax;
-    __device__ __forceinline__ void key(int64_t p, uint32_t k) const { ow[p] = wmax - (int32_t)k; }
-    __device__ __forceinline__ void val(int q, int64_t p, uint32_t x) const {
-        (q == 0 ? ou : ov)[p] = (int32_t)x;
+    __device__ __forceinline__ void store(int64_t p, const uint4& r) const {
+        ow[p] = wmax - (int32_t)r.x;
+        ou[p] = (int32_t)r.y;
+        ov[p] = (int32_t)r.z;
     }
 };
 
 // Virtual stream of adjacency entries in edge order: entry i belongs to edge
-// r = i / 2; side 0 is (row u, col v), side 1 is (row v, col u).
-// Values: col, weight, r.
+// r = i / 2; side 0 is (row u, col v), side 1 is (row v, col u).  Record:
+// (row, col, weight, r).
 struct OrderEntryLoader {
-    static constexpr double KEY_BYTES = 4.0;  // u or v: 8 bytes per edge, two entries
     static constexpr double REC_BYTES = 6.0;  // u, v, w: 12 bytes per edge, two entries
-    static constexpr int NARR = 3;            // TMA source arrays: ou, ov, ow (half a tile each)
-    static constexpr uint32_t TILE_ELEMS = radix::TT / 2;
+    static constexpr int NARR = 3;            // ou, ov, ow (half a tile of edges each)
+    static constexpr uint32_t TILE_WORDS = TT / 2;
     const int32_t* ou;
     const int32_t* ov;
     const int32_t* ow;
     __device__ __forceinline__ const void* tile_src(int a, int64_t tbase) const {
         return (a == 0 ? ou : (a == 1 ? ov : ow)) + (tbase >> 1);
     }
-    __device__ __forceinline__ uint32_t skey(const uint32_t* in, int li, int64_t) const {
-        return in[((li & 1) ? radix::TT : 0) + (li >> 1)];
+    __device__ __forceinline__ uint4 srec(const uint32_t* in, int li, int64_t tbase) const {
+        const int e = li >> 1, side = li & 1;
+        const uint32_t a = in[e], b = in[TT + e];
+        return make_uint4(side ? b : a, side ? a : b, in[2 * TT + e], (uint32_t)((tbase >> 1) + e));
     }
-    __device__ __forceinline__ uint32_t sval(const uint32_t* in, int q, int li, int64_t tbase) const {
-        if (q == 0) return in[((li & 1) ? 0 : radix::TT) + (li >> 1)];
-        if (q == 1) return in[2 * radix::TT + (li >> 1)];
-        return (uint32_t)((tbase >> 1) + (li >> 1));
-    }
-    bool tma_ok() const {
-        return (((uintptr_t)ou | (uintptr_t)ov | (uintptr_t)ow) & 15) == 0;
+    __device__ __forceinline__ uint4 grec(int64_t i) const {
+        const int64_t r = i >> 1;
+        const uint32_t a = (uint32_t)__ldg(ou + r), b = (uint32_t)__ldg(ov + r);
+        return (i & 1) ? make_uint4(b, a, (uint32_t)__ldg(ow + r), (uint32_t)r)
+                       : make_uint4(a, b, (uint32_t)__ldg(ow + r), (uint32_t)r);
     }
     __device__ __forceinline__ uint32_t key(int64_t i) const {
-        const int64_t r = i >> 1;
-        return (uint32_t)__ldg(((i & 1) ? ov : ou) + r);
+        return (uint32_t)__ldg(((i & 1) ? ov : ou) + (i >> 1));
     }
-    __device__ __forceinline__ uint32_t val(int q, int64_t i) const {
-        const int64_t r = i >> 1;
-        if (q == 0) return (uint32_t)__ldg(((i & 1) ? ou : ov) + r);
-        if (q == 1) return (uint32_t)__ldg(ow + r);
-        return (uint32_t)r;
-    }
+    bool tma_ok() const { return (((uintptr_t)ou | (uintptr_t)ov | (uintptr_t)ow) & 15) == 0; }
 };
 
 // Mirrored weight-sorted entries: entry i of row x (= wrow[i]) with
-// neighbour c becomes (row c; values x, weight, r).
+// neighbour c becomes the record (row c, col x, weight, r).
 struct MirrorLoader {
-    static constexpr double KEY_BYTES = 4.0;   // wcol
     static constexpr double REC_BYTES = 16.0;  // wcol, wrow, wwt, wrk
-    static constexpr int NARR = 4;             // TMA source arrays: wcol, wrow, wwt, wrk
-    static constexpr uint32_t TILE_ELEMS = radix::TT;
+    static constexpr int NARR = 4;
+    static constexpr uint32_t TILE_WORDS = TT;
     const int32_t* wrow;
     const int32_t* wcol;
     const int32_t* wwt;
@@ -263,71 +251,33 @@ struct MirrorLoader {
     __device__ __forceinline__ const void* tile_src(int a, int64_t tbase) const {
         return (a == 0 ? wcol : (a == 1 ? wrow : (a == 2 ? wwt : wrk))) + tbase;
     }
-    __device__ __forceinline__ uint32_t skey(const uint32_t* in, int li, int64_t) const { return in[li]; }
-    __device__ __forceinline__ uint32_t sval(const uint32_t* in, int q, int li, int64_t) const {
-        return in[(q + 1) * radix::TT + li];
+    __device__ __forceinline__ uint4 srec(const uint32_t* in, int li, int64_t) const {
+        return make_uint4(in[li], in[TT + li], in[2 * TT + li], in[3 * TT + li]);
     }
+    __device__ __forceinline__ uint4 grec(int64_t i) const {
+        return make_uint4((uint32_t)__ldg(wcol + i), (uint32_t)__ldg(wrow + i), (uint32_t)__ldg(wwt + i),
+                          (uint32_t)__ldg(wrk + i));
+    }
+    __device__ __forceinline__ uint32_t key(int64_t i) const { return (uint32_t)__ldg(wcol + i); }
     bool tma_ok() const {
         return (((uintptr_t)wrow | (uintptr_t)wcol | (uintptr_t)wwt | (uintptr_t)wrk) & 15) == 0;
     }
-    __device__ __forceinline__ uint32_t key(int64_t i) const { return (uint32_t)__ldg(wcol + i); }
-    __device__ __forceinline__ uint32_t val(int q, int64_t i) const {
-        return (uint32_t)__ldg((q == 0 ? wrow : (q == 1 ? wwt : wrk)) + i);
-    }
 };
 
-// Final row-sorted output: key (row) optional, values col, weight, r.
+// Final row-sorted output: row (optional), col, weight, r.
 struct RowsStorer {
     __host__ __device__ double rec_bytes() const { return row ? 16.0 : 12.0; }
     int32_t* row;  // may be null
     int32_t* col;
     int32_t* wt;
     int32_t* rk;
-    __device__ __forceinline__ void key(int64_t p, uint32_t k) const {
-        if (row) row[p] = (int32_t)k;
-    }
-    __device__ __forceinline__ void val(int q, int64_t p, uint32_t x) const {
-        (q == 0 ? col : (q == 1 ? wt : rk))[p] = (int32_t)x;
+    __device__ __forceinline__ void store(int64_t p, const uint4& r) const {
+        if (row) row[p] = (int32_t)r.x;
+        col[p] = (int32_t)r.y;
+        wt[p] = (int32_t)r.z;
+        rk[p] = (int32_t)r.w;
     }
 };
-
-// Runs a full LSD sort over 'bits' key bits: first pass from 'first',
-// middle passes through ping-pong arrays, last pass into 'last'.
-template <int NV, class First, class Last>
-int lsd_sort(const First& first, const Last& last, int64_t n, int bits, uint32_t* pp_a,
-             uint32_t* pp_b, int64_t cap, uint32_t* scratch, cudaStream_t s, uint32_t* err) {
-    using namespace radix;
-    const int passes = (bits + BITS - 1) / BITS;
-    (void)cap;
-    if (passes == 0) return set_error(WTRI_EINVAL, "internal: zero-pass sort");
-    uint32_t* cur = pp_a;
-    uint32_t* nxt = pp_b;
-    for (int p = 0; p < passes; p++) {
-        const int shift = p * BITS;
-        const int pb = std::min(BITS, bits - shift);
-        ArrLoader<NV> al;
-        ArrStorer<NV> as;
-        al.k = cur;
-        as.k = nxt;
-        const size_t stride = ((size_t)n + 3) & ~size_t(3);  // 16-byte aligned arrays
-        for (int q = 0; q < NV; q++) {
-            al.v[q] = cur + (size_t)(q + 1) * stride;
-            as.v[q] = nxt + (size_t)(q + 1) * stride;
-        }
-        if (p == 0 && p == passes - 1) {
-            WTRI_TRY((run_pass<NV, true>(first, last, n, shift, pb, scratch, s, err)));
-        } else if (p == 0) {
-            WTRI_TRY((run_pass<NV, true>(first, as, n, shift, pb, scratch, s, err)));
-            std::swap(cur, nxt);
-        } else if (p == passes - 1) {
-            WTRI_TRY((run_pass<NV, true>(al, last, n, shift, pb, scratch, s, err)));
-        } else {
-            WTRI_TRY((run_pass<NV, true>(al, as, n, shift, pb, scratch, s, err)));
-            std::swap(cur, nxt);
-        }
-    }
-    return WTRI_OK;
-}
 
 __global__ void k_copy_identity_order(int64_t m, const int32_t* u, const int32_t* v,
                                       const int32_t* w, int32_t* ou, int32_t* ov, int32_t* ow) {
@@ -353,27 +303,55 @@ __global__ void k_rowptr_from_rows(int32_t n, int64_t n2, const int32_t* __restr
     }
 }
 
-constexpr int LONG_ROW = 1024;
+constexpr int SHORT_ROW = 32;   // rows below: one thread each
+constexpr int LONG_ROW = 1024;  // rows from here: one block each; in between: one warp each
 
-// Degrees, the maximum degree, and the list of long rows (oriented by blocks).
+// Degrees (also saturated to 16 bits, the form the orientation test gathers),
+// the maximum degree, and the lists of long rows (front of 'rows') and
+// medium rows (back of 'rows').  counters: [0] long, [1] next long,
+// [2] medium.
 __global__ void k_degrees(int32_t n, const int64_t* __restrict__ rowptr, int32_t* __restrict__ deg,
-                          BuildStatus* st, int32_t* long_rows, int32_t* long_count) {
+                          uint16_t* __restrict__ deg16, BuildStatus* st, int32_t* rows,
+                          int32_t* counters) {
     int32_t mx = 0;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         const int32_t d = (int32_t)(rowptr[x + 1] - rowptr[x]);
         deg[x] = d;
+        deg16[x] = (uint16_t)min(d, 0xffff);
         mx = max(mx, d);
-        if (d >= LONG_ROW) long_rows[atomicAdd(long_count, 1)] = (int32_t)x;
+        // one atomic per warp and list
+        const uint32_t act = __activemask();
+        const int lane = threadIdx.x & 31;
+        const uint32_t bl = __ballot_sync(act, d >= LONG_ROW);
+        const uint32_t bm = __ballot_sync(act, d >= SHORT_ROW && d < LONG_ROW);
+        const int leader = __ffs(act) - 1;
+        int32_t base_l = 0, base_m = 0;
+        if (lane == leader) {
+            if (bl) base_l = atomicAdd(&counters[0], __popc(bl));
+            if (bm) base_m = atomicAdd(&counters[2], __popc(bm));
+        }
+        base_l = __shfl_sync(act, base_l, leader);
+        base_m = __shfl_sync(act, base_m, leader);
+        const uint32_t below = (1u << lane) - 1u;
+        if (d >= LONG_ROW) rows[base_l + __popc(bl & below)] = (int32_t)x;
+        else if (d >= SHORT_ROW) rows[n - 1 - (base_m + __popc(bm & below))] = (int32_t)x;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx) atomicMax(&st->maxdeg, mx);
 }
 
-__device__ __forceinline__ bool rank_less(const int32_t* deg, int32_t a, int32_t b) {
-    const int32_t da = __ldg(deg + a), db = __ldg(deg + b);
-    return da < db || (da == db && a < b);
+// Whether x (degree dx) comes before its neighbour c in the (degree, id)
+// order.  The 16-bit degrees decide unless both saturate.
+__device__ __forceinline__ bool before(int32_t x, int32_t dx, const uint16_t* __restrict__ deg16,
+                                       const int32_t* __restrict__ deg, int32_t c) {
+    uint32_t dc = __ldg(deg16 + c);
+    if (dx >= 0xffff) {
+        if (dc < 0xffffu) return false;
+        dc = (uint32_t)__ldg(deg + c);
+    }
+    return (uint32_t)dx < dc || ((uint32_t)dx == dc && x < c);
 }
 
 constexpr int OBLK = 512;
@@ -381,37 +359,99 @@ constexpr int OBLK = 512;
 // Degree orientation, in the slots of the symmetric rows: row x keeps its
 // neighbours of higher (degree, id) rank, in id order, at
 // [rowptr[x], rowptr[x] + odeg[x]).  The same pass finds repeated pairs
-// (equal neighbours next to each other in an id-sorted row).  Blocks first
-// take long rows from a queue, then warps take short rows.
+// (equal neighbours next to each other in an id-sorted row).
+//
+// Every pass loads an entry's id, weight and rank together (the weight and
+// rank of a dropped entry are read but unused), so the only dependent load
+// is the neighbour's degree.
+//
+// Short rows: one thread per row walks its entries, eight at a time.
+__global__ void k_orient_short(int32_t n, const int64_t* __restrict__ rowptr,
+                               const int32_t* __restrict__ scol, const int32_t* __restrict__ swt,
+                               const int32_t* __restrict__ srk, const uint16_t* __restrict__ deg16,
+                               const int32_t* __restrict__ deg, int32_t* __restrict__ ocol,
+                               int32_t* __restrict__ owt, int32_t* __restrict__ ork,
+                               int32_t* __restrict__ odeg, BuildStatus* st) {
+    constexpr int B = 8;
+    unsigned long long dup = ~0ull;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = rowptr[x], e = rowptr[x + 1];
+        const int32_t dx = (int32_t)(e - s);
+        if (dx >= SHORT_ROW) continue;
+        int64_t out = s;
+        int32_t prev = -1;
+        for (int64_t j0 = s; j0 < e; j0 += B) {
+            int32_t c[B], wv[B], rv[B];
+            bool f[B];
+#pragma unroll
+            for (int i = 0; i < B; i++) {
+                const bool ok = j0 + i < e;
+                c[i] = ok ? __ldcs(scol + j0 + i) : -1;
+                wv[i] = ok ? __ldcs(swt + j0 + i) : 0;
+                rv[i] = ok ? __ldcs(srk + j0 + i) : 0;
+            }
+#pragma unroll
+            for (int i = 0; i < B; i++) f[i] = c[i] >= 0 && before((int32_t)x, dx, deg16, deg, c[i]);
+#pragma unroll
+            for (int i = 0; i < B; i++) {
+                if (c[i] < 0) break;
+                if (c[i] == prev) dup = min(dup, (unsigned long long)(j0 + i));
+                prev = c[i];
+                if (f[i]) {
+                    ocol[out] = c[i];
+                    owt[out] = wv[i];
+                    ork[out] = rv[i];
+                    out++;
+                }
+            }
+        }
+        odeg[x] = (int32_t)(out - s);
+    }
+    if (dup != ~0ull) {
+        atomicOr(&st->err, DEV_ERR_DUPLICATE);
+        atomicMin(&st->first_bad, dup);
+    }
+}
+
+// Long rows: blocks take them from a queue; then medium rows: warp i takes
+// entries i, i + warps, ... of their list, four 32-entry chunks at a time.
 __global__ void __launch_bounds__(OBLK) k_orient(
     int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ scol,
-    const int32_t* __restrict__ swt, const int32_t* __restrict__ srk, const int32_t* __restrict__ deg,
-    int32_t* __restrict__ ocol, int32_t* __restrict__ owt, int32_t* __restrict__ ork,
-    int32_t* __restrict__ odeg, const int32_t* __restrict__ long_rows,
-    const int32_t* __restrict__ long_count, int32_t* next_long, BuildStatus* st) {
+    const int32_t* __restrict__ swt, const int32_t* __restrict__ srk,
+    const uint16_t* __restrict__ deg16, const int32_t* __restrict__ deg, int32_t* __restrict__ ocol,
+    int32_t* __restrict__ owt, int32_t* __restrict__ ork, int32_t* __restrict__ odeg,
+    const int32_t* __restrict__ rows, int32_t* counters, BuildStatus* st) {
     __shared__ uint32_t warp_cnt[OBLK / 32];
     __shared__ uint32_t tot;
     __shared__ int32_t item;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t below = (1u << lane) - 1u;
     unsigned long long dup = ~0ull;
-    const int nlong = *long_count;
+    const int nlong = counters[0];
     for (;;) {
-        if (threadIdx.x == 0) item = atomicAdd(next_long, 1);
+        if (threadIdx.x == 0) item = atomicAdd(&counters[1], 1);
         __syncthreads();
         const int it = item;
         __syncthreads();
         if (it >= nlong) break;
-        const int32_t x = long_rows[it];
+        const int32_t x = rows[it];
         const int64_t s = rowptr[x], e = rowptr[x + 1];
+        const int32_t dx = (int32_t)(e - s);
         int64_t out = s;
         for (int64_t j0 = s; j0 < e; j0 += OBLK) {
             const int64_t j = j0 + threadIdx.x;
             bool fwd = false;
-            int32_t c = 0;
+            int32_t c = 0, wv = 0, rv = 0, cp = -1;
             if (j < e) {
-                c = __ldg(scol + j);
-                if (j > s && __ldg(scol + j - 1) == c) dup = min(dup, (unsigned long long)j);
-                fwd = rank_less(deg, x, c);
+                c = __ldcs(scol + j);
+                wv = __ldcs(swt + j);
+                rv = __ldcs(srk + j);
+                if (j > s) cp = __ldg(scol + j - 1);
+            }
+            if (j < e) {
+                if (cp == c) dup = min(dup, (unsigned long long)j);
+                fwd = before(x, dx, deg16, deg, c);
             }
             const uint32_t b = __ballot_sync(0xffffffffu, fwd);
             if (lane == 0) warp_cnt[wid] = __popc(b);
@@ -427,39 +467,54 @@ __global__ void __launch_bounds__(OBLK) k_orient(
             }
             __syncthreads();
             if (fwd) {
-                const int64_t p = out + warp_cnt[wid] + __popc(b & ((1u << lane) - 1u));
+                const int64_t p = out + warp_cnt[wid] + __popc(b & below);
                 ocol[p] = c;
-                owt[p] = __ldg(swt + j);
-                ork[p] = __ldg(srk + j);
+                owt[p] = wv;
+                ork[p] = rv;
             }
             out += tot;
             __syncthreads();
         }
         if (threadIdx.x == 0) odeg[x] = (int32_t)(out - s);
     }
-    const int64_t warp = ((int64_t)blockIdx.x * OBLK + threadIdx.x) >> 5;
+    constexpr int CH = 4;
+    const int nmed = counters[2];
     const int64_t nwarps = ((int64_t)gridDim.x * OBLK) >> 5;
-    for (int64_t x = warp; x < n; x += nwarps) {
+    for (int64_t it = ((int64_t)blockIdx.x * OBLK + threadIdx.x) >> 5; it < nmed; it += nwarps) {
+        const int32_t x = rows[n - 1 - it];
         const int64_t s = rowptr[x], e = rowptr[x + 1];
-        if (e - s >= LONG_ROW) continue;  // taken by a block above
+        const int32_t dx = (int32_t)(e - s);
         int64_t out = s;
-        for (int64_t j0 = s; j0 < e; j0 += 32) {
-            const int64_t j = j0 + lane;
-            bool fwd = false;
-            int32_t c = 0;
-            if (j < e) {
-                c = __ldg(scol + j);
-                if (j > s && __ldg(scol + j - 1) == c) dup = min(dup, (unsigned long long)j);
-                fwd = rank_less(deg, (int32_t)x, c);
+        int32_t carry = -1;  // id of the entry before the current chunk
+        for (int64_t j0 = s; j0 < e; j0 += 32 * CH) {
+            int32_t c[CH], wv[CH], rv[CH];
+            bool f[CH];
+#pragma unroll
+            for (int i = 0; i < CH; i++) {
+                const int64_t j = j0 + 32 * i + lane;
+                const bool ok = j < e;
+                c[i] = ok ? __ldcs(scol + j) : -1;
+                wv[i] = ok ? __ldcs(swt + j) : 0;
+                rv[i] = ok ? __ldcs(srk + j) : 0;
             }
-            const uint32_t b = __ballot_sync(0xffffffffu, fwd);
-            if (fwd) {
-                const int64_t p = out + __popc(b & ((1u << lane) - 1u));
-                ocol[p] = c;
-                owt[p] = __ldg(swt + j);
-                ork[p] = __ldg(srk + j);
+#pragma unroll
+            for (int i = 0; i < CH; i++) f[i] = c[i] >= 0 && before(x, dx, deg16, deg, c[i]);
+#pragma unroll
+            for (int i = 0; i < CH; i++) {
+                const int32_t up = __shfl_up_sync(0xffffffffu, c[i], 1);
+                const int32_t pc = lane == 0 ? carry : up;
+                const int64_t j = j0 + 32 * i + lane;
+                if (c[i] >= 0 && pc == c[i]) dup = min(dup, (unsigned long long)j);
+                carry = __shfl_sync(0xffffffffu, c[i], 31);
+                const uint32_t b = __ballot_sync(0xffffffffu, f[i]);
+                if (f[i]) {
+                    const int64_t p = out + __popc(b & below);
+                    ocol[p] = c[i];
+                    owt[p] = wv[i];
+                    ork[p] = rv[i];
+                }
+                out += __popc(b);
             }
-            out += __popc(b);
         }
         if (lane == 0) odeg[x] = (int32_t)(out - s);
     }
@@ -629,24 +684,28 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     g->d.maxdeg = 0;
 
     if (m > 0) {
-        // Scratch: two ping-pong record buffers of (key + 3 values) x 2m, the
-        // radix counts, the row keys of the weight-sorted layout, long rows.
+        // Scratch: two buffers of 16-byte records and one of 16-bit digits for
+        // 2m records, the radix counts, the row keys of the weight-sorted
+        // layout, long rows.
         const int64_t n2 = 2 * m;
-        const size_t rec_words = 4 * ((((size_t)n2) + 3) & ~size_t(3)) + 4;
+        const size_t rec_words = 4 * (size_t)n2 + 4;
+        const size_t dig_words = ((size_t)n2 + 1) / 2 + 4;
         const size_t cnt_words = radix::scratch_words(n2);
-        const size_t words = 2 * rec_words + cnt_words + (size_t)n2 + N1 + 8;
+        const size_t words = 2 * rec_words + dig_words + cnt_words + (size_t)n2 + N1 + 8 + (N1 + 1) / 2 + 4;
         Scratch tmp(s);
         if (cudaMallocAsync(&tmp.p, words * 4, s) != cudaSuccess) {
             cudaGetLastError();
             return fail(set_error(WTRI_ENOMEM, "device scratch allocation failed"));
         }
-        uint32_t* pp_a = (uint32_t*)tmp.p;
-        uint32_t* pp_b = pp_a + rec_words;
-        uint32_t* counts = pp_b + rec_words;
+        uint4* rec_a = (uint4*)tmp.p;
+        uint4* rec_b = rec_a + rec_words / 4;
+        uint16_t* dig = (uint16_t*)(rec_b + rec_words / 4);
+        uint32_t* counts = (uint32_t*)dig + dig_words;
         int32_t* wrow = (int32_t*)(counts + cnt_words);
-        int32_t* long_rows = wrow + n2;
-        int32_t* long_count = long_rows + n;  // [0] count, [1] next
-        if (cudaMemsetAsync(long_count, 0, 8, s) != cudaSuccess)
+        int32_t* row_list = wrow + n2;                    // long rows first, medium rows last
+        int32_t* row_counters = row_list + n;             // 8 words, see k_degrees
+        uint16_t* deg16 = (uint16_t*)(row_counters + 8);  // n half-words
+        if (cudaMemsetAsync(row_counters, 0, 32, s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "memset", __FILE__, __LINE__));
 
         // 2. edge order
@@ -657,7 +716,7 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         } else {
             EdgeLoader el{u, v, w, h_st.wmax};
             EdgeOrderStorer es{ou, ov, ow, h_st.wmax};
-            int rc = lsd_sort<2>(el, es, m, wbits, pp_a, pp_b, m, counts, s, &d_st->err);
+            int rc = radix::lsd_sort(el, es, m, wbits, rec_a, rec_b, dig, counts, s, &d_st->err);
             if (rc != WTRI_OK) return fail(rc);
         }
         // 3. weight-sorted rows (row key kept in wrow)
@@ -665,30 +724,40 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         {
             OrderEntryLoader ol{ou, ov, ow};
             RowsStorer rs{wrow, wcol, wwt, wrk};
-            int rc = lsd_sort<3>(ol, rs, n2, nbits, pp_a, pp_b, n2, counts, s, &d_st->err);
+            int rc = radix::lsd_sort(ol, rs, n2, nbits, rec_a, rec_b, dig, counts, s, &d_st->err);
             if (rc != WTRI_OK) return fail(rc);
         }
         // 4. row offsets, degrees, long rows
         {
             ProfScope ps("row_offsets", s, 4.0 * n2 + 8.0 * (n + 1) + 4.0 * n, 2);
             k_rowptr_from_rows<<<grid_for(n2), BLK, 0, s>>>(n, n2, wrow, rowptr);
-            k_degrees<<<grid_for(n), BLK, 0, s>>>(n, rowptr, deg, d_st, long_rows, long_count);
+            k_degrees<<<grid_for(n), BLK, 0, s>>>(n, rowptr, deg, deg16, d_st, row_list, row_counters);
         }
         // 5. id-sorted rows
         {
             MirrorLoader ml{wrow, wcol, wwt, wrk};
             RowsStorer rs{nullptr, scol, swt, srk};
-            int rc = lsd_sort<3>(ml, rs, n2, nbits, pp_a, pp_b, n2, counts, s, &d_st->err);
+            int rc = radix::lsd_sort(ml, rs, n2, nbits, rec_a, rec_b, dig, counts, s, &d_st->err);
             if (rc != WTRI_OK) return fail(rc);
         }
         // 6. orientation + repeated pairs
         {
-            // reads every id-sorted neighbour, weight and rank of the kept
-            // half, writes m oriented entries and the out-degrees
-            ProfScope ps("orient", s, 4.0 * n2 + 8.0 * m + 12.0 * m + 8.0 * n + 8.0 * (n + 1), 1);
-            k_orient<<<sm_count() * 4, OBLK, 0, s>>>(n, rowptr, scol, swt, srk, deg, ocol, owt, ork,
-                                                     odeg, long_rows, long_count, long_count + 1,
-                                                     d_st);
+            {
+                ProfScope ps("orient_short", s, 0.0, 1);
+                k_orient_short<<<grid_for(n), BLK, 0, s>>>(n, rowptr, scol, swt, srk, deg16, deg, ocol,
+                                                           owt, ork, odeg, d_st);
+            }
+            // reads every id-sorted neighbour, weight and rank, writes m
+            // oriented entries and the out-degrees (bytes of both launches)
+            ProfScope ps("orient", s, 12.0 * n2 + 12.0 * m + 4.0 * n + 8.0 * (n + 1), 1);
+            // persistent: as many blocks as fit at once (rows are dealt by block and warp index)
+            static int per_sm = 0;
+            if (per_sm == 0 &&
+                (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_orient, OBLK, 0) != cudaSuccess ||
+                 per_sm < 1))
+                per_sm = 1;
+            k_orient<<<sm_count() * per_sm, OBLK, 0, s>>>(n, rowptr, scol, swt, srk, deg16, deg, ocol,
+                                                          owt, ork, odeg, row_list, row_counters, d_st);
         }
         if (cudaGetLastError() != cudaSuccess)
             return fail(set_error(WTRI_ECUDA, "build kernel launch failed"));

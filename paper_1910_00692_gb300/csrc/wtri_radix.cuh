@@ -1,19 +1,32 @@
-// Stable LSD radix sort passes (reduce-then-scan), 8-bit digits.
+// Stable LSD radix sort passes (reduce-then-scan) over 16-byte records.
 //
-// One pass orders N records by digit (key >> shift) & mask, stably, where a
-// record is a 32-bit key plus NV 32-bit values.  Records come from a Loader
-// and go to a Storer, so a pass can read a virtual stream (e.g. two
-// adjacency entries per edge) and write final arrays without staging copies.
+// A record is (key, v0, v1, v2), four 32-bit words.  One pass orders N
+// records by the digit (key >> shift) & mask, stably, with digits of up to
+// MAX_BITS bits.  The first pass of a sort reads its records through a
+// Loader (a view of the source arrays, possibly a virtual stream such as
+// "two adjacency entries per edge"); the last writes them through a Storer
+// (the final arrays).  Passes in between read and write whole 16-byte
+// records (one vector access each) and, beside every record, the next
+// pass's digit as a 16-bit word, so the next histogram reads 2 bytes per
+// record instead of the record.
 //
-//   Loader: __device__ uint32_t key(int64_t i) const;
-//           __device__ uint32_t val(int q, int64_t i) const;   // q < NV
-//   Storer: __device__ void key(int64_t pos, uint32_t k) const;
-//           __device__ void val(int q, int64_t pos, uint32_t x) const;
+//   Loader: static NARR, TILE_WORDS     source arrays copied per tile, words each
+//           static REC_BYTES            bytes read per record
+//           const void* tile_src(int a, int64_t tbase)
+//           uint4 srec(const uint32_t* in, int li, int64_t tbase)   from a copied tile
+//           uint4 grec(int64_t i)       from global memory
+//           uint32_t key(int64_t i)     (first-pass histogram)
+//           bool tma_ok()               sources 16-byte aligned
+//   Storer: void store(int64_t p, const uint4& rec); double rec_bytes()
 //
 // Three kernels per pass: per-chunk digit histograms (upsweep), a per-digit
-// scan over chunks, and the scatter (downsweep).  Within a tile the scatter
-// ranks records with warp match + per-warp counters (stable), stages them in
-// shared memory in digit order, and writes each digit's run contiguously.
+// scan over chunks, and the scatter.  The scatter streams its chunk tile by
+// tile; the next tile's sources arrive by bulk asynchronous copies
+// (cp.async.bulk, one mbarrier per half of a double buffer) while the
+// current one is ranked (warp match + per-warp counters, stable), staged in
+// digit order in the same shared-memory buffer it was read from, and written
+// out so that consecutive threads store consecutive positions of one
+// digit's run.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,13 +38,24 @@
 namespace wtri {
 namespace radix {
 
-constexpr int BITS = 8;
-constexpr int RADIX = 1 << BITS;
-constexpr int THREADS = 256;
-constexpr int WARPS = THREADS / 32;
-constexpr int ITEMS = 12;
-constexpr int TILE = THREADS * ITEMS;
-static_assert(THREADS == RADIX, "one thread per digit in the tile scan");
+constexpr int MAX_BITS = 10;               // widest digit of a pass
+constexpr int MAX_BINS = 1 << MAX_BITS;
+constexpr int NT = 256;                    // threads of the histogram and scatter CTAs
+constexpr int NW = NT / 32;
+#ifndef WTRI_RADIX_IT
+#define WTRI_RADIX_IT 24
+#endif
+#ifndef WTRI_RADIX_CTAS
+#define WTRI_RADIX_CTAS 1
+#endif
+constexpr int IT = WTRI_RADIX_IT;          // records per thread per tile
+constexpr int TT = NT * IT;                // records per tile
+constexpr int CTAS_PER_SM = WTRI_RADIX_CTAS;
+constexpr int DPT = MAX_BINS / NT;         // digits owned by a thread in the tile scan
+constexpr int UP_SPLIT = 8;                // histogram blocks per chunk
+constexpr uint32_t WAIT_LIMIT = 1u << 24;  // bounded mbarrier polling
+static_assert(TT % 16 == 0, "tiles are whole 16-byte lines of every source array");
+static_assert(DPT == 4, "a thread's digits are one 8-byte word of each warp's counters");
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -39,40 +63,11 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// Exclusive scan of one value per thread over a 256-thread block.
-__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_t* warp_tot,
-                                                             uint32_t* total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) warp_tot[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        uint32_t t = lane < WARPS ? warp_tot[lane] : 0;
-        uint32_t ti = t;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
-            if (lane >= o) ti += y;
-        }
-        if (lane < WARPS) warp_tot[lane] = ti - t;
-        if (lane == WARPS - 1) *total = ti;
-    }
-    __syncthreads();
-    uint32_t r = warp_tot[w] + inc - x;
-    __syncthreads();
-    return r;
-}
-
-// Exclusive scan of one value per thread over an NT-thread block (NT <= 1024).
-template <int NT>
+// Exclusive scan of one value per thread over an NTH-thread block (NTH <= 1024).
+template <int NTH>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* warp_tot,
                                                          uint32_t* total) {
-    constexpr int NW = NT / 32;
+    constexpr int NWW = NTH / 32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t inc = x;
 #pragma unroll
@@ -83,15 +78,15 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* w
     if (lane == 31) warp_tot[w] = inc;
     __syncthreads();
     if (w == 0) {
-        uint32_t t = lane < NW ? warp_tot[lane] : 0;
+        uint32_t t = lane < NWW ? warp_tot[lane] : 0;
         uint32_t ti = t;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
             if (lane >= o) ti += y;
         }
-        if (lane < NW) warp_tot[lane] = ti - t;
-        if (lane == NW - 1) *total = ti;
+        if (lane < NWW) warp_tot[lane] = ti - t;
+        if (lane == NWW - 1) *total = ti;
     }
     __syncthreads();
     uint32_t r = warp_tot[w] + inc - x;
@@ -101,194 +96,138 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* w
 
 struct PassGeom {
     int64_t n;        // records
-    int64_t chunk;    // records per chunk (multiple of TILE)
+    int64_t chunk;    // records per chunk (whole tiles)
     int chunks;       // G
     int shift;
+    int bins;         // 1 << digit bits
+    int bits;
     uint32_t mask;
 };
 
-// Digit histogram of each chunk.  UP_SPLIT blocks share a chunk (each a
-// slice of it) and add their counts into the zeroed per-chunk histogram.
-constexpr int UP_SPLIT = 8;
-
+// ---- histogram sources ------------------------------------------------------
 template <class Loader>
-__global__ void __launch_bounds__(THREADS) k_upsweep(Loader ld, PassGeom g, uint32_t* counts) {
-    __shared__ uint32_t hist[WARPS][RADIX];
+struct KeyDigits {  // first pass: the loader's keys
+    static constexpr bool PACKED = false;
+    Loader ld;
+    int shift;
+    uint32_t mask;
+    __device__ __forceinline__ uint32_t digit(int64_t i) const { return (ld.key(i) >> shift) & mask; }
+};
+struct StoredDigits {  // later passes: 16-bit digits written by the previous scatter
+    static constexpr bool PACKED = true;
+    const uint16_t* d;
+    __device__ __forceinline__ uint32_t digit(int64_t i) const { return __ldg(d + i); }
+};
+
+// Digit histogram of each chunk.  UP_SPLIT blocks share a chunk (each a
+// slice of it, a multiple of 8 records) and add their counts into the
+// zeroed per-chunk histogram; each warp counts into its own shared copy.
+// Stored digits are read eight at a time (one 16-byte load).
+template <class Dig>
+__global__ void __launch_bounds__(NT) k_upsweep(Dig dg, PassGeom g, uint32_t* counts) {
+    __shared__ uint32_t hist[NW][MAX_BINS];
     const int w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < WARPS * RADIX; i += THREADS) (&hist[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < NW * MAX_BINS; i += NT) (&hist[0][0])[i] = 0;
     __syncthreads();
+    uint32_t* h = hist[w];
     const int chunk = blockIdx.x / UP_SPLIT, part = blockIdx.x % UP_SPLIT;
     const int64_t cbeg = (int64_t)chunk * g.chunk;
     const int64_t cend = min(g.n, cbeg + g.chunk);
-    const int64_t slice = (g.chunk + UP_SPLIT - 1) / UP_SPLIT;
-    const int64_t beg = cbeg + part * slice;
+    const int64_t slice = ((g.chunk + UP_SPLIT - 1) / UP_SPLIT + 7) & ~int64_t(7);
+    const int64_t beg = min(cend, cbeg + part * slice);
     const int64_t end = min(cend, beg + slice);
-    for (int64_t i = beg + threadIdx.x; i < end; i += THREADS) {
-        uint32_t d = (ld.key(i) >> g.shift) & g.mask;
-        atomicAdd(&hist[w][d], 1u);
-    }
-    __syncthreads();
-    uint32_t s = 0;
+    int64_t i0 = beg;
+    if constexpr (Dig::PACKED) {
+        const int64_t nv = (end - beg) >> 3;  // whole groups of 8 (beg is a multiple of 8)
+        const uint4* v = reinterpret_cast<const uint4*>(dg.d + beg);
+        for (int64_t q = threadIdx.x; q < nv; q += NT) {
+            const uint4 x = __ldg(v + q);
+            atomicAdd(&h[x.x & 0xffffu], 1u);
+            atomicAdd(&h[x.x >> 16], 1u);
+            atomicAdd(&h[x.y & 0xffffu], 1u);
+            atomicAdd(&h[x.y >> 16], 1u);
+            atomicAdd(&h[x.z & 0xffffu], 1u);
+            atomicAdd(&h[x.z >> 16], 1u);
+            atomicAdd(&h[x.w & 0xffffu], 1u);
+            atomicAdd(&h[x.w >> 16], 1u);
+        }
+        i0 = beg + (nv << 3);
+    } else {
+        constexpr int U = 4;
+        for (; i0 + (int64_t)U * NT <= end; i0 += (int64_t)U * NT) {
+            uint32_t d[U];
 #pragma unroll
-    for (int k = 0; k < WARPS; k++) s += hist[k][threadIdx.x];
-    if (s) atomicAdd(&counts[(int64_t)threadIdx.x * g.chunks + chunk], s);
+            for (int u = 0; u < U; u++) d[u] = dg.digit(i0 + (int64_t)u * NT + threadIdx.x);
+#pragma unroll
+            for (int u = 0; u < U; u++) atomicAdd(&h[d[u]], 1u);
+        }
+    }
+    for (int64_t i = i0 + threadIdx.x; i < end; i += NT) atomicAdd(&h[dg.digit(i)], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < g.bins; d += NT) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int k = 0; k < NW; k++) s += hist[k][d];
+        if (s) atomicAdd(&counts[(int64_t)d * g.chunks + chunk], s);
+    }
 }
 
 // Block d: exclusive scan of counts[d][0..G) in place; totals[d] = sum.
-__global__ void __launch_bounds__(THREADS) k_digit_scan(uint32_t* counts, int chunks,
-                                                        uint32_t* totals) {
-    __shared__ uint32_t warp_tot[WARPS];
+__global__ void __launch_bounds__(NT) k_digit_scan(uint32_t* counts, int chunks, uint32_t* totals) {
+    __shared__ uint32_t warp_tot[NW];
     __shared__ uint32_t tot;
     uint32_t* c = counts + (int64_t)blockIdx.x * chunks;
     uint32_t carry = 0;
-    for (int base = 0; base < chunks; base += THREADS) {
+    for (int base = 0; base < chunks; base += NT) {
         int i = base + threadIdx.x;
         uint32_t x = i < chunks ? c[i] : 0;
-        uint32_t ex = block_exclusive_scan_256(x, warp_tot, &tot);
+        uint32_t ex = block_exclusive_scan<NT>(x, warp_tot, &tot);
         if (i < chunks) c[i] = carry + ex;
         carry += tot;
-        __syncthreads();
     }
     if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
-template <int NV>
-struct TileSmem {
-    uint32_t cnt[WARPS][RADIX];
-    uint32_t stage[NV + 1][TILE];  // key, then values, in tile-sorted order
-    uint32_t run[RADIX];           // global position of this chunk's next record per digit
-    uint32_t tile_start[RADIX];    // tile-local start of each digit
-    uint32_t tile_total[RADIX];
-    uint32_t warp_tot[WARPS];
-    uint32_t total;
-};
-
-template <int NV, class Loader, class Storer, bool STORE_KEY>
-__global__ void __launch_bounds__(THREADS) k_downsweep(Loader ld, Storer st, PassGeom g,
-                                                       const uint32_t* counts,
-                                                       const uint32_t* totals) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileSmem<NV>& S = *reinterpret_cast<TileSmem<NV>*>(smem_raw);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-
-    {   // global base of each digit = exclusive scan of digit totals
-        uint32_t t = totals[threadIdx.x];
-        uint32_t base = block_exclusive_scan_256(t, S.warp_tot, &S.total);
-        S.run[threadIdx.x] = base + counts[(int64_t)threadIdx.x * g.chunks + blockIdx.x];
-    }
-    __syncthreads();
-
-    const int64_t beg = (int64_t)blockIdx.x * g.chunk;
-    const int64_t end = min(g.n, beg + g.chunk);
-    const uint32_t lt = lanemask_lt();
-
-    for (int64_t tbase = beg; tbase < end; tbase += TILE) {
-        const int tcount = (int)min((int64_t)TILE, end - tbase);
-        for (int i = threadIdx.x; i < WARPS * RADIX; i += THREADS) (&S.cnt[0][0])[i] = 0;
-
-        // Every load of the tile is issued before any use (one round trip).
-        uint32_t key[ITEMS];
-        uint32_t val[NV > 0 ? NV : 1][ITEMS];
-        uint32_t rank[ITEMS];
-#pragma unroll
-        for (int j = 0; j < ITEMS; j++) {
-            const int li = w * 32 * ITEMS + j * 32 + lane;
-            const bool valid = li < tcount;
-            key[j] = valid ? ld.key(tbase + li) : 0u;
-#pragma unroll
-            for (int q = 0; q < NV; q++) val[q][j] = valid ? ld.val(q, tbase + li) : 0u;
-        }
-        __syncthreads();  // counters cleared
-#pragma unroll
-        for (int j = 0; j < ITEMS; j++) {
-            const int li = w * 32 * ITEMS + j * 32 + lane;
-            const bool valid = li < tcount;
-            const uint32_t d = valid ? ((key[j] >> g.shift) & g.mask) : (uint32_t)RADIX;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            uint32_t base = valid ? S.cnt[w][d] : 0u;
-            rank[j] = base + __popc(peers & lt);
-            __syncwarp();
-            if (valid && (__ffs(peers) - 1) == lane) S.cnt[w][d] = base + __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        {   // per digit: warp offsets, tile totals, tile starts
-            const int d = threadIdx.x;
-            uint32_t s = 0;
-#pragma unroll
-            for (int k = 0; k < WARPS; k++) {
-                uint32_t c = S.cnt[k][d];
-                S.cnt[k][d] = s;
-                s += c;
-            }
-            S.tile_total[d] = s;
-            uint32_t st0 = block_exclusive_scan_256(s, S.warp_tot, &S.total);
-            S.tile_start[d] = st0;
-#pragma unroll
-            for (int k = 0; k < WARPS; k++) S.cnt[k][d] += st0;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < ITEMS; j++) {
-            const int li = w * 32 * ITEMS + j * 32 + lane;
-            if (li < tcount) {
-                const uint32_t d = (key[j] >> g.shift) & g.mask;
-                const uint32_t pos = rank[j] + S.cnt[w][d];
-                S.stage[0][pos] = key[j];
-#pragma unroll
-                for (int q = 0; q < NV; q++) S.stage[q + 1][pos] = val[q][j];
-            }
-        }
-        __syncthreads();
-        // Consecutive threads write consecutive positions of one digit's run.
-#pragma unroll
-        for (int i = 0; i < ITEMS; i++) {
-            const int p = i * THREADS + threadIdx.x;
-            if (p < tcount) {
-                const uint32_t k = S.stage[0][p];
-                const uint32_t d = (k >> g.shift) & g.mask;
-                const int64_t gp = (int64_t)S.run[d] + (p - (int64_t)S.tile_start[d]);
-                if (STORE_KEY) st.key(gp, k);
-#pragma unroll
-                for (int q = 0; q < NV; q++) st.val(q, gp, S.stage[q + 1][p]);
-            }
-        }
-        __syncthreads();
-        S.run[threadIdx.x] += S.tile_total[threadIdx.x];
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// TMA-fed scatter.  One CTA per SM streams its chunk tile by tile; while a
-// tile is ranked and scattered, the next tile's source arrays arrive in the
-// other half of a double buffer by bulk async copies (cp.async.bulk) that
-// complete on one mbarrier per buffer.  Waits are bounded: on timeout the
-// pass records DEV_ERR_TIMEOUT and the CTA returns.  Only whole tiles go
-// through TMA; a chunk's last partial tile is loaded with plain loads.
-// ---------------------------------------------------------------------------
-constexpr int TMA_ARRS = 4;                 // source arrays per loader, at most
-constexpr uint32_t TMA_WAIT_LIMIT = 1u << 24;
-
+// ---- scatter -----------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void tma_bar_init(uint64_t* bar) {
+__device__ __forceinline__ void bar_init(uint64_t* bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
 }
-__device__ __forceinline__ void tma_expect(uint64_t* bar, uint32_t bytes) {
+__device__ __forceinline__ void bar_expect(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
                  "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+#ifndef WTRI_RADIX_LOAD_HINT
+#define WTRI_RADIX_LOAD_HINT 1
+#endif
+// Tile sources are read once: an evict-first L2 policy keeps them from
+// displacing the partially written lines of the digit runs.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                          uint64_t policy) {
+#if WTRI_RADIX_LOAD_HINT
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+#else
+    (void)policy;
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
             smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+#endif
 }
-__device__ __forceinline__ bool tma_try_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool bar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -298,194 +237,208 @@ __device__ __forceinline__ bool tma_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// One CTA per SM with full 3,072-record tiles: on the mid build this beat
-// half tiles at two CTAs per SM (3.40 vs 4.16 ms) and 512-thread CTAs (3.57
-// ms), longer per-digit write runs mattering more than overlap.
-constexpr int TMA_THREADS = 256;
-constexpr int TMA_WARPS = TMA_THREADS / 32;
-constexpr int TMA_ITEMS = 12;
-constexpr int TT = TMA_THREADS * TMA_ITEMS;  // records per TMA tile
-constexpr int TMA_CTAS_PER_SM = 1;
-static_assert(TILE % TT == 0, "chunks of whole plain tiles are whole TMA tiles");
-
-constexpr int RANK_GROUPS = 1;  // counter sets per warp (4 independent groups measured slower: 3.61 vs 3.29 ms)
-
-template <int NV>
-struct TmaSmem {
-    uint32_t in[2][TMA_ARRS][TT];  // source arrays of the current / next tile
-    uint4 stage4[TT];              // (key, values) of each record in digit order
-    uint32_t cnt[TMA_WARPS][RANK_GROUPS][RADIX];
-    uint32_t run[RADIX];
-    uint32_t tile_start[RADIX];
-    uint32_t tile_total[RADIX];
+struct ScatterSmem {
+    uint4 buf[2][TT];              // a tile's sources, then its records in digit order
+    uint16_t cnt[NW][MAX_BINS];    // per (warp, digit): count, then staging offset
+    uint32_t delta[MAX_BINS];      // output position of a staged record = delta[d] + index
     uint32_t warp_tot[32];
     uint32_t total;
     int timed_out;
     uint64_t bar[2];
 };
 
-// Records of the current tile from the TMA buffer.
-template <class Loader>
-struct SmemSrc {
-    const Loader& ld;
-    const uint32_t* in;  // in[b][0]; array a at in + a * TILE
-    int64_t tbase;
-    __device__ __forceinline__ uint32_t key(int li) const { return ld.skey(in, li, tbase); }
-    __device__ __forceinline__ uint32_t val(int q, int li) const { return ld.sval(in, q, li, tbase); }
-};
+__device__ __forceinline__ uint32_t lo16(uint32_t x) { return x & 0xffffu; }
 
-// Records of a tile straight from global memory.
-template <class Loader>
-struct GlobalSrc {
-    const Loader& ld;
-    int64_t tbase;
-    __device__ __forceinline__ uint32_t key(int li) const { return ld.key(tbase + li); }
-    __device__ __forceinline__ uint32_t val(int q, int li) const { return ld.val(q, tbase + li); }
-};
+#ifndef WTRI_RANK_BALLOT
+#define WTRI_RANK_BALLOT 1
+#endif
+// Lanes of the warp holding the same digit as this lane (digits of 'bits'
+// bits; lanes with valid == false group only among themselves): one ballot
+// per digit bit.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, int bits, bool valid) {
+#if WTRI_RANK_BALLOT
+    const uint32_t vb = __ballot_sync(0xffffffffu, valid);
+    uint32_t p = valid ? vb : ~vb;
+#pragma unroll
+    for (int k = 0; k < MAX_BITS; k++) {
+        if (k < bits) {
+            const bool bit = (d >> k) & 1u;
+            const uint32_t b = __ballot_sync(0xffffffffu, bit);
+            p &= bit ? b : ~b;
+        }
+    }
+    return p;
+#else
+    return __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu);
+#endif
+}
+__device__ __forceinline__ uint32_t hi16(uint32_t x) { return x >> 16; }
 
-// Rank, stage and scatter one tile of tcount <= TL records (all NT threads).
-// A warp's items are ranked in RANK_GROUPS groups of consecutive item
-// indices, each with its own digit counters, so the groups' match/count
-// chains are independent; the per-digit scan over (warp, group) in order
-// keeps the ranking stable.
-template <int NT, int TL, int NV, bool STORE_KEY, class Src, class Storer, class Smem>
-__device__ __forceinline__ void scatter_tile(const Src& src, const Storer& st, const PassGeom& g,
-                                             int tcount, Smem& S) {
-    constexpr int NW = NT / 32, IT = TL / NT, NG = RANK_GROUPS, PER = IT / NG;
-    static_assert(PER * NG == IT, "items split evenly into groups");
+// Rank, stage and write one tile of tcount <= TT records held in registers.
+// Item j of warp w, lane l is record w * 32 * IT + j * 32 + l of the tile;
+// ranking strips in order and warps in order keeps equal digits stable.
+// run[] holds this thread's digits' next output positions (digits
+// threadIdx.x * DPT + i).
+template <class Storer>
+__device__ __forceinline__ void scatter_tile(const uint4 (&rec)[IT], int tcount, uint4* stage,
+                                             const Storer& st, const PassGeom& g,
+                                             uint32_t (&run)[DPT], ScatterSmem& S) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
-    for (int i = threadIdx.x; i < NW * NG * RADIX; i += NT) (&S.cnt[0][0][0])[i] = 0;
+    // 1. zero the counters of the used digits (16-byte words, 8 digits each)
+    const int zw = (g.bins + 7) >> 3;  // at least one word, so digits 0..3 always start at zero
+    for (int q = threadIdx.x; q < zw; q += NT) {
+#pragma unroll
+        for (int k = 0; k < NW; k++) reinterpret_cast<uint4*>(&S.cnt[k][0])[q] = make_uint4(0, 0, 0, 0);
+    }
     __syncthreads();
-    uint32_t key[IT];
+    // 2. rank within the warp: first every item's peers (ballots, independent
+    //    across strips), then the running per-warp counters strip by strip
     uint32_t rank[IT];
 #pragma unroll
     for (int j = 0; j < IT; j++) {
         const int li = w * 32 * IT + j * 32 + lane;
-        key[j] = li < tcount ? src.key(li) : 0u;
+        rank[j] = digit_peers((rec[j].x >> g.shift) & g.mask, g.bits, li < tcount);
     }
 #pragma unroll
-    for (int t = 0; t < PER; t++) {
-        uint32_t dd[NG], pp[NG], bb[NG];
-#pragma unroll
-        for (int gi = 0; gi < NG; gi++) {
-            const int j = gi * PER + t;
-            const int li = w * 32 * IT + j * 32 + lane;
-            const bool valid = li < tcount;
-            dd[gi] = valid ? ((key[j] >> g.shift) & g.mask) : (uint32_t)RADIX;
-            pp[gi] = __match_any_sync(0xffffffffu, dd[gi]);
-            bb[gi] = valid ? S.cnt[w][gi][dd[gi]] : 0u;
-            rank[j] = bb[gi] + __popc(pp[gi] & lt);
-        }
+    for (int j = 0; j < IT; j++) {
+        const int li = w * 32 * IT + j * 32 + lane;
+        const bool valid = li < tcount;
+        const uint32_t d = (rec[j].x >> g.shift) & g.mask;
+        const uint32_t peers = rank[j];
+        const uint32_t b = valid ? (uint32_t)S.cnt[w][d] : 0u;
+        rank[j] = b + __popc(peers & lt);
         __syncwarp();
-#pragma unroll
-        for (int gi = 0; gi < NG; gi++)
-            if (dd[gi] < (uint32_t)RADIX && (__ffs(pp[gi]) - 1) == lane)
-                S.cnt[w][gi][dd[gi]] = bb[gi] + __popc(pp[gi]);
+        if (valid && lane == __ffs(peers) - 1) S.cnt[w][d] = (uint16_t)(b + __popc(peers));
         __syncwarp();
     }
     __syncthreads();
-    {   // per digit (first RADIX threads): offsets of (warp, group), tile totals and starts
-        const int d = threadIdx.x;
-        uint32_t s = 0;
-        if (d < RADIX) {
+    // 3. per digit: offsets of each warp, tile start, output delta.  Thread t
+    //    owns digits 4t..4t+3: one 8-byte word of each warp's counters.
+    {
+        const int d0 = threadIdx.x * DPT;
+        const bool mine = d0 < g.bins;
+        uint32_t tot[DPT] = {0, 0, 0, 0};
+        if (mine) {
 #pragma unroll
-            for (int k = 0; k < NW; k++)
-#pragma unroll
-                for (int gi = 0; gi < NG; gi++) {
-                    uint32_t c = S.cnt[k][gi][d];
-                    S.cnt[k][gi][d] = s;
-                    s += c;
-                }
-            S.tile_total[d] = s;
+            for (int k = 0; k < NW; k++) {
+                const uint2 r = *reinterpret_cast<const uint2*>(&S.cnt[k][d0]);
+                tot[0] += lo16(r.x);
+                tot[1] += hi16(r.x);
+                tot[2] += lo16(r.y);
+                tot[3] += hi16(r.y);
+            }
         }
-        const uint32_t st0 = block_exclusive_scan<NT>(d < RADIX ? s : 0u, S.warp_tot, &S.total);
-        if (d < RADIX) {
-            S.tile_start[d] = st0;
+        const uint32_t sum = tot[0] + tot[1] + tot[2] + tot[3];
+        const uint32_t start = block_exclusive_scan<NT>(sum, S.warp_tot, &S.total);
+        if (mine) {
+            uint32_t s[DPT];
+            s[0] = start;
+            s[1] = s[0] + tot[0];
+            s[2] = s[1] + tot[1];
+            s[3] = s[2] + tot[2];
 #pragma unroll
-            for (int k = 0; k < NW; k++)
+            for (int i = 0; i < DPT; i++) {
+                S.delta[d0 + i] = run[i] - s[i];
+                run[i] += tot[i];
+            }
 #pragma unroll
-                for (int gi = 0; gi < NG; gi++) S.cnt[k][gi][d] += st0;
+            for (int k = 0; k < NW; k++) {
+                uint2* p = reinterpret_cast<uint2*>(&S.cnt[k][d0]);
+                const uint2 r = *p;
+                *p = make_uint2(s[0] | (s[1] << 16), s[2] | (s[3] << 16));
+                s[0] += lo16(r.x);
+                s[1] += hi16(r.x);
+                s[2] += lo16(r.y);
+                s[3] += hi16(r.y);
+            }
         }
     }
     __syncthreads();
-    static_assert(NV <= 3, "a record (key + values) is staged as one 16-byte word");
+    // 4. stage in digit order (the tile's sources were read by every thread
+    //    before the barriers above)
 #pragma unroll
     for (int j = 0; j < IT; j++) {
         const int li = w * 32 * IT + j * 32 + lane;
         if (li < tcount) {
-            const uint32_t d = (key[j] >> g.shift) & g.mask;
-            const uint32_t pos = rank[j] + S.cnt[w][j / PER][d];
-            uint4 rec;
-            rec.x = key[j];
-            rec.y = NV > 0 ? src.val(0, li) : 0u;
-            rec.z = NV > 1 ? src.val(1, li) : 0u;
-            rec.w = NV > 2 ? src.val(2, li) : 0u;
-            S.stage4[pos] = rec;  // one 16-byte store per record
+            const uint32_t d = (rec[j].x >> g.shift) & g.mask;
+            stage[rank[j] + S.cnt[w][d]] = rec[j];
         }
     }
     __syncthreads();
+    // 5. write: consecutive threads, consecutive positions of one digit's run
 #pragma unroll
     for (int i = 0; i < IT; i++) {
         const int p = i * NT + threadIdx.x;
         if (p < tcount) {
-            const uint4 rec = S.stage4[p];
-            const uint32_t d = (rec.x >> g.shift) & g.mask;
-            const int64_t gp = (int64_t)S.run[d] + (p - (int64_t)S.tile_start[d]);
-            if (STORE_KEY) st.key(gp, rec.x);
-            if (NV > 0) st.val(0, gp, rec.y);
-            if (NV > 1) st.val(1, gp, rec.z);
-            if (NV > 2) st.val(2, gp, rec.w);
+            const uint4 r = stage[p];
+            const uint32_t d = (r.x >> g.shift) & g.mask;
+            st.store((int64_t)S.delta[d] + p, r);
         }
     }
-    __syncthreads();
-    if (threadIdx.x < RADIX) S.run[threadIdx.x] += S.tile_total[threadIdx.x];
+    // generic accesses to the buffer are ordered before the next bulk copy into it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
 }
 
-template <int NV, class Loader, class Storer, bool STORE_KEY>
-__global__ void __launch_bounds__(TMA_THREADS, TMA_CTAS_PER_SM) k_downsweep_tma(Loader ld, Storer st, PassGeom g,
-                                                               const uint32_t* counts,
-                                                               const uint32_t* totals, uint32_t* err) {
+// One CTA per chunk; whole tiles arrive by bulk copies when USE_BULK (sources
+// 16-byte aligned), the last partial tile (and every tile otherwise) by plain
+// loads.  Waits are bounded: on timeout the pass sets DEV_ERR_TIMEOUT, gives
+// copies in flight a bounded chance to land and the CTA returns.
+template <class Loader, class Storer, bool USE_BULK>
+__global__ void __launch_bounds__(NT, CTAS_PER_SM) k_scatter(Loader ld, Storer st, PassGeom g,
+                                                           const uint32_t* counts,
+                                                           const uint32_t* totals, uint32_t* err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    TmaSmem<NV>& S = *reinterpret_cast<TmaSmem<NV>*>(smem_raw);
-    {
-        const int d = threadIdx.x;
-        const uint32_t t = d < RADIX ? totals[d] : 0u;
-        const uint32_t base = block_exclusive_scan<TMA_THREADS>(t, S.warp_tot, &S.total);
-        if (d < RADIX) S.run[d] = base + counts[(int64_t)d * g.chunks + blockIdx.x];
+    ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(smem_raw);
+    uint32_t run[DPT];
+    {   // global start of this chunk's records of each digit
+        uint32_t t[DPT], sum = 0;
+#pragma unroll
+        for (int i = 0; i < DPT; i++) {
+            const int d = threadIdx.x * DPT + i;
+            t[i] = d < g.bins ? totals[d] : 0u;
+            sum += t[i];
+        }
+        uint32_t base = block_exclusive_scan<NT>(sum, S.warp_tot, &S.total);
+#pragma unroll
+        for (int i = 0; i < DPT; i++) {
+            const int d = threadIdx.x * DPT + i;
+            run[i] = d < g.bins ? base + counts[(int64_t)d * g.chunks + blockIdx.x] : 0u;
+            base += t[i];
+        }
     }
     const int64_t beg = (int64_t)blockIdx.x * g.chunk;
     const int64_t end = min(g.n, beg + g.chunk);
-    const int64_t nfull = end > beg ? (end - beg) / TT : 0;
-    const uint32_t arr_bytes = Loader::TILE_ELEMS * 4u;
+    const int64_t nfull = USE_BULK && end > beg ? (end - beg) / TT : 0;
+    constexpr uint32_t ARR_BYTES = Loader::TILE_WORDS * 4u;
+    static_assert(Loader::NARR * Loader::TILE_WORDS <= 4 * TT, "a tile's sources fit one buffer");
     if (threadIdx.x == 0) {
-        tma_bar_init(&S.bar[0]);
-        tma_bar_init(&S.bar[1]);
+        bar_init(&S.bar[0]);
+        bar_init(&S.bar[1]);
         S.timed_out = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    const uint64_t policy = evict_first_policy();
     auto issue = [&](int64_t t, int b) {
         const int64_t tbase = beg + t * TT;
-        tma_expect(&S.bar[b], arr_bytes * Loader::NARR);
+        bar_expect(&S.bar[b], ARR_BYTES * Loader::NARR);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&S.buf[b][0]);
 #pragma unroll
         for (int a = 0; a < Loader::NARR; a++)
-            tma_load_1d(&S.in[b][a][0], ld.tile_src(a, tbase), arr_bytes, &S.bar[b]);
+            bulk_load(dst + (size_t)a * TT, ld.tile_src(a, tbase), ARR_BYTES, &S.bar[b], policy);
     };
     if (threadIdx.x == 0 && nfull > 0) issue(0, 0);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t t = 0; t < nfull; t++) {
         const int b = (int)(t & 1);
-        if (threadIdx.x == 0 && t + 1 < nfull) {
-            // the other buffer was last read by tile t-1, finished at its
-            // closing barrier; order those reads before the async writes
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(t + 1, b ^ 1);
-        }
+        // the other buffer was last used by tile t-1, released at its closing barrier
+        if (threadIdx.x == 0 && t + 1 < nfull) issue(t + 1, b ^ 1);
         const uint32_t parity = (uint32_t)((t >> 1) & 1);
         uint32_t spins = 0;
-        while (!tma_try_wait(&S.bar[b], parity)) {
-            if (++spins >= TMA_WAIT_LIMIT) {
+        while (!bar_try_wait(&S.bar[b], parity)) {
+            if (++spins >= WAIT_LIMIT) {
                 S.timed_out = 1;
                 break;
             }
@@ -493,103 +446,87 @@ __global__ void __launch_bounds__(TMA_THREADS, TMA_CTAS_PER_SM) k_downsweep_tma(
         __syncthreads();
         if (S.timed_out) {
             if (threadIdx.x == 0) atomicOr(err, DEV_ERR_TIMEOUT);
-            // give copies still in flight a bounded chance to land
             for (int bb = 0; bb < 2; bb++) {
                 uint32_t s2 = 0;
-                while (!tma_try_wait(&S.bar[bb], parity) && ++s2 < TMA_WAIT_LIMIT) {
+                while (!bar_try_wait(&S.bar[bb], parity) && ++s2 < WAIT_LIMIT) {
                 }
             }
             return;
         }
-        SmemSrc<Loader> src{ld, &S.in[b][0][0], beg + t * TT};
-        scatter_tile<TMA_THREADS, TT, NV, STORE_KEY>(src, st, g, TT, S);
+        const int64_t tbase = beg + t * TT;
+        const uint32_t* in = reinterpret_cast<const uint32_t*>(&S.buf[b][0]);
+        uint4 rec[IT];
+#pragma unroll
+        for (int j = 0; j < IT; j++) rec[j] = ld.srec(in, w * 32 * IT + j * 32 + lane, tbase);
+        scatter_tile(rec, TT, &S.buf[b][0], st, g, run, S);
     }
-    const int64_t tail = beg + nfull * TT;
-    if (tail < end) {
-        GlobalSrc<Loader> src{ld, tail};
-        scatter_tile<TMA_THREADS, TT, NV, STORE_KEY>(src, st, g, (int)(end - tail), S);
+    for (int64_t tbase = beg + nfull * TT; tbase < end; tbase += TT) {
+        const int tcount = (int)min((int64_t)TT, end - tbase);
+        uint4 rec[IT];
+#pragma unroll
+        for (int j = 0; j < IT; j++) {
+            const int li = w * 32 * IT + j * 32 + lane;
+            rec[j] = li < tcount ? ld.grec(tbase + li) : make_uint4(0, 0, 0, 0);
+        }
+        scatter_tile(rec, tcount, &S.buf[0][0], st, g, run, S);
     }
 }
 
-// Record arrays (ping-pong buffers between passes).
-template <int NV>
-struct ArrLoader {
-    static constexpr double KEY_BYTES = 4.0;
-    static constexpr double REC_BYTES = 4.0 * (1 + NV);
-    static constexpr int NARR = 1 + NV;
-    static constexpr uint32_t TILE_ELEMS = TT;
-    const uint32_t* k;
-    const uint32_t* v[NV > 0 ? NV : 1];
-    __device__ __forceinline__ uint32_t key(int64_t i) const { return __ldg(k + i); }
-    __device__ __forceinline__ uint32_t val(int q, int64_t i) const { return __ldg(v[q] + i); }
-    __device__ __forceinline__ const void* tile_src(int a, int64_t tbase) const {
-        return (a == 0 ? k : v[a - 1]) + tbase;
+// ---- intermediate records -----------------------------------------------------
+struct AosLoader {
+    static constexpr double REC_BYTES = 16.0;
+    static constexpr int NARR = 1;
+    static constexpr uint32_t TILE_WORDS = 4 * TT;
+    const uint4* r;
+    __device__ __forceinline__ uint32_t key(int64_t i) const { return __ldg(&r[i].x); }
+    __device__ __forceinline__ const void* tile_src(int, int64_t tbase) const { return r + tbase; }
+    __device__ __forceinline__ uint4 srec(const uint32_t* in, int li, int64_t) const {
+        return reinterpret_cast<const uint4*>(in)[li];
     }
-    __device__ __forceinline__ uint32_t skey(const uint32_t* in, int li, int64_t) const { return in[li]; }
-    __device__ __forceinline__ uint32_t sval(const uint32_t* in, int q, int li, int64_t) const {
-        return in[(q + 1) * TT + li];
-    }
-    bool tma_ok() const {
-        bool ok = ((uintptr_t)k & 15) == 0;
-        for (int q = 0; q < NV; q++) ok = ok && ((uintptr_t)v[q] & 15) == 0;
-        return ok;
+    __device__ __forceinline__ uint4 grec(int64_t i) const { return __ldg(r + i); }
+    bool tma_ok() const { return ((uintptr_t)r & 15) == 0; }
+};
+
+struct AosStorer {
+    uint4* r;
+    uint16_t* dig;  // next pass's digit of each record
+    int next_shift;
+    uint32_t next_mask;
+    __host__ __device__ double rec_bytes() const { return 18.0; }
+    __device__ __forceinline__ void store(int64_t p, const uint4& x) const {
+        r[p] = x;
+        dig[p] = (uint16_t)((x.x >> next_shift) & next_mask);
     }
 };
 
-template <int NV>
-struct ArrStorer {
-    __host__ __device__ double rec_bytes() const { return 4.0 * (1 + NV); }
-    uint32_t* k;
-    uint32_t* v[NV > 0 ? NV : 1];
-    __device__ __forceinline__ void key(int64_t p, uint32_t x) const { k[p] = x; }
-    __device__ __forceinline__ void val(int q, int64_t p, uint32_t x) const { v[q][p] = x; }
-};
-
-// Chunks per SM.  Each chunk keeps one partially written line per digit and
-// output array in L2 while it streams, so the chunk count is kept small
-// enough that those write fronts fit in L2 (WTRI_RADIX_CHUNKS_PER_SM
-// overrides the default of 2 for tuning).
-inline int chunks_per_sm() {
-    static int v = 0;
-    if (v == 0) {
-        const char* e = getenv("WTRI_RADIX_CHUNKS_PER_SM");
-        int x = e ? atoi(e) : 0;
-        v = (x >= 1 && x <= 64) ? x : 2;
-    }
-    return v;
-}
-
-// Chunking: enough chunks to fill the GPU, each a whole number of tiles.
-inline PassGeom make_geom(int64_t n, int shift, int bits, int per_sm = 0) {
+// ---- host side ------------------------------------------------------------------
+// Chunking: CTAS_PER_SM chunks per SM at most, each a whole number of tiles.
+inline PassGeom make_geom(int64_t n, int shift, int bits) {
     PassGeom g;
     g.n = n;
-    const int64_t tiles = (n + TILE - 1) / TILE;
-    int64_t want = (int64_t)sm_count() * (per_sm > 0 ? per_sm : chunks_per_sm());
+    const int64_t tiles = (n + TT - 1) / TT;
+    int64_t want = (int64_t)sm_count() * CTAS_PER_SM;
     if (want > tiles) want = tiles;
     if (want < 1) want = 1;
     const int64_t tiles_per = (tiles + want - 1) / want;
-    g.chunk = tiles_per * TILE;
+    g.chunk = tiles_per * TT;
     g.chunks = (int)((n + g.chunk - 1) / g.chunk);
     if (g.chunks < 1) g.chunks = 1;
     g.shift = shift;
-    g.mask = (bits >= 32) ? 0xffffffffu : ((1u << bits) - 1u);
+    g.bins = 1 << bits;
+    g.bits = bits;
+    g.mask = (uint32_t)g.bins - 1u;
     return g;
 }
 
-template <int NV>
-inline size_t downsweep_smem() {
-    return sizeof(TileSmem<NV>);
-}
-
-// Scratch for counts: RADIX * chunks + RADIX totals (uint32).
+// Scratch for counts: MAX_BINS * chunks + MAX_BINS (uint32).
 inline size_t scratch_words(int64_t n) {
-    PassGeom g = make_geom(n, 0, BITS);
-    return (size_t)RADIX * g.chunks + RADIX;
+    PassGeom g = make_geom(n, 0, MAX_BITS);
+    return (size_t)MAX_BINS * g.chunks + MAX_BINS;
 }
 
-// One pass.  'scratch' holds scratch_words(n) uint32 (device).
-// Whether the TMA-fed scatter is used (WTRI_RADIX_TMA=0 turns it off).
-inline bool tma_enabled() {
+// Whether whole tiles use bulk copies (WTRI_RADIX_TMA=0 turns them off).
+inline bool bulk_enabled() {
     static int v = -1;
     if (v < 0) {
         const char* e = getenv("WTRI_RADIX_TMA");
@@ -598,47 +535,91 @@ inline bool tma_enabled() {
     return v == 1;
 }
 
-template <int NV, bool STORE_KEY, class Loader, class Storer>
-int run_pass(const Loader& ld, const Storer& st, int64_t n, int shift, int bits,
-             uint32_t* scratch, cudaStream_t s, uint32_t* err) {
-    if (n <= 0) return WTRI_OK;
-    const bool use_tma = tma_enabled() && err != nullptr && ld.tma_ok();
-    PassGeom g = make_geom(n, shift, bits, use_tma ? TMA_CTAS_PER_SM : 0);
+// Digit widths of a sort over 'bits' key bits: as few passes as MAX_BITS
+// allows, bits spread evenly (e.g. 26 -> 9, 9, 8; 20 -> 10, 10).
+inline int pass_count(int bits) { return (bits + MAX_BITS - 1) / MAX_BITS; }
+inline int pass_bits(int bits, int p) {
+    const int passes = pass_count(bits);
+    return bits / passes + (p < bits % passes ? 1 : 0);
+}
+inline int pass_shift(int bits, int p) {
+    int s = 0;
+    for (int q = 0; q < p; q++) s += pass_bits(bits, q);
+    return s;
+}
+
+template <class Dig, class Loader, class Storer>
+int run_pass(const Dig& dg, const Loader& ld, const Storer& st, const PassGeom& g, uint32_t* scratch,
+             cudaStream_t s, uint32_t* err, double hist_bytes) {
+    if (g.n <= 0) return WTRI_OK;
     uint32_t* counts = scratch;
-    uint32_t* totals = scratch + (size_t)RADIX * g.chunks;
+    uint32_t* totals = scratch + (size_t)MAX_BINS * g.chunks;
     {
-        ProfScope ps("radix_upsweep", s, (double)n * Loader::KEY_BYTES + 4.0 * RADIX * g.chunks, 1);
-        WTRI_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * RADIX * (size_t)g.chunks, s));
-        k_upsweep<Loader><<<g.chunks * UP_SPLIT, THREADS, 0, s>>>(ld, g, counts);
+        ProfScope ps("radix_upsweep", s, hist_bytes * (double)g.n + 4.0 * g.bins * g.chunks, 1);
+        WTRI_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)g.bins * g.chunks, s));
+        k_upsweep<Dig><<<g.chunks * UP_SPLIT, NT, 0, s>>>(dg, g, counts);
     }
     {
-        ProfScope ps("radix_digit_scan", s, 8.0 * RADIX * g.chunks, 1);
-        k_digit_scan<<<RADIX, THREADS, 0, s>>>(counts, g.chunks, totals);
+        ProfScope ps("radix_digit_scan", s, 8.0 * g.bins * g.chunks, 1);
+        k_digit_scan<<<g.bins, NT, 0, s>>>(counts, g.chunks, totals);
     }
-    if (use_tma) {
-        const size_t smem = sizeof(TmaSmem<NV>);
-        static bool attr_tma = false;  // per instantiation; idempotent
-        if (!attr_tma) {
-            WTRI_CUDA(cudaFuncSetAttribute(k_downsweep_tma<NV, Loader, Storer, STORE_KEY>,
+    const size_t smem = sizeof(ScatterSmem);
+    ProfScope ps("radix_downsweep", s, (double)g.n * (Loader::REC_BYTES + st.rec_bytes()), 1);
+    if (bulk_enabled() && ld.tma_ok()) {
+        static bool attr = false;  // per instantiation; idempotent
+        if (!attr) {
+            WTRI_CUDA(cudaFuncSetAttribute(k_scatter<Loader, Storer, true>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr_tma = true;
+            attr = true;
         }
-        ProfScope ps("radix_downsweep", s, (double)n * (Loader::REC_BYTES + st.rec_bytes()), 1);
-        k_downsweep_tma<NV, Loader, Storer, STORE_KEY><<<g.chunks, TMA_THREADS, smem, s>>>(
-            ld, st, g, counts, totals, err);
+        k_scatter<Loader, Storer, true><<<g.chunks, NT, smem, s>>>(ld, st, g, counts, totals, err);
     } else {
-        const size_t smem = downsweep_smem<NV>();
-        static bool attr_set = false;  // per instantiation; idempotent
-        if (!attr_set) {
-            WTRI_CUDA(cudaFuncSetAttribute(k_downsweep<NV, Loader, Storer, STORE_KEY>,
+        static bool attr = false;
+        if (!attr) {
+            WTRI_CUDA(cudaFuncSetAttribute(k_scatter<Loader, Storer, false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr_set = true;
+            attr = true;
         }
-        ProfScope ps("radix_downsweep", s, (double)n * (Loader::REC_BYTES + st.rec_bytes()), 1);
-        k_downsweep<NV, Loader, Storer, STORE_KEY><<<g.chunks, THREADS, smem, s>>>(ld, st, g, counts,
-                                                                                  totals);
+        k_scatter<Loader, Storer, false><<<g.chunks, NT, smem, s>>>(ld, st, g, counts, totals, err);
     }
     WTRI_CUDA(cudaGetLastError());
+    return WTRI_OK;
+}
+
+// Full stable LSD sort of n records over 'bits' key bits: first pass from
+// 'first', middle passes through the 16-byte record buffers rec_a / rec_b
+// (n records each) with digits in 'dig' (n 16-bit words), last pass into
+// 'last'.
+template <class First, class Last>
+int lsd_sort(const First& first, const Last& last, int64_t n, int bits, uint4* rec_a, uint4* rec_b,
+             uint16_t* dig, uint32_t* scratch, cudaStream_t s, uint32_t* err) {
+    const int passes = pass_count(bits);
+    if (passes == 0) return set_error(WTRI_EINVAL, "internal: zero-pass sort");
+    uint4* cur = rec_a;
+    uint4* nxt = rec_b;
+    for (int p = 0; p < passes; p++) {
+        const PassGeom g = make_geom(n, pass_shift(bits, p), pass_bits(bits, p));
+        AosStorer as{nxt, dig, 0, 0u};
+        if (p + 1 < passes) {
+            as.next_shift = pass_shift(bits, p + 1);
+            as.next_mask = (1u << pass_bits(bits, p + 1)) - 1u;
+        }
+        AosLoader al{cur};
+        StoredDigits sd{dig};
+        if (p == 0) {
+            KeyDigits<First> kd{first, g.shift, g.mask};
+            if (passes == 1) {
+                WTRI_TRY(run_pass(kd, first, last, g, scratch, s, err, 4.0));
+            } else {
+                WTRI_TRY(run_pass(kd, first, as, g, scratch, s, err, 4.0));
+            }
+        } else if (p == passes - 1) {
+            WTRI_TRY(run_pass(sd, al, last, g, scratch, s, err, 2.0));
+        } else {
+            WTRI_TRY(run_pass(sd, al, as, g, scratch, s, err, 2.0));
+        }
+        if (p + 1 < passes) std::swap(cur, nxt);
+    }
     return WTRI_OK;
 }
 
