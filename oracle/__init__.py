@@ -28,6 +28,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "wtri_oracle.c")
+_SRC_DHL = os.path.join(_HERE, "wtri_dhl.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
@@ -38,10 +39,10 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP) into oracle/_build/liboracle.so."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_DHL))):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC, _SRC_DHL, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -83,7 +84,11 @@ def lib():
         L.or_topk_shard.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, i64p, ctypes.c_int,
                                     ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, i32p,
                                     u64p, f64p, I64P, I64P]
-        for f in (L.or_validate, L.or_sym_csr, L.or_edge_order, L.or_oriented_csr,
+        L.dhl_topk.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, ctypes.c_int,
+                               ctypes.c_int64, ctypes.c_double, i32p, u64p, f64p, I64P, i64p]
+        L.dhl_alpha.argtypes = [ctypes.c_int, ctypes.c_double]
+        L.dhl_alpha.restype = ctypes.c_double
+        for f in (L.dhl_topk, L.or_validate, L.or_sym_csr, L.or_edge_order, L.or_oriented_csr,
                   L.or_score, L.or_topk, L.or_count_triangles, L.or_sample_edges,
                   L.or_topk_of_sampled, L.or_topk_shard):
             f.restype = ctypes.c_int
@@ -193,6 +198,36 @@ def topk(n, u, v, w, p, k, nthreads=0):
     c = int(cnt.value)
     return {"tri": tri[: 3 * c].reshape(c, 3), "key": key[:c], "value": val[:c],
             "count": c, "ntri": int(ntri.value)}
+
+
+def dhl_alpha(p, beta=2.0):
+    """alpha_p = 2 - p / (p - 1 + beta) for power-law weights (Section 3.3)."""
+    return float(lib().dhl_alpha(pcode(p), float(beta)))
+
+
+def dhl_topk(n, u, v, w, p, k, alpha=None, beta=2.0):
+    """The paper's dynamic heavy-light algorithm (Algorithm 2), single
+    thread: exact top-k like topk().  alpha=None uses alpha_p for power-law
+    weights of exponent beta; alpha <= 0 runs Auto-HL (Section 3.3).
+    Adds 'stats': L->H moves, H->S moves, distinct triangles listed, edge
+    probes, final h and l."""
+    u, v, w = _arr(u), _arr(v), _arr(w)
+    m = u.shape[0]
+    k = int(k)
+    if alpha is None:
+        alpha = dhl_alpha(p, beta)
+    tri = np.zeros(3 * max(k, 1), np.int32)
+    key = np.zeros(max(k, 1), np.uint64)
+    val = np.zeros(max(k, 1), np.float64)
+    cnt = ctypes.c_int64(0)
+    stats = np.zeros(6, np.int64)
+    rc = lib().dhl_topk(n, m, u, v, w, pcode(p), k, float(alpha), tri, key, val, ctypes.byref(cnt), stats)
+    if rc != 0:
+        raise OracleError(f"dhl_topk failed (rc={rc})")
+    c = int(cnt.value)
+    names = ("light_to_heavy", "heavy_to_super", "listed", "probes", "h", "l")
+    return {"tri": tri[: 3 * c].reshape(c, 3), "key": key[:c], "value": val[:c], "count": c,
+            "stats": dict(zip(names, (int(x) for x in stats)))}
 
 
 def philox4x64_10(counter, key):
