@@ -8,12 +8,20 @@ whole path on one graph: wtri_build_csr from device-resident COO
 lists) followed by the exact top-1000 query at p = -inf, 1, 2 and +inf.
 --workload large: Chung-Lu n=5e7, m=1e9, exponent 2.0 drawn on the device,
 one step = build + the exact top-1000 query at p = 1, plus 1e7 weighted edge
-draws (Philox seed 7) reported with their recall.  The value is edges of the
+draws (Philox seed 7) reported with their recall.
+--workload batch: 4,096 Chung-Lu graphs (n log-uniform in [100, 2e5], m = 10 n,
+exponent 2.2) drawn on the device, each with its own k and p; the value is
+queries per second of one wtri_topk_batch call over all of them, reported
+beside the same queries as back-to-back wtri_topk calls.
+--workload serve: the 1e9-edge graph and two 2e8-edge graphs resident (drawn
+on the device), 100,000 Poisson requests at 2,000 req/s through the server;
+the value is served queries per second, with p50/p99 latency beside a
+sequential wtri_topk loop fed the same arrivals.  The value is edges of the
 graph pushed through a step per second (whole job: all ranks' edges over
 the max-over-ranks time).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wtri|reference]
-                  [--workload mid|large|quarter|tiny]
+                  [--workload mid|large|quarter|tiny|batch|serve]
 
 --impl reference times the CPU oracle (brute force, all host cores) on a
 bounded sample of the same workload.
@@ -42,6 +50,11 @@ METRIC = "top-k query latency & oriented-edges/sec (HBM GB/s vs peak), batched/s
 WORKLOAD = "chung-lu n=1e6 m=2e7 gamma=2.1 dmax=5e4 zipf(2,1e6) int32 weights, k=1000, p in {-inf,1,2,+inf}"
 WORKLOAD_LARGE = ("chung-lu n=5e7 m=1e9 gamma=2.0 dmax=5e4 zipf(2,1e6) int32 weights (drawn on the "
                   "device, seed 2), k=1000, p=1")
+WORKLOAD_BATCH = ("4096 chung-lu graphs, n log-uniform [100, 2e5], m=10n, gamma=2.2, zipf(2,1e6) int32 "
+                  "weights (drawn on the device, seed 3); per-graph k ~ U[10,1000], p ~ U{-inf,1,2,+inf}")
+WORKLOAD_SERVE = ("serving pool: the 1e9-edge graph + two chung-lu graphs n=1e7 m=2e8 gamma=2.1 zipf(2,1e6) "
+                  "(drawn on the device); Poisson 2,000 req/s, 100,000 requests, k ~ U[10,1000], "
+                  "p ~ U{-inf,1,2,+inf}, HBM budget 120 GB")
 STEP_DEF = "wtri_build_csr from device COO + exact top-k queries at the workload's p values"
 FALLBACK_HBM_GBS = 6800.0
 
@@ -53,9 +66,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wtri", choices=["wtri", "reference"])
     ap.add_argument("--k", type=int, default=1000)
-    ap.add_argument("--workload", default="mid", choices=["mid", "large", "quarter", "tiny"],
+    ap.add_argument("--workload", default="mid", choices=["mid", "large", "quarter", "tiny", "batch", "serve"],
                     help="mid: the bench workload; large: n=5e7 m=1e9 (device-generated); "
-                         "quarter: n=1e6 m=5e6 (profiling captures); tiny: n=2000 m=20000")
+                         "quarter: n=1e6 m=5e6 (profiling captures); tiny: n=2000 m=20000; "
+                         "batch: the 4,096-graph batch (batched vs plain queries); "
+                         "serve: the full serving pool and request stream")
     ap.add_argument("--large-size", default=None,
                     help="n,m: the large workload's recipe at another size (profiling captures)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -122,7 +137,7 @@ def ncu_traffic():
     """DRAM bytes per radix-scatter launch at the bench size, from the committed
     ncu capture, if the kernel sources are unchanged since it was taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "radix_downsweep_traffic_quarter.txt")
+    path = os.path.join(ROOT, "profiles", "radix_scatter_traffic_quarter.txt")
     if not os.path.exists(path):
         return None, "no capture"
     fields = {}
@@ -264,73 +279,204 @@ def bench_batch(wt, stream, count=1024, n_hi=20_000):
             d.free()
 
 
+def bench_batch_full(wt, count=4096, n_hi=200_000, reps=3):
+    """The full batch workload: `count` Chung-Lu graphs (n log-uniform in
+    [100, n_hi], m = 10 n, exponent 2.2, Zipf(2)) drawn on the device, each
+    with its own k ~ U[10,1000] and p ~ U{-inf,1,2,+inf}: wtri_topk_batch
+    over all of them against the same queries as back-to-back wtri_topk
+    calls (host results both; results compared bit for bit)."""
+    import synth
+    import torch
+    t0 = time.perf_counter()
+    b = synth.batch_graphs_device(count, seed=3, n_hi=n_hi)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    ps, ks = synth.batch_queries(count, seed=3)
+    t0 = time.perf_counter()
+    ds = [wt.build_csr(*b.graph(i)) for i in range(count)]
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    edges = int(b.ms.sum())
+    del b
+    torch.cuda.empty_cache()
+    try:
+        wt.topk_batch(ds[:64], ps[:64], ks[:64])
+        for i in range(8):
+            ds[i].topk(ps[i], int(ks[i]))
+        times = []
+        res = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = wt.topk_batch(ds, ps, ks)
+            times.append(time.perf_counter() - t0)
+        t_batch = statistics.median(times)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plain = [d.topk(ps[i], int(ks[i])) for i, d in enumerate(ds)]
+        t_plain = time.perf_counter() - t0
+        same = all(np.array_equal(res[i][0], plain[i][0]) and np.array_equal(res[i][1], plain[i][1])
+                   for i in range(count))
+        return {"graphs": count, "edges": edges, "n_range": [100, n_hi],
+                "batched_ms": 1e3 * t_batch, "batched_ms_all": [1e3 * x for x in times],
+                "plain_calls_ms": 1e3 * t_plain, "speedup": t_plain / t_batch,
+                "results_identical": bool(same), "build_all_ms": 1e3 * t_build,
+                "device_generation_ms": 1e3 * t_gen,
+                "api": "wtri_topk_batch vs wtri_topk, host results"}
+    finally:
+        for d in ds:
+            d.free()
+
+
+def run_batch_workload(args, world, rank):
+    """--workload batch: the 4,096-graph batch at full size, one JSON line."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_1910_00692_gb300 as wt
+    wt.lib()
+    r = bench_batch_full(wt)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": r["graphs"] / (r["batched_ms"] / 1e3), "unit": "queries/s",
+        "n_gpus": world, "steps": 3, "warmup": 1, "ms_per_step": r["batched_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_BATCH, "global_batch": r["graphs"],
+                   "step": "one wtri_topk_batch call over every graph's query (graphs resident)"},
+        "batch": r,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def serve_run(wt, ds, edges, rate, count, seq_count, note, seq_budget_s=1e9):
+    """Poisson arrivals at `rate` req/s over the resident graphs `ds`, k ~
+    U[10,1000], p ~ U{-inf,1,2,+inf}, through the continuous-batching server
+    (latency = submission to completion, measured by the server).  Baseline:
+    a sequential loop of wtri_topk over the first `seq_count` requests, fed
+    the same arrival times (its latency includes waiting for the requests
+    before it); the server's figures over the same requests sit beside it."""
+    rng = np.random.default_rng(6)
+    gaps = rng.exponential(1.0 / rate, size=count)
+    arrive = np.cumsum(gaps)
+    gid = rng.integers(0, len(ds), size=count)
+    ks = rng.integers(10, 1001, size=count)
+    ps = np.array(PS)[rng.integers(0, 4, size=count)]
+    srv = wt.Server(120 << 30, 256)
+    ids = [srv.add_graph(d) for d in ds]
+    for i in range(16):  # warm-up
+        t = srv.submit(ids[i % len(ds)], PS[i % 4], 100)
+        while srv.poll(t, 100) is None:
+            time.sleep(0.0002)
+    tickets = []
+    t0 = time.perf_counter()
+    for i in range(count):
+        while time.perf_counter() - t0 < arrive[i]:
+            pass
+        tickets.append(srv.submit(ids[gid[i]], ps[i], int(ks[i])))
+    lat = [None] * count
+    t_last = 0.0
+    for i in range(count):
+        r = srv.poll(tickets[i], int(ks[i]))
+        while r is None:
+            time.sleep(0.0001)
+            r = srv.poll(tickets[i], int(ks[i]))
+        lat[i] = r[2]
+        t_last = max(t_last, arrive[i] + r[2])
+    st = srv.stats()
+    srv.free()
+    lat = np.array(lat)
+    # sequential loop: real service times, queueing from the same arrivals
+    # (stopped early, at a whole request, once it has run seq_budget_s)
+    service = np.empty(seq_count)
+    t_seq = time.perf_counter()
+    done = seq_count
+    for i in range(seq_count):
+        a = time.perf_counter()
+        ds[gid[i]].topk(ps[i], int(ks[i]))
+        service[i] = time.perf_counter() - a
+        if a - t_seq > seq_budget_s:
+            done = i + 1
+            break
+    seq_count = done
+    service = service[:done]
+    finish = 0.0
+    seq_lat = np.empty(seq_count)
+    for i in range(seq_count):
+        start = max(arrive[i], finish)
+        finish = start + service[i]
+        seq_lat[i] = finish - arrive[i]
+    head = lat[:seq_count]
+    out = {"requests": count, "rate_req_s": rate, "graphs_edges": [int(x) for x in edges],
+           "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+           "qps": count / t_last, "micro_batches": int(st["batches"]), "retries": int(st["retries"]),
+           "sequential_requests": seq_count,
+           "sequential_p50_ms": 1e3 * float(np.percentile(seq_lat, 50)),
+           "sequential_p99_ms": 1e3 * float(np.percentile(seq_lat, 99)),
+           "sequential_qps": seq_count / finish,
+           "sequential_mean_service_ms": 1e3 * float(service.mean()),
+           "budget_gb": 120, "note": note}
+    if seq_count < count:
+        out["server_first_requests_p50_ms"] = 1e3 * float(np.percentile(head, 50))
+        out["server_first_requests_p99_ms"] = 1e3 * float(np.percentile(head, 99))
+    return out
+
+
 def bench_serve(wt, g_mid, rate=2000.0, count=4000):
-    """Serving: Poisson arrivals at `rate` req/s over resident graphs (the
-    bench graph plus two Chung-Lu graphs of 2e6 and 5e6 edges), k ~ U[10,1000],
-    p ~ U{-inf,1,2,+inf}.  Latency = submission to completion.  Baseline: a
-    sequential loop of wtri_topk fed the same arrival times (its latency
-    includes waiting for the previous requests)."""
+    """Serving, reduced pool: the bench graph plus two Chung-Lu graphs of 2e6
+    and 5e6 edges."""
     import synth
     gs = [g_mid, synth.scaled_mid_graph(200_000, 2_000_000, seed=5),
           synth.scaled_mid_graph(500_000, 5_000_000, seed=6)]
     ds = [wt.build_csr(x.n, x.u, x.v, x.w) for x in gs]
-    rng = np.random.default_rng(6)
-    gaps = rng.exponential(1.0 / rate, size=count)
-    arrive = np.cumsum(gaps)
-    gid = rng.integers(0, len(gs), size=count)
-    ks = rng.integers(10, 1001, size=count)
-    ps = np.array(PS)[rng.integers(0, 4, size=count)]
     try:
-        srv = wt.Server(120 << 30, 256)
-        ids = [srv.add_graph(d) for d in ds]
-        for i in range(16):  # warm-up
-            t = srv.submit(ids[i % 3], PS[i % 4], 100)
-            while srv.poll(t, 100) is None:
-                time.sleep(0.0002)
-        tickets = []
-        t0 = time.perf_counter()
-        for i in range(count):
-            while time.perf_counter() - t0 < arrive[i]:
-                pass
-            tickets.append(srv.submit(ids[gid[i]], ps[i], int(ks[i])))
-        # latency is measured by the server (submission to completion), so
-        # collecting the results in order does not change it
-        lat = [None] * count
-        t_last = 0.0
-        for i in range(count):
-            r = srv.poll(tickets[i], int(ks[i]))
-            while r is None:
-                time.sleep(0.0001)
-                r = srv.poll(tickets[i], int(ks[i]))
-            lat[i] = r[2]
-            t_last = max(t_last, arrive[i] + r[2])
-        t_end = t_last
-        st = srv.stats()
-        srv.free()
-        lat = np.array(lat)
-        # sequential loop: real service times, queueing from the same arrivals
-        service = np.empty(count)
-        for i in range(count):
-            a = time.perf_counter()
-            ds[gid[i]].topk(ps[i], int(ks[i]))
-            service[i] = time.perf_counter() - a
-        finish = 0.0
-        seq_lat = np.empty(count)
-        for i in range(count):
-            start = max(arrive[i], finish)
-            finish = start + service[i]
-            seq_lat[i] = finish - arrive[i]
-        return {"requests": count, "rate_req_s": rate, "graphs_edges": [int(x.m) for x in gs],
-                "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                "qps": count / t_end, "micro_batches": int(st["batches"]), "retries": int(st["retries"]),
-                "sequential_p50_ms": 1e3 * float(np.percentile(seq_lat, 50)),
-                "sequential_p99_ms": 1e3 * float(np.percentile(seq_lat, 99)),
-                "sequential_qps": count / finish, "budget_gb": 120,
-                "note": "reduced pool: the bench graph and two Chung-Lu graphs instead of the "
-                        "1e9- and 2e8-edge graphs (host generation time)"}
+        return serve_run(wt, ds, [x.m for x in gs], rate, count, count,
+                         "reduced pool: the bench graph and two Chung-Lu graphs instead of the "
+                         "1e9- and 2e8-edge graphs (the full pool runs under --workload serve)")
     finally:
         for d in ds:
             d.free()
+
+
+def run_serve_workload(args, world, rank, count=100_000, seq_count=20_000):
+    """--workload serve: the full pool (the 1e9-edge graph and two 2e8-edge
+    graphs, drawn on the device, 118 GB resident), 100,000 requests at
+    2,000 req/s; one JSON line."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_1910_00692_gb300 as wt
+    import synth
+    wt.lib()
+    ds, edges = [], []
+    t0 = time.perf_counter()
+    for g in synth.serve_pool_device():
+        ds.append(wt.build_csr(g.n, g.u, g.v, g.w))
+        edges.append(g.m)
+        del g
+        torch.cuda.empty_cache()
+    torch.cuda.synchronize()
+    t_pool = time.perf_counter() - t0
+    try:
+        r = serve_run(wt, ds, edges, 2000.0, count, seq_count,
+                      "full pool; sequential baseline over the first sequential_requests requests "
+                      "(same arrivals, at most 150 s of sequential service), server figures over "
+                      "all requests and over those", seq_budget_s=150.0)
+    finally:
+        for d in ds:
+            d.free()
+    r["pool_draw_and_build_s"] = t_pool
+    r["resident_gb"] = 84 * sum(edges) / 1e9
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": r["qps"], "unit": "queries/s", "n_gpus": world,
+        "steps": count, "warmup": 16, "ms_per_step": r["p50_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_SERVE, "global_batch": count,
+                   "step": "one served top-k request (p50 latency in ms_per_step)"},
+        "serve": r,
+    }
+    print(json.dumps(line), flush=True)
 
 
 def host_arrays(g, limit=None):
@@ -398,6 +544,13 @@ def main():
             import torch.distributed as dist
             dist.init_process_group("gloo")
         run_reference(args, world, rank)
+        return
+
+    if args.workload == "batch":
+        run_batch_workload(args, world, rank)
+        return
+    if args.workload == "serve":
+        run_serve_workload(args, world, rank)
         return
 
     import torch
@@ -573,6 +726,15 @@ def main():
         t0 = time.perf_counter()
         oracle.topk(g.n, cu, cv, cw, 1.0, k)
         t_q = time.perf_counter() - t0
+        # the paper's own algorithm (Algorithm 2, alpha_p for beta = 2), one
+        # thread, on the same edges: the prior-art CPU line
+        t0 = time.perf_counter()
+        dr = oracle.dhl_topk(g.n, cu, cv, cw, 1.0, k)
+        t_dhl = time.perf_counter() - t0
+        dhl = {"value": cu.shape[0] / t_dhl, "unit": "edges/s", "cores": 1, "s": t_dhl,
+               "algorithm": "dynamic heavy-light (Algorithm 2), alpha_p = 1.5, one thread, "
+                            "edge sort and adjacency build included",
+               "listed": dr["stats"]["listed"], "light_to_heavy": dr["stats"]["light_to_heavy"]}
         if large:
             cpu = {"value": cu.shape[0] / t_q, "unit": "edges/s", "cores": os.cpu_count(),
                    "kind": "oracle",
@@ -583,6 +745,7 @@ def main():
             cpu = {"value": m / (4 * t_q), "unit": "edges/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": "one brute-force top-1000 query (p=1) on the full graph including the "
                              f"oracle's own CSR build, {t_q:.2f} s; a step is four such queries"}
+        cpu["dhl"] = dhl
 
     if rank == 0:
         line = {

@@ -252,6 +252,9 @@ __device__ __forceinline__ uint32_t lo16(uint32_t x) { return x & 0xffffu; }
 #ifndef WTRI_RANK_BALLOT
 #define WTRI_RANK_BALLOT 1
 #endif
+#ifndef WTRI_PEERS_ALL_BITS
+#define WTRI_PEERS_ALL_BITS 0
+#endif
 // Lanes of the warp holding the same digit as this lane (digits of 'bits'
 // bits; lanes with valid == false group only among themselves): one ballot
 // per digit bit.
@@ -259,6 +262,17 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d, int bits, bool valid
 #if WTRI_RANK_BALLOT
     const uint32_t vb = __ballot_sync(0xffffffffu, valid);
     uint32_t p = valid ? vb : ~vb;
+#if WTRI_PEERS_ALL_BITS
+    // digits are below 1 << bits, so the ballots of the bits above are all
+    // zero and leave p unchanged: no per-bit test
+    (void)bits;
+#pragma unroll
+    for (int k = 0; k < MAX_BITS; k++) {
+        const bool bit = (d >> k) & 1u;
+        const uint32_t b = __ballot_sync(0xffffffffu, bit);
+        p &= bit ? b : ~b;
+    }
+#else
 #pragma unroll
     for (int k = 0; k < MAX_BITS; k++) {
         if (k < bits) {
@@ -267,6 +281,7 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d, int bits, bool valid
             p &= bit ? b : ~b;
         }
     }
+#endif
     return p;
 #else
     return __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu);

@@ -331,17 +331,206 @@ def zipf_weights_device(m: int, s: float, cap: int, seed: int, device="cuda"):
 
 
 def large_graph_device(seed: int = 2, n: int = 50_000_000, m: int = 1_000_000_000,
-                       device="cuda") -> DeviceGraph:
+                       device="cuda", gamma: float = 2.0, lookup: bool = True) -> DeviceGraph:
     """The billion-edge workload: Chung-Lu n=5e7, m=1e9, exponent 2.0,
     d_max 5e4, Zipf(2) int32 weights capped at 1e6, drawn on the device
-    (about 36 GB of device memory for the result).  Smaller n, m give the
-    same recipe at reduced size."""
+    (about 36 GB of device memory for the result).  Smaller n, m (and
+    another exponent) give the same recipe at another size; lookup=False
+    drops the sorted edge keys and weights kept for edge lookups."""
     import torch
-    u, v, keys, order = chung_lu_device(n, m, 2.0, 50_000.0, seed, device)
+    u, v, keys, order = chung_lu_device(n, m, gamma, 50_000.0, seed, device)
     w = zipf_weights_device(m, 2.0, 1_000_000, seed, device)
-    w_by_key = torch.empty_like(w)
-    w_by_key[order] = w
+    if lookup:
+        w_by_key = torch.empty_like(w)
+        w_by_key[order] = w
+    else:
+        keys = w_by_key = None
     del order
     torch.cuda.empty_cache()
     return DeviceGraph(n, m, u, v, w, keys, w_by_key,
-                       f"chung-lu n={n} m={m} gamma=2.0 dmax=5e4 zipf(2,1e6) seed={seed} (device)")
+                       f"chung-lu n={n} m={m} gamma={gamma} dmax=5e4 zipf(2,1e6) seed={seed} (device)")
+
+
+def serve_pool_device(device="cuda"):
+    """The serving pool's graphs, one at a time (a generator, so that each
+    can be built and dropped before the next is drawn): the billion-edge
+    graph (seed 2) and two Chung-Lu graphs of 2e8 edges, n = 1e7, exponent
+    2.1, d_max 5e4, Zipf(2) weights (seeds 5 and 6)."""
+    yield large_graph_device(2, device=device, lookup=False)
+    for seed in (5, 6):
+        yield large_graph_device(seed, n=10_000_000, m=200_000_000, device=device, gamma=2.1,
+                                 lookup=False)
+
+
+# ---------------------------------------------------------------------------
+# The 4,096-graph batch drawn on the device in one pass.  Graph g has the
+# size batch_graph(g) gives (n from the same seeded stream, m = 10 n,
+# exponent 2.2, d_max = min(n - 1, sqrt(2 m))) and the same recipe (erased
+# Chung-Lu, truncated Zipf(2) weights capped at 1e6); all graphs' endpoint
+# draws, deduplication, top-ups and subset choice run as a few device-wide
+# sorts instead of 4,096 numpy calls.
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class DeviceBatch:
+    ns: np.ndarray    # int64 [G] vertices of each graph
+    ms: np.ndarray    # int64 [G] edges of each graph
+    offs: np.ndarray  # int64 [G] first edge of graph g in u/v/w (a multiple of 4)
+    u: "object"       # int32 device [sum of padded m], local vertex ids
+    v: "object"
+    w: "object"
+    name: str = ""
+
+    @property
+    def count(self) -> int:
+        return int(self.ns.shape[0])
+
+    def graph(self, g: int):
+        """(n, u, v, w) of graph g: contiguous device slices, 16-byte aligned."""
+        a, b = int(self.offs[g]), int(self.offs[g] + self.ms[g])
+        return int(self.ns[g]), self.u[a:b], self.v[a:b], self.w[a:b]
+
+
+def batch_sizes(count: int, seed: int = 3, n_hi: int = 200_000):
+    """(n, m) of graphs 0..count-1 of the batch, as batch_graph draws them."""
+    ns = np.empty(count, np.int64)
+    for g in range(count):
+        rng = _rng(seed, 10, g)
+        ns[g] = int(round(math.exp(rng.uniform(math.log(100), math.log(n_hi)))))
+    ms = np.minimum(10 * ns, ns * (ns - 1) // 2)
+    return ns, ms
+
+
+_PAIR_BITS = 36  # n <= 2e5 per graph, so min * n + max < 2**36
+
+
+def batch_graphs_device(count: int = 4096, seed: int = 3, n_hi: int = 200_000,
+                        device="cuda") -> DeviceBatch:
+    """The batch workload drawn on the device: ``count`` Chung-Lu graphs,
+    n log-uniform in [100, n_hi], m = 10 n, exponent 2.2, d_max = min(n - 1,
+    sqrt(2 m)), Zipf(2) int32 weights capped at 1e6."""
+    import torch
+    ns, ms = batch_sizes(count, seed, n_hi)
+    if int(ns.max()) ** 2 >= 2 ** _PAIR_BITS:
+        raise ValueError("graph too large for the batch key packing")
+    G = count
+    gamma = 2.2
+    a_exp = 1.0 / (gamma - 1.0)
+    dmax = np.minimum(ns - 1, np.sqrt(2.0 * ms))
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 1_000_003 + 41)
+
+    # expected degrees of every graph, i0 solved by a vectorised bisection
+    N = int(ns.sum())
+    ns_t = torch.as_tensor(ns, device=device)
+    vstart = torch.as_tensor(np.concatenate([[0], np.cumsum(ns)[:-1]]), device=device)
+    gid = torch.repeat_interleave(torch.arange(G, device=device), ns_t)
+    idx = torch.arange(N, dtype=torch.float64, device=device) - vstart[gid].double()
+    dm = torch.as_tensor(dmax, dtype=torch.float64, device=device)
+    target = torch.as_tensor(2.0 * ms, dtype=torch.float64, device=device)
+
+    def theta_of(i0):
+        i0v = i0[gid]
+        return dm[gid] * i0v ** a_exp * (idx + i0v) ** (-a_exp)
+
+    def total(i0):
+        return torch.zeros(G, dtype=torch.float64, device=device).index_add_(0, gid, theta_of(i0))
+
+    lo = torch.full((G,), 1e-9, dtype=torch.float64, device=device)
+    hi = torch.full((G,), 1e12, dtype=torch.float64, device=device)
+    flat = total(hi) < target
+    for _ in range(64):
+        mid = torch.sqrt(lo * hi)
+        below = total(mid) < target
+        lo = torch.where(below, mid, lo)
+        hi = torch.where(below, hi, mid)
+    theta = theta_of(hi)
+    theta = torch.where(flat[gid], (target / ns_t.double())[gid], theta)
+    del lo, hi, idx
+    # per-graph cdf, offset by the graph index: draws for graph g are g + U
+    cum = torch.cumsum(theta, 0)
+    del theta
+    seg_end = torch.as_tensor(np.cumsum(ns) - 1, device=device)
+    before = torch.where(vstart > 0, cum[(vstart - 1).clamp(min=0)], torch.zeros_like(cum[:G]))
+    tot = cum[seg_end] - before
+    cdf = (cum - before[gid]) / tot[gid]
+    cdf[seg_end] = 1.0
+    cdf += gid.double()
+    del cum, before, tot
+    vend = vstart + ns_t
+
+    ms_t = torch.as_tensor(ms, device=device)
+    keys = torch.empty(0, dtype=torch.int64, device=device)
+    have = torch.zeros(G, dtype=torch.int64, device=device)
+    CH = 1 << 27
+    for _round in range(100):
+        need = (ms_t - have).clamp(min=0)
+        if int(need.sum().item()) == 0:
+            break
+        draws = torch.where(need > 0, (need.double() * 1.15).long() + 64, torch.zeros_like(need)).cpu().numpy()
+        parts = [keys]
+        cdraw = np.cumsum(draws)
+        g0 = 0
+        while g0 < G:
+            base = cdraw[g0 - 1] if g0 else 0
+            g1 = int(np.searchsorted(cdraw, base + CH, side="right"))
+            g1 = max(g1, g0 + 1)
+            cnt_g = torch.as_tensor(draws[g0:g1], device=device)
+            gs = torch.repeat_interleave(torch.arange(g0, g1, device=device), cnt_g)
+            if gs.numel():
+                x, y = [torch.searchsorted(cdf, gs.double() + torch.rand(gs.numel(), dtype=torch.float64,
+                                                                        device=device, generator=gen),
+                                           right=True) for _ in range(2)]
+                last = vend[gs] - 1
+                x = torch.minimum(x, last) - vstart[gs]
+                y = torch.minimum(y, last) - vstart[gs]
+                ok = x != y
+                gs, x, y = gs[ok], x[ok], y[ok]
+                parts.append((gs << _PAIR_BITS) + torch.minimum(x, y) * ns_t[gs] + torch.maximum(x, y))
+                del x, y, ok, last
+            del gs
+            g0 = g1
+        keys = torch.unique(torch.cat(parts))
+        del parts
+        have = torch.bincount(keys >> _PAIR_BITS, minlength=G)
+    else:
+        raise RuntimeError("batch Chung-Lu top-up did not converge")
+    del cdf, gid, vstart, vend
+
+    # exactly m of each graph's distinct pairs, uniformly, in random order:
+    # sort by (graph, random priority) and keep each graph's first m
+    gk = keys >> _PAIR_BITS
+    prio = gk.double() + torch.rand(keys.numel(), dtype=torch.float64, device=device, generator=gen)
+    order = torch.sort(prio, stable=True).indices
+    del prio
+    keys = keys[order]
+    gk = gk[order]
+    del order
+    cstart = torch.cumsum(have, 0) - have
+    rank = torch.arange(keys.numel(), device=device) - cstart[gk]
+    keep = rank < ms_t[gk]
+    keys, gk = keys[keep], gk[keep]
+    del rank, keep
+
+    # pad every graph to a multiple of 4 edges so slices stay 16-byte aligned
+    pad = (ms + 3) // 4 * 4
+    offs = np.concatenate([[0], np.cumsum(pad)[:-1]]).astype(np.int64)
+    estart = torch.as_tensor(np.concatenate([[0], np.cumsum(ms)[:-1]]), device=device)
+    dest = torch.as_tensor(offs, device=device)[gk] + (torch.arange(keys.numel(), device=device) - estart[gk])
+    pair = keys & ((1 << _PAIR_BITS) - 1)
+    ng = ns_t[gk]
+    lo_, hi_ = (pair // ng).to(torch.int32), (pair % ng).to(torch.int32)
+    del pair, ng, keys, gk
+    flip = torch.rand(lo_.numel(), device=device, generator=gen) < 0.5
+    total_pad = int(pad.sum())
+    u = torch.zeros(total_pad, dtype=torch.int32, device=device)
+    v = torch.zeros(total_pad, dtype=torch.int32, device=device)
+    u[dest] = torch.where(flip, hi_, lo_)
+    v[dest] = torch.where(flip, lo_, hi_)
+    del flip, lo_, hi_
+    w = torch.ones(total_pad, dtype=torch.int32, device=device)
+    w[dest] = zipf_weights_device(int(ms.sum()), 2.0, 1_000_000, seed + 7919, device)
+    del dest
+    torch.cuda.empty_cache()
+    return DeviceBatch(ns, ms, offs, u, v, w,
+                       f"{count} chung-lu graphs, n log-uniform [100, {n_hi}], m=10n, gamma=2.2, "
+                       f"zipf(2,1e6), seed={seed} (device)")
