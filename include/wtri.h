@@ -11,15 +11,18 @@
  * graph with positive integer edge weights.  A triangle {a, b, c} weighs the
  * generalized p-mean of its three edge weights (Eq. 1):
  *     m_p = ((w_ab^p + w_bc^p + w_ac^p) / 3)^(1/p),
- * with p = +inf the max and p = -inf the min.  This library supports
- * p in {-inf, 1, 2, +inf}; any other p returns WTRI_EUNSUPPORTED.
+ * with p = +inf the max, p = -inf the min and p = 0 the geometric mean
+ * (abc)^(1/3), the limit of Eq. 1 as p -> 0.  This library supports
+ * p in {-inf, 0, 1, 2, +inf}; any other p returns WTRI_EUNSUPPORTED, and so
+ * does p = 0 on a graph with a weight of 2^21 or more (its exact product key
+ * would not fit 63 bits).
  *
  * Results are ranked by a total order: weight descending, then the sorted
  * vertex triple (a < b < c) ascending.  The paper notes that ties may make
  * several answers valid (Section 3.2); the triple order makes the answer
  * unique.  Ranking uses exact integer keys (a+b+c for p=1, a^2+b^2+c^2 for
- * p=2, max, min), never the floating value; the reported fp64 weight is
- * (a+b+c)/3.0, sqrt((a^2+b^2+c^2)/3.0), max or min.
+ * p=2, a*b*c for p=0, max, min), never the floating value; the reported fp64
+ * weight is (a+b+c)/3.0, sqrt((a^2+b^2+c^2)/3.0), cbrt(a*b*c), max or min.
  *
  * A graph with fewer than k triangles returns all of them: count < k
  * (Section 3.2, "provided the graph has at least k triangles").
@@ -269,7 +272,8 @@ WTRI_API int wtri_set_tune(wtri_graph* g, int64_t first_round, int32_t growth, i
  * Philox4x64-10 (Salmon et al., SC'11) with key = seed and counter = the
  * sample index, so a seed gives the same samples on any device.
  *
- * p in {1, 2}; +-inf -> WTRI_EUNSUPPORTED (w^p has no meaning there).
+ * p in {1, 2}; +-inf -> WTRI_EUNSUPPORTED (w^p has no meaning there), and
+ * p = 0 too (its draws would be uniform; not provided).
  * nsamples >= 0 (0 returns count 0).
  */
 WTRI_API int wtri_sample_topk(const wtri_graph* g, double p, int32_t k, int64_t nsamples,

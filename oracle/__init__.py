@@ -32,7 +32,7 @@ _SRC_DHL = os.path.join(_HERE, "wtri_dhl.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
-P_CODES = {-math.inf: 0, 1.0: 1, 2.0: 2, math.inf: 3}
+P_CODES = {-math.inf: 0, 1.0: 1, 2.0: 2, math.inf: 3, 0.0: 4}
 
 
 def build(force: bool = False) -> str:
@@ -104,10 +104,18 @@ def _arr(x):
     return np.ascontiguousarray(x, dtype=np.int32)
 
 
+GEO_WMAX = (1 << 21) - 1  # p = 0 ranks by the product of the weights: exact below 2^63
+
+
 def pcode(p: float) -> int:
     if p not in P_CODES:
-        raise OracleError(f"p={p} is outside {{-inf, 1, 2, +inf}}")
+        raise OracleError(f"p={p} is outside {{-inf, 0, 1, 2, +inf}}")
     return P_CODES[p]
+
+
+def _check_geo(p, w):
+    if p == 0.0 and w.shape[0] and int(w.max()) > GEO_WMAX:
+        raise OracleError("p = 0 needs weights below 2^21 (exact product key)")
 
 
 def validate(n, u, v, w):
@@ -184,6 +192,7 @@ def topk(n, u, v, w, p, k, nthreads=0):
     """Exact top-k triangles.  Returns dict(tri [count,3] int32, key uint64,
     value float64, count, ntri)."""
     u, v, w = _arr(u), _arr(v), _arr(w)
+    _check_geo(p, w)
     m = u.shape[0]
     k = int(k)
     tri = np.zeros(3 * max(k, 1), np.int32)
@@ -212,6 +221,7 @@ def dhl_topk(n, u, v, w, p, k, alpha=None, beta=2.0):
     Adds 'stats': L->H moves, H->S moves, distinct triangles listed, edge
     probes, final h and l."""
     u, v, w = _arr(u), _arr(v), _arr(w)
+    _check_geo(p, w)
     m = u.shape[0]
     k = int(k)
     if alpha is None:
@@ -256,6 +266,7 @@ def topk_of_marked(n, u, v, w, mark, p, k, nthreads=0):
     """Top-k of the triangles that have at least one marked edge (mark[i] != 0
     for input edge i): the triangle set T of Algorithm 3 for a given draw."""
     u, v, w = _arr(u), _arr(v), _arr(w)
+    _check_geo(p, w)
     m = u.shape[0]
     mark = np.ascontiguousarray(mark, dtype=np.uint8)
     k = int(k)
@@ -291,6 +302,7 @@ def topk_shard(n, u, v, w, p, k, shard, nshards, chunk_shift=10):
     shard `shard` (edge positions dealt in chunks of 2^chunk_shift,
     round-robin over nshards)."""
     u, v, w = _arr(u), _arr(v), _arr(w)
+    _check_geo(p, w)
     m = u.shape[0]
     perm = edge_order(w)
     rank = np.empty(max(m, 1), np.int64)

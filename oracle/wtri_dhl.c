@@ -48,12 +48,14 @@
 #define DHL_EINVAL (-1)
 #define DHL_ENOMEM (-2)
 
-/* exact key of the p-mean (pcode 0: -inf, 1: p=1, 2: p=2, 3: +inf) */
+/* exact key of the p-mean (pcode 0: -inf, 1: p=1, 2: p=2, 3: +inf, 4: p=0,
+ * the geometric mean, ranked by the product of the weights) */
 static uint64_t dhl_key(int pcode, uint64_t a, uint64_t b, uint64_t c) {
     switch (pcode) {
         case 0: return a < b ? (a < c ? a : c) : (b < c ? b : c);
         case 1: return a + b + c;
         case 2: return a * a + b * b + c * c;
+        case 4: return a * b * c;
         default: return a > b ? (a > c ? a : c) : (b > c ? b : c);
     }
 }
@@ -61,6 +63,7 @@ static uint64_t dhl_key(int pcode, uint64_t a, uint64_t b, uint64_t c) {
 static double dhl_value(int pcode, uint64_t key) {
     if (pcode == 1) return (double)key / 3.0;
     if (pcode == 2) return sqrt((double)key / 3.0);
+    if (pcode == 4) return cbrt((double)key);
     return (double)key;
 }
 
@@ -391,7 +394,7 @@ int dhl_topk(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int
              int64_t k, double alpha, int32_t* tri, uint64_t* key, double* value, int64_t* count,
              int64_t* stats) {
     *count = 0;
-    if (n <= 0 || m < 0 || k <= 0 || pcode < 0 || pcode > 3 || m > (int64_t)UINT32_MAX)
+    if (n <= 0 || m < 0 || k <= 0 || pcode < 0 || pcode > 4 || m > (int64_t)UINT32_MAX)
         return DHL_EINVAL;
     dhl_ctx g;
     memset(&g, 0, sizeof(g));
@@ -472,9 +475,9 @@ int dhl_topk(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int
 }
 
 /* alpha_p = 2 - p / (p - 1 + beta) for power-law weights of exponent beta
- * (Section 3.3); 1 at p = +-inf. */
+ * (Section 3.3); 1 at p = +-inf, 2 at p = 0. */
 double dhl_alpha(int pcode, double beta) {
     if (pcode == 0 || pcode == 3) return 1.0;
-    const double p = pcode == 2 ? 2.0 : 1.0;
+    const double p = pcode == 2 ? 2.0 : (pcode == 4 ? 0.0 : 1.0);
     return 2.0 - p / (p - 1.0 + beta);
 }

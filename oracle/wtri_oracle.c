@@ -10,8 +10,8 @@
  * Triangles in Graphs", WSDM 2020):
  *
  *  - the triangle weight is the generalized p-mean of its three edge weights
- *    (Eq. 1, Section 1), for p in {-inf, 1, 2, +inf}: min, arithmetic mean,
- *    quadratic mean, max;
+ *    (Eq. 1, Section 1), for p in {-inf, 0, 1, 2, +inf}: min, geometric mean
+ *    (Eq. 1's limit as p -> 0), arithmetic mean, quadratic mean, max;
  *  - the top-k triangles are the k of largest weight (Section 1); ties are
  *    broken by the sorted vertex triple ascending, which makes the answer
  *    unique (the paper notes ties may exist, Section 3.2);
@@ -20,10 +20,11 @@
  *
  * Ranking never uses the floating value.  Each triangle gets an exact integer
  * key that is monotone in m_p: a+b+c (p=1), a^2+b^2+c^2 (p=2), max (p=+inf),
- * min (p=-inf).  Eq. 4 (Section 4) ranks by the sum of p-th powers, which is
- * only order-preserving for p>0; these keys are the order-preserving choice
- * for all four p.  The reported value is fp64: (a+b+c)/3, sqrt((a^2+b^2+c^2)/3),
- * max, min.
+ * min (p=-inf), a*b*c (p=0; exact for weights below 2^21).  Eq. 4 (Section 4)
+ * ranks by the sum of p-th powers, which is only order-preserving for p>0;
+ * these keys are the order-preserving choice for every supported p.  The
+ * reported value is fp64: (a+b+c)/3, sqrt((a^2+b^2+c^2)/3), max, min,
+ * cbrt(a*b*c).
  *
  * Input hygiene (Section 1: "simple, undirected graph with positive edge
  * weights"): self-loops, ids outside [0,n), weights <= 0 and repeated
@@ -226,6 +227,8 @@ static uint64_t tri_key(int pcode, int32_t a, int32_t b, int32_t c) {
             return (uint64_t)a + (uint64_t)b + (uint64_t)c;
         case 2:
             return (uint64_t)a * (uint64_t)a + (uint64_t)b * (uint64_t)b + (uint64_t)c * (uint64_t)c;
+        case 4: /* p = 0: the geometric mean ranks as the product (weights < 2^21) */
+            return (uint64_t)a * (uint64_t)b * (uint64_t)c;
         default: {
             int32_t x = a > b ? a : b;
             return (uint64_t)(x > c ? x : c);
@@ -239,6 +242,8 @@ static double tri_value(int pcode, uint64_t key) {
             return (double)key / 3.0;
         case 2:
             return sqrt((double)key / 3.0);
+        case 4:
+            return cbrt((double)key);
         default:
             return (double)key;
     }
@@ -246,7 +251,7 @@ static double tri_value(int pcode, uint64_t key) {
 
 /* Public scorer, so that tests can pin it against hand-computed means. */
 int or_score(int pcode, int32_t a, int32_t b, int32_t c, uint64_t* key, double* value) {
-    if (pcode < 0 || pcode > 3) return OR_EINVAL;
+    if (pcode < 0 || pcode > 4) return OR_EINVAL;
     *key = tri_key(pcode, a, b, c);
     *value = tri_value(pcode, *key);
     return OR_OK;
@@ -339,7 +344,7 @@ int or_topk(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int3
             int64_t* count, int64_t* ntri) {
     *count = 0;
     *ntri = 0;
-    if (pcode < 0 || pcode > 3 || k <= 0) return OR_EINVAL;
+    if (pcode < 0 || pcode > 4 || k <= 0) return OR_EINVAL;
     int64_t* orow = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
     int32_t* ocol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
     int32_t* owt = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
@@ -577,7 +582,7 @@ int or_topk_of_sampled(int32_t n, int64_t m, const int32_t* u, const int32_t* v,
                        int32_t* tri, uint64_t* key, double* value, int64_t* count, int64_t* ntri) {
     *count = 0;
     *ntri = 0;
-    if (pcode < 0 || pcode > 3 || k <= 0) return OR_EINVAL;
+    if (pcode < 0 || pcode > 4 || k <= 0) return OR_EINVAL;
     int64_t* orow = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
     int32_t* ocol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
     int32_t* owt = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
@@ -699,7 +704,7 @@ int or_topk_shard(int32_t n, int64_t m, const int32_t* u, const int32_t* v, cons
                   int64_t* ntri) {
     *count = 0;
     *ntri = 0;
-    if (pcode < 0 || pcode > 3 || k <= 0 || nshards < 1 || shard < 0 || shard >= nshards)
+    if (pcode < 0 || pcode > 4 || k <= 0 || nshards < 1 || shard < 0 || shard >= nshards)
         return OR_EINVAL;
     int64_t* orow = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
     int32_t* ocol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));

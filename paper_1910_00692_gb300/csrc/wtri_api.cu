@@ -34,7 +34,15 @@ int p_to_code(double p, int* code) {
     else if (p == 2.0) *code = P_TWO;
     else if (isinf(p) && p > 0) *code = P_MAX;
     else if (isinf(p) && p < 0) *code = P_MIN;
-    else return set_error(WTRI_EUNSUPPORTED, "p must be -inf, 1, 2 or +inf");
+    else if (p == 0.0) *code = P_GEO;
+    else return set_error(WTRI_EUNSUPPORTED, "p must be -inf, 0, 1, 2 or +inf");
+    return WTRI_OK;
+}
+
+int p_to_code_for(double p, const wtri_graph* g, int* code) {
+    WTRI_TRY(p_to_code(p, code));
+    if (*code == P_GEO && g && g->d.wmax > GEO_WMAX)
+        return set_error(WTRI_EUNSUPPORTED, "p = 0 needs weights below 2^21 (exact product key)");
     return WTRI_OK;
 }
 
@@ -155,7 +163,7 @@ WTRI_API int wtri_topk(const wtri_graph* g, double p, int32_t k, wtri_result* ou
     out->count = 0;
     int code = 0;
     WTRI_TRY(check_query(g, k));
-    WTRI_TRY(p_to_code(p, &code));
+    WTRI_TRY(p_to_code_for(p, g, &code));
     if (!out->tris || !out->weight) return set_error(WTRI_EINVAL, "result arrays are NULL");
     if (out->capacity < k) return set_error(WTRI_EINVAL, "result capacity below k");
     if (g->d.m == 0) return WTRI_OK;
@@ -172,7 +180,7 @@ WTRI_API int wtri_topk_shard(const wtri_graph* g, double p, int32_t k, int32_t s
     out->count = 0;
     int code = 0;
     WTRI_TRY(check_query(g, k));
-    WTRI_TRY(p_to_code(p, &code));
+    WTRI_TRY(p_to_code_for(p, g, &code));
     if (nshards < 1 || shard < 0 || shard >= nshards)
         return set_error(WTRI_EINVAL, "need 0 <= shard < nshards");
     if (!out->tris || !out->weight || !keys) return set_error(WTRI_EINVAL, "result arrays are NULL");
@@ -330,7 +338,7 @@ WTRI_API int wtri_topk_device(const wtri_graph* g, double p, int32_t k, wtri_tri
                               double* d_weight, int32_t* d_count, void* stream) {
     int code = 0;
     WTRI_TRY(check_query(g, k));
-    WTRI_TRY(p_to_code(p, &code));
+    WTRI_TRY(p_to_code_for(p, g, &code));
     if (!d_tris || !d_weight || !d_count) return set_error(WTRI_EINVAL, "output pointers are NULL");
     cudaStream_t s = stream ? (cudaStream_t)stream : g->stream;
     if (g->d.m == 0) {
@@ -374,7 +382,7 @@ WTRI_API int wtri_topk_batch(const wtri_graph* const* gs, const double* p, const
         if (dev < 0) dev = gs[i]->device;
         if (gs[i]->device != dev) return set_error(WTRI_EINVAL, "batch graphs on different devices");
         int c = 0;
-        int rc = p_to_code(p[i], &c);
+        int rc = p_to_code_for(p[i], gs[i], &c);
         if (rc != WTRI_OK) return rc;
         codes[(size_t)i] = c;
         rc = check_query(gs[i], k[i]);

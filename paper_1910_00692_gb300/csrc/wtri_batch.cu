@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(RBLK) k_round_batch(BatchDev B, const int64_t*
             case P_MIN: process_edge<P_MIN, false>(G, q, tau, (int32_t)idx); break;
             case P_ONE: process_edge<P_ONE, false>(G, q, tau, (int32_t)idx); break;
             case P_TWO: process_edge<P_TWO, false>(G, q, tau, (int32_t)idx); break;
+            case P_GEO: process_edge<P_GEO, false>(G, q, tau, (int32_t)idx); break;
             default: process_edge<P_MAX, false>(G, q, tau, (int32_t)idx); break;
         }
     }
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(LBLK) k_long_batch(BatchDev B, const LongItem*
             case P_MIN: long_scan<P_MIN, false>(G, q, tau, item, srow, off, ybeg, dy, staged); break;
             case P_ONE: long_scan<P_ONE, false>(G, q, tau, item, srow, off, ybeg, dy, staged); break;
             case P_TWO: long_scan<P_TWO, false>(G, q, tau, item, srow, off, ybeg, dy, staged); break;
+            case P_GEO: long_scan<P_GEO, false>(G, q, tau, item, srow, off, ybeg, dy, staged); break;
             default: long_scan<P_MAX, false>(G, q, tau, item, srow, off, ybeg, dy, staged); break;
         }
         __syncthreads();
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(256) k_rank_batch(BatchDev B, const int64_t* _
             case P_MIN: rank_one<P_MIN>(q, i, ot, ow, status + qi); break;
             case P_ONE: rank_one<P_ONE>(q, i, ot, ow, status + qi); break;
             case P_TWO: rank_one<P_TWO>(q, i, ot, ow, status + qi); break;
+            case P_GEO: rank_one<P_GEO>(q, i, ot, ow, status + qi); break;
             default: rank_one<P_MAX>(q, i, ot, ow, status + qi); break;
         }
     }

@@ -40,10 +40,15 @@ enum : uint32_t {
     DEV_ERR_TIMEOUT = 1u << 6,    // a bounded wait ran out
 };
 
-// p codes (template parameter of the scoring kernels).
-enum PCode : int { P_MIN = 0, P_ONE = 1, P_TWO = 2, P_MAX = 3 };
+// p codes (template parameter of the scoring kernels).  P_GEO is p = 0, the
+// geometric mean (Eq. 1's limit), ranked by the exact product of the weights.
+enum PCode : int { P_MIN = 0, P_ONE = 1, P_TWO = 2, P_MAX = 3, P_GEO = 4 };
+// Largest weight for which the product key of p = 0 fits 63 bits.
+constexpr int32_t GEO_WMAX = (1 << 21) - 1;
 
 int p_to_code(double p, int* code);
+// p_to_code, and p = 0 only for graphs whose weights keep the product key exact.
+int p_to_code_for(double p, const wtri_graph* g, int* code);
 
 // ---------------------------------------------------------------------------
 // Device-resident graph (all arrays library-owned device memory).

@@ -122,6 +122,7 @@ __device__ __forceinline__ unsigned long long keyof(uint32_t a, uint32_t b, uint
     if (P == P_TWO)
         return (unsigned long long)a * a + (unsigned long long)b * b + (unsigned long long)c * c;
     if (P == P_MAX) return (unsigned long long)max(a, max(b, c));
+    if (P == P_GEO) return (unsigned long long)a * b * c;  // weights < 2^21: below 2^63
     return (unsigned long long)min(a, min(b, c));
 }
 
@@ -775,6 +776,7 @@ __device__ __forceinline__ void rank_one(const Query& q, uint32_t i, wtri_tri* o
         double val;
         if (P == P_ONE) val = (double)ki / 3.0;
         else if (P == P_TWO) val = sqrt((double)ki / 3.0);
+        else if (P == P_GEO) val = cbrt((double)ki);
         else val = (double)ki;
         out_w[rank] = val;
         if (out_key) out_key[rank] = ki;

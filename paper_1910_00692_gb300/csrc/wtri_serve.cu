@@ -301,6 +301,8 @@ WTRI_API int wtri_submit(wtri_server* S, int32_t graph_id, double p, int32_t k, 
         std::lock_guard<std::mutex> lk(S->mu);
         if (graph_id < 0 || graph_id >= (int32_t)S->graphs.size())
             return set_error(WTRI_ENOTFOUND, "unknown graph id");
+        if (code == P_GEO && S->graphs[(size_t)graph_id]->d.wmax > GEO_WMAX)
+            return set_error(WTRI_EUNSUPPORTED, "p = 0 needs weights below 2^21 (exact product key)");
         r->bytes = request_bytes(k, S->graphs[(size_t)graph_id]->d.m);
         if (S->stop) return set_error(WTRI_EINVAL, "server is shutting down");
         if (S->graph_bytes + BATCH_FIXED_BYTES + r->bytes > S->budget)

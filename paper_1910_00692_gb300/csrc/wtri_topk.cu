@@ -377,6 +377,8 @@ int topk_device(const wtri_graph* g, int pcode, int32_t k, wtri_tri* d_tris, dou
             return run_query<P_ONE>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys);
         case P_TWO:
             return run_query<P_TWO>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys);
+        case P_GEO:
+            return run_query<P_GEO>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys);
         default:
             return run_query<P_MAX>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys);
     }
@@ -517,7 +519,7 @@ extern "C" WTRI_API int wtri_topk_device_noalloc(const wtri_graph* g, double p, 
     if (k > NOALLOC_K_MAX)
         return set_error(WTRI_EINVAL, "k above 16384, the most the fixed query scratch supports");
     int code = 0;
-    WTRI_TRY(p_to_code(p, &code));
+    WTRI_TRY(p_to_code_for(p, g, &code));
     if (!d_tris || !d_weight || !d_count) return set_error(WTRI_EINVAL, "output pointers are NULL");
     cudaStream_t s = stream ? (cudaStream_t)stream : g->stream;
     if (g->d.m == 0) {
@@ -528,6 +530,7 @@ extern "C" WTRI_API int wtri_topk_device_noalloc(const wtri_graph* g, double p, 
         case P_MIN: return run_query_noalloc<P_MIN>(g, k, d_tris, d_weight, d_count, s);
         case P_ONE: return run_query_noalloc<P_ONE>(g, k, d_tris, d_weight, d_count, s);
         case P_TWO: return run_query_noalloc<P_TWO>(g, k, d_tris, d_weight, d_count, s);
+        case P_GEO: return run_query_noalloc<P_GEO>(g, k, d_tris, d_weight, d_count, s);
         default: return run_query_noalloc<P_MAX>(g, k, d_tris, d_weight, d_count, s);
     }
 }

@@ -391,4 +391,4 @@ def sample_edges(g: Graph, p: float, nsamples: int, seed: int) -> np.ndarray:
 
 
 def p_values():
-    return [-math.inf, 1.0, 2.0, math.inf]
+    return [-math.inf, 0.0, 1.0, 2.0, math.inf]

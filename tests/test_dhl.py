@@ -16,7 +16,7 @@ import oracle
 import synth
 from golden_io import P_OF, closed_form, load_all
 
-PS = [-math.inf, 1.0, 2.0, math.inf]
+PS = [-math.inf, 0.0, 1.0, 2.0, math.inf]
 ALPHAS = [None, 1.0, 3.0, 0.0]  # alpha_p(beta=2), two fixed rules, Auto-HL
 
 
@@ -32,6 +32,7 @@ def test_alpha_closed_form():
     assert oracle.dhl_alpha(1.0, 3.0) == pytest.approx(5.0 / 3.0)
     assert oracle.dhl_alpha(math.inf, 2.0) == 1.0
     assert oracle.dhl_alpha(-math.inf, 2.0) == 1.0
+    assert oracle.dhl_alpha(0.0, 2.0) == 2.0
 
 
 @pytest.mark.parametrize("fx", load_all(), ids=lambda d: d["name"])

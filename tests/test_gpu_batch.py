@@ -3,7 +3,7 @@
 The batch mixes graphs of very different sizes (n log-uniform, as in the
 batch workload but with a smaller upper end so that the oracle finishes in
 seconds), per-query p and k, an empty graph, a triangle-free graph and one
-graph queried at all four p.
+graph queried at every supported p (including p = 0).
 """
 import math
 
@@ -31,7 +31,7 @@ def test_batch_vs_oracle():
                               np.arange(1, 6, dtype=np.int32)))
     ps.append(2.0)
     ks.append(3)
-    for p in (-math.inf, 1.0, 2.0, math.inf):
+    for p in (-math.inf, 0.0, 1.0, 2.0, math.inf):
         graphs.append(graphs[5])
         ps.append(p)
         ks.append(777)

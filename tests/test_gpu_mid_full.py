@@ -1,5 +1,5 @@
 """GPU parity at the full mid workload size (Chung-Lu n=1e6, m=2e7, exponent
-2.1, d_max 5e4, Zipf(2) weights capped at 1e6; k=1000 at all four p), the
+2.1, d_max 5e4, Zipf(2) weights capped at 1e6; k=1000 at every supported p), the
 configuration bench.py times: every output element against the oracle."""
 import pytest
 

@@ -2,7 +2,7 @@
 
 Triangle sets and order are compared element by element (bit-exact ids);
 weights bit-exact for p in {-inf, 1, +inf} and within 1e-12 relative at
-p = 2.  Inputs are the seeded synthetic graphs of synth/.
+p = 2 and p = 0.  Inputs are the seeded synthetic graphs of synth/.
 """
 import math
 
@@ -186,6 +186,28 @@ def test_bad_queries(tiny_dev):
     assert ei.value.code == -1
 
 
+def test_geometric_mean_weight_limit():
+    """p = 0 ranks by the exact product of the weights, which fits 63 bits
+    only for weights below 2^21; heavier graphs are refused, not rounded."""
+    u = np.array([0, 1, 0], np.int32)
+    v = np.array([1, 2, 2], np.int32)
+    for wmax, ok in ((2**21 - 1, True), (2**21, False)):
+        w = np.array([wmax, 3, 5], np.int32)
+        d = wt.build_csr(3, u, v, w)
+        try:
+            if ok:
+                t, x = d.topk(0.0, 1)
+                assert t.tolist() == [[0, 1, 2]]
+                assert abs(x[0] - (wmax * 15) ** (1 / 3)) <= 1e-12 * x[0]
+            else:
+                with pytest.raises(wt.WtriError) as ei:
+                    d.topk(0.0, 1)
+                assert ei.value.code == -5
+                assert d.topk(1.0, 1)[0].tolist() == [[0, 1, 2]]
+        finally:
+            d.free()
+
+
 def test_empty_and_degenerate():
     d = wt.build_csr(5, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32))
     try:
@@ -206,6 +228,11 @@ def test_empty_and_degenerate():
                      np.array([W, W, W, 1], np.int32))
     try:
         for p in PS:
+            if p == 0.0:  # the product key of such weights would not fit: refused
+                with pytest.raises(wt.WtriError) as ei:
+                    d.topk(p, 2)
+                assert ei.value.code == -5
+                continue
             want = oracle.topk(4, np.array([0, 1, 0, 2], np.int32), np.array([1, 2, 2, 3], np.int32),
                                np.array([W, W, W, 1], np.int32), p, 2)
             tris, wts = d.topk(p, 2)

@@ -17,7 +17,7 @@ import oracle
 import synth
 from golden_io import P_OF, closed_form, load_all
 
-PS = [-math.inf, 1.0, 2.0, math.inf]
+PS = [-math.inf, 0.0, 1.0, 2.0, math.inf]
 
 
 def complete_graph(n, wfun):
@@ -92,6 +92,11 @@ def test_score_closed_forms():
     assert k == 9 and val == math.sqrt(3.0)
     assert oracle.score(math.inf, 1, 2, 2) == (2, 2.0)
     assert oracle.score(-math.inf, 1, 2, 2) == (1, 1.0)
+    # p = 0: the geometric mean (2 * 4 * 8)^(1/3) = 4, ranked by the product
+    k, val = oracle.score(0.0, 2, 4, 8)
+    assert k == 64 and abs(val - 4.0) <= 4e-16 * 4.0
+    W = 2**21 - 1
+    assert oracle.score(0.0, W, W, W)[0] == W**3
     # Largest int32 weights: the p=2 key must not wrap (3 * (2^31-1)^2 < 2^64).
     W = 2**31 - 1
     k, val = oracle.score(2.0, W, W, W)
@@ -115,6 +120,8 @@ def _python_bruteforce(n, u, v, w, p):
                 key = sum(x * x for x in ws)
             elif p == math.inf:
                 key = max(ws)
+            elif p == 0.0:
+                key = ws[0] * ws[1] * ws[2]
             else:
                 key = min(ws)
             out.append((key, (a, b, c)))
