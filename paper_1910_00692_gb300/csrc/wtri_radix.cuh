@@ -255,13 +255,20 @@ __device__ __forceinline__ uint32_t lo16(uint32_t x) { return x & 0xffffu; }
 #ifndef WTRI_PEERS_ALL_BITS
 #define WTRI_PEERS_ALL_BITS 0
 #endif
+#ifndef WTRI_FULL_TILES
+#define WTRI_FULL_TILES 0
+#endif
 // Lanes of the warp holding the same digit as this lane (digits of 'bits'
 // bits; lanes with valid == false group only among themselves): one ballot
 // per digit bit.
+template <bool FULL>
 __device__ __forceinline__ uint32_t digit_peers(uint32_t d, int bits, bool valid) {
 #if WTRI_RANK_BALLOT
-    const uint32_t vb = __ballot_sync(0xffffffffu, valid);
-    uint32_t p = valid ? vb : ~vb;
+    uint32_t p = 0xffffffffu;  // a full tile: every lane holds a record
+    if (!FULL) {
+        const uint32_t vb = __ballot_sync(0xffffffffu, valid);
+        p = valid ? vb : ~vb;
+    }
 #if WTRI_PEERS_ALL_BITS
     // digits are below 1 << bits, so the ballots of the bits above are all
     // zero and leave p unchanged: no per-bit test
@@ -294,7 +301,7 @@ __device__ __forceinline__ uint32_t hi16(uint32_t x) { return x >> 16; }
 // ranking strips in order and warps in order keeps equal digits stable.
 // run[] holds this thread's digits' next output positions (digits
 // threadIdx.x * DPT + i).
-template <class Storer>
+template <bool FULL, class Storer>
 __device__ __forceinline__ void scatter_tile(const uint4 (&rec)[IT], int tcount, uint4* stage,
                                              const Storer& st, const PassGeom& g,
                                              uint32_t (&run)[DPT], ScatterSmem& S) {
@@ -313,12 +320,12 @@ __device__ __forceinline__ void scatter_tile(const uint4 (&rec)[IT], int tcount,
 #pragma unroll
     for (int j = 0; j < IT; j++) {
         const int li = w * 32 * IT + j * 32 + lane;
-        rank[j] = digit_peers((rec[j].x >> g.shift) & g.mask, g.bits, li < tcount);
+        rank[j] = digit_peers<FULL>((rec[j].x >> g.shift) & g.mask, g.bits, FULL || li < tcount);
     }
 #pragma unroll
     for (int j = 0; j < IT; j++) {
         const int li = w * 32 * IT + j * 32 + lane;
-        const bool valid = li < tcount;
+        const bool valid = FULL || li < tcount;
         const uint32_t d = (rec[j].x >> g.shift) & g.mask;
         const uint32_t peers = rank[j];
         const uint32_t b = valid ? (uint32_t)S.cnt[w][d] : 0u;
@@ -375,7 +382,7 @@ __device__ __forceinline__ void scatter_tile(const uint4 (&rec)[IT], int tcount,
 #pragma unroll
     for (int j = 0; j < IT; j++) {
         const int li = w * 32 * IT + j * 32 + lane;
-        if (li < tcount) {
+        if (FULL || li < tcount) {
             const uint32_t d = (rec[j].x >> g.shift) & g.mask;
             stage[rank[j] + S.cnt[w][d]] = rec[j];
         }
@@ -385,7 +392,7 @@ __device__ __forceinline__ void scatter_tile(const uint4 (&rec)[IT], int tcount,
 #pragma unroll
     for (int i = 0; i < IT; i++) {
         const int p = i * NT + threadIdx.x;
-        if (p < tcount) {
+        if (FULL || p < tcount) {
             const uint4 r = stage[p];
             const uint32_t d = (r.x >> g.shift) & g.mask;
             st.store((int64_t)S.delta[d] + p, r);
@@ -473,7 +480,7 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_scatter(Loader ld, Storer s
         uint4 rec[IT];
 #pragma unroll
         for (int j = 0; j < IT; j++) rec[j] = ld.srec(in, w * 32 * IT + j * 32 + lane, tbase);
-        scatter_tile(rec, TT, &S.buf[b][0], st, g, run, S);
+        scatter_tile<WTRI_FULL_TILES != 0>(rec, TT, &S.buf[b][0], st, g, run, S);
     }
     for (int64_t tbase = beg + nfull * TT; tbase < end; tbase += TT) {
         const int tcount = (int)min((int64_t)TT, end - tbase);
@@ -483,7 +490,7 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_scatter(Loader ld, Storer s
             const int li = w * 32 * IT + j * 32 + lane;
             rec[j] = li < tcount ? ld.grec(tbase + li) : make_uint4(0, 0, 0, 0);
         }
-        scatter_tile(rec, tcount, &S.buf[0][0], st, g, run, S);
+        scatter_tile<false>(rec, tcount, &S.buf[0][0], st, g, run, S);
     }
 }
 
