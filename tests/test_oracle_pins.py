@@ -60,6 +60,11 @@ def test_complete_graph_sum_weights_closed_form(n):
     assert [int(x) for x in r["key"]] == [2 * sum(t) + 3 for t in want[1.0]]
     r2 = oracle.topk(n, u, v, w, 2.0, 1)
     assert tuple(r2["tri"][0]) == (n - 3, n - 2, n - 1)
+    # p = 0: key (a+b+1)(a+c+1)(b+c+1), the full order by that product
+    geo = sorted(triples, key=lambda t: (-(t[0] + t[1] + 1) * (t[0] + t[2] + 1) * (t[1] + t[2] + 1), t))
+    r0 = oracle.topk(n, u, v, w, 0.0, N)
+    assert [tuple(x) for x in r0["tri"]] == geo
+    assert tuple(r0["tri"][0]) == (n - 3, n - 2, n - 1)
 
 
 def test_trace_a_cubed_count():
