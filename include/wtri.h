@@ -206,7 +206,12 @@ WTRI_API int wtri_topk_batch(const wtri_graph* const* gs, const double* p, const
  *   requests running at once.  A scheduler thread admits waiting requests,
  *   oldest first, as slots and budget free up, and launches them as
  *   micro-batches on its own worker streams (several overlap on the
- *   device).  The server uses the device current at creation.
+ *   device).  Requests of one micro-batch on the same graph with the same p
+ *   share one query at their largest k; each still receives exactly its own
+ *   top-k (the first k of that answer under the total order), the same as
+ *   wtri_topk would return.  The environment variable WTRI_SERVE_COALESCE=0
+ *   runs one query per request instead.  The server uses the device current
+ *   at creation.
  * wtri_server_add_graph: registers a built graph (borrowed: it must outlive
  *   the server); its device bytes count against the budget (WTRI_ENOMEM if
  *   it does not fit).  *graph_id receives its id.

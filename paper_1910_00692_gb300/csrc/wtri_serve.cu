@@ -11,7 +11,14 @@
 // Requests that arrive while others run are admitted as soon as slots and
 // memory free up, and several micro-batches overlap on the device (one per
 // worker stream).  wtri_poll only looks at host state.
+//
+// Within a micro-batch, requests on the same graph with the same p are
+// answered by one query at their largest k: under the total order (weight
+// desc, triple asc) the top-k is exactly the first k of the top-k' for any
+// k' >= k, so each request gets the prefix it asked for, identical to the
+// result of its own query.  WTRI_SERVE_COALESCE=0 runs one query per request.
 #include <chrono>
+#include <cstdlib>
 #include <condition_variable>
 #include <deque>
 #include <memory>
@@ -53,7 +60,17 @@ struct InFlight {
     int stream = -1;
     cudaEvent_t done = nullptr;
     std::vector<std::shared_ptr<Request>> reqs;
+    std::vector<int> query_of;  // request i is answered by query query_of[i] of the plan
 };
+
+bool coalesce_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("WTRI_SERVE_COALESCE");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
 
 size_t request_bytes(int32_t k, int64_t m) {
     const size_t cap = batch_query_cap(k, m);
@@ -93,7 +110,9 @@ void finish_batch(wtri_server* S, InFlight& f) {
     const double t = now_s();
     for (size_t i = 0; i < f.reqs.size(); i++) {
         auto& r = f.reqs[i];
-        int32_t c = rc == WTRI_OK ? batch_plan_status(f.plan, (int)i) : rc;
+        const int qi = f.query_of[i];
+        int32_t c = rc == WTRI_OK ? batch_plan_status(f.plan, qi) : rc;
+        if (c > r->k) c = r->k;  // the prefix this request asked for
         r->tris.assign((size_t)std::max(r->k, 1), wtri_tri{0, 0, 0});
         r->w.assign((size_t)std::max(r->k, 1), 0.0);
         int rrc = WTRI_OK;
@@ -107,9 +126,8 @@ void finish_batch(wtri_server* S, InFlight& f) {
                                   r->w.data(), &cnt);
             c = rrc == WTRI_OK ? cnt : rrc;
         } else if (c >= 0) {
-            std::copy(batch_plan_tris(f.plan, (int)i), batch_plan_tris(f.plan, (int)i) + c, r->tris.begin());
-            std::copy(batch_plan_weights(f.plan, (int)i), batch_plan_weights(f.plan, (int)i) + c,
-                      r->w.begin());
+            std::copy(batch_plan_tris(f.plan, qi), batch_plan_tris(f.plan, qi) + c, r->tris.begin());
+            std::copy(batch_plan_weights(f.plan, qi), batch_plan_weights(f.plan, qi) + c, r->w.begin());
         }
         std::lock_guard<std::mutex> lk(S->mu);
         if (c >= 0) {
@@ -140,15 +158,30 @@ void launch_batch(wtri_server* S, std::vector<std::shared_ptr<Request>>& reqs, i
     f.reqs = reqs;
     f.bytes = bytes;
     cudaStream_t s = S->streams[si];
-    std::vector<const wtri_graph*> gs(reqs.size());
-    std::vector<int32_t> pc(reqs.size()), ks(reqs.size());
+    // one query per (graph, p) at the group's largest k, or one per request
+    std::vector<const wtri_graph*> gs;
+    std::vector<int32_t> pc, ks;
+    std::unordered_map<int64_t, int> group;
+    f.query_of.resize(reqs.size());
+    const bool merge = coalesce_enabled();
     for (size_t i = 0; i < reqs.size(); i++) {
-        gs[i] = S->graphs[(size_t)reqs[i]->graph_id];
-        pc[i] = reqs[i]->pcode;
-        ks[i] = reqs[i]->k;
+        const int64_t key = (int64_t)reqs[i]->graph_id * 8 + reqs[i]->pcode;
+        auto it = merge ? group.find(key) : group.end();
+        if (it == group.end()) {
+            if (merge) group.emplace(key, (int)gs.size());
+            f.query_of[i] = (int)gs.size();
+            gs.push_back(S->graphs[(size_t)reqs[i]->graph_id]);
+            pc.push_back(reqs[i]->pcode);
+            ks.push_back(reqs[i]->k);
+        } else {
+            f.query_of[i] = it->second;
+            ks[(size_t)it->second] = std::max(ks[(size_t)it->second], reqs[i]->k);
+        }
     }
     int rc = WTRI_OK;
-    f.plan = batch_plan_create(gs.data(), pc.data(), ks.data(), (int32_t)reqs.size());
+    // the plan's scratch is at most the sum of its requests' estimates
+    // (one of them asked for the group's largest k), so admission holds
+    f.plan = batch_plan_create(gs.data(), pc.data(), ks.data(), (int32_t)gs.size());
     if (!f.plan) rc = WTRI_ENOMEM;
     if (rc == WTRI_OK && cudaMallocAsync(&f.dbuf, batch_plan_bytes(f.plan), s) != cudaSuccess) {
         cudaGetLastError();

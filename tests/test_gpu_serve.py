@@ -97,6 +97,28 @@ def test_burst_and_waves_equal_alone(graphs):
     srv.free()
 
 
+def test_same_graph_and_p_share_a_query(graphs):
+    """Requests on one graph with one p and many k (some above the number of
+    triangles) submitted together: each gets exactly its own top-k, the
+    prefix of the shared query's answer."""
+    gs, ds = graphs
+    srv = wt.Server(8 << 30, 256)
+    gid = srv.add_graph(ds[0])
+    ntri = len(ds[0].topk(1.0, 60000)[0])
+    assert ntri < 20000
+    ks = [1, 7, 100, 999, ntri - 1, ntri, ntri + 50, 20000, 3, 100]
+    cache = {}
+    for p in (1.0, 0.0, -math.inf):
+        pending = {srv.submit(gid, p, k): (0, p, k) for k in ks}
+        res = _drain(srv, dict(pending))
+        for t, (g, pp, k) in pending.items():
+            at, aw = _alone(ds, g, pp, k, cache)
+            assert res[t][0].shape[0] == min(k, ntri)
+            assert np.array_equal(res[t][0], at), (pp, k)
+            assert np.array_equal(res[t][1], aw), (pp, k)
+    srv.free()
+
+
 def test_small_slot_limit(graphs):
     gs, ds = graphs
     srv = wt.Server(8 << 30, 3)
