@@ -64,12 +64,11 @@ struct InFlight {
 };
 
 bool coalesce_enabled() {
-    static int v = -1;
-    if (v < 0) {
+    static const bool on = [] {
         const char* e = getenv("WTRI_SERVE_COALESCE");
-        v = (e && e[0] == '0') ? 0 : 1;
-    }
-    return v == 1;
+        return !(e && e[0] == '0');
+    }();
+    return on;
 }
 
 size_t request_bytes(int32_t k, int64_t m) {
