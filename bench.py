@@ -780,7 +780,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic",
-            "config": {"workload": wl, "global_batch": world, "seq_len": None, "k": k,
+            "config": {"workload": wl, "global_batch": world, "k": k,
                        "step": STEP_DEF,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": (f"inputs larger than L2: COO {12 * m / 1e9:.2f} GB, resident graph "
