@@ -117,8 +117,8 @@ WTRI_API int wtri_graph_info(const wtri_graph* g, int32_t* n, int64_t* m, int32_
  * Algorithm 2 solves.  Runs on the graph's stream, then copies the k results
  * to the caller's host arrays and returns when they are there.
  *
- * p   -INFINITY, 1.0, 2.0 or +INFINITY; NaN -> WTRI_EINVAL; others ->
- *     WTRI_EUNSUPPORTED.
+ * p   -INFINITY, 0.0, 1.0, 2.0 or +INFINITY; NaN -> WTRI_EINVAL; others ->
+ *     WTRI_EUNSUPPORTED, as is 0.0 on a graph with a weight of 2^21 or more.
  * k   1 <= k <= out->capacity and k <= 65536 (WTRI_EUNSUPPORTED above).
  */
 WTRI_API int wtri_topk(const wtri_graph* g, double p, int32_t k, wtri_result* out);
@@ -168,7 +168,7 @@ WTRI_API int wtri_topk_device_noalloc(const wtri_graph* g, double p, int32_t k, 
  * dealt to nshards shards in chunks of 1024 consecutive positions,
  * round-robin.  Returns the exact top-k of the triangles whose first edge
  * belongs to `shard` (results as wtri_topk) and their integer ranking keys
- * (a+b+c, a^2+b^2+c^2, max or min) in keys[0..count).  The union of all
+ * (a+b+c, a^2+b^2+c^2, max, min or a*b*c) in keys[0..count).  The union of all
  * shards' results holds the global top-k: merge them with wtri_merge_topk.
  * 0 <= shard < nshards; keys has room for k entries.
  */
