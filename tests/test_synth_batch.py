@@ -31,3 +31,21 @@ def test_batch_graphs_device_seeded():
     a = synth.batch_graphs_device(8, seed=5, n_hi=1000, device="cpu")
     b = synth.batch_graphs_device(8, seed=5, n_hi=1000, device="cpu")
     assert torch.equal(a.u, b.u) and torch.equal(a.v, b.v) and torch.equal(a.w, b.w)
+
+
+def test_large_recipe_device_draw_small():
+    """The billion-edge recipe (and the serving pool's exponent) drawn at a
+    small size on the CPU device: simple graph, exactly m edges, the lookup
+    arrays consistent with the edge list, and none kept when not asked for."""
+    g = synth.large_graph_device(9, n=200_000, m=400_000, device="cpu", gamma=2.1)
+    u = g.u.numpy().astype(np.int64)
+    v = g.v.numpy().astype(np.int64)
+    assert u.shape[0] == 400_000 and np.all(u != v)
+    key = np.minimum(u, v) * g.n + np.maximum(u, v)
+    assert np.unique(key).shape[0] == 400_000
+    order = np.argsort(key)
+    assert np.array_equal(g.keys.numpy(), key[order])
+    assert np.array_equal(g.w_by_key.numpy(), g.w.numpy()[order])
+    bare = synth.large_graph_device(9, n=200_000, m=400_000, device="cpu", gamma=2.1, lookup=False)
+    assert bare.keys is None and bare.w_by_key is None
+    assert torch.equal(bare.u, g.u) and torch.equal(bare.w, g.w)
