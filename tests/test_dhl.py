@@ -60,6 +60,19 @@ def test_dhl_complete_graph(n):
     assert int(r["key"][0]) == 2 * (3 * n - 6)
 
 
+@pytest.mark.parametrize("n", [5, 300])
+def test_dhl_wheel(n):
+    # hub n, rim 0..n-1: n triangles {i, i+1, hub}; spokes 2i+2, rim edges 1
+    u = np.array(list(range(n)) * 2, np.int32)
+    v = np.array([n] * n + [(i + 1) % n for i in range(n)], np.int32)
+    w = np.array([2 * i + 2 for i in range(n)] + [1] * n, np.int32)
+    tris = [tuple(sorted((i, (i + 1) % n, n))) for i in range(n)]
+    key = {t: 2 * t[0] + 2 * t[1] + 5 for t in tris}
+    for a in ALPHAS:
+        r = oracle.dhl_topk(n + 1, u, v, w, 1.0, n, alpha=a)
+        assert [tuple(x) for x in r["tri"]] == sorted(tris, key=lambda t: (-key[t], t))
+
+
 @pytest.mark.parametrize("seed", range(60))
 def test_dhl_random_small(seed):
     g = synth.random_small_graph(6 + seed % 40, 0.15 + 0.8 * ((seed * 37) % 100) / 100, 1 + seed % 9, seed)

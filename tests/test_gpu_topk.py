@@ -241,6 +241,27 @@ def test_empty_and_degenerate():
         d.free()
 
 
+@pytest.mark.parametrize("n", [5, 300, 5000])
+def test_wheel_closed_form(n):
+    """A hub joined to every vertex of a rim cycle: n triangles {i, i+1, hub},
+    spokes weigh 2i+2 and rim edges 1, so the p = 1 order is by 2i+2j+5 and
+    every p = -inf key is 1 (triple order)."""
+    u = np.array(list(range(n)) * 2, np.int32)
+    v = np.array([n] * n + [(i + 1) % n for i in range(n)], np.int32)
+    w = np.array([2 * i + 2 for i in range(n)] + [1] * n, np.int32)
+    tris = [tuple(sorted((i, (i + 1) % n, n))) for i in range(n)]
+    key = {t: 2 * t[0] + 2 * t[1] + 5 for t in tris}
+    d = wt.build_csr(n + 1, u, v, w)
+    try:
+        t1, w1 = d.topk(1.0, n)
+        assert [tuple(x) for x in t1] == sorted(tris, key=lambda t: (-key[t], t))
+        np.testing.assert_array_equal(w1, np.array(sorted(key.values(), reverse=True)) / 3.0)
+        tm, wm = d.topk(-math.inf, n)
+        assert [tuple(x) for x in tm] == sorted(tris) and np.all(wm == 1.0)
+    finally:
+        d.free()
+
+
 def test_complete_graph_closed_form():
     n = 40
     iu, ju = np.triu_indices(n, 1)

@@ -67,6 +67,29 @@ def test_complete_graph_sum_weights_closed_form(n):
     assert tuple(r0["tri"][0]) == (n - 3, n - 2, n - 1)
 
 
+@pytest.mark.parametrize("n", [5, 17, 300])
+def test_wheel_closed_form(n):
+    """Wheel: hub h = n joined to rim vertices 0..n-1, rim cycle i -- i+1
+    (mod n).  Exactly n triangles {i, i+1, hub}.  Spokes weigh 2 i + 2 and rim
+    edges 1, so triangle {i, i+1 mod n, hub} has p = 1 key
+    (2 i + 2) + (2 (i+1 mod n) + 2) + 1 and min key 1: the p = 1 order is by
+    that sum, the p = -inf order (all keys 1) is the triple order."""
+    hub = n
+    u = np.array(list(range(n)) + list(range(n)), np.int32)
+    v = np.array([hub] * n + [(i + 1) % n for i in range(n)], np.int32)
+    w = np.array([2 * i + 2 for i in range(n)] + [1] * n, np.int32)
+    tris = [tuple(sorted((i, (i + 1) % n, hub))) for i in range(n)]
+    key1 = {t: (2 * t[0] + 2) + (2 * t[1] + 2) + 1 for t in tris}
+    r = oracle.topk(n + 1, u, v, w, 1.0, n + 3)
+    assert r["ntri"] == n and r["count"] == n
+    assert [tuple(x) for x in r["tri"]] == sorted(tris, key=lambda t: (-key1[t], t))
+    assert [int(k) for k in r["key"]] == sorted(key1.values(), reverse=True)
+    r = oracle.topk(n + 1, u, v, w, -math.inf, n)
+    assert [tuple(x) for x in r["tri"]] == sorted(tris) and set(int(k) for k in r["key"]) == {1}
+    r = oracle.topk(n + 1, u, v, w, math.inf, 1)
+    assert int(r["key"][0]) == 2 * (n - 1) + 2
+
+
 def test_trace_a_cubed_count():
     for g in [synth.tiny_graph(0), synth.scaled_mid_graph(3000, 30000, seed=5)]:
         A = np.zeros((g.n, g.n), dtype=np.float64)
