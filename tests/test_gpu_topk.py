@@ -241,6 +241,43 @@ def test_empty_and_degenerate():
         d.free()
 
 
+@pytest.mark.parametrize("p", [1.0, -math.inf])
+def test_largest_k(p):
+    """k at the library's limit (65536) on a graph with more triangles than
+    that, against the oracle; one more is refused."""
+    g = synth.scaled_mid_graph(100_000, 1_000_000, seed=31)
+    d = wt.build_csr(g.n, g.u, g.v, g.w)
+    try:
+        want = oracle.topk(g.n, g.u, g.v, g.w, p, 65536)
+        assert want["count"] == 65536
+        t, w = d.topk(p, 65536)
+        assert_topk_equal(t, w, want, p, f"k=65536 p={p}")
+        with pytest.raises(wt.WtriError) as ei:
+            d.topk(p, 65537)
+        assert ei.value.code == -5
+    finally:
+        d.free()
+
+
+def test_huge_sparse_vertex_range():
+    """5e7 vertex ids (26-bit row keys: three radix passes per row sort) and
+    two triangles at the two ends of the id range, the rest isolated."""
+    n = 50_000_000
+    a, b, c = n - 3, n - 2, n - 1
+    u = np.array([a, b, a, 0, 1, 0, 7], np.int32)
+    v = np.array([b, c, c, 1, 2, 2, a], np.int32)
+    w = np.array([5, 6, 7, 1, 1, 1, 9], np.int32)
+    d = wt.build_csr(n, u, v, w)
+    try:
+        t, x = d.topk(1.0, 5)
+        assert t.tolist() == [[a, b, c], [0, 1, 2]]
+        assert x.tolist() == [18 / 3.0, 1.0]
+        t, x = d.topk(-math.inf, 1)
+        assert t.tolist() == [[a, b, c]] and x.tolist() == [5.0]
+    finally:
+        d.free()
+
+
 @pytest.mark.parametrize("n", [5, 300, 5000])
 def test_wheel_closed_form(n):
     """A hub joined to every vertex of a rim cycle: n triangles {i, i+1, hub},
