@@ -47,16 +47,33 @@ int p_to_code_for(double p, const wtri_graph* g, int* code) {
 }
 
 int sm_count() {
-    static int cached = 0;
-    if (cached == 0) {
-        int dev = 0, c = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && c > 0)
-            cached = c;
-        else
-            return 132;
-    }
-    return cached;
+    static std::atomic<int> cached[64];
+    int dev = 0, c = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 132;
+    if (dev >= 0 && dev < 64 && (c = cached[dev].load(std::memory_order_relaxed)) > 0) return c;
+    if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0)
+        return 132;
+    if (dev >= 0 && dev < 64) cached[dev].store(c, std::memory_order_relaxed);
+    return c;
+}
+
+int smem_optin(const void* fn, int bytes, std::atomic<uint64_t>& done) {
+    int dev = 0;
+    WTRI_CUDA(cudaGetDevice(&dev));
+    const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return WTRI_OK;
+    WTRI_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    if (bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return WTRI_OK;
+}
+
+const char* query_name(int pcode) {
+    static const char* const names[P_COUNT] = {"query_p=-inf", "query_p=1", "query_p=2",
+                                               "query_p=+inf", "query_p=0"};
+    static_assert(P_MIN < P_COUNT && P_ONE < P_COUNT && P_TWO < P_COUNT && P_MAX < P_COUNT &&
+                      P_GEO < P_COUNT,
+                  "every p code names a query");
+    return (pcode >= 0 && pcode < P_COUNT) ? names[pcode] : "query_p=?";
 }
 
 namespace {

@@ -333,12 +333,10 @@ int batch_plan_launch(BatchPlan* P, void* dbuf, cudaStream_t s, int use_graph) {
         WTRI_CUDA(cudaMemcpyAsync(d_los, P->los.data(), 8 * P->los.size(), cudaMemcpyHostToDevice, s));
     WTRI_CUDA(cudaMemcpyAsync(d_koffs, P->koffs.data(), 8 * P->koffs.size(), cudaMemcpyHostToDevice, s));
 
-    const size_t lsmem = (size_t)STAGE_MAX * 4 + 16;
-    static bool attr_done = false;  // idempotent
-    if (!attr_done) {
-        WTRI_CUDA(cudaFuncSetAttribute(k_long_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)lsmem));
-        attr_done = true;
+    const size_t lsmem = LONG_SMEM;
+    {
+        static std::atomic<uint64_t> done{0};
+        WTRI_TRY(smem_optin((const void*)k_long_batch, (int)lsmem, done));
     }
     const int long_grid = sm_count() * 2;
     const int R = P->R;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/wtri.h"
@@ -43,6 +44,9 @@ enum : uint32_t {
 // p codes (template parameter of the scoring kernels).  P_GEO is p = 0, the
 // geometric mean (Eq. 1's limit), ranked by the exact product of the weights.
 enum PCode : int { P_MIN = 0, P_ONE = 1, P_TWO = 2, P_MAX = 3, P_GEO = 4 };
+constexpr int P_COUNT = 5;
+// Phase-timer name of a query at p code P ("query_p=...").
+const char* query_name(int pcode);
 // Largest weight for which the product key of p = 0 fits 63 bits.
 constexpr int32_t GEO_WMAX = (1 << 21) - 1;
 
@@ -162,7 +166,14 @@ struct ProfScope {
 
 // Shared launch helpers.
 inline unsigned int ceil_div_u(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }
-int sm_count();
+int sm_count();  // of the current device
+
+// Raises a kernel's dynamic shared-memory limit to 'bytes' on the current
+// device.  The attribute belongs to the device that is current when it is
+// set, so 'done' keeps one bit per device (ordinals 0..63; higher ordinals
+// set the attribute on every call).  Two threads may both set it the first
+// time: the call is idempotent.
+int smem_optin(const void* fn, int bytes, std::atomic<uint64_t>& done);
 
 // Device-wide exclusive scan of int32 counts into int64 offsets (n+1
 // outputs; out[n] = total).  Scratch is stream-ordered.

@@ -434,6 +434,20 @@ __device__ __forceinline__ void long_scan(const DevGraph& G, const Query& q, uns
 // the closing edge are binary searches there.  Rows longer than STAGE_MAX
 // fall back to the oriented lists in global memory.
 template <int P, bool SAMPLED = false>
+__global__ void __launch_bounds__(LBLK) k_long(DevGraph G, Query q);
+
+// Dynamic shared memory of k_long: one staged row plus 16 bytes of rounding.
+constexpr size_t LONG_SMEM = (size_t)STAGE_MAX * 4 + 16;
+
+// Opts k_long<P, SAMPLED> in to LONG_SMEM bytes of dynamic shared memory on
+// the current device (once per device).
+template <int P, bool SAMPLED>
+int long_optin() {
+    static std::atomic<uint64_t> done{0};
+    return smem_optin((const void*)k_long<P, SAMPLED>, (int)LONG_SMEM, done);
+}
+
+template <int P, bool SAMPLED>
 __global__ void __launch_bounds__(LBLK) k_long(DevGraph G, Query q) {
     extern __shared__ __align__(128) unsigned char lsm[];
     int32_t* srow = reinterpret_cast<int32_t*>(lsm);

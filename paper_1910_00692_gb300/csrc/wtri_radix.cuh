@@ -588,20 +588,12 @@ int run_pass(const Dig& dg, const Loader& ld, const Storer& st, const PassGeom& 
     const size_t smem = sizeof(ScatterSmem);
     ProfScope ps("radix_downsweep", s, (double)g.n * (Loader::REC_BYTES + st.rec_bytes()), 1);
     if (bulk_enabled() && ld.tma_ok()) {
-        static bool attr = false;  // per instantiation; idempotent
-        if (!attr) {
-            WTRI_CUDA(cudaFuncSetAttribute(k_scatter<Loader, Storer, true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = true;
-        }
+        static std::atomic<uint64_t> done{0};  // per instantiation and device
+        WTRI_TRY(smem_optin((const void*)k_scatter<Loader, Storer, true>, (int)smem, done));
         k_scatter<Loader, Storer, true><<<g.chunks, NT, smem, s>>>(ld, st, g, counts, totals, err);
     } else {
-        static bool attr = false;
-        if (!attr) {
-            WTRI_CUDA(cudaFuncSetAttribute(k_scatter<Loader, Storer, false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = true;
-        }
+        static std::atomic<uint64_t> done{0};
+        WTRI_TRY(smem_optin((const void*)k_scatter<Loader, Storer, false>, (int)smem, done));
         k_scatter<Loader, Storer, false><<<g.chunks, NT, smem, s>>>(ld, st, g, counts, totals, err);
     }
     WTRI_CUDA(cudaGetLastError());

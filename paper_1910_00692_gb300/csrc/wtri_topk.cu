@@ -45,16 +45,10 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
     q.t_short = g->tune.t_short;
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
 
-    const size_t lsmem = (size_t)STAGE_MAX * 4 + 16;
-    static bool attr_done[4] = {false, false, false, false};
-    if (!attr_done[P]) {
-        WTRI_CUDA(cudaFuncSetAttribute(k_long<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)lsmem));
-        attr_done[P] = true;
-    }
+    const size_t lsmem = LONG_SMEM;
+    WTRI_TRY((long_optin<P, false>()));
     const int long_grid = sm_count() * 2;
-    static const char* qname[4] = {"query_p=-inf", "query_p=1", "query_p=2", "query_p=+inf"};
-    ProfScope whole(qname[P], s, 0.0, 0);
+    ProfScope whole(query_name(P), s, 0.0, 0);
     int64_t lo = 0, size = g->tune.first_round;
     while (lo < m) {
         const int64_t hi = std::min(m, lo + size);
@@ -328,13 +322,8 @@ int run_sample(const wtri_graph* g, int32_t k, int64_t nsamples, uint64_t seed, 
     int64_t nlist = 0;
     WTRI_CUDA(cudaMemcpyAsync(&nlist, off + words, 8, cudaMemcpyDeviceToHost, s));
     WTRI_CUDA(cudaStreamSynchronize(s));
-    const size_t lsmem = (size_t)STAGE_MAX * 4 + 16;
-    static bool attr_done[4] = {false, false, false, false};
-    if (!attr_done[P]) {
-        WTRI_CUDA(cudaFuncSetAttribute(k_long<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)lsmem));
-        attr_done[P] = true;
-    }
+    const size_t lsmem = LONG_SMEM;
+    WTRI_TRY((long_optin<P, true>()));
     const int long_grid = sm_count() * 2;
     int64_t lo = 0, size = g->tune.first_round;
     while (lo < nlist) {
@@ -467,13 +456,8 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
     // (counters, threshold, stop flag, error bits).
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
 
-    const size_t lsmem = (size_t)STAGE_MAX * 4 + 16;
-    static bool attr_done[4] = {false, false, false, false};
-    if (!attr_done[P]) {
-        WTRI_CUDA(cudaFuncSetAttribute(k_long<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)lsmem));
-        attr_done[P] = true;
-    }
+    const size_t lsmem = LONG_SMEM;
+    WTRI_TRY((long_optin<P, false>()));
     const int long_grid = sm_count() * 2;
     int64_t lo = 0, size = g->tune.first_round;
     while (lo < m) {
