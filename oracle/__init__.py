@@ -33,6 +33,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
 P_CODES = {-math.inf: 0, 1.0: 1, 2.0: 2, math.inf: 3, 0.0: 4}
+P_GENERAL = 5  # any other finite p: fp64 key (the mean itself)
 
 
 def build(force: bool = False) -> str:
@@ -67,10 +68,12 @@ def lib():
         L.or_edge_order.argtypes = [ctypes.c_int64, i32p, i64p]
         L.or_oriented_csr.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p,
                                       i64p, i32p, i32p, i64p]
-        L.or_score.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                               ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]
+        L.or_score.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                               ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
+                               ctypes.POINTER(ctypes.c_double)]
         L.or_topk.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, ctypes.c_int,
-                              ctypes.c_int64, ctypes.c_int, i32p, u64p, f64p, I64P, I64P]
+                              ctypes.c_double, ctypes.c_int64, ctypes.c_int, i32p, u64p, f64p, I64P,
+                              I64P]
         L.or_count_triangles.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, I64P]
         u64p_ = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
         u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
@@ -79,18 +82,23 @@ def lib():
         L.or_sample_edges.argtypes = [ctypes.c_int64, i32p, i64p, ctypes.c_int, ctypes.c_int64,
                                       ctypes.c_uint64, i64p]
         L.or_topk_of_sampled.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, u8p,
-                                         ctypes.c_int, ctypes.c_int64, ctypes.c_int, i32p, u64p, f64p,
-                                         I64P, I64P]
+                                         ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_int,
+                                         i32p, u64p, f64p, I64P, I64P]
         L.or_topk_shard.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, i64p, ctypes.c_int,
-                                    ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, i32p,
-                                    u64p, f64p, I64P, I64P]
+                                    ctypes.c_double, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_int, i32p, u64p, f64p, I64P, I64P]
+        L.or_wedge_samples.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, ctypes.c_int,
+                                       ctypes.c_int64, ctypes.c_uint64, i32p, i32p, i32p, i32p]
+        L.or_wedge_topk.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, ctypes.c_int,
+                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, i32p, u64p, f64p,
+                                    I64P, I64P]
         L.dhl_topk.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, ctypes.c_int,
                                ctypes.c_int64, ctypes.c_double, i32p, u64p, f64p, I64P, i64p]
         L.dhl_alpha.argtypes = [ctypes.c_int, ctypes.c_double]
         L.dhl_alpha.restype = ctypes.c_double
         for f in (L.dhl_topk, L.or_validate, L.or_sym_csr, L.or_edge_order, L.or_oriented_csr,
                   L.or_score, L.or_topk, L.or_count_triangles, L.or_sample_edges,
-                  L.or_topk_of_sampled, L.or_topk_shard):
+                  L.or_topk_of_sampled, L.or_topk_shard, L.or_wedge_samples, L.or_wedge_topk):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -108,9 +116,14 @@ GEO_WMAX = (1 << 21) - 1  # p = 0 ranks by the product of the weights: exact bel
 
 
 def pcode(p: float) -> int:
-    if p not in P_CODES:
-        raise OracleError(f"p={p} is outside {{-inf, 0, 1, 2, +inf}}")
-    return P_CODES[p]
+    """p code of the C oracle: exact integer keys for -inf, 0, 1, 2, +inf;
+    code 5 (an fp64 key) for any other finite p."""
+    p = float(p)
+    if math.isnan(p):
+        raise OracleError("p is NaN")
+    if p in P_CODES:
+        return P_CODES[p]
+    return P_GENERAL
 
 
 def _check_geo(p, w):
@@ -182,7 +195,8 @@ def score(p, a, b, c):
     """(key, value) of one triangle with edge weights a, b, c (Eq. 1)."""
     key = ctypes.c_uint64(0)
     val = ctypes.c_double(0.0)
-    rc = lib().or_score(pcode(p), int(a), int(b), int(c), ctypes.byref(key), ctypes.byref(val))
+    rc = lib().or_score(pcode(p), float(p), int(a), int(b), int(c), ctypes.byref(key),
+                        ctypes.byref(val))
     if rc != 0:
         raise OracleError("bad p")
     return int(key.value), float(val.value)
@@ -200,7 +214,7 @@ def topk(n, u, v, w, p, k, nthreads=0):
     val = np.zeros(max(k, 1), np.float64)
     cnt = ctypes.c_int64(0)
     ntri = ctypes.c_int64(0)
-    rc = lib().or_topk(n, m, u, v, w, pcode(p), k, int(nthreads), tri, key, val,
+    rc = lib().or_topk(n, m, u, v, w, pcode(p), float(p), k, int(nthreads), tri, key, val,
                        ctypes.byref(cnt), ctypes.byref(ntri))
     if rc != 0:
         raise OracleError(f"or_topk failed (rc={rc})")
@@ -250,7 +264,8 @@ def philox4x64_10(counter, key):
 
 
 def sample_edges(w, p, nsamples, seed):
-    """Algorithm 3's edge draws (probability w^p / Z), p in {1, 2}.  Returns
+    """Algorithm 3's edge draws (probability w^p / Z), p in {0, 1, 2} (p = 0:
+    every edge equally likely).  Returns
     (perm, hits): hits[r] counts draws of the r-th edge of edge_order()."""
     w = _arr(w)
     perm = edge_order(w)
@@ -275,8 +290,8 @@ def topk_of_marked(n, u, v, w, mark, p, k, nthreads=0):
     val = np.zeros(max(k, 1), np.float64)
     cnt = ctypes.c_int64(0)
     ntri = ctypes.c_int64(0)
-    rc = lib().or_topk_of_sampled(n, m, u, v, w, mark, pcode(p), k, int(nthreads), tri, key, val,
-                                  ctypes.byref(cnt), ctypes.byref(ntri))
+    rc = lib().or_topk_of_sampled(n, m, u, v, w, mark, pcode(p), float(p), k, int(nthreads), tri,
+                                  key, val, ctypes.byref(cnt), ctypes.byref(ntri))
     if rc != 0:
         raise OracleError(f"or_topk_of_sampled failed (rc={rc})")
     c = int(cnt.value)
@@ -313,8 +328,8 @@ def topk_shard(n, u, v, w, p, k, shard, nshards, chunk_shift=10):
     val = np.zeros(max(k, 1), np.float64)
     cnt = ctypes.c_int64(0)
     ntri = ctypes.c_int64(0)
-    rc = lib().or_topk_shard(n, m, u, v, w, rank, pcode(p), k, int(shard), int(nshards), int(chunk_shift),
-                             tri, key, val, ctypes.byref(cnt), ctypes.byref(ntri))
+    rc = lib().or_topk_shard(n, m, u, v, w, rank, pcode(p), float(p), k, int(shard), int(nshards),
+                             int(chunk_shift), tri, key, val, ctypes.byref(cnt), ctypes.byref(ntri))
     if rc != 0:
         raise OracleError(f"or_topk_shard failed (rc={rc})")
     c = int(cnt.value)
@@ -337,3 +352,39 @@ def count_triangles(n, u, v, w=None):
 if __name__ == "__main__":  # pragma: no cover
     build(force="--force" in sys.argv)
     print(_LIB_PATH)
+
+
+def wedge_samples(n, u, v, w, p, nsamples, seed):
+    """Algorithm 4's draws (Eqs. 6-8), p in {0, 1, 2}: per sample the center
+    a, the positions jb, jc of b and c in a's weight-sorted row, and the
+    sorted triangle (or -1s when the wedge does not close)."""
+    u, v, w = _arr(u), _arr(v), _arr(w)
+    ns = int(nsamples)
+    center = np.zeros(max(ns, 1), np.int32)
+    jb = np.zeros(max(ns, 1), np.int32)
+    jc = np.zeros(max(ns, 1), np.int32)
+    tri = np.zeros(3 * max(ns, 1), np.int32)
+    rc = lib().or_wedge_samples(n, u.shape[0], u, v, w, pcode(p), ns,
+                                ctypes.c_uint64(int(seed) & (2**64 - 1)), center, jb, jc, tri)
+    if rc != 0:
+        raise OracleError(f"or_wedge_samples failed (rc={rc})")
+    return center[:ns], jb[:ns], jc[:ns], tri[: 3 * ns].reshape(ns, 3)
+
+
+def wedge_topk(n, u, v, w, p, k, nsamples, seed):
+    """Top-k of Algorithm 4's triangle set T (distinct closed wedges)."""
+    u, v, w = _arr(u), _arr(v), _arr(w)
+    k = int(k)
+    tri = np.zeros(3 * max(k, 1), np.int32)
+    key = np.zeros(max(k, 1), np.uint64)
+    val = np.zeros(max(k, 1), np.float64)
+    cnt = ctypes.c_int64(0)
+    ntri = ctypes.c_int64(0)
+    rc = lib().or_wedge_topk(n, u.shape[0], u, v, w, pcode(p), k, int(nsamples),
+                             ctypes.c_uint64(int(seed) & (2**64 - 1)), tri, key, val, ctypes.byref(cnt),
+                             ctypes.byref(ntri))
+    if rc != 0:
+        raise OracleError(f"or_wedge_topk failed (rc={rc})")
+    c = int(cnt.value)
+    return {"tri": tri[: 3 * c].reshape(c, 3), "key": key[:c], "value": val[:c], "count": c,
+            "ntri": int(ntri.value)}

@@ -18,13 +18,22 @@
  *  - enumeration is the paper's brute-force baseline (Section 3, Section 5.2):
  *    NodeIterator++ over a degree ordering, keeping a heap of the k heaviest.
  *
- * Ranking never uses the floating value.  Each triangle gets an exact integer
- * key that is monotone in m_p: a+b+c (p=1), a^2+b^2+c^2 (p=2), max (p=+inf),
- * min (p=-inf), a*b*c (p=0; exact for weights below 2^21).  Eq. 4 (Section 4)
- * ranks by the sum of p-th powers, which is only order-preserving for p>0;
- * these keys are the order-preserving choice for every supported p.  The
- * reported value is fp64: (a+b+c)/3, sqrt((a^2+b^2+c^2)/3), max, min,
- * cbrt(a*b*c).
+ * For p in {-inf, 0, 1, 2, +inf} ranking never uses the floating value.
+ * Each triangle gets an exact integer key that is monotone in m_p: a+b+c
+ * (p=1), a^2+b^2+c^2 (p=2), max (p=+inf), min (p=-inf), a*b*c (p=0; exact
+ * for weights below 2^21).  Eq. 4 (Section 4) ranks by the sum of p-th
+ * powers, which is only order-preserving for p>0; these keys are the
+ * order-preserving choice for every supported p.  The reported value is
+ * fp64: (a+b+c)/3, sqrt((a^2+b^2+c^2)/3), max, min, cbrt(a*b*c).
+ *
+ * Any other finite p (code 5: the harmonic mean p = -1, p = -2, p = 3, ...)
+ * has no exact 64-bit integer key; there the key is m_p itself in fp64
+ * (its bit pattern, which orders positive doubles like their values),
+ * computed from Eq. 1 with the largest weight factored out for p > 0 (the
+ * smallest for p < 0) so that no power overflows:
+ *     m_p = s * ((( a/s)^p + (b/s)^p + (c/s)^p) / 3)^(1/p).
+ * Two triangles whose means differ by less than fp64 rounding may then rank
+ * either way; the tests allow exactly that and nothing more.
  *
  * Input hygiene (Section 1: "simple, undirected graph with positive edge
  * weights"): self-loops, ids outside [0,n), weights <= 0 and repeated
@@ -46,7 +55,9 @@
 #define OR_EINVAL -1
 #define OR_ENOMEM -2
 
-/* p codes: 0 -> -inf, 1 -> 1, 2 -> 2, 3 -> +inf */
+/* p codes: 0 -> -inf, 1 -> 1, 2 -> 2, 3 -> +inf, 4 -> 0, 5 -> any other
+ * finite p (passed beside the code as a double) */
+#define OR_PCODE_MAX 5
 
 /* ------------------------------------------------------------------------ */
 /* Validation and the symmetric adjacency (N(a), d_a of Section 4).          */
@@ -217,7 +228,21 @@ int or_oriented_csr(int32_t n, int64_t m, const int32_t* u, const int32_t* v,
 /* Scoring: exact key and fp64 value of m_p (Eq. 1).                        */
 /* ------------------------------------------------------------------------ */
 
-static uint64_t tri_key(int pcode, int32_t a, int32_t b, int32_t c) {
+/* m_p of Eq. 1 for a finite p other than 0, in fp64, scaled so that no power
+ * overflows: s = max(a,b,c) for p > 0, min(a,b,c) for p < 0.  The weights
+ * are summed in ascending order, so equal multisets give equal bits. */
+static double general_mean(double p, int32_t a, int32_t b, int32_t c) {
+    int32_t t3[3] = {a, b, c}, x;
+    if (t3[0] > t3[1]) { x = t3[0]; t3[0] = t3[1]; t3[1] = x; }
+    if (t3[1] > t3[2]) { x = t3[1]; t3[1] = t3[2]; t3[2] = x; }
+    if (t3[0] > t3[1]) { x = t3[0]; t3[0] = t3[1]; t3[1] = x; }
+    const double s = p > 0 ? (double)t3[2] : (double)t3[0];
+    const double t = (pow((double)t3[0] / s, p) + pow((double)t3[1] / s, p) +
+                      pow((double)t3[2] / s, p)) / 3.0;
+    return s * pow(t, 1.0 / p);
+}
+
+static uint64_t tri_key(int pcode, double p, int32_t a, int32_t b, int32_t c) {
     switch (pcode) {
         case 0: {
             int32_t x = a < b ? a : b;
@@ -229,6 +254,12 @@ static uint64_t tri_key(int pcode, int32_t a, int32_t b, int32_t c) {
             return (uint64_t)a * (uint64_t)a + (uint64_t)b * (uint64_t)b + (uint64_t)c * (uint64_t)c;
         case 4: /* p = 0: the geometric mean ranks as the product (weights < 2^21) */
             return (uint64_t)a * (uint64_t)b * (uint64_t)c;
+        case 5: { /* the positive fp64 mean's bit pattern orders like its value */
+            const double m = general_mean(p, a, b, c);
+            uint64_t k;
+            memcpy(&k, &m, sizeof k);
+            return k;
+        }
         default: {
             int32_t x = a > b ? a : b;
             return (uint64_t)(x > c ? x : c);
@@ -244,15 +275,27 @@ static double tri_value(int pcode, uint64_t key) {
             return sqrt((double)key / 3.0);
         case 4:
             return cbrt((double)key);
+        case 5: {
+            double m;
+            memcpy(&m, &key, sizeof m);
+            return m;
+        }
         default:
             return (double)key;
     }
 }
 
+/* Checks a (code, p) pair: code 5 needs a finite p outside {0, 1, 2}. */
+static int pcode_ok(int pcode, double p) {
+    if (pcode < 0 || pcode > OR_PCODE_MAX) return 0;
+    if (pcode == 5) return isfinite(p) && p != 0.0 && p != 1.0 && p != 2.0;
+    return 1;
+}
+
 /* Public scorer, so that tests can pin it against hand-computed means. */
-int or_score(int pcode, int32_t a, int32_t b, int32_t c, uint64_t* key, double* value) {
-    if (pcode < 0 || pcode > 4) return OR_EINVAL;
-    *key = tri_key(pcode, a, b, c);
+int or_score(int pcode, double p, int32_t a, int32_t b, int32_t c, uint64_t* key, double* value) {
+    if (!pcode_ok(pcode, p)) return OR_EINVAL;
+    *key = tri_key(pcode, p, a, b, c);
     *value = tri_value(pcode, *key);
     return OR_OK;
 }
@@ -340,11 +383,11 @@ static void sort3(int32_t* t) {
  * of triangles in the graph.  nthreads <= 0 means all available threads.
  */
 int or_topk(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int32_t* w,
-            int pcode, int64_t k, int nthreads, int32_t* tri, uint64_t* key, double* value,
-            int64_t* count, int64_t* ntri) {
+            int pcode, double preal, int64_t k, int nthreads, int32_t* tri, uint64_t* key,
+            double* value, int64_t* count, int64_t* ntri) {
     *count = 0;
     *ntri = 0;
-    if (pcode < 0 || pcode > 4 || k <= 0) return OR_EINVAL;
+    if (!pcode_ok(pcode, preal) || k <= 0) return OR_EINVAL;
     int64_t* orow = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
     int32_t* ocol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
     int32_t* owt = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
@@ -399,7 +442,7 @@ int or_topk(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int3
                             q++;
                         } else {
                             or_tri x;
-                            x.key = tri_key(pcode, wab, owt[p], owt[q]);
+                            x.key = tri_key(pcode, preal, wab, owt[p], owt[q]);
                             x.t[0] = a;
                             x.t[1] = b;
                             x.t[2] = ocol[p];
@@ -539,13 +582,13 @@ void or_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64
  */
 int or_sample_edges(int64_t m, const int32_t* w, const int64_t* perm, int pcode, int64_t nsamples,
                     uint64_t seed, int64_t* hits) {
-    if (pcode != 1 && pcode != 2) return OR_EINVAL;
+    if (pcode != 1 && pcode != 2 && pcode != 4) return OR_EINVAL;
     unsigned __int128* C = (unsigned __int128*)malloc(sizeof(unsigned __int128) * (size_t)(m + 1));
     if (!C) return OR_ENOMEM;
     unsigned __int128 acc = 0;
     for (int64_t r = 0; r < m; r++) {
         unsigned __int128 x = (unsigned __int128)(uint64_t)w[perm[r]];
-        acc += pcode == 1 ? x : x * x;
+        acc += pcode == 4 ? 1 : (pcode == 1 ? x : x * x); /* w^p, p = 0 -> 1 */
         C[r] = acc;
         hits[r] = 0;
     }
@@ -578,11 +621,12 @@ int or_sample_edges(int64_t m, const int32_t* w, const int64_t* perm, int pcode,
  * edge_sampled[i] != 0 marks input edge i.
  */
 int or_topk_of_sampled(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int32_t* w,
-                       const uint8_t* edge_sampled, int pcode, int64_t k, int nthreads,
-                       int32_t* tri, uint64_t* key, double* value, int64_t* count, int64_t* ntri) {
+                       const uint8_t* edge_sampled, int pcode, double preal, int64_t k,
+                       int nthreads, int32_t* tri, uint64_t* key, double* value, int64_t* count,
+                       int64_t* ntri) {
     *count = 0;
     *ntri = 0;
-    if (pcode < 0 || pcode > 4 || k <= 0) return OR_EINVAL;
+    if (!pcode_ok(pcode, preal) || k <= 0) return OR_EINVAL;
     int64_t* orow = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
     int32_t* ocol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
     int32_t* owt = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
@@ -635,7 +679,7 @@ int or_topk_of_sampled(int32_t n, int64_t m, const int32_t* u, const int32_t* v,
                         } else {
                             if (edge_sampled[oeid[i]] || edge_sampled[oeid[p]] || edge_sampled[oeid[q]]) {
                                 or_tri x;
-                                x.key = tri_key(pcode, owt[i], owt[p], owt[q]);
+                                x.key = tri_key(pcode, preal, owt[i], owt[p], owt[q]);
                                 x.t[0] = a;
                                 x.t[1] = b;
                                 x.t[2] = ocol[p];
@@ -699,12 +743,12 @@ int or_topk_of_sampled(int32_t n, int64_t m, const int32_t* u, const int32_t* v,
  * every triangle (NodeIterator++), like or_topk.
  */
 int or_topk_shard(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int32_t* w,
-                  const int64_t* rank, int pcode, int64_t k, int32_t shard, int32_t nshards,
-                  int chunk_shift, int32_t* tri, uint64_t* key, double* value, int64_t* count,
-                  int64_t* ntri) {
+                  const int64_t* rank, int pcode, double preal, int64_t k, int32_t shard,
+                  int32_t nshards, int chunk_shift, int32_t* tri, uint64_t* key, double* value,
+                  int64_t* count, int64_t* ntri) {
     *count = 0;
     *ntri = 0;
-    if (pcode < 0 || pcode > 4 || k <= 0 || nshards < 1 || shard < 0 || shard >= nshards)
+    if (!pcode_ok(pcode, preal) || k <= 0 || nshards < 1 || shard < 0 || shard >= nshards)
         return OR_EINVAL;
     int64_t* orow = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
     int32_t* ocol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
@@ -741,7 +785,7 @@ int or_topk_shard(int32_t n, int64_t m, const int32_t* u, const int32_t* v, cons
                     own = own < r2 ? own : r2;
                     if ((int32_t)((own >> chunk_shift) % nshards) == shard) {
                         or_tri x;
-                        x.key = tri_key(pcode, owt[i], owt[p], owt[q]);
+                        x.key = tri_key(pcode, preal, owt[i], owt[p], owt[q]);
                         x.t[0] = a;
                         x.t[1] = b;
                         x.t[2] = ocol[p];
@@ -772,5 +816,266 @@ int or_topk_shard(int32_t n, int64_t m, const int32_t* u, const int32_t* v, cons
     free(ocol);
     free(owt);
     free(oeid);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Weighted wedge sampling (Algorithm 4, Proposition 4.2, Section 4.2).     */
+/* ------------------------------------------------------------------------ */
+
+typedef unsigned __int128 or_u128;
+
+/* floor(x * Z / 2^64) for a 64-bit x and Z < 2^128 (Z's high half < 2^64). */
+static or_u128 mulhi_z(uint64_t x, or_u128 Z) {
+    const uint64_t zl = (uint64_t)Z, zh = (uint64_t)(Z >> 64);
+    return (or_u128)x * zh + (((or_u128)x * zl) >> 64);
+}
+
+static or_u128 wpow(int pcode, int32_t w) {
+    const or_u128 x = (or_u128)(uint64_t)w;
+    return pcode == 4 ? (or_u128)1 : (pcode == 1 ? x : x * x);
+}
+
+/*
+ * Draws of Algorithm 4.  D(a) = sum over b in N(a) of w_ab^p.  Sample s uses
+ * the words (x0, x1, x2) of Philox4x64-10(counter (s, 0, 0, 0), key
+ * (seed, 1)):
+ *   a: t = floor(x0 * Z1 / 2^64), Z1 = sum_v 2 d_v D(v); a = first vertex
+ *      (by id) whose cumulative 2 d_v D(v) exceeds t (Eq. 6);
+ *   b: a's neighbours in the edge order (the weight-sorted row), entry j with
+ *      weight d_a w_j^p + D(a) (Eq. 7): t = floor(x1 * 2 d_a D(a) / 2^64);
+ *      t < d_a D(a) picks j with the cumulative w^p first above t / d_a, else
+ *      j = (t - d_a D(a)) / D(a) (the uniform part);
+ *   c: entry j with weight w_j^p + w_ab^p (Eq. 8): t = floor(x2 * (D(a) +
+ *      d_a w_ab^p) / 2^64); t < D(a) picks the cumulative w^p first above t,
+ *      else j = (t - D(a)) / w_ab^p.
+ * The wedge closes when c differs from b and {b, c} is an edge.  Outputs per
+ * sample: center[s] = a, jb[s], jc[s] (positions in a's weight-sorted row)
+ * and tri[3s..3s+2] = the sorted triangle or -1, -1, -1.  p codes 4 (p = 0),
+ * 1 and 2 (w^p is an exact integer).
+ */
+int or_wedge_samples(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int32_t* w,
+                     int pcode, int64_t nsamples, uint64_t seed, int32_t* center, int32_t* jb_out,
+                     int32_t* jc_out, int32_t* tri) {
+    if (pcode != 1 && pcode != 2 && pcode != 4) return OR_EINVAL;
+    if (m <= 0) {
+        for (int64_t s = 0; s < nsamples; s++) {
+            center[s] = jb_out[s] = jc_out[s] = -1;
+            tri[3 * s] = tri[3 * s + 1] = tri[3 * s + 2] = -1;
+        }
+        return OR_OK;
+    }
+    int rc = OR_OK;
+    int64_t* perm = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+    int64_t* deg = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t* wrow = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    int32_t* wc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * m));
+    int32_t* ww = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * m));
+    or_u128* P = (or_u128*)malloc(sizeof(or_u128) * (size_t)(2 * m));
+    or_u128* D = (or_u128*)calloc((size_t)n, sizeof(or_u128));
+    or_u128* C1 = (or_u128*)malloc(sizeof(or_u128) * (size_t)n);
+    int64_t* srow = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    int32_t* scl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * m));
+    int32_t* swt = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * m));
+    int64_t* seid = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * m));
+    if (!perm || !deg || !wrow || !fill || !wc || !ww || !P || !D || !C1 || !srow || !scl || !swt || !seid) {
+        rc = OR_ENOMEM;
+        goto done;
+    }
+    rc = or_edge_order(m, w, perm);
+    if (rc != OR_OK) goto done;
+    rc = or_sym_csr(n, m, u, v, w, srow, scl, swt, seid); /* validates too */
+    if (rc != OR_OK) goto done;
+    /* weight-sorted rows: append every edge, in edge order, to both rows */
+    for (int64_t i = 0; i < m; i++) {
+        deg[u[i]]++;
+        deg[v[i]]++;
+    }
+    wrow[0] = 0;
+    for (int32_t x = 0; x < n; x++) wrow[x + 1] = wrow[x] + deg[x];
+    for (int32_t x = 0; x <= n; x++) fill[x] = wrow[x];
+    for (int64_t r = 0; r < m; r++) {
+        const int64_t e = perm[r];
+        wc[fill[u[e]]] = v[e];
+        ww[fill[u[e]]++] = w[e];
+        wc[fill[v[e]]] = u[e];
+        ww[fill[v[e]]++] = w[e];
+    }
+    {
+        or_u128 acc = 0;
+        for (int32_t x = 0; x < n; x++) {
+            or_u128 rs = 0;
+            for (int64_t j = wrow[x]; j < wrow[x + 1]; j++) {
+                rs += wpow(pcode, ww[j]);
+                P[j] = rs; /* cumulative w^p within the row */
+            }
+            D[x] = rs;
+            acc += (or_u128)2 * (or_u128)(uint64_t)deg[x] * rs;
+            C1[x] = acc;
+        }
+    }
+    {
+        const or_u128 Z1 = C1[n - 1];
+        const uint64_t key[2] = {seed, 1};
+        for (int64_t s = 0; s < nsamples; s++) {
+            uint64_t ctr[4] = {(uint64_t)s, 0, 0, 0}, x[4];
+            or_philox4x64_10(ctr, key, x);
+            const or_u128 t1 = mulhi_z(x[0], Z1);
+            int32_t lo = 0, hi = n - 1; /* first vertex with C1 > t1 */
+            while (lo < hi) {
+                const int32_t mid = lo + (hi - lo) / 2;
+                if (C1[mid] > t1) hi = mid;
+                else lo = mid + 1;
+            }
+            const int32_t a = lo;
+            const int64_t b0 = wrow[a], da = deg[a];
+            const or_u128 Da = D[a];
+            /* b: d_a w^p + D(a) */
+            const or_u128 dD = (or_u128)(uint64_t)da * Da;
+            const or_u128 t2 = mulhi_z(x[1], 2 * dD);
+            int64_t jb;
+            if (t2 < dD) {
+                const or_u128 tp = t2 / (or_u128)(uint64_t)da;
+                int64_t l2 = 0, h2 = da - 1;
+                while (l2 < h2) {
+                    const int64_t mid = l2 + (h2 - l2) / 2;
+                    if (P[b0 + mid] > tp) h2 = mid;
+                    else l2 = mid + 1;
+                }
+                jb = l2;
+            } else {
+                jb = (int64_t)((t2 - dD) / Da);
+            }
+            /* c: w_c^p + w_ab^p */
+            const or_u128 wab = wpow(pcode, ww[b0 + jb]);
+            const or_u128 t3 = mulhi_z(x[2], Da + (or_u128)(uint64_t)da * wab);
+            int64_t jc;
+            if (t3 < Da) {
+                int64_t l2 = 0, h2 = da - 1;
+                while (l2 < h2) {
+                    const int64_t mid = l2 + (h2 - l2) / 2;
+                    if (P[b0 + mid] > t3) h2 = mid;
+                    else l2 = mid + 1;
+                }
+                jc = l2;
+            } else {
+                jc = (int64_t)((t3 - Da) / wab);
+            }
+            center[s] = a;
+            jb_out[s] = (int32_t)jb;
+            jc_out[s] = (int32_t)jc;
+            tri[3 * s] = tri[3 * s + 1] = tri[3 * s + 2] = -1;
+            if (jb != jc) {
+                const int32_t b = wc[b0 + jb], c = wc[b0 + jc];
+                /* closure: is c in N(b)?  (id-sorted row of b) */
+                int64_t l2 = srow[b], h2 = srow[b + 1];
+                while (l2 < h2) {
+                    const int64_t mid = l2 + (h2 - l2) / 2;
+                    if (scl[mid] < c) l2 = mid + 1;
+                    else h2 = mid;
+                }
+                if (l2 < srow[b + 1] && scl[l2] == c) {
+                    int32_t t3v[3] = {a, b, c};
+                    sort3(t3v);
+                    tri[3 * s] = t3v[0];
+                    tri[3 * s + 1] = t3v[1];
+                    tri[3 * s + 2] = t3v[2];
+                }
+            }
+        }
+    }
+done:
+    free(perm); free(deg); free(wrow); free(fill); free(wc); free(ww); free(P); free(D); free(C1);
+    free(srow); free(scl); free(swt); free(seid);
+    return rc;
+}
+
+static int cmp_triple(const void* pa, const void* pb) {
+    const int32_t* x = (const int32_t*)pa;
+    const int32_t* y = (const int32_t*)pb;
+    for (int i = 0; i < 3; i++)
+        if (x[i] != y[i]) return x[i] < y[i] ? -1 : 1;
+    return 0;
+}
+
+/*
+ * Top-k of Algorithm 4's triangle set T (every distinct triangle some sample
+ * closed), scored like or_topk.  *ntri receives |T|.
+ */
+int or_wedge_topk(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int32_t* w,
+                  int pcode, int64_t k, int64_t nsamples, uint64_t seed, int32_t* tri, uint64_t* key,
+                  double* value, int64_t* count, int64_t* ntri) {
+    *count = 0;
+    *ntri = 0;
+    if ((pcode != 1 && pcode != 2 && pcode != 4) || k <= 0 || nsamples < 0) return OR_EINVAL;
+    if (nsamples == 0 || m == 0) return OR_OK;
+    int32_t* ctr = (int32_t*)malloc(sizeof(int32_t) * (size_t)nsamples * 3);
+    int32_t* st = (int32_t*)malloc(sizeof(int32_t) * (size_t)nsamples * 3);
+    int64_t* rowp = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    int32_t* col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * m));
+    int32_t* wt = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * m));
+    int64_t* eid = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * m));
+    int rc = OR_ENOMEM;
+    if (ctr && st && rowp && col && wt && eid) {
+        rc = or_wedge_samples(n, m, u, v, w, pcode, nsamples, seed, ctr, ctr + nsamples,
+                              ctr + 2 * nsamples, st);
+        if (rc == OR_OK) rc = or_sym_csr(n, m, u, v, w, rowp, col, wt, eid);
+    }
+    if (rc == OR_OK) {
+        /* the distinct closed triangles */
+        int64_t nt = 0;
+        for (int64_t s = 0; s < nsamples; s++)
+            if (st[3 * s] >= 0) {
+                st[3 * nt] = st[3 * s];
+                st[3 * nt + 1] = st[3 * s + 1];
+                st[3 * nt + 2] = st[3 * s + 2];
+                nt++;
+            }
+        qsort(st, (size_t)nt, 3 * sizeof(int32_t), cmp_triple);
+        int64_t nu = 0;
+        for (int64_t i = 0; i < nt; i++)
+            if (nu == 0 || cmp_triple(st + 3 * i, st + 3 * (nu - 1)) != 0) {
+                memmove(st + 3 * nu, st + 3 * i, 3 * sizeof(int32_t));
+                nu++;
+            }
+        or_tri* all = (or_tri*)malloc(sizeof(or_tri) * (size_t)(nu + 1));
+        if (!all) {
+            rc = OR_ENOMEM;
+        } else {
+            for (int64_t i = 0; i < nu; i++) {
+                int32_t ws[3];
+                const int32_t a = st[3 * i], b = st[3 * i + 1], c = st[3 * i + 2];
+                const int32_t pr[3][2] = {{a, b}, {b, c}, {a, c}};
+                for (int e = 0; e < 3; e++) {
+                    const int32_t x = pr[e][0], y = pr[e][1];
+                    int64_t l2 = rowp[x], h2 = rowp[x + 1];
+                    while (l2 < h2) {
+                        const int64_t mid = l2 + (h2 - l2) / 2;
+                        if (col[mid] < y) l2 = mid + 1;
+                        else h2 = mid;
+                    }
+                    ws[e] = wt[l2];
+                }
+                all[i].key = tri_key(pcode, 0.0, ws[0], ws[1], ws[2]);
+                all[i].t[0] = a;
+                all[i].t[1] = b;
+                all[i].t[2] = c;
+            }
+            qsort(all, (size_t)nu, sizeof(or_tri), cmp_tri);
+            const int64_t out = nu < k ? nu : k;
+            for (int64_t i = 0; i < out; i++) {
+                tri[3 * i] = all[i].t[0];
+                tri[3 * i + 1] = all[i].t[1];
+                tri[3 * i + 2] = all[i].t[2];
+                key[i] = all[i].key;
+                value[i] = tri_value(pcode, all[i].key);
+            }
+            *count = out;
+            *ntri = nu;
+            free(all);
+        }
+    }
+    free(ctr); free(st); free(rowp); free(col); free(wt); free(eid);
     return rc;
 }

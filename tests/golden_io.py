@@ -8,14 +8,17 @@ import os
 import numpy as np
 
 GOLDEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-P_OF = {"1": 1.0, "2": 2.0, "inf": math.inf, "-inf": -math.inf}
+P_OF = {"1": 1.0, "2": 2.0, "inf": math.inf, "-inf": -math.inf, "-1": -1.0, "3": 3.0}
 
 
 def closed_form(expr: str) -> float:
-    """Evaluates the closed forms used in the fixtures: "a/b", "sqrt(a/b)", "a"."""
+    """Evaluates the closed forms used in the fixtures: "a/b", "sqrt(a/b)",
+    "cbrt(a/b)", "a"."""
     expr = expr.strip()
     if expr.startswith("sqrt(") and expr.endswith(")"):
         return math.sqrt(closed_form(expr[5:-1]))
+    if expr.startswith("cbrt(") and expr.endswith(")"):
+        return closed_form(expr[5:-1]) ** (1.0 / 3.0)
     if "/" in expr:
         a, b = expr.split("/")
         return float(int(a)) / float(int(b))

@@ -38,6 +38,8 @@ def test_alpha_closed_form():
 @pytest.mark.parametrize("fx", load_all(), ids=lambda d: d["name"])
 def test_dhl_golden(fx):
     for pname, rows in fx["expected"].items():
+        if rows and rows[0][3] is None:
+            continue  # fp64-keyed p: the CPU DHL takes the five exact-key p only
         for a in ALPHAS:
             r = oracle.dhl_topk(fx["n"], fx["u"], fx["v"], fx["w"], P_OF[pname], fx["k"], alpha=a)
             assert r["count"] == len(rows)

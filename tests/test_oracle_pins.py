@@ -109,9 +109,10 @@ def test_golden_hand_enumerated(fx):
         assert r["count"] == len(rows)
         for i, row in enumerate(rows):
             assert tuple(int(x) for x in r["tri"][i]) == tuple(row[:3])
-            assert int(r["key"][i]) == row[3]
+            if row[3] is not None:  # exact integer key (p in {-inf, 0, 1, 2, +inf})
+                assert int(r["key"][i]) == row[3]
             want = closed_form(row[4])
-            assert abs(r["value"][i] - want) <= 1e-15 * max(1.0, abs(want))
+            assert abs(r["value"][i] - want) <= 4e-16 * max(1.0, abs(want))
 
 
 def test_score_closed_forms():
@@ -132,6 +133,38 @@ def test_score_closed_forms():
     assert abs(val - W) <= 1e-12 * W
     k, val = oracle.score(1.0, W, W, W)
     assert k == 3 * W and val == float(W)
+
+
+def test_score_general_p_closed_forms():
+    """Any other finite p ranks by the fp64 p-mean of Eq. 1; values against
+    closed forms worked here with exact fractions."""
+    from fractions import Fraction as F
+
+    def harmonic(a, b, c):
+        return 3 / (F(1, a) + F(1, b) + F(1, c))
+    for a, b, c in [(1, 2, 4), (2, 3, 6), (4, 5, 6), (1, 1, 1), (7, 1000000, 3)]:
+        want = float(harmonic(a, b, c))
+        for perm in itertools.permutations((a, b, c)):
+            k, val = oracle.score(-1.0, *perm)
+            assert abs(val - want) <= 4e-16 * want, (a, b, c, perm)
+            assert k == oracle.score(-1.0, a, b, c)[0]  # equal multisets: equal keys
+    # p = -2: ((1 + 1 + 1/4) / 3)^(-1/2) = (3/4)^(-1/2) = 2/sqrt(3)
+    assert abs(oracle.score(-2.0, 1, 1, 2)[1] - 2 / math.sqrt(3)) <= 4e-16 * 2
+    # p = 3: ((1 + 8 + 64) / 3)^(1/3); p = 1/2: ((1 + 2 + 3) / 3)^2 = 4
+    assert abs(oracle.score(3.0, 1, 2, 4)[1] - (73 / 3) ** (1 / 3)) <= 1e-15 * 3
+    assert abs(oracle.score(0.5, 1, 4, 9)[1] - 4.0) <= 1e-15 * 4
+    # equal weights: every mean is that weight exactly
+    for p in (-7.5, -1.0, 0.25, 3.0, 40.0):
+        assert oracle.score(p, 9, 9, 9)[1] == 9.0
+    # the limits p -> +-inf: max and min (Section 1)
+    assert abs(oracle.score(400.0, 3, 5, 11)[1] - 11.0) <= 11.0 * 3e-3
+    assert abs(oracle.score(-400.0, 3, 5, 11)[1] - 3.0) <= 3.0 * 3e-3
+    # weights near 2^31 and large |p|: no overflow (the largest or smallest
+    # weight is factored out)
+    W = 2**31 - 1
+    for p in (-60.0, 60.0):
+        val = oracle.score(p, W, W - 1, 5)[1]
+        assert math.isfinite(val) and 5 <= val <= W
 
 
 def _python_bruteforce(n, u, v, w, p):
@@ -171,6 +204,59 @@ def test_python_bruteforce_random_small(seed):
         assert r["ntri"] == len(want)
         got = [(int(key), tuple(int(x) for x in t)) for key, t in zip(r["key"], r["tri"])]
         assert got == want[: r["count"]]
+
+
+def _exact_mean(p, ws):
+    """m_p with exact rationals where p is an integer (p = -1, -2, 3 are
+    rational; the cube root of p = 3 is taken on the float of the exact
+    power mean)."""
+    from fractions import Fraction as F
+    if p == -1.0:
+        return 3 / sum(F(1, x) for x in ws)
+    if p == 3.0:
+        return float(sum(F(x) ** 3 for x in ws) / 3) ** (1.0 / 3.0)
+    raise ValueError(p)
+
+
+@pytest.mark.parametrize("seed", range(24))
+@pytest.mark.parametrize("p", [-1.0, 3.0])
+def test_python_bruteforce_general_p(seed, p):
+    """Any other finite p: the oracle's top-k against a Python itertools brute
+    force over vertex triples with exact rational harmonic means (p = -1) or
+    exact power sums (p = 3), under the fp64-key comparison rule."""
+    from wtri_testutil import assert_topk_close
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(3, 30))
+    g = synth.random_small_graph(n, float(rng.uniform(0.2, 0.9)), int(rng.integers(2, 9)), seed)
+    if g.m == 0:
+        return
+    adj = {}
+    for a, b, x in zip(g.u.tolist(), g.v.tolist(), g.w.tolist()):
+        adj[(min(a, b), max(a, b))] = x
+    tris = []
+    for a, b, c in itertools.combinations(range(g.n), 3):
+        if (a, b) in adj and (b, c) in adj and (a, c) in adj:
+            tris.append((_exact_mean(p, [adj[(a, b)], adj[(b, c)], adj[(a, c)]]), (a, b, c)))
+    tris.sort(key=lambda t: (-t[0], t[1]))
+    k = max(1, min(len(tris), int(rng.integers(1, 40))))
+    r = oracle.topk(g.n, g.u, g.v, g.w, p, k)
+    assert r["ntri"] == len(tris)
+    want = tris[:k]
+    assert_topk_close(r["tri"], r["value"], np.array([t for _, t in want], np.int32).reshape(-1, 3),
+                      np.array([float(v) for v, _ in want]), f"seed={seed} p={p}")
+
+
+@pytest.mark.parametrize("n", [5, 13, 40])
+@pytest.mark.parametrize("p", [-1.0, -2.0, 0.5, 3.0])
+def test_complete_graph_general_p_top1(n, p):
+    """K_n with w(u, v) = u + v: the mean is increasing in each weight, so the
+    heaviest triangle {n-3, n-2, n-1} is first for every p."""
+    u, v, w = complete_graph(n, lambda a, b: a + b)
+    r = oracle.topk(n, u, v, w, p, 3)
+    assert tuple(int(x) for x in r["tri"][0]) == (n - 3, n - 2, n - 1)
+    ws = [2 * n - 5, 2 * n - 4, 2 * n - 3]
+    want = (sum(x ** p for x in ws) / 3) ** (1 / p)
+    assert abs(r["value"][0] - want) <= 1e-13 * want
 
 
 def test_invariants_tiny():

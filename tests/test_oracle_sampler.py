@@ -31,7 +31,7 @@ def test_philox_matches_numpy(s, seed):
     assert np.array_equal(mine, numpy_philox_block(s, seed))
 
 
-@pytest.mark.parametrize("p", [1.0, 2.0])
+@pytest.mark.parametrize("p", [1.0, 2.0, 0.0])
 def test_edge_draws_follow_w_to_the_p(p):
     stats = pytest.importorskip("scipy.stats")
     w = np.array([1, 2, 3, 5, 8, 13, 21, 1, 1, 4, 30, 7], np.int32)

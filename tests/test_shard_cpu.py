@@ -31,6 +31,18 @@ def test_shards_partition_the_triangles():
         assert total == oracle.count_triangles(g.n, g.u, g.v)
 
 
+def test_shard_rule_hand_built():
+    """The ownership rule itself, on a graph whose per-shard triangles are
+    written out by hand (tests/shard_pin.py)."""
+    import shard_pin
+    n, u, v, w = shard_pin.graph()
+    for nsh, want in shard_pin.EXPECTED.items():
+        for sh in range(nsh):
+            r = oracle.topk_shard(n, u, v, w, 1.0, 100, sh, nsh)
+            got = sorted(tuple(int(x) for x in t) for t in r["tri"])
+            assert got == sorted(want[sh]), (nsh, sh, got)
+
+
 def test_host_merge():
     wt = pytest.importorskip("paper_1910_00692_gb300")
     from paper_1910_00692_gb300 import build_lib
