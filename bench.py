@@ -1,14 +1,20 @@
 #!/usr/bin/env python3
 """Benchmark: exact top-k weighted triangles.
 
-Default workload (mid): Chung-Lu n=1e6, m=2e7, exponent 2.1, d_max 5e4,
-Zipf(2) int32 weights capped at 1e6 (seed 1).  One step = one pass of the
-whole path on one graph: wtri_build_csr from device-resident COO
-(validation, degrees, edge order, weight-sorted / id-sorted / oriented
-lists) followed by the exact top-1000 query at p = -inf, 1, 2 and +inf.
---workload large: Chung-Lu n=5e7, m=1e9, exponent 2.0 drawn on the device,
-one step = build + the exact top-1000 query at p = 1, plus 1e7 weighted edge
-draws (Philox seed 7) reported with their recall.
+Default workload (large): Chung-Lu n=5e7, m=1e9, exponent 2.0, d_max 5e4,
+Zipf(2) int32 weights capped at 1e6, drawn on the device (seed 2).  One step
+= one pass of the path on that graph: wtri_build_csr from device-resident
+COO (validation, edge order, weight-sorted / id-sorted / oriented lists)
+followed by the exact top-1000 query at p = 1.  Reported beside the step on
+the same graph: the exact query at p = -inf, 1, 2, +inf (CUDA events, and
+the adjacency bytes each one reads, from an instrumented run), 1e7 weighted
+edge draws (Philox seed 7) with their recall of the exact top-1000, the
+end-to-end step through host buffers, and the oracle on a uniform edge
+sample.  The value is edges of the graph pushed through a step per second
+(whole job: all ranks' edges over the max-over-ranks time).
+--workload mid: Chung-Lu n=1e6, m=2e7, exponent 2.1 (seed 1); a step is the
+build plus the exact top-1000 at all four p; extras: a reduced batch and
+reduced serving run.
 --workload batch: 4,096 Chung-Lu graphs (n log-uniform in [100, 2e5], m = 10 n,
 exponent 2.2) drawn on the device, each with its own k and p; the value is
 queries per second of one wtri_topk_batch call over all of them, reported
@@ -16,15 +22,14 @@ beside the same queries as back-to-back wtri_topk calls.
 --workload serve: the 1e9-edge graph and two 2e8-edge graphs resident (drawn
 on the device), 100,000 Poisson requests at 2,000 req/s through the server;
 the value is served queries per second, with p50/p99 latency beside a
-sequential wtri_topk loop fed the same arrivals.  The value is edges of the
-graph pushed through a step per second (whole job: all ranks' edges over
-the max-over-ranks time).
+sequential wtri_topk loop fed the same arrivals.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wtri|reference]
-                  [--workload mid|large|quarter|tiny|batch|serve]
+                  [--workload large|mid|quarter|tiny|batch|serve]
 
---impl reference times the CPU oracle (brute force, all host cores) on a
-bounded sample of the same workload.
+--impl reference times the CPU oracle (brute force, all host cores): each
+step is one brute-force top-k query at p = 1 on a bounded uniform sample of
+the workload's edges, timed as run.
 """
 from __future__ import annotations
 
@@ -62,12 +67,13 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wtri", choices=["wtri", "reference"])
     ap.add_argument("--k", type=int, default=1000)
-    ap.add_argument("--workload", default="mid", choices=["mid", "large", "quarter", "tiny", "batch", "serve"],
-                    help="mid: the bench workload; large: n=5e7 m=1e9 (device-generated); "
+    ap.add_argument("--workload", default="large",
+                    choices=["mid", "large", "quarter", "tiny", "batch", "serve"],
+                    help="large: n=5e7 m=1e9 (device-generated, the default); mid: n=1e6 m=2e7; "
                          "quarter: n=1e6 m=5e6 (profiling captures); tiny: n=2000 m=20000; "
                          "batch: the 4,096-graph batch (batched vs plain queries); "
                          "serve: the full serving pool and request stream")
@@ -133,13 +139,15 @@ def measured_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def ncu_traffic():
-    """DRAM bytes per radix-scatter launch at the bench size, from the committed
-    ncu capture, if the kernel sources are unchanged since it was taken."""
+def ncu_traffic(phase, workload, profiles_dir=None):
+    """DRAM bytes per launch of the phase's kernel at the bench size, from the
+    committed ncu capture, if that capture covers this phase and workload
+    and the kernel sources are unchanged since it was taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "radix_scatter_traffic_quarter.txt")
+    path = os.path.join(profiles_dir or os.path.join(ROOT, "profiles"),
+                        f"{phase}_traffic_{workload}.txt")
     if not os.path.exists(path):
-        return None, "no capture"
+        return None, f"no capture for {phase} on the {workload} workload"
     fields = {}
     for line in open(path):
         if ":" in line:
@@ -154,7 +162,7 @@ def ncu_traffic():
         h.update(open(fp, "rb").read())
     if not srcs or h.hexdigest() != fields.get("source_sha256"):
         return None, "kernel changed since the capture"
-    return float(fields["dram_bytes_per_launch_mid"]), "ncu capture of the quarter workload scaled x4"
+    return float(fields["dram_bytes_per_launch"]), fields.get("how", "ncu capture")
 
 
 class ClockSampler:
@@ -213,18 +221,6 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
-
-
-def prof_snapshot(L):
-    import ctypes
-    out = {}
-    i = 0
-    name = ctypes.create_string_buffer(128)
-    calls, ms, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
-    while L.wtri_prof_read(i, name, 128, ctypes.byref(calls), ctypes.byref(ms), ctypes.byref(by)) == 0:
-        out[name.value.decode()] = {"calls": calls.value, "ms": ms.value, "bytes": by.value}
-        i += 1
-    return out
 
 
 def bench_sampler(wt, g, stream, k):
@@ -508,19 +504,35 @@ def run_serve_workload(args, world, rank, count=100_000, seq_count=20_000):
 
 def host_arrays(g, limit=None):
     """(u, v, w) as numpy arrays on the host; at most `limit` edges (the
-    large workload's edge list is shuffled, so a prefix is a uniform
-    sample)."""
+    workloads' edge lists are shuffled, so a prefix is a uniform sample)."""
     if isinstance(g.u, np.ndarray):
         return (g.u, g.v, g.w) if limit is None else (g.u[:limit], g.v[:limit], g.w[:limit])
     sl = slice(0, limit if limit is not None else g.m)
     return tuple(x[sl].cpu().numpy() for x in (g.u, g.v, g.w))
 
 
-LARGE_CPU_SAMPLE = 20_000_000
+# The oracle's bounded sample: at most this many edges of the workload (a
+# prefix of the shuffled edge list, i.e. a uniform sample), a few seconds of
+# brute force on the host cores per query.
+CPU_SAMPLE_EDGES = 20_000_000
+
+
+def oracle_sample(g, k):
+    """(u, v, w, description) of the oracle's bounded sample of g."""
+    limit = CPU_SAMPLE_EDGES if g.m > CPU_SAMPLE_EDGES else None
+    hu, hv, hw = host_arrays(g, limit)
+    if limit is None:
+        desc = f"the whole graph ({g.m} edges)"
+    else:
+        desc = (f"a uniform sample of {hu.shape[0]} of the {g.m} edges (a prefix of the shuffled "
+                "edge list)")
+    return hu, hv, hw, desc
 
 
 def run_reference(args, world, rank):
-    """The oracle as it stands, on the host cores, bounded sample."""
+    """The oracle as it stands, on the host cores: each step is one
+    brute-force top-k query at p = 1 on the bounded sample, oracle CSR build
+    included, timed as run (ms_per_step is the mean of exactly those runs)."""
     if rank != 0:
         return
     import oracle
@@ -530,32 +542,28 @@ def run_reference(args, world, rank):
             print(json.dumps({"impl": "reference", "unavailable": "the large workload is drawn on the GPU"}))
             return
     g, wl = workload(args.workload, args.large_size)
-    large = args.workload == "large"
-    hu, hv, hw = host_arrays(g, LARGE_CPU_SAMPLE if large else None)
-    ps = [1.0] if large else PS
+    n = g.n
+    hu, hv, hw, desc = oracle_sample(g, args.k)
+    del g
     times = []
     nthreads = os.cpu_count() or 1
     for step in range(args.warmup + args.steps):
-        p = ps[step % len(ps)]
         t0 = time.perf_counter()
-        oracle.topk(g.n, hu, hv, hw, p, args.k)
+        oracle.topk(n, hu, hv, hw, 1.0, args.k)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
-    # one query of the step's len(ps) per timed iteration
-    step_s = len(ps) * statistics.mean(times)
+    step_s = statistics.mean(times)
     value = hu.shape[0] / step_s
-    sample = ("one brute-force query per step (p cycling -inf,1,2,+inf) on the full graph, oracle "
-              "CSR build included; step time = 4 x mean") if not large else (
-              f"one brute-force p=1 top-{args.k} query per step on a uniform sample of "
-              f"{hu.shape[0]} of the {g.m} edges (a prefix of the shuffled edge list), oracle "
-              "CSR build included; value = sampled edges / time")
+    sample = (f"one brute-force top-{args.k} query at p = 1 per step on {desc}, oracle CSR build "
+              "included; value = sampled edges / step time")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": wl, "global_batch": 1, "k": args.k, "step": STEP_DEF},
+        "config": {"workload": wl, "global_batch": 1, "k": args.k,
+                   "step": "oracle: brute-force exact top-k at p = 1 on the bounded sample"},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": nthreads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -563,22 +571,62 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    args = parse()
-    world, rank, local = dist_env()
-    if args.impl == "reference":
-        if world > 1:
-            import torch.distributed as dist
-            dist.init_process_group("gloo")
-        run_reference(args, world, rank)
-        return
+def prof_table(L):
+    """Phase name -> {calls, ms, bytes (algorithmic), moved}."""
+    import ctypes
+    out = {}
+    i = 0
+    name = ctypes.create_string_buffer(128)
+    calls, ms, by, mv = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    while L.wtri_prof_read_ex(i, name, 128, ctypes.byref(calls), ctypes.byref(ms), ctypes.byref(by),
+                              ctypes.byref(mv)) == 0:
+        out[name.value.decode()] = {"calls": calls.value, "ms": ms.value, "bytes": by.value,
+                                    "moved": mv.value}
+        i += 1
+    return out
 
-    if args.workload == "batch":
-        run_batch_workload(args, world, rank)
-        return
-    if args.workload == "serve":
-        run_serve_workload(args, world, rank)
-        return
+
+# Kernel families the phase timers name, by the kernels they launch.
+KERNEL_OF = {"radix_downsweep": "radix::k_scatter", "radix_upsweep": "radix::k_upsweep",
+             "radix_digit_scan": "radix::k_digit_scan",
+             "rows_sort": "rows::k_rows_small/k_rows_warp/k_rows_block (per-row sort by id)"}
+
+
+def query_extras(wt, L, d, k, stream, reps=5):
+    """Each p on the built graph: median query time (CUDA events on the
+    stream, device outputs) and the adjacency bytes the query reads (one
+    instrumented run, counted on the device)."""
+    import ctypes
+    import torch
+    out_t = torch.zeros((k, 3), dtype=torch.int32, device=stream.device)
+    out_w = torch.zeros(k, dtype=torch.float64, device=stream.device)
+    out_c = torch.zeros(1, dtype=torch.int32, device=stream.device)
+    res = {}
+    peak = measured_peak()[0]
+    for p in PS:
+        wt.topk_device(d, p, k, out_t, out_w, out_c, stream=stream)
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wt.topk_device(d, p, k, out_t, out_w, out_c, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        b = ctypes.c_ulonglong()
+        L.wtri_query_bytes(1, 1, None)
+        wt.topk_device(d, p, k, out_t, out_w, out_c, stream=stream)
+        L.wtri_query_bytes(0, 1, ctypes.byref(b))
+        ms = statistics.median(ts)
+        res[P_NAMES[p]] = {"ms": ms, "count": int(out_c.item()), "adjacency_bytes": int(b.value),
+                           "achieved_gbs": b.value / 1e9 / (ms / 1e3),
+                           "frac": b.value / 1e9 / (ms / 1e3) / peak}
+    return res
+
+
+def run_step_workload(args, world, rank, local):
+    import ctypes
 
     import torch
     torch.cuda.set_device(local)
@@ -589,22 +637,21 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         pg = dist
 
-    import ctypes
-
     import paper_1910_00692_gb300 as wt
     L = wt.lib()
     L.wtri_prof_enable.argtypes = [ctypes.c_int]
     L.wtri_prof_enable.restype = None
     L.wtri_prof_reset.restype = None
     L.wtri_launch_count.restype = ctypes.c_longlong
-    L.wtri_prof_read.argtypes = [ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
-                                 ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
-                                 ctypes.POINTER(ctypes.c_double)]
+    L.wtri_prof_read_ex.argtypes = [ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.wtri_query_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)]
 
     g, wl = workload(args.workload, args.large_size)
     large = args.workload == "large"
     ps_step = [1.0] if large else PS
-    m = g.m
+    m, n = g.m, g.n
     k = args.k
     stream = torch.cuda.Stream(device=dev)
     if isinstance(g.u, np.ndarray):
@@ -626,13 +673,13 @@ def main():
         f, gr, ts = (int(x) for x in args.tune.split(","))
         tune = {"first_round": f, "growth": gr, "t_short": ts, "source": "--tune"}
     elif not args.no_tune:
-        d0 = wt.build_csr(g.n, du, dv, dw, stream=stream)
+        d0 = wt.build_csr(n, du, dv, dw, stream=stream)
         tune = d0.autotune(k=k, reps=3)
         d0.free()
 
     def step():
         with torch.cuda.stream(stream):
-            d = wt.build_csr(g.n, du, dv, dw, stream=stream)
+            d = wt.build_csr(n, du, dv, dw, stream=stream)
             if tune:
                 d.set_tune(tune["first_round"], tune["growth"], tune["t_short"])
             for i, p in enumerate(ps_step):
@@ -668,38 +715,65 @@ def main():
     launches = L.wtri_launch_count() - launches0
     clocks = sampler.stop()
     L.wtri_prof_enable(0)
-    prof = prof_snapshot(L)
+    prof = prof_table(L)
     ms = e0.elapsed_time(e1) / args.steps
     if pg:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
     value = world * m / (ms / 1e3)
-
-    # ---- roofline of the dominant kernel -----------------------------------
     peak, peak_kind = measured_peak()
-    kernels = {n_: v for n_, v in prof.items() if not n_.startswith("query_")}
+
+    # ---- per-query figures on one built graph (outside the timed steps) ----
+    d = wt.build_csr(n, du, dv, dw, stream=stream)
+    if tune:
+        d.set_tune(tune["first_round"], tune["growth"], tune["t_short"])
+    info = d.info()
+    queries = query_extras(wt, L, d, k, stream)
+    d.free()
+    torch.cuda.synchronize()
+
+    # ---- roofline of the dominant kernel (algorithmic bytes) ---------------
+    # leaf phases and whole kernel families; the per-class timers inside the
+    # per-row sort (rows_sort_*) are detail of the rows_sort family
+    kernels = {n_: v for n_, v in prof.items()
+               if not n_.startswith("query_") and not n_.startswith("rows_sort_")}
     dom = max(kernels.items(), key=lambda kv: kv[1]["ms"]) if kernels else None
     roofline = None
     if dom:
         name, d0 = dom
-        per_launch_ms = d0["ms"] / max(1, d0["calls"])
-        per_launch_bytes = d0["bytes"] / max(1, d0["calls"])
+        calls = max(1, d0["calls"])
+        per_launch_ms = d0["ms"] / calls
+        per_launch_bytes = d0["bytes"] / calls
         achieved = (per_launch_bytes / 1e9) / (per_launch_ms / 1e3) if per_launch_ms > 0 else 0.0
-        traffic, traffic_src = (ncu_traffic() if name == "radix_downsweep" and args.workload == "mid"
-                                else (None, "no capture for this kernel/workload"))
-        roofline = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
-                    "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": traffic, "traffic_source": traffic_src,
-                    "launch_ms": per_launch_ms, "algorithmic_bytes": per_launch_bytes}
+        traffic, traffic_src = ncu_traffic(name, args.workload)
+        roofline = {"kernel": KERNEL_OF.get(name, name), "phase": name, "bound": "hbm",
+                    "achieved": achieved, "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+                    "launch_ms": per_launch_ms, "launches_per_step": calls / args.steps,
+                    "algorithmic_bytes": per_launch_bytes,
+                    "pass_bytes": d0["moved"] / calls,
+                    "traffic_over_algorithmic": (traffic / per_launch_bytes) if traffic else None,
+                    "bytes_rule": ("one read + one write of each sort's payload (edge order 16 B/edge, "
+                                   "weight-sorted rows 48 B/edge) plus the resident outputs the passes "
+                                   "write, spread evenly over the launches; pass_bytes = what one pass "
+                                   "moves by design")}
     step_ms_parts = {n_: v["ms"] / args.steps for n_, v in prof.items()}
-    query_ms = {P_NAMES[p]: step_ms_parts.get(f"query_p={P_NAMES[p]}", None) for p in ps_step}
-    # whole-step HBM figure: algorithmic bytes of every phase over the step time
-    step_bytes = sum(v["bytes"] for v in prof.values()) / args.steps
-    step_hbm = {"algorithmic_bytes_per_step": step_bytes,
+    # whole step: every phase's algorithmic bytes (query: the counted
+    # adjacency bytes of the instrumented run of the step's queries)
+    build_bytes = sum(v["bytes"] for n_, v in kernels.items()) / args.steps
+    build_moved = sum(v["moved"] for n_, v in kernels.items()) / args.steps
+    q_bytes = sum(queries[P_NAMES[p]]["adjacency_bytes"] for p in ps_step)
+    step_bytes = build_bytes + q_bytes
+    step_hbm = {"algorithmic_bytes_per_step": step_bytes, "build_bytes": build_bytes,
+                "query_bytes": q_bytes, "moved_bytes_per_step": build_moved + q_bytes,
                 "achieved_gbs": step_bytes / 1e9 / (ms / 1e3),
-                "frac": step_bytes / 1e9 / (ms / 1e3) / measured_peak()[0],
-                "note": "query phases count no bytes (their reads are data dependent)"}
+                "frac": step_bytes / 1e9 / (ms / 1e3) / peak,
+                "bytes_per_edge": step_bytes / m,
+                "rule": ("COO read 12 B/edge; symmetric id-sorted CSR 16 B/edge and oriented CSR "
+                         "12 B/edge written once; row offsets 8 B/vertex each; edge order sort "
+                         "8+8 B/edge and weight-sorted rows 24+24 B/edge (one read + one write); "
+                         "query: adjacency bytes counted by the instrumented run")}
 
     # ---- end to end through the C ABI with host buffers --------------------
     e2e = None
@@ -711,7 +785,7 @@ def main():
 
         def e2e_step():
             nonlocal d2h
-            d = wt.build_csr(g.n, hub, hvb, hwb, stream=stream)
+            d = wt.build_csr(n, hub, hvb, hwb, stream=stream)
             if tune:
                 d.set_tune(tune["first_round"], tune["growth"], tune["t_short"])
             for p in ps_step:
@@ -734,13 +808,12 @@ def main():
             t_e2e = float(t.item())
         e2e = {"value": world * m / t_e2e, "unit": "edges/s", "h2d_bytes_per_step": 12 * m,
                "d2h_bytes_per_step": d2h // e2e_steps, "ms_per_step": t_e2e * 1e3}
+        del hu, hv, hw, hub, hvb, hwb
 
-    # ---- weighted edge sampling (Algorithm 3) on the same graph --------------
-    sampler = None
-    batch = None
-    serve = None
+    # ---- weighted edge sampling (Algorithm 3) and the mid extras -----------
+    samp = batch = serve = None
     if rank == 0 and not args.no_extras and args.workload in ("mid", "large"):
-        sampler = bench_sampler(wt, g, stream, k)
+        samp = bench_sampler(wt, g, stream, k)
         if not large:
             batch = bench_batch(wt, stream)
             serve = bench_serve(wt, g)
@@ -749,30 +822,24 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
-        cu, cv, cw = host_arrays(g, LARGE_CPU_SAMPLE if large else None)
+        cu, cv, cw, desc = oracle_sample(g, k)
         t0 = time.perf_counter()
-        oracle.topk(g.n, cu, cv, cw, 1.0, k)
+        oracle.topk(n, cu, cv, cw, 1.0, k)
         t_q = time.perf_counter() - t0
         # the paper's own algorithm (Algorithm 2, alpha_p for beta = 2), one
         # thread, on the same edges: the prior-art CPU line
         t0 = time.perf_counter()
-        dr = oracle.dhl_topk(g.n, cu, cv, cw, 1.0, k)
+        dr = oracle.dhl_topk(n, cu, cv, cw, 1.0, k)
         t_dhl = time.perf_counter() - t0
         dhl = {"value": cu.shape[0] / t_dhl, "unit": "edges/s", "cores": 1, "s": t_dhl,
                "algorithm": "dynamic heavy-light (Algorithm 2), alpha_p = 1.5, one thread, "
                             "edge sort and adjacency build included",
                "listed": dr["stats"]["listed"], "light_to_heavy": dr["stats"]["light_to_heavy"]}
-        if large:
-            cpu = {"value": cu.shape[0] / t_q, "unit": "edges/s", "cores": os.cpu_count(),
-                   "kind": "oracle",
-                   "sample": f"one brute-force top-{k} query (p=1) on a uniform sample of {cu.shape[0]} "
-                             f"of the {m} edges, oracle CSR build included, {t_q:.2f} s; "
-                             "value = sampled edges / time"}
-        else:
-            cpu = {"value": m / (4 * t_q), "unit": "edges/s", "cores": os.cpu_count(), "kind": "oracle",
-                   "sample": "one brute-force top-1000 query (p=1) on the full graph including the "
-                             f"oracle's own CSR build, {t_q:.2f} s; a step is four such queries"}
-        cpu["dhl"] = dhl
+        cpu = {"value": cu.shape[0] / t_q, "unit": "edges/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": (f"one brute-force top-{k} query at p = 1 on {desc}, oracle CSR build "
+                          f"included, {t_q:.2f} s; value = sampled edges / that time"),
+               "dhl": dhl}
 
     if rank == 0:
         line = {
@@ -781,19 +848,39 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic",
             "config": {"workload": wl, "global_batch": world, "k": k,
-                       "step": STEP_DEF,
+                       "step": STEP_DEF if not large else
+                       "wtri_build_csr from device COO + exact top-1000 at p = 1",
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": (f"inputs larger than L2: COO {12 * m / 1e9:.2f} GB, resident graph "
-                              f"{84 * m / 1e9:.1f} GB per step")},
-            "query_ms": query_ms, "phase_ms_per_step": step_ms_parts, "step_hbm": step_hbm,
-            "tune": tune,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "sampler": sampler, "batch": batch, "serve": serve,
+                              f"{info['device_bytes'] / 1e9:.1f} GB per step")},
+            "graph": info,
+            "query_ms": {k_: v["ms"] for k_, v in queries.items()}, "queries": queries,
+            "phase_ms_per_step": step_ms_parts, "step_hbm": step_hbm,
+            "tune": tune, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "sampler": samp, "batch": batch, "serve": serve,
             "gpu_launches": int(launches), "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, world, rank)
+        return
+    if args.workload == "batch":
+        run_batch_workload(args, world, rank)
+        return
+    if args.workload == "serve":
+        run_serve_workload(args, world, rank)
+        return
+    run_step_workload(args, world, rank, local)
 
 
 if __name__ == "__main__":

@@ -12,17 +12,27 @@
  * generalized p-mean of its three edge weights (Eq. 1):
  *     m_p = ((w_ab^p + w_bc^p + w_ac^p) / 3)^(1/p),
  * with p = +inf the max, p = -inf the min and p = 0 the geometric mean
- * (abc)^(1/3), the limit of Eq. 1 as p -> 0.  This library supports
- * p in {-inf, 0, 1, 2, +inf}; any other p returns WTRI_EUNSUPPORTED, and so
- * does p = 0 on a graph with a weight of 2^21 or more (its exact product key
- * would not fit 63 bits).
+ * (abc)^(1/3), the limit of Eq. 1 as p -> 0.  p = 0 is refused
+ * (WTRI_EUNSUPPORTED) on a graph with a weight of 2^21 or more (its exact
+ * product key would not fit 63 bits).
  *
  * Results are ranked by a total order: weight descending, then the sorted
  * vertex triple (a < b < c) ascending.  The paper notes that ties may make
  * several answers valid (Section 3.2); the triple order makes the answer
- * unique.  Ranking uses exact integer keys (a+b+c for p=1, a^2+b^2+c^2 for
- * p=2, a*b*c for p=0, max, min), never the floating value; the reported fp64
- * weight is (a+b+c)/3.0, sqrt((a^2+b^2+c^2)/3.0), cbrt(a*b*c), max or min.
+ * unique.  For p in {-inf, 0, 1, 2, +inf} ranking uses exact integer keys
+ * (a+b+c for p=1, a^2+b^2+c^2 for p=2, a*b*c for p=0, max, min), never the
+ * floating value; the reported fp64 weight is (a+b+c)/3.0,
+ * sqrt((a^2+b^2+c^2)/3.0), cbrt(a*b*c), max or min.
+ *
+ * Any other finite p (the harmonic mean p = -1, p = -2, p = 0.5, p = 3, ...)
+ * has no exact 64-bit integer key.  wtri_topk, wtri_topk_device,
+ * wtri_topk_device_noalloc and wtri_topk_shard then rank by the fp64 mean
+ * itself, computed from Eq. 1 with the weights in ascending order and the
+ * largest (p > 0) or smallest (p < 0) factored out so that no power
+ * overflows: m_p = s * (((a/s)^p + (b/s)^p + (c/s)^p)/3)^(1/p).  Means that
+ * differ by less than fp64 rounding may rank either way; the set returned
+ * is exact except for triangles within that rounding of the k-th mean.  The
+ * batched and serving calls and the samplers take only the five exact p.
  *
  * A graph with fewer than k triangles returns all of them: count < k
  * (Section 3.2, "provided the graph has at least k triangles").
@@ -117,8 +127,10 @@ WTRI_API int wtri_graph_info(const wtri_graph* g, int32_t* n, int64_t* m, int32_
  * Algorithm 2 solves.  Runs on the graph's stream, then copies the k results
  * to the caller's host arrays and returns when they are there.
  *
- * p   -INFINITY, 0.0, 1.0, 2.0 or +INFINITY; NaN -> WTRI_EINVAL; others ->
- *     WTRI_EUNSUPPORTED, as is 0.0 on a graph with a weight of 2^21 or more.
+ * p   any non-NaN value (NaN -> WTRI_EINVAL): -INFINITY, 0.0, 1.0, 2.0 and
+ *     +INFINITY rank by exact keys, any other finite p by the fp64 mean
+ *     (see above); 0.0 on a graph with a weight of 2^21 or more ->
+ *     WTRI_EUNSUPPORTED.
  * k   1 <= k <= out->capacity and k <= 65536 (WTRI_EUNSUPPORTED above).
  */
 WTRI_API int wtri_topk(const wtri_graph* g, double p, int32_t k, wtri_result* out);
@@ -167,8 +179,9 @@ WTRI_API int wtri_topk_device_noalloc(const wtri_graph* g, double p, int32_t k, 
  * Every triangle belongs to its first edge in the edge order; the edges are
  * dealt to nshards shards in chunks of 1024 consecutive positions,
  * round-robin.  Returns the exact top-k of the triangles whose first edge
- * belongs to `shard` (results as wtri_topk) and their integer ranking keys
- * (a+b+c, a^2+b^2+c^2, max, min or a*b*c) in keys[0..count).  The union of all
+ * belongs to `shard` (results as wtri_topk) and their ranking keys
+ * (a+b+c, a^2+b^2+c^2, max, min or a*b*c; for other p the fp64 mean's bit
+ * pattern) in keys[0..count).  The union of all
  * shards' results holds the global top-k: merge them with wtri_merge_topk.
  * 0 <= shard < nshards; keys has room for k entries.
  */
@@ -240,6 +253,18 @@ WTRI_API int wtri_server_stats(wtri_server* s, uint64_t* batches, uint64_t* admi
 WTRI_API void wtri_server_free(wtri_server* s);
 
 /*
+ * Server options (no counterpart in the paper).
+ * WTRI_SERVER_COALESCE (default 1, or 0 when the environment has
+ * WTRI_SERVE_COALESCE=0 at creation): requests of one micro-batch that ask
+ * the same graph at the same p share one query at their largest k (each
+ * gets the prefix it asked for: under the total order the top-k is the
+ * first k of any top-k' with k' >= k).  0 runs one query per request.
+ * Takes effect for micro-batches launched after the call.
+ */
+enum { WTRI_SERVER_COALESCE = 1 };
+WTRI_API int wtri_server_set_option(wtri_server* s, int option, int64_t value);
+
+/*
  * Query schedule tuning (no counterpart in the paper).  A query sweeps the
  * edge order in rounds over [0, first_round), then ranges growing by
  * `growth`; a thread scans up to t_short wedges of an edge itself and hands
@@ -277,8 +302,9 @@ WTRI_API int wtri_set_tune(wtri_graph* g, int64_t first_round, int32_t growth, i
  * Philox4x64-10 (Salmon et al., SC'11) with key = seed and counter = the
  * sample index, so a seed gives the same samples on any device.
  *
- * p in {1, 2}; +-inf -> WTRI_EUNSUPPORTED (w^p has no meaning there), and
- * p = 0 too (its draws would be uniform; not provided).
+ * p in {0, 1, 2}: w^p is an exact integer (p = 0 draws every edge with the
+ * same probability); +-inf -> WTRI_EUNSUPPORTED (w^p has no meaning there),
+ * and so does any other p (no exact integer cumulative mass).
  * nsamples >= 0 (0 returns count 0).
  */
 WTRI_API int wtri_sample_topk(const wtri_graph* g, double p, int32_t k, int64_t nsamples,
@@ -293,6 +319,37 @@ WTRI_API int wtri_sample_topk(const wtri_graph* g, double p, int32_t k, int64_t 
  */
 WTRI_API int wtri_sample_edges(const wtri_graph* g, double p, int64_t nsamples, uint64_t seed,
                                uint32_t* mark_words, int64_t words_capacity);
+
+/*
+ * Weighted wedge sampling (Algorithm 4, Eqs. 6-8, Section 4.2).  Each of
+ * nsamples iterations draws a center a with probability 2 d_a D(a) / Z1
+ * (D(a) = sum over N(a) of w^p), then b in N(a) with weight
+ * d_a w_ab^p + D(a), then c in N(a) with weight w_ac^p + w_ab^p; when c is
+ * not b and {b, c} is an edge, the triangle joins the set T.  Returns the
+ * top-k of T in the order and format of wtri_topk.  Each iteration closes a
+ * given triangle with probability 2 w_p(a,b,c) / sum_v d_v D(v): b and c
+ * are drawn in order, so every unordered wedge arises twice (the paper's
+ * Proposition 4.2 prints w_p / sum_v d_v D(v)).  The draws are exact
+ * integer inverse CDFs (the vertices in id order, a's neighbours in the
+ * edge order) driven by Philox4x64-10 (Salmon et al., SC'11) words 0, 1, 2
+ * of counter (sample index, 0, 0, 0) and key (seed, 1), so a seed gives the
+ * same draws on any device.
+ *
+ * p in {0, 1, 2}; any other p -> WTRI_EUNSUPPORTED, and so does a graph
+ * with a vertex whose sum of w^p reaches 2^64.  0 <= nsamples < 2^31.
+ */
+WTRI_API int wtri_wedge_topk(const wtri_graph* g, double p, int32_t k, int64_t nsamples,
+                             uint64_t seed, wtri_result* out);
+
+/*
+ * Only the draws of wtri_wedge_topk, to host arrays of nsamples entries:
+ * center[s] = a, jb[s] and jc[s] = the positions of b and c in a's
+ * neighbour list in the edge order (weight desc, input index asc), and
+ * tri[3s..3s+2] = the closed triangle (ascending ids) or -1, -1, -1.
+ * Exists so that the draws can be compared with another implementation.
+ */
+WTRI_API int wtri_sample_wedges(const wtri_graph* g, double p, int64_t nsamples, uint64_t seed,
+                                int32_t* center, int32_t* jb, int32_t* jc, int32_t* tri);
 
 /*
  * Copies one internal array of a built graph to host memory, for tests that
@@ -326,15 +383,52 @@ WTRI_API int wtri_graph_copy_array(const wtri_graph* g, int which, void* dst,
  * wtri_launch_count: kernels launched by this library since load (always on).
  * wtri_prof_enable(1): every library phase is bracketed by CUDA events on its
  * stream; wtri_prof_read(i, ...) returns phase i (sorted by name) with its
- * number of calls, summed device milliseconds and summed algorithmic bytes
- * (the bytes the phase must read and write once), WTRI_ENOTFOUND past the
- * last phase.  wtri_prof_reset clears the totals.
+ * number of calls, summed device milliseconds and summed algorithmic bytes,
+ * WTRI_ENOTFOUND past the last phase.  wtri_prof_reset clears the totals.
+ *
+ * Algorithmic bytes: the COO input read once (12 per edge); each resident
+ * output written once (the symmetric id-sorted rows 16 per edge, the
+ * oriented rows 12 per edge, each row-offset array 8 per vertex); each
+ * sort one read and one write of its payload (the edge order 8 + 8 per
+ * edge, the weight-sorted rows 24 + 24 per edge) whatever its number of
+ * passes, spread evenly over the passes; histogram, scan and other helper
+ * kernels none.  wtri_prof_read_ex also returns the bytes each phase moves
+ * by design (`moved`: every pass of a sort reads and writes its records),
+ * so moved / bytes shows what the design spends beyond the algorithmic
+ * bytes.  Query phases count bytes only while wtri_query_bytes is on.
  */
 WTRI_API void wtri_prof_enable(int on);
 WTRI_API void wtri_prof_reset(void);
 WTRI_API long long wtri_launch_count(void);
 WTRI_API int wtri_prof_read(int idx, char* name, int name_cap, long long* calls, double* ms,
                             double* bytes);
+WTRI_API int wtri_prof_read_ex(int idx, char* name, int name_cap, long long* calls, double* ms,
+                               double* bytes, double* moved);
+
+/*
+ * Instrumented query (no counterpart in the paper): while on != 0, the
+ * exact top-k kernels (single and device queries) count the bytes of every
+ * global load they issue on the graph's adjacency structures (edge order,
+ * weight-sorted, id-sorted and oriented rows, offsets, degrees) into a
+ * counter of the current device.  The counting costs time: time queries
+ * with it off.  *bytes receives the counter after the device is idle
+ * (cudaDeviceSynchronize); reset != 0 zeroes it afterwards.  bytes may be
+ * NULL (only set or reset).
+ */
+WTRI_API int wtri_query_bytes(int on, int reset, unsigned long long* bytes);
+
+/*
+ * Fault injection for tests (no counterpart in the paper).  The long-scan
+ * kernel of the exact query stages a vertex's neighbour list in shared
+ * memory with a bulk copy and waits for it with a bounded number of polls
+ * of an mbarrier; when the polls run out the query reports WTRI_ETIMEOUT
+ * (the copy in flight is still waited for, with the full bound, before the
+ * block moves on).  This sets the bound of that first wait for queries
+ * started afterwards in this process: polls = 0 makes every staged wait
+ * report a timeout at once; polls < 0 restores the default.  Nothing else
+ * changes; a query after restoring the default is unaffected.
+ */
+WTRI_API int wtri_debug_set_wait_limit(int64_t polls);
 
 /* Thread-local message for the last failing call on this thread ("" if none). */
 WTRI_API const char* wtri_last_error(void);

@@ -15,17 +15,22 @@ from .wtri import (  # noqa: F401
     WtriError,
     WtriUnavailable,
     build_csr,
+    debug_set_wait_limit,
     lib,
     lib_path,
     merge_topk,
     sample_edges,
     sample_topk,
+    sample_wedges,
     topk,
     topk_batch,
     topk_device,
     topk_device_noalloc,
     topk_shard,
+    wedge_topk,
 )
 
-__all__ = ["ARRAYS", "Graph", "Server", "WtriError", "WtriUnavailable", "build_csr", "lib", "lib_path", "merge_topk", "topk_shard",
-           "sample_edges", "sample_topk", "topk", "topk_batch", "topk_device", "topk_device_noalloc"]
+__all__ = ["ARRAYS", "Graph", "Server", "WtriError", "WtriUnavailable", "build_csr",
+           "debug_set_wait_limit", "lib", "lib_path", "merge_topk", "topk_shard",
+           "sample_edges", "sample_topk", "sample_wedges", "topk", "topk_batch", "topk_device",
+           "topk_device_noalloc", "wedge_topk"]

@@ -35,7 +35,7 @@ int p_to_code(double p, int* code) {
     else if (isinf(p) && p > 0) *code = P_MAX;
     else if (isinf(p) && p < 0) *code = P_MIN;
     else if (p == 0.0) *code = P_GEO;
-    else return set_error(WTRI_EUNSUPPORTED, "p must be -inf, 0, 1, 2 or +inf");
+    else *code = P_GEN;  // any other finite p: fp64 key
     return WTRI_OK;
 }
 
@@ -69,9 +69,9 @@ int smem_optin(const void* fn, int bytes, std::atomic<uint64_t>& done) {
 
 const char* query_name(int pcode) {
     static const char* const names[P_COUNT] = {"query_p=-inf", "query_p=1", "query_p=2",
-                                               "query_p=+inf", "query_p=0"};
+                                               "query_p=+inf", "query_p=0", "query_p=general"};
     static_assert(P_MIN < P_COUNT && P_ONE < P_COUNT && P_TWO < P_COUNT && P_MAX < P_COUNT &&
-                      P_GEO < P_COUNT,
+                      P_GEO < P_COUNT && P_GEN < P_COUNT,
                   "every p code names a query");
     return (pcode >= 0 && pcode < P_COUNT) ? names[pcode] : "query_p=?";
 }
@@ -187,7 +187,7 @@ WTRI_API int wtri_topk(const wtri_graph* g, double p, int32_t k, wtri_result* ou
     return host_result_query(g, k, out,
                              [&](wtri_tri* t, double* wv, int32_t* c, cudaStream_t s, int scale,
                                  unsigned long long*) {
-                                 return topk_device(g, code, k, t, wv, c, s, scale);
+                                 return topk_device(g, code, k, t, wv, c, s, scale, 0, 1, nullptr, p);
                              });
 }
 
@@ -206,7 +206,8 @@ WTRI_API int wtri_topk_shard(const wtri_graph* g, double p, int32_t k, int32_t s
     return host_result_query(g, k, out,
                              [&](wtri_tri* t, double* wv, int32_t* c, cudaStream_t s, int scale,
                                  unsigned long long* dk) {
-                                 return topk_device(g, code, k, t, wv, c, s, scale, shard, nshards, dk);
+                                 return topk_device(g, code, k, t, wv, c, s, scale, shard, nshards, dk,
+                                                    p);
                              },
                              keys);
 }
@@ -362,7 +363,7 @@ WTRI_API int wtri_topk_device(const wtri_graph* g, double p, int32_t k, wtri_tri
         WTRI_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int32_t), s));
         return WTRI_OK;
     }
-    return topk_device(g, code, k, d_tris, d_weight, d_count, s, 1);
+    return topk_device(g, code, k, d_tris, d_weight, d_count, s, 1, 0, 1, nullptr, p);
 }
 
 WTRI_API int wtri_sample_topk(const wtri_graph* g, double p, int32_t k, int64_t nsamples,
@@ -371,9 +372,9 @@ WTRI_API int wtri_sample_topk(const wtri_graph* g, double p, int32_t k, int64_t 
     out->count = 0;
     int code = 0;
     WTRI_TRY(check_query(g, k));
-    WTRI_TRY(p_to_code(p, &code));
-    if (code != P_ONE && code != P_TWO)
-        return set_error(WTRI_EUNSUPPORTED, "edge sampling needs p = 1 or 2");
+    WTRI_TRY(p_to_code_for(p, g, &code));
+    if (code != P_ONE && code != P_TWO && code != P_GEO)
+        return set_error(WTRI_EUNSUPPORTED, "edge sampling needs p = 0, 1 or 2 (exact integer w^p)");
     if (nsamples < 0) return set_error(WTRI_EINVAL, "nsamples must be non-negative");
     if (!out->tris || !out->weight) return set_error(WTRI_EINVAL, "result arrays are NULL");
     if (out->capacity < k) return set_error(WTRI_EINVAL, "result capacity below k");
@@ -384,6 +385,47 @@ WTRI_API int wtri_sample_topk(const wtri_graph* g, double p, int32_t k, int64_t 
                                  return sample_topk_device(g, code, k, nsamples, seed, t, wv, c, s,
                                                            scale);
                              });
+}
+
+WTRI_API int wtri_wedge_topk(const wtri_graph* g, double p, int32_t k, int64_t nsamples,
+                             uint64_t seed, wtri_result* out) {
+    if (!out) return set_error(WTRI_EINVAL, "out is NULL");
+    out->count = 0;
+    int code = 0;
+    WTRI_TRY(check_query(g, k));
+    WTRI_TRY(p_to_code_for(p, g, &code));
+    if (code != P_ONE && code != P_TWO && code != P_GEO)
+        return set_error(WTRI_EUNSUPPORTED, "wedge sampling needs p = 0, 1 or 2 (exact integer w^p)");
+    if (nsamples < 0) return set_error(WTRI_EINVAL, "nsamples must be non-negative");
+    if (nsamples >= (int64_t(1) << 31)) return set_error(WTRI_EUNSUPPORTED, "nsamples of 2^31 or more");
+    if (!out->tris || !out->weight) return set_error(WTRI_EINVAL, "result arrays are NULL");
+    if (out->capacity < k) return set_error(WTRI_EINVAL, "result capacity below k");
+    if (g->d.m == 0 || nsamples == 0) return WTRI_OK;
+    return host_result_query(g, k, out,
+                             [&](wtri_tri* t, double* wv, int32_t* c, cudaStream_t s, int,
+                                 unsigned long long*) {
+                                 return wedge_topk_device(g, code, k, nsamples, seed, t, wv, c, s);
+                             });
+}
+
+WTRI_API int wtri_sample_wedges(const wtri_graph* g, double p, int64_t nsamples, uint64_t seed,
+                                int32_t* center, int32_t* jb, int32_t* jc, int32_t* tri) {
+    if (!g) return set_error(WTRI_EINVAL, "graph is NULL");
+    int code = 0;
+    WTRI_TRY(p_to_code_for(p, g, &code));
+    if (code != P_ONE && code != P_TWO && code != P_GEO)
+        return set_error(WTRI_EUNSUPPORTED, "wedge sampling needs p = 0, 1 or 2 (exact integer w^p)");
+    if (nsamples < 0) return set_error(WTRI_EINVAL, "nsamples must be non-negative");
+    if (nsamples == 0) return WTRI_OK;
+    if (!center || !jb || !jc || !tri) return set_error(WTRI_EINVAL, "output arrays are NULL");
+    if (g->d.m == 0) {
+        for (int64_t s = 0; s < nsamples; s++) {
+            center[s] = jb[s] = jc[s] = -1;
+            tri[3 * s] = tri[3 * s + 1] = tri[3 * s + 2] = -1;
+        }
+        return WTRI_OK;
+    }
+    return wedge_draws_host(g, code, nsamples, seed, center, jb, jc, tri);
 }
 
 WTRI_API int wtri_topk_batch(const wtri_graph* const* gs, const double* p, const int32_t* k,
@@ -401,6 +443,9 @@ WTRI_API int wtri_topk_batch(const wtri_graph* const* gs, const double* p, const
         int c = 0;
         int rc = p_to_code_for(p[i], gs[i], &c);
         if (rc != WTRI_OK) return rc;
+        if (c == P_GEN)
+            return set_error(WTRI_EUNSUPPORTED,
+                             "batched queries take p in {-inf, 0, 1, 2, +inf}; other p through wtri_topk");
         codes[(size_t)i] = c;
         rc = check_query(gs[i], k[i]);
         if (rc != WTRI_OK) return rc;
@@ -415,8 +460,8 @@ WTRI_API int wtri_sample_edges(const wtri_graph* g, double p, int64_t nsamples, 
     if (!g) return set_error(WTRI_EINVAL, "graph is NULL");
     int code = 0;
     WTRI_TRY(p_to_code(p, &code));
-    if (code != P_ONE && code != P_TWO)
-        return set_error(WTRI_EUNSUPPORTED, "edge sampling needs p = 1 or 2");
+    if (code != P_ONE && code != P_TWO && code != P_GEO)
+        return set_error(WTRI_EUNSUPPORTED, "edge sampling needs p = 0, 1 or 2 (exact integer w^p)");
     if (nsamples < 0) return set_error(WTRI_EINVAL, "nsamples must be non-negative");
     const int64_t words = (g->d.m + 31) / 32;
     if (!mark_words || words_capacity < words)
@@ -447,9 +492,8 @@ WTRI_API int wtri_graph_copy_array(const wtri_graph* g, int which, void* dst,
     const int64_t n = g->d.n, m = g->d.m;
     const void* src = nullptr;
     int64_t bytes = 0;
-    bool oriented = false;
     switch (which) {
-        case WTRI_ARR_DEGREE: src = g->d.deg; bytes = 4 * n; break;
+        case WTRI_ARR_DEGREE: bytes = 4 * n; break;  // from the row offsets
         case WTRI_ARR_ROWPTR: src = g->d.rowptr; bytes = 8 * (n + 1); break;
         case WTRI_ARR_ORDER_U: src = g->d.ord_u; bytes = 4 * m; break;
         case WTRI_ARR_ORDER_V: src = g->d.ord_v; bytes = 4 * m; break;
@@ -459,45 +503,31 @@ WTRI_API int wtri_graph_copy_array(const wtri_graph* g, int which, void* dst,
         case WTRI_ARR_WRANK: src = g->d.wrk; bytes = 8 * m; break;
         case WTRI_ARR_SCOL: src = g->d.scol; bytes = 8 * m; break;
         case WTRI_ARR_SWT: src = g->d.swt; bytes = 8 * m; break;
-        case WTRI_ARR_SRANK: src = g->d.srk; bytes = 8 * m; break;
-        case WTRI_ARR_OROWPTR: bytes = 8 * (n + 1); oriented = true; break;
-        case WTRI_ARR_OCOL: src = g->d.ocol; bytes = 4 * m; oriented = true; break;
-        case WTRI_ARR_OWT: src = g->d.owt; bytes = 4 * m; oriented = true; break;
-        case WTRI_ARR_ORANK: src = g->d.ork; bytes = 4 * m; oriented = true; break;
+        case WTRI_ARR_SRANK:
+            return set_error(WTRI_EUNSUPPORTED,
+                             "edge ranks of the id-sorted rows are not kept (the oriented rows carry them)");
+        case WTRI_ARR_OROWPTR: src = g->d.orowptr; bytes = 8 * (n + 1); break;
+        case WTRI_ARR_OCOL: src = g->d.ocol; bytes = 4 * m; break;
+        case WTRI_ARR_OWT: src = g->d.owt; bytes = 4 * m; break;
+        case WTRI_ARR_ORANK: src = g->d.ork; bytes = 4 * m; break;
         default: return set_error(WTRI_EINVAL, "unknown array id");
     }
     if (bytes_out) *bytes_out = bytes;
     if (!dst) return WTRI_OK;
     if (bytes_capacity < bytes) return set_error(WTRI_EINVAL, "destination too small");
     if (bytes == 0) return WTRI_OK;
-    if (!oriented) {
+    if (src) {
         WTRI_CUDA(cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyDeviceToHost, g->stream));
         WTRI_CUDA(cudaStreamSynchronize(g->stream));
         return WTRI_OK;
     }
-    // The device keeps oriented row x in the slots of symmetric row x; the
-    // exported form is the compact CSR (offsets n+1, entries m).
-    std::vector<int32_t> od((size_t)n);
+    // degrees: differences of the row offsets
     std::vector<int64_t> rp((size_t)n + 1);
-    WTRI_CUDA(cudaMemcpyAsync(od.data(), g->d.odeg, 4 * (size_t)n, cudaMemcpyDeviceToHost, g->stream));
     WTRI_CUDA(cudaMemcpyAsync(rp.data(), g->d.rowptr, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost,
                               g->stream));
-    std::vector<int32_t> gap;
-    if (src) {
-        gap.resize((size_t)(2 * m));
-        WTRI_CUDA(cudaMemcpyAsync(gap.data(), src, 8 * (size_t)m, cudaMemcpyDeviceToHost, g->stream));
-    }
     WTRI_CUDA(cudaStreamSynchronize(g->stream));
-    if (!src) {
-        int64_t* o = (int64_t*)dst;
-        o[0] = 0;
-        for (int64_t x = 0; x < n; x++) o[x + 1] = o[x] + od[(size_t)x];
-        return WTRI_OK;
-    }
     int32_t* o = (int32_t*)dst;
-    int64_t at = 0;
-    for (int64_t x = 0; x < n; x++)
-        for (int64_t j = 0; j < od[(size_t)x]; j++) o[at++] = gap[(size_t)(rp[(size_t)x] + j)];
+    for (int64_t x = 0; x < n; x++) o[x] = (int32_t)(rp[(size_t)x + 1] - rp[(size_t)x]);
     return WTRI_OK;
 }
 

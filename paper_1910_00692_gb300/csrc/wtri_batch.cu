@@ -92,12 +92,13 @@ __global__ void __launch_bounds__(RBLK) k_round_batch(BatchDev B, const int64_t*
         if (idx >= (int64_t)(STOP_NONE - *(volatile const uint32_t*)&q.st->stop_rev)) continue;
         const unsigned long long tau = ld_volatile_u64(&q.st->tau);
         const DevGraph& G = B.graphs[qi];
+        Tally tb;  // batched queries are not instrumented
         switch (B.pcodes[qi]) {
-            case P_MIN: process_edge<P_MIN, false>(G, q, tau, (int32_t)idx); break;
-            case P_ONE: process_edge<P_ONE, false>(G, q, tau, (int32_t)idx); break;
-            case P_TWO: process_edge<P_TWO, false>(G, q, tau, (int32_t)idx); break;
-            case P_GEO: process_edge<P_GEO, false>(G, q, tau, (int32_t)idx); break;
-            default: process_edge<P_MAX, false>(G, q, tau, (int32_t)idx); break;
+            case P_MIN: process_edge<P_MIN, false>(G, q, tau, (int32_t)idx, tb); break;
+            case P_ONE: process_edge<P_ONE, false>(G, q, tau, (int32_t)idx, tb); break;
+            case P_TWO: process_edge<P_TWO, false>(G, q, tau, (int32_t)idx, tb); break;
+            case P_GEO: process_edge<P_GEO, false>(G, q, tau, (int32_t)idx, tb); break;
+            default: process_edge<P_MAX, false>(G, q, tau, (int32_t)idx, tb); break;
         }
     }
 }
@@ -127,14 +128,16 @@ __global__ void __launch_bounds__(LBLK) k_long_batch(BatchDev B, const LongItem*
         const int32_t dy = (int32_t)(yend - ybeg);
         const bool staged = dy <= STAGE_MAX;
         int32_t off = 0;
-        if (staged && !stage_row(G, ybeg, dy, srow, &bar, phase, off, &q.st->err, &timed_out))
+        if (staged && !stage_row(G, ybeg, dy, srow, &bar, phase, off, &q.st->err, &timed_out,
+                                 WAIT_LIMIT))
             return;
+        Tally tb;
         switch (B.pcodes[qi]) {
-            case P_MIN: long_scan<P_MIN, false>(G, q, tau, item, srow, off, ybeg, dy, staged); break;
-            case P_ONE: long_scan<P_ONE, false>(G, q, tau, item, srow, off, ybeg, dy, staged); break;
-            case P_TWO: long_scan<P_TWO, false>(G, q, tau, item, srow, off, ybeg, dy, staged); break;
-            case P_GEO: long_scan<P_GEO, false>(G, q, tau, item, srow, off, ybeg, dy, staged); break;
-            default: long_scan<P_MAX, false>(G, q, tau, item, srow, off, ybeg, dy, staged); break;
+            case P_MIN: long_scan<P_MIN, false>(G, q, tau, item, srow, off, ybeg, dy, staged, tb); break;
+            case P_ONE: long_scan<P_ONE, false>(G, q, tau, item, srow, off, ybeg, dy, staged, tb); break;
+            case P_TWO: long_scan<P_TWO, false>(G, q, tau, item, srow, off, ybeg, dy, staged, tb); break;
+            case P_GEO: long_scan<P_GEO, false>(G, q, tau, item, srow, off, ybeg, dy, staged, tb); break;
+            default: long_scan<P_MAX, false>(G, q, tau, item, srow, off, ybeg, dy, staged, tb); break;
         }
         __syncthreads();
     }
@@ -311,6 +314,9 @@ int batch_plan_launch(BatchPlan* P, void* dbuf, cudaStream_t s, int use_graph) {
         q.shard = 0;
         q.nshards = 1;
         q.t_short = P->tshort[(size_t)i];
+        q.qbytes = nullptr;
+        q.gp = 0.0;  // batched queries take the exact-key p values only
+        q.wait_first = WAIT_LIMIT;
         c0 += P->caps[(size_t)i];
     }
     BatchDev Bd;

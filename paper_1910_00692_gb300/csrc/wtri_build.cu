@@ -5,19 +5,22 @@
 // (Algorithm 2, first step), neighbour sets N(a) and degrees d_a (Section
 // 4), and the NodeIterator++ degree ordering (Section 5.2).
 //
-// Pipeline (one stream, inputs read once from HBM or host):
+// Pipeline (one stream, inputs read once from HBM or host; no host round
+// trip until the end: every kernel after validation reads the device status
+// word and returns at once if an earlier step failed):
 //   1. k_validate: rejects bad edges, finds the max weight.
-//   2. Edge order: stable LSD radix sort of key (wmax - w) carrying (u, v).
+//   2. Edge order: stable LSD radix sort of key ~w carrying (u, v), planned
+//      for 31-bit weights; the passes above the max weight's bit length
+//      skip themselves on the device.
 //   3. Weight-sorted lists: the virtual stream "two entries per edge, in edge
 //      order" is stably radix-sorted by row, so each row keeps edge order.
 //   4. Row offsets and degrees from the boundaries of the sorted rows (no
-//      atomics), plus the list of long rows.
-//   5. Id-sorted lists: the weight-sorted entries, read row by row (so the
-//      stream is ascending in its row x), are mirrored to (row c, col x) and
-//      stably sorted by row c, which leaves each row ascending in x.
-//   6. Oriented lists: per row, keep neighbours of higher (degree, id) rank,
-//      in place of the row's own slots; repeated pairs show up in the same
-//      pass as equal neighbours next to each other.
+//      atomics).
+//   5. Oriented out-degrees (neighbours of higher (degree, id) rank) and
+//      their scan, the oriented row offsets.
+//   6. Per-row segmented sort of the weight-sorted rows by neighbour id
+//      (wtri_rows.cuh): the id-sorted rows, the oriented rows in place, and
+//      repeated pairs (equal neighbours next to each other).
 #include <cuda_runtime.h>
 #include <stdio.h>
 
@@ -26,6 +29,7 @@
 
 #include "wtri_internal.cuh"
 #include "wtri_radix.cuh"
+#include "wtri_rows.cuh"
 
 namespace wtri {
 
@@ -172,7 +176,7 @@ __global__ void k_scan_apply(const int32_t* __restrict__ in, int64_t n,
 // stride of radix::TT words.
 using radix::TT;
 
-// Edge order input: key = wmax - w, values (u, v).
+// Edge order input: key ~w (ascending key = weight descending), values (u, v).
 struct EdgeLoader {
     static constexpr double REC_BYTES = 12.0;  // u, v, w
     static constexpr int NARR = 3;             // w, u, v
@@ -180,13 +184,12 @@ struct EdgeLoader {
     const int32_t* u;
     const int32_t* v;
     const int32_t* w;
-    int32_t wmax;
-    __device__ __forceinline__ uint32_t key(int64_t i) const { return (uint32_t)(wmax - __ldg(w + i)); }
+    __device__ __forceinline__ uint32_t key(int64_t i) const { return ~(uint32_t)__ldg(w + i); }
     __device__ __forceinline__ const void* tile_src(int a, int64_t tbase) const {
         return (a == 0 ? w : (a == 1 ? u : v)) + tbase;
     }
     __device__ __forceinline__ uint4 srec(const uint32_t* in, int li, int64_t) const {
-        return make_uint4((uint32_t)(wmax - (int32_t)in[li]), in[TT + li], in[2 * TT + li], 0u);
+        return make_uint4(~in[li], in[TT + li], in[2 * TT + li], 0u);
     }
     __device__ __forceinline__ uint4 grec(int64_t i) const {
         return make_uint4(key(i), (uint32_t)__ldg(u + i), (uint32_t)__ldg(v + i), 0u);
@@ -200,9 +203,9 @@ struct EdgeOrderStorer {
     int32_t* ou;
     int32_t* ov;
     int32_t* ow;
-    int32_t wmax;
+    __device__ __forceinline__ void prepare() {}
     __device__ __forceinline__ void store(int64_t p, const uint4& r) const {
-        ow[p] = wmax - (int32_t)r.x;
+        ow[p] = (int32_t)~r.x;
         ou[p] = (int32_t)r.y;
         ov[p] = (int32_t)r.z;
     }
@@ -238,61 +241,27 @@ struct OrderEntryLoader {
     bool tma_ok() const { return (((uintptr_t)ou | (uintptr_t)ov | (uintptr_t)ow) & 15) == 0; }
 };
 
-// Mirrored weight-sorted entries: entry i of row x (= wrow[i]) with
-// neighbour c becomes the record (row c, col x, weight, r).
-struct MirrorLoader {
-    static constexpr double REC_BYTES = 16.0;  // wcol, wrow, wwt, wrk
-    static constexpr int NARR = 4;
-    static constexpr uint32_t TILE_WORDS = TT;
-    const int32_t* wrow;
-    const int32_t* wcol;
-    const int32_t* wwt;
-    const int32_t* wrk;
-    __device__ __forceinline__ const void* tile_src(int a, int64_t tbase) const {
-        return (a == 0 ? wcol : (a == 1 ? wrow : (a == 2 ? wwt : wrk))) + tbase;
-    }
-    __device__ __forceinline__ uint4 srec(const uint32_t* in, int li, int64_t) const {
-        return make_uint4(in[li], in[TT + li], in[2 * TT + li], in[3 * TT + li]);
-    }
-    __device__ __forceinline__ uint4 grec(int64_t i) const {
-        return make_uint4((uint32_t)__ldg(wcol + i), (uint32_t)__ldg(wrow + i), (uint32_t)__ldg(wwt + i),
-                          (uint32_t)__ldg(wrk + i));
-    }
-    __device__ __forceinline__ uint32_t key(int64_t i) const { return (uint32_t)__ldg(wcol + i); }
-    bool tma_ok() const {
-        return (((uintptr_t)wrow | (uintptr_t)wcol | (uintptr_t)wwt | (uintptr_t)wrk) & 15) == 0;
-    }
-};
-
-// Final row-sorted output: row (optional), col, weight, r.
+// Final row-sorted output: row, col, weight, r.
 struct RowsStorer {
-    __host__ __device__ double rec_bytes() const { return row ? 16.0 : 12.0; }
-    int32_t* row;  // may be null
+    __host__ __device__ double rec_bytes() const { return 16.0; }
+    int32_t* row;
     int32_t* col;
     int32_t* wt;
     int32_t* rk;
+    __device__ __forceinline__ void prepare() {}
     __device__ __forceinline__ void store(int64_t p, const uint4& r) const {
-        if (row) row[p] = (int32_t)r.x;
+        row[p] = (int32_t)r.x;
         col[p] = (int32_t)r.y;
         wt[p] = (int32_t)r.z;
         rk[p] = (int32_t)r.w;
     }
 };
 
-__global__ void k_copy_identity_order(int64_t m, const int32_t* u, const int32_t* v,
-                                      const int32_t* w, int32_t* ou, int32_t* ov, int32_t* ow) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        ou[i] = u[i];
-        ov[i] = v[i];
-        ow[i] = w[i];
-    }
-}
-
 // Row offsets from the row-sorted entry stream: entry i starts row x for
 // every x in (row[i-1], row[i]]; rows past the last entry start at n2.
 __global__ void k_rowptr_from_rows(int32_t n, int64_t n2, const int32_t* __restrict__ row,
-                                   int64_t* __restrict__ rowptr) {
+                                   int64_t* __restrict__ rowptr, const uint32_t* gate) {
+    if (*(volatile const uint32_t*)gate) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t cur = __ldg(row + i);
@@ -303,225 +272,21 @@ __global__ void k_rowptr_from_rows(int32_t n, int64_t n2, const int32_t* __restr
     }
 }
 
-constexpr int SHORT_ROW = 32;   // rows below: one thread each
-constexpr int LONG_ROW = 1024;  // rows from here: one block each; in between: one warp each
-
-// Degrees (also saturated to 16 bits, the form the orientation test gathers),
-// the maximum degree, and the lists of long rows (front of 'rows') and
-// medium rows (back of 'rows').  counters: [0] long, [1] next long,
-// [2] medium.
-__global__ void k_degrees(int32_t n, const int64_t* __restrict__ rowptr, int32_t* __restrict__ deg,
-                          uint16_t* __restrict__ deg16, BuildStatus* st, int32_t* rows,
-                          int32_t* counters) {
+// Degrees saturated to 8 bits (the form the orientation test gathers: one
+// byte per vertex, small enough to stay in L2) and the maximum degree.
+__global__ void k_degrees(int32_t n, const int64_t* __restrict__ rowptr, uint8_t* __restrict__ deg8,
+                          BuildStatus* st) {
+    if (*(volatile const uint32_t*)&st->err) return;
     int32_t mx = 0;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t d = (int32_t)(rowptr[x + 1] - rowptr[x]);
-        deg[x] = d;
-        deg16[x] = (uint16_t)min(d, 0xffff);
-        mx = max(mx, d);
-        // one atomic per warp and list
-        const uint32_t act = __activemask();
-        const int lane = threadIdx.x & 31;
-        const uint32_t bl = __ballot_sync(act, d >= LONG_ROW);
-        const uint32_t bm = __ballot_sync(act, d >= SHORT_ROW && d < LONG_ROW);
-        const int leader = __ffs(act) - 1;
-        int32_t base_l = 0, base_m = 0;
-        if (lane == leader) {
-            if (bl) base_l = atomicAdd(&counters[0], __popc(bl));
-            if (bm) base_m = atomicAdd(&counters[2], __popc(bm));
-        }
-        base_l = __shfl_sync(act, base_l, leader);
-        base_m = __shfl_sync(act, base_m, leader);
-        const uint32_t below = (1u << lane) - 1u;
-        if (d >= LONG_ROW) rows[base_l + __popc(bl & below)] = (int32_t)x;
-        else if (d >= SHORT_ROW) rows[n - 1 - (base_m + __popc(bm & below))] = (int32_t)x;
+        const int64_t d = rowptr[x + 1] - rowptr[x];
+        deg8[x] = (uint8_t)min(d, (int64_t)rows::DEG8_SAT);
+        mx = max(mx, (int32_t)min(d, (int64_t)INT32_MAX));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx) atomicMax(&st->maxdeg, mx);
-}
-
-// Whether x (degree dx) comes before its neighbour c in the (degree, id)
-// order.  The 16-bit degrees decide unless both saturate.
-__device__ __forceinline__ bool before(int32_t x, int32_t dx, const uint16_t* __restrict__ deg16,
-                                       const int32_t* __restrict__ deg, int32_t c) {
-    uint32_t dc = __ldg(deg16 + c);
-    if (dx >= 0xffff) {
-        if (dc < 0xffffu) return false;
-        dc = (uint32_t)__ldg(deg + c);
-    }
-    return (uint32_t)dx < dc || ((uint32_t)dx == dc && x < c);
-}
-
-constexpr int OBLK = 512;
-
-// Degree orientation, in the slots of the symmetric rows: row x keeps its
-// neighbours of higher (degree, id) rank, in id order, at
-// [rowptr[x], rowptr[x] + odeg[x]).  The same pass finds repeated pairs
-// (equal neighbours next to each other in an id-sorted row).
-//
-// Every pass loads an entry's id, weight and rank together (the weight and
-// rank of a dropped entry are read but unused), so the only dependent load
-// is the neighbour's degree.
-//
-// Short rows: one thread per row walks its entries, eight at a time.
-__global__ void k_orient_short(int32_t n, const int64_t* __restrict__ rowptr,
-                               const int32_t* __restrict__ scol, const int32_t* __restrict__ swt,
-                               const int32_t* __restrict__ srk, const uint16_t* __restrict__ deg16,
-                               const int32_t* __restrict__ deg, int32_t* __restrict__ ocol,
-                               int32_t* __restrict__ owt, int32_t* __restrict__ ork,
-                               int32_t* __restrict__ odeg, BuildStatus* st) {
-    constexpr int B = 8;
-    unsigned long long dup = ~0ull;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = rowptr[x], e = rowptr[x + 1];
-        const int32_t dx = (int32_t)(e - s);
-        if (dx >= SHORT_ROW) continue;
-        int64_t out = s;
-        int32_t prev = -1;
-        for (int64_t j0 = s; j0 < e; j0 += B) {
-            int32_t c[B], wv[B], rv[B];
-            bool f[B];
-#pragma unroll
-            for (int i = 0; i < B; i++) {
-                const bool ok = j0 + i < e;
-                c[i] = ok ? __ldcs(scol + j0 + i) : -1;
-                wv[i] = ok ? __ldcs(swt + j0 + i) : 0;
-                rv[i] = ok ? __ldcs(srk + j0 + i) : 0;
-            }
-#pragma unroll
-            for (int i = 0; i < B; i++) f[i] = c[i] >= 0 && before((int32_t)x, dx, deg16, deg, c[i]);
-#pragma unroll
-            for (int i = 0; i < B; i++) {
-                if (c[i] < 0) break;
-                if (c[i] == prev) dup = min(dup, (unsigned long long)(j0 + i));
-                prev = c[i];
-                if (f[i]) {
-                    ocol[out] = c[i];
-                    owt[out] = wv[i];
-                    ork[out] = rv[i];
-                    out++;
-                }
-            }
-        }
-        odeg[x] = (int32_t)(out - s);
-    }
-    if (dup != ~0ull) {
-        atomicOr(&st->err, DEV_ERR_DUPLICATE);
-        atomicMin(&st->first_bad, dup);
-    }
-}
-
-// Long rows: blocks take them from a queue; then medium rows: warp i takes
-// entries i, i + warps, ... of their list, four 32-entry chunks at a time.
-__global__ void __launch_bounds__(OBLK) k_orient(
-    int32_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ scol,
-    const int32_t* __restrict__ swt, const int32_t* __restrict__ srk,
-    const uint16_t* __restrict__ deg16, const int32_t* __restrict__ deg, int32_t* __restrict__ ocol,
-    int32_t* __restrict__ owt, int32_t* __restrict__ ork, int32_t* __restrict__ odeg,
-    const int32_t* __restrict__ rows, int32_t* counters, BuildStatus* st) {
-    __shared__ uint32_t warp_cnt[OBLK / 32];
-    __shared__ uint32_t tot;
-    __shared__ int32_t item;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint32_t below = (1u << lane) - 1u;
-    unsigned long long dup = ~0ull;
-    const int nlong = counters[0];
-    for (;;) {
-        if (threadIdx.x == 0) item = atomicAdd(&counters[1], 1);
-        __syncthreads();
-        const int it = item;
-        __syncthreads();
-        if (it >= nlong) break;
-        const int32_t x = rows[it];
-        const int64_t s = rowptr[x], e = rowptr[x + 1];
-        const int32_t dx = (int32_t)(e - s);
-        int64_t out = s;
-        for (int64_t j0 = s; j0 < e; j0 += OBLK) {
-            const int64_t j = j0 + threadIdx.x;
-            bool fwd = false;
-            int32_t c = 0, wv = 0, rv = 0, cp = -1;
-            if (j < e) {
-                c = __ldcs(scol + j);
-                wv = __ldcs(swt + j);
-                rv = __ldcs(srk + j);
-                if (j > s) cp = __ldg(scol + j - 1);
-            }
-            if (j < e) {
-                if (cp == c) dup = min(dup, (unsigned long long)j);
-                fwd = before(x, dx, deg16, deg, c);
-            }
-            const uint32_t b = __ballot_sync(0xffffffffu, fwd);
-            if (lane == 0) warp_cnt[wid] = __popc(b);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                uint32_t acc = 0;
-                for (int k = 0; k < OBLK / 32; k++) {
-                    const uint32_t t = warp_cnt[k];
-                    warp_cnt[k] = acc;
-                    acc += t;
-                }
-                tot = acc;
-            }
-            __syncthreads();
-            if (fwd) {
-                const int64_t p = out + warp_cnt[wid] + __popc(b & below);
-                ocol[p] = c;
-                owt[p] = wv;
-                ork[p] = rv;
-            }
-            out += tot;
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) odeg[x] = (int32_t)(out - s);
-    }
-    constexpr int CH = 4;
-    const int nmed = counters[2];
-    const int64_t nwarps = ((int64_t)gridDim.x * OBLK) >> 5;
-    for (int64_t it = ((int64_t)blockIdx.x * OBLK + threadIdx.x) >> 5; it < nmed; it += nwarps) {
-        const int32_t x = rows[n - 1 - it];
-        const int64_t s = rowptr[x], e = rowptr[x + 1];
-        const int32_t dx = (int32_t)(e - s);
-        int64_t out = s;
-        int32_t carry = -1;  // id of the entry before the current chunk
-        for (int64_t j0 = s; j0 < e; j0 += 32 * CH) {
-            int32_t c[CH], wv[CH], rv[CH];
-            bool f[CH];
-#pragma unroll
-            for (int i = 0; i < CH; i++) {
-                const int64_t j = j0 + 32 * i + lane;
-                const bool ok = j < e;
-                c[i] = ok ? __ldcs(scol + j) : -1;
-                wv[i] = ok ? __ldcs(swt + j) : 0;
-                rv[i] = ok ? __ldcs(srk + j) : 0;
-            }
-#pragma unroll
-            for (int i = 0; i < CH; i++) f[i] = c[i] >= 0 && before(x, dx, deg16, deg, c[i]);
-#pragma unroll
-            for (int i = 0; i < CH; i++) {
-                const int32_t up = __shfl_up_sync(0xffffffffu, c[i], 1);
-                const int32_t pc = lane == 0 ? carry : up;
-                const int64_t j = j0 + 32 * i + lane;
-                if (c[i] >= 0 && pc == c[i]) dup = min(dup, (unsigned long long)j);
-                carry = __shfl_sync(0xffffffffu, c[i], 31);
-                const uint32_t b = __ballot_sync(0xffffffffu, f[i]);
-                if (f[i]) {
-                    const int64_t p = out + __popc(b & below);
-                    ocol[p] = c[i];
-                    owt[p] = wv[i];
-                    ork[p] = rv[i];
-                }
-                out += __popc(b);
-            }
-        }
-        if (lane == 0) odeg[x] = (int32_t)(out - s);
-    }
-    if (dup != ~0ull) {
-        atomicOr(&st->err, DEV_ERR_DUPLICATE);
-        atomicMin(&st->first_bad, dup);  // entry index of the repeat
-    }
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -548,7 +313,7 @@ int exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaSt
     int64_t* tile_sums = nullptr;
     WTRI_CUDA(cudaMallocAsync((void**)&tile_sums, sizeof(int64_t) * (size_t)std::max<int64_t>(tiles, 1), s));
     if (tiles > 0) {
-        ProfScope ps("scan_offsets", s, 4.0 * n * 2 + 8.0 * (n + 1), 3);
+        ProfScope ps("scan_offsets", s, 0.0, 3, 4.0 * n * 2 + 8.0 * (n + 1));
         k_scan_reduce<<<(unsigned)tiles, BLK, 0, s>>>(in, n, tile_sums, nullptr);
         k_scan_tiles<<<1, BLK, 0, s>>>(tile_sums, tiles, out + n);
         k_scan_apply<<<(unsigned)tiles, BLK, 0, s>>>(in, n, tile_sums, out);
@@ -577,6 +342,58 @@ unsigned grid_for(int64_t work, int per_block = BLK) {
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     return (unsigned)g;
+}
+
+// Per-row sorts (wtri_rows.cuh): launches of every size class, each under its
+// own phase timer (the bytes of the whole step are declared by the caller).
+// g0/g1: the hub rows' runs (8 bytes per entry each).  max_deg_bound: an
+// upper bound on any degree (sets the number of hub merge levels launched;
+// levels that no row needs return at once).
+int sort_rows(const rows::RowsOut& R, unsigned long long* g0, unsigned long long* g1, int32_t* cursor,
+              int64_t max_deg_bound, const uint32_t* gate, cudaStream_t s) {
+    const int sms = sm_count();
+    {
+        ProfScope ps("rows_sort_small", s, 0.0, 3);
+        rows::k_rows_small<8><<<sms * 8, rows::NT, 0, s>>>(R, rows::CLS_G8, gate);
+        rows::k_rows_small<16><<<sms * 8, rows::NT, 0, s>>>(R, rows::CLS_G16, gate);
+        rows::k_rows_small<32><<<sms * 8, rows::NT, 0, s>>>(R, rows::CLS_G32, gate);
+    }
+    {
+        ProfScope ps("rows_sort_warp", s, 0.0, 5);
+        auto launch = [&](auto kern, int epl, int cls) -> int {
+            static std::atomic<uint64_t> done[6];
+            const int smem = rows::NWARPS * 32 * epl * 16;  // keys + weights + ranks
+            int slot = 0;
+            for (int e = epl; e > 2; e >>= 1) slot++;
+            WTRI_TRY(smem_optin((const void*)kern, smem, done[slot]));
+            kern<<<sms * 4, rows::NT, smem, s>>>(R, cls, gate);
+            return WTRI_OK;
+        };
+        WTRI_TRY(launch(rows::k_rows_warp<2>, 2, rows::CLS_W2));
+        WTRI_TRY(launch(rows::k_rows_warp<4>, 4, rows::CLS_W4));
+        WTRI_TRY(launch(rows::k_rows_warp<8>, 8, rows::CLS_W8));
+        WTRI_TRY(launch(rows::k_rows_warp<16>, 16, rows::CLS_W16));
+        WTRI_TRY(launch(rows::k_rows_warp<32>, 32, rows::CLS_W32));
+    }
+    {
+        ProfScope ps("rows_sort_block", s, 0.0, 1);
+        static std::atomic<uint64_t> done{0};
+        const int smem = (int)sizeof(rows::BlockSmem);
+        WTRI_TRY(smem_optin((const void*)rows::k_rows_block, smem, done));
+        rows::k_rows_block<<<sms, rows::NT, smem, s>>>(R, g0, cursor, gate);
+    }
+    {
+        int levels = 0;
+        for (int64_t len = rows::SB; len < max_deg_bound; len <<= 1) levels++;
+        ProfScope ps("rows_sort_hub", s, 0.0, levels + 1);
+        int64_t len = rows::SB;
+        for (int l = 0; l < levels; l++, len <<= 1)
+            rows::k_rows_merge<<<sms * 4, rows::NT, 0, s>>>(R, (l & 1) ? g1 : g0, (l & 1) ? g0 : g1, len,
+                                                            gate);
+        rows::k_rows_hub_out<<<sms * 4, rows::NT, 0, s>>>(R, g0, g1, gate);
+    }
+    WTRI_CUDA(cudaGetLastError());
+    return WTRI_OK;
 }
 
 }  // namespace
@@ -616,12 +433,11 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         off = align_up(off + bytes + 16, 256);
         return o;
     };
-    const size_t o_deg = take(4 * N1), o_odeg = take(4 * N1);
-    const size_t o_rowptr = take(8 * (N1 + 1));
+    const size_t o_rowptr = take(8 * (N1 + 1)), o_orowptr = take(8 * (N1 + 1));
     const size_t o_ou = take(4 * M), o_ov = take(4 * M), o_ow = take(4 * M);
     const size_t o_wcol = take(4 * M2), o_wwt = take(4 * M2), o_wrk = take(4 * M2);
-    const size_t o_scol = take(4 * M2), o_swt = take(4 * M2), o_srk = take(4 * M2);
-    const size_t o_ocol = take(4 * M2), o_owt = take(4 * M2), o_ork = take(4 * M2);
+    const size_t o_scol = take(4 * M2), o_swt = take(4 * M2);
+    const size_t o_ocol = take(4 * M), o_owt = take(4 * M), o_ork = take(4 * M);
     const size_t total = off;
 
     wtri_graph* g = new (std::nothrow) wtri_graph();
@@ -636,12 +452,11 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         return set_error(WTRI_ENOMEM, "device allocation of " + std::to_string(total) + " bytes failed");
     }
     char* B = (char*)g->base;
-    int32_t* deg = (int32_t*)(B + o_deg);
-    int32_t* odeg = (int32_t*)(B + o_odeg);
     int64_t* rowptr = (int64_t*)(B + o_rowptr);
+    int64_t* orowptr = (int64_t*)(B + o_orowptr);
     int32_t *ou = (int32_t*)(B + o_ou), *ov = (int32_t*)(B + o_ov), *ow = (int32_t*)(B + o_ow);
     int32_t *wcol = (int32_t*)(B + o_wcol), *wwt = (int32_t*)(B + o_wwt), *wrk = (int32_t*)(B + o_wrk);
-    int32_t *scol = (int32_t*)(B + o_scol), *swt = (int32_t*)(B + o_swt), *srk = (int32_t*)(B + o_srk);
+    int32_t *scol = (int32_t*)(B + o_scol), *swt = (int32_t*)(B + o_swt);
     int32_t *ocol = (int32_t*)(B + o_ocol), *owt = (int32_t*)(B + o_owt), *ork = (int32_t*)(B + o_ork);
 
     auto fail = [&](int rc) {
@@ -654,44 +469,37 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     BuildStatus* d_st = nullptr;
     BuildStatus h_st;
     Scratch st_buf(s);
-    if (cudaMallocAsync(&st_buf.p, sizeof(BuildStatus), s) != cudaSuccess)
+    if (cudaMallocAsync(&st_buf.p, sizeof(BuildStatus) + 64, s) != cudaSuccess)
         return fail(set_error(WTRI_ENOMEM, "status allocation failed"));
     d_st = (BuildStatus*)st_buf.p;
     {
-        BuildStatus init = {0u, 0, 0, 0, ~0ull};
+        static const BuildStatus init = {0u, 0, 0, 0, ~0ull};
         if (cudaMemcpyAsync(d_st, &init, sizeof(init), cudaMemcpyHostToDevice, s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "status init", __FILE__, __LINE__));
     }
+    const uint32_t* gate = &d_st->err;
 
     // 1. validation + max weight
     if (m > 0) {
-        ProfScope ps("validate", s, 12.0 * m, 1);
+        ProfScope ps("validate", s, 12.0 * m, 1);  // the COO input, read once
         k_validate<<<grid_for(m), BLK, 0, s>>>(n, m, u, v, w, d_st);
-    }
-    if (cudaMemcpyAsync(&h_st, d_st, sizeof(h_st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return fail(cuda_error(cudaGetLastError(), "validation", __FILE__, __LINE__));
-    if (h_st.err) {
-        std::string what = (h_st.err & DEV_ERR_RANGE) ? "vertex id outside [0, n)"
-                           : (h_st.err & DEV_ERR_SELF_LOOP) ? "self-loop"
-                                                            : "non-positive weight";
-        return fail(set_error(WTRI_EINVAL, "invalid edge " + std::to_string(h_st.first_bad) +
-                                               ": " + what));
     }
     g->d.n = n;
     g->d.m = m;
-    g->d.wmax = h_st.wmax;
+    g->d.wmax = 0;
     g->d.maxdeg = 0;
 
     if (m > 0) {
         // Scratch: two buffers of 16-byte records and one of 16-bit digits for
-        // 2m records, the radix counts, the row keys of the weight-sorted
-        // layout, long rows.
+        // 2m records (the record buffers are reused by the per-row sort of
+        // the longest rows), the radix counts, the row of each weight-sorted
+        // entry, 16-bit degrees, oriented out-degrees, the class lists.
         const int64_t n2 = 2 * m;
         const size_t rec_words = 4 * (size_t)n2 + 4;
         const size_t dig_words = ((size_t)n2 + 1) / 2 + 4;
         const size_t cnt_words = radix::scratch_words(n2);
-        const size_t words = 2 * rec_words + dig_words + cnt_words + (size_t)n2 + N1 + 8 + (N1 + 1) / 2 + 4;
+        const size_t words = 2 * rec_words + dig_words + cnt_words + (size_t)n2 + (N1 + 1) / 2 + 4 +
+                             N1 + 4 + N1 + 4 + 64;
         Scratch tmp(s);
         if (cudaMallocAsync(&tmp.p, words * 4, s) != cudaSuccess) {
             cudaGetLastError();
@@ -702,21 +510,27 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         uint16_t* dig = (uint16_t*)(rec_b + rec_words / 4);
         uint32_t* counts = (uint32_t*)dig + dig_words;
         int32_t* wrow = (int32_t*)(counts + cnt_words);
-        int32_t* row_list = wrow + n2;                    // long rows first, medium rows last
-        int32_t* row_counters = row_list + n;             // 8 words, see k_degrees
-        uint16_t* deg16 = (uint16_t*)(row_counters + 8);  // n half-words
-        if (cudaMemsetAsync(row_counters, 0, 32, s) != cudaSuccess)
+        uint8_t* deg8 = (uint8_t*)(wrow + n2);  // n bytes (room for 2n reserved)
+        int32_t* odeg = (int32_t*)(deg8 + 4 * ((N1 + 1) / 2 + 4));
+        int32_t* list = odeg + N1 + 4;
+        int32_t* small = list + N1 + 4;  // class counts, offsets, fill cursors, block-row cursor
+        int32_t* cls_cnt = small;
+        int32_t* cls_off = small + 16;
+        int32_t* cls_cur = small + 32;
+        int32_t* cursor = small + 48;
+        static_assert(rows::NCLS + 1 <= 16, "class arrays fit their 16-word slots");
+        if (cudaMemsetAsync(small, 0, 64 * 4, s) != cudaSuccess ||
+            cudaMemsetAsync(odeg, 0, 4 * N1, s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "memset", __FILE__, __LINE__));
 
-        // 2. edge order
-        const int wbits = radix::bit_length((uint64_t)(h_st.wmax - 1));
-        if (wbits == 0) {
-            ProfScope ps("edge_order_copy", s, 24.0 * m, 1);
-            k_copy_identity_order<<<grid_for(m), BLK, 0, s>>>(m, u, v, w, ou, ov, ow);
-        } else {
-            EdgeLoader el{u, v, w, h_st.wmax};
-            EdgeOrderStorer es{ou, ov, ow, h_st.wmax};
-            int rc = radix::lsd_sort(el, es, m, wbits, rec_a, rec_b, dig, counts, s, &d_st->err);
+        // 2. edge order (weights up to 31 bits; passes above the max weight's
+        //    bit length skip themselves)
+        {
+            EdgeLoader el{u, v, w};
+            EdgeOrderStorer es{ou, ov, ow};
+            // one read + one write of (edge id, weight): 16 B per edge
+            int rc = radix::lsd_sort_device_width(el, es, m, 31, &d_st->wmax, rec_a, rec_b, dig, counts,
+                                                  s, &d_st->err, 16.0 * m, 2);
             if (rc != WTRI_OK) return fail(rc);
         }
         // 3. weight-sorted rows (row key kept in wrow)
@@ -724,69 +538,83 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         {
             OrderEntryLoader ol{ou, ov, ow};
             RowsStorer rs{wrow, wcol, wwt, wrk};
-            int rc = radix::lsd_sort(ol, rs, n2, nbits, rec_a, rec_b, dig, counts, s, &d_st->err);
+            // one read + one write of (neighbour, weight, rank): 24 + 24 B per edge
+            int rc = radix::lsd_sort(ol, rs, n2, nbits, rec_a, rec_b, dig, counts, s, &d_st->err,
+                                     48.0 * m);
             if (rc != WTRI_OK) return fail(rc);
         }
-        // 4. row offsets, degrees, long rows
+        // 4. row offsets, degrees
         {
-            ProfScope ps("row_offsets", s, 4.0 * n2 + 8.0 * (n + 1) + 4.0 * n, 2);
-            k_rowptr_from_rows<<<grid_for(n2), BLK, 0, s>>>(n, n2, wrow, rowptr);
-            k_degrees<<<grid_for(n), BLK, 0, s>>>(n, rowptr, deg, deg16, d_st, row_list, row_counters);
+            ProfScope ps("row_offsets", s, 8.0 * (n + 1), 2, 4.0 * n2 + 8.0 * (n + 1) + 2.0 * n);
+            k_rowptr_from_rows<<<grid_for(n2), BLK, 0, s>>>(n, n2, wrow, rowptr, gate);
+            k_degrees<<<grid_for(n), BLK, 0, s>>>(n, rowptr, deg8, d_st);
         }
-        // 5. id-sorted rows
+        // 5. row classes by degree
         {
-            MirrorLoader ml{wrow, wcol, wwt, wrk};
-            RowsStorer rs{nullptr, scol, swt, srk};
-            int rc = radix::lsd_sort(ml, rs, n2, nbits, rec_a, rec_b, dig, counts, s, &d_st->err);
-            if (rc != WTRI_OK) return fail(rc);
+            ProfScope ps("orient_classes", s, 0.0, 3, 4.0 * n + 24.0 * n);
+            rows::k_class_count<<<grid_for(n, rows::NT), rows::NT, 0, s>>>(n, rowptr, cls_cnt, gate);
+            rows::k_class_offsets<<<1, 32, 0, s>>>(cls_cnt, cls_off, cls_cur, gate);
+            rows::k_class_fill<<<grid_for(n, rows::NT), rows::NT, 0, s>>>(n, rowptr, cls_cur, list, gate);
         }
-        // 6. orientation + repeated pairs
+        // 6. orientation of every entry (a bit each) and the oriented
+        //    out-degrees, their scan (the oriented row offsets), then the
+        //    per-row sort by id: the id-sorted rows and the oriented rows in
+        //    place.  Scratch: the record buffers, free once the radix sorts
+        //    are done (g0/g1: the hub rows' runs, 8 bytes per entry each, in
+        //    rec_a; the orientation bits in rec_b).
         {
+            // reads the weight-sorted rows once; writes the symmetric
+            // id-sorted rows (16 B per edge), the oriented rows (12 B per
+            // edge) and their offsets (8 B per vertex)
+            ProfScope ps("rows_sort", s, 16.0 * m + 12.0 * m + 8.0 * (n + 1), 0,
+                         8.0 * n2 + 0.125 * n2 + 24.0 * n2 + 16.0 * m + 12.0 * m + 8.0 * (n + 1));
+            unsigned long long* g0 = (unsigned long long*)rec_a;
+            unsigned long long* g1 = g0 + n2;
+            uint32_t* fwd = (uint32_t*)rec_b;
             {
-                ProfScope ps("orient_short", s, 0.0, 1);
-                k_orient_short<<<grid_for(n), BLK, 0, s>>>(n, rowptr, scol, swt, srk, deg16, deg, ocol,
-                                                           owt, ork, odeg, d_st);
+                ProfScope pf("rows_sort_fwd", s, 0.0, 1);
+                rows::k_fwd<<<grid_for(n2, rows::NT), rows::NT, 0, s>>>(n2, wrow, wcol, rowptr, deg8, fwd, odeg,
+                                                                        gate);
             }
-            // reads every id-sorted neighbour, weight and rank, writes m
-            // oriented entries and the out-degrees (bytes of both launches)
-            ProfScope ps("orient", s, 12.0 * n2 + 12.0 * m + 4.0 * n + 8.0 * (n + 1), 1);
-            // persistent: as many blocks as fit at once (rows are dealt by block and warp index)
-            static int per_sm = 0;
-            if (per_sm == 0 &&
-                (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_orient, OBLK, 0) != cudaSuccess ||
-                 per_sm < 1))
-                per_sm = 1;
-            k_orient<<<sm_count() * per_sm, OBLK, 0, s>>>(n, rowptr, scol, swt, srk, deg16, deg, ocol,
-                                                          owt, ork, odeg, row_list, row_counters, d_st);
+            WTRI_TRY(exclusive_scan_i32_to_i64(odeg, orowptr, n, s));
+            rows::RowsOut R{rowptr, wcol, wwt, wrk, deg8, scol, swt, fwd, orowptr, ocol, owt, ork,
+                            &d_st->err, &d_st->first_bad, list, cls_off};
+            const int64_t max_deg = std::min<int64_t>((int64_t)n - 1, m);
+            WTRI_TRY(sort_rows(R, g0, g1, cursor, max_deg, gate, s));
         }
         if (cudaGetLastError() != cudaSuccess)
             return fail(set_error(WTRI_ECUDA, "build kernel launch failed"));
-        if (cudaMemcpyAsync(&h_st, d_st, sizeof(h_st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
-            return fail(cuda_error(cudaGetLastError(), "build", __FILE__, __LINE__));
-        if (h_st.err & DEV_ERR_TIMEOUT)
-            return fail(set_error(WTRI_ETIMEOUT, "a bounded wait in the radix sort ran out"));
-        if (h_st.err & DEV_ERR_DUPLICATE) {
-            int32_t col[2] = {-1, -1};
-            const int64_t j = (int64_t)h_st.first_bad;
-            cudaMemcpyAsync(&col[0], scol + j, 4, cudaMemcpyDeviceToHost, s);
-            cudaStreamSynchronize(s);
-            return fail(set_error(WTRI_EINVAL, "repeated undirected pair: neighbour " +
-                                                   std::to_string(col[0]) +
-                                                   " appears twice in one row"));
-        }
-        g->d.maxdeg = h_st.maxdeg;
     } else {
         if (cudaMemsetAsync(rowptr, 0, 8 * (N1 + 1), s) != cudaSuccess ||
-            cudaMemsetAsync(deg, 0, 4 * N1, s) != cudaSuccess ||
-            cudaMemsetAsync(odeg, 0, 4 * N1, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
+            cudaMemsetAsync(orowptr, 0, 8 * (N1 + 1), s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "build", __FILE__, __LINE__));
     }
-
-    g->d.deg = deg;
-    g->d.odeg = odeg;
+    // The one host round trip: the status of every step.
+    if (cudaMemcpyAsync(&h_st, d_st, sizeof(h_st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(cuda_error(cudaGetLastError(), "build", __FILE__, __LINE__));
+    if (h_st.err & (DEV_ERR_RANGE | DEV_ERR_SELF_LOOP | DEV_ERR_WEIGHT)) {
+        std::string what = (h_st.err & DEV_ERR_RANGE) ? "vertex id outside [0, n)"
+                           : (h_st.err & DEV_ERR_SELF_LOOP) ? "self-loop"
+                                                            : "non-positive weight";
+        return fail(set_error(WTRI_EINVAL, "invalid edge " + std::to_string(h_st.first_bad) +
+                                               ": " + what));
+    }
+    if (h_st.err & DEV_ERR_TIMEOUT)
+        return fail(set_error(WTRI_ETIMEOUT, "a bounded wait in the radix sort ran out"));
+    if (h_st.err & DEV_ERR_DUPLICATE) {
+        int32_t col = -1;
+        const int64_t j = (int64_t)h_st.first_bad;
+        cudaMemcpyAsync(&col, scol + j, 4, cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        return fail(set_error(WTRI_EINVAL, "repeated undirected pair: neighbour " + std::to_string(col) +
+                                               " appears twice in one row"));
+    }
+    if (h_st.err) return fail(set_error(WTRI_ECUDA, "internal error in the build"));
+    g->d.wmax = h_st.wmax;
+    g->d.maxdeg = h_st.maxdeg;
     g->d.rowptr = rowptr;
+    g->d.orowptr = orowptr;
     g->d.ord_u = ou;
     g->d.ord_v = ov;
     g->d.ord_w = ow;
@@ -795,7 +623,6 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     g->d.wrk = wrk;
     g->d.scol = scol;
     g->d.swt = swt;
-    g->d.srk = srk;
     g->d.ocol = ocol;
     g->d.owt = owt;
     g->d.ork = ork;

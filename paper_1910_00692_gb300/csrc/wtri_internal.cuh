@@ -43,14 +43,17 @@ enum : uint32_t {
 
 // p codes (template parameter of the scoring kernels).  P_GEO is p = 0, the
 // geometric mean (Eq. 1's limit), ranked by the exact product of the weights.
-enum PCode : int { P_MIN = 0, P_ONE = 1, P_TWO = 2, P_MAX = 3, P_GEO = 4 };
-constexpr int P_COUNT = 5;
+// P_GEN is any other finite p (p = -1, the harmonic mean; p = 3; ...): no
+// exact 64-bit integer key exists there, so the key is the fp64 mean itself
+// (its bit pattern, which orders positive doubles like their values).
+enum PCode : int { P_MIN = 0, P_ONE = 1, P_TWO = 2, P_MAX = 3, P_GEO = 4, P_GEN = 5 };
+constexpr int P_COUNT = 6;
 // Phase-timer name of a query at p code P ("query_p=...").
 const char* query_name(int pcode);
 // Largest weight for which the product key of p = 0 fits 63 bits.
 constexpr int32_t GEO_WMAX = (1 << 21) - 1;
 
-int p_to_code(double p, int* code);
+int p_to_code(double p, int* code);  // any finite p (general p -> P_GEN)
 // p_to_code, and p = 0 only for graphs whose weights keep the product key exact.
 int p_to_code_for(double p, const wtri_graph* g, int* code);
 
@@ -59,21 +62,22 @@ int p_to_code_for(double p, const wtri_graph* g, int* code);
 // Layouts (r is an edge's position in the edge order: weight desc, input
 // index asc):
 //   ord_u/v/w[r]          edge order
-//   rowptr[n+1]           offsets of both symmetric layouts
+//   rowptr[n+1]           offsets of both symmetric layouts (degree d_x =
+//                         rowptr[x+1] - rowptr[x])
 //   wcol/wwt/wrk[2m]      per-vertex lists in edge order (weight-sorted)
-//   scol/swt/srk[2m]      per-vertex lists by neighbour id
-//   odeg[n]               oriented out-degree
-//   ocol/owt/ork[2m]      oriented lists by neighbour id: row x occupies
-//                         [rowptr[x], rowptr[x] + odeg[x]) (gaps after it)
+//   scol/swt[2m]          per-vertex lists by neighbour id
+//   orowptr[n+1]          offsets of the oriented lists
+//   ocol/owt/ork[m]       oriented lists by neighbour id: each edge once, at
+//                         its endpoint of lower (degree, id) rank
+// 64 bytes per edge and 16 per vertex.
 // ---------------------------------------------------------------------------
 struct DevGraph {
     int32_t n;
     int64_t m;
     int32_t wmax;
     int32_t maxdeg;
-    const int32_t* deg;
-    const int32_t* odeg;
     const int64_t* rowptr;
+    const int64_t* orowptr;
     const int32_t* ord_u;
     const int32_t* ord_v;
     const int32_t* ord_w;
@@ -82,7 +86,6 @@ struct DevGraph {
     const int32_t* wrk;
     const int32_t* scol;
     const int32_t* swt;
-    const int32_t* srk;
     const int32_t* ocol;
     const int32_t* owt;
     const int32_t* ork;
@@ -119,9 +122,10 @@ int build_graph(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const 
 
 // Exact top-k (wtri_topk.cu).  Writes device outputs; status (count or a
 // negative code) to d_count.  'retry_scale' enlarges the scratch buffers.
+// gp: the value of p for P_GEN (ignored otherwise).
 int topk_device(const wtri_graph* g, int pcode, int32_t k, wtri_tri* d_tris, double* d_weight,
                 int32_t* d_count, cudaStream_t stream, int retry_scale, int shard = 0,
-                int nshards = 1, unsigned long long* d_keys = nullptr);
+                int nshards = 1, unsigned long long* d_keys = nullptr, double gp = 0.0);
 
 // Edge sampling (wtri_topk.cu).
 int sample_topk_device(const wtri_graph* g, int pcode, int32_t k, int64_t nsamples,
@@ -130,6 +134,12 @@ int sample_topk_device(const wtri_graph* g, int pcode, int32_t k, int64_t nsampl
 // Only the draws: bitmap over edge-order positions (ceil(m/32) words).
 int sample_edges_device(const wtri_graph* g, int pcode, int64_t nsamples, uint64_t seed,
                         uint32_t* d_mark, cudaStream_t stream);
+
+// Weighted wedge sampling (wtri_wedge.cu), p codes P_GEO, P_ONE, P_TWO.
+int wedge_topk_device(const wtri_graph* g, int pcode, int32_t k, int64_t nsamples, uint64_t seed,
+                      wtri_tri* d_tris, double* d_weight, int32_t* d_count, cudaStream_t s);
+int wedge_draws_host(const wtri_graph* g, int pcode, int64_t nsamples, uint64_t seed, int32_t* center,
+                     int32_t* jb, int32_t* jc, int32_t* tri);
 
 // Batched top-k (wtri_batch.cu): host results, optional CUDA-graph capture.
 int topk_batch(const wtri_graph* const* gs, const int32_t* pcodes, const int32_t* ks, int32_t nq,
@@ -151,18 +161,27 @@ int topk_retry_host(const wtri_graph* g, int pcode, int32_t k, cudaStream_t s, w
                     double* hw, int32_t* count);
 
 // Phase timers / launch counter (wtri_prof.cu).  'bytes' is the phase's
-// algorithmic traffic; 'launches' the number of kernels it launches.
-void prof_begin(const char* name, cudaStream_t s, double bytes, int launches);
+// share of the algorithmic bytes; 'moved' the bytes its accesses move by
+// design (negative: the same as 'bytes'); 'launches' the number of kernels
+// it launches.
+void prof_begin(const char* name, cudaStream_t s, double bytes, int launches, double moved = -1.0);
 void prof_end(cudaStream_t s);
 void count_launches(int launches);  // launch counter only, no events
 
 struct ProfScope {
     cudaStream_t s;
-    ProfScope(const char* name, cudaStream_t st, double bytes, int launches) : s(st) {
-        prof_begin(name, st, bytes, launches);
+    ProfScope(const char* name, cudaStream_t st, double bytes, int launches, double moved = -1.0)
+        : s(st) {
+        prof_begin(name, st, bytes, launches, moved);
     }
     ~ProfScope() { prof_end(s); }
 };
+
+// Instrumented query byte counting (wtri_topk.cu): when on, the query
+// kernels add the bytes of every global load they issue on the adjacency
+// structures to a per-device counter.
+bool query_bytes_on();
+unsigned long long* query_bytes_counter();  // device address for the current device
 
 // Shared launch helpers.
 inline unsigned int ceil_div_u(int64_t a, int64_t b) { return (unsigned int)((a + b - 1) / b); }

@@ -1,11 +1,16 @@
 // Launch counting and CUDA-event phase timers.
 //
 // Every kernel launch of the library goes through prof_begin/prof_end with a
-// phase name, the number of launches it covers and the algorithmic bytes the
-// phase must move (what it reads and writes once, by construction).  When
-// timing is enabled the pair records CUDA events on the launching stream;
-// wtri_prof_read resolves them and reports per-phase calls, device time and
-// bytes.  The launch counter is always on (one atomic add per phase).
+// phase name, the number of launches it covers and two byte figures: the
+// phase's share of the path's algorithmic bytes (each input read once and
+// each resident output written once; a sort counts one read and one write of
+// its payload however many passes it takes, spread evenly over the passes,
+// and helper kernels such as histograms count none), and the bytes the
+// phase's own accesses move by its design (every pass of a sort reads and
+// writes its records).  When timing is enabled the pair records CUDA events
+// on the launching stream; wtri_prof_read / wtri_prof_read_ex resolve them
+// and report per-phase calls, device time and bytes.  The launch counter is
+// always on (one atomic add per phase).
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -27,12 +32,14 @@ struct Pending {
     std::string name;
     cudaEvent_t a, b;
     double bytes;
+    double moved;
 };
 
 struct Agg {
     long long calls = 0;
     double ms = 0.0;
     double bytes = 0.0;
+    double moved = 0.0;
 };
 
 std::mutex g_mu;
@@ -64,6 +71,7 @@ void resolve_locked() {
             a.calls++;
             a.ms += ms;
             a.bytes += p.bytes;
+            a.moved += p.moved;
         }
         g_free_events.push_back(p.a);
         g_free_events.push_back(p.b);
@@ -73,12 +81,13 @@ void resolve_locked() {
 
 }  // namespace
 
-void prof_begin(const char* name, cudaStream_t s, double bytes, int launches) {
+void prof_begin(const char* name, cudaStream_t s, double bytes, int launches, double moved) {
     g_launches.fetch_add(launches, std::memory_order_relaxed);
     if (!g_enabled.load(std::memory_order_relaxed)) return;
     Pending p;
     p.name = name;
     p.bytes = bytes;
+    p.moved = moved < 0 ? bytes : moved;
     p.a = get_event();
     p.b = get_event();
     cudaEventRecord(p.a, s);
@@ -112,8 +121,8 @@ WTRI_API void wtri_prof_reset(void) {
 
 WTRI_API long long wtri_launch_count(void) { return g_launches.load(); }
 
-WTRI_API int wtri_prof_read(int idx, char* name, int name_cap, long long* calls, double* ms,
-                            double* bytes) {
+WTRI_API int wtri_prof_read_ex(int idx, char* name, int name_cap, long long* calls, double* ms,
+                               double* bytes, double* moved) {
     std::lock_guard<std::mutex> lk(g_mu);
     resolve_locked();
     if (idx < 0 || idx >= (int)g_agg.size()) return WTRI_ENOTFOUND;
@@ -126,7 +135,13 @@ WTRI_API int wtri_prof_read(int idx, char* name, int name_cap, long long* calls,
     if (calls) *calls = it->second.calls;
     if (ms) *ms = it->second.ms;
     if (bytes) *bytes = it->second.bytes;
+    if (moved) *moved = it->second.moved;
     return WTRI_OK;
+}
+
+WTRI_API int wtri_prof_read(int idx, char* name, int name_cap, long long* calls, double* ms,
+                            double* bytes) {
+    return wtri_prof_read_ex(idx, name, name_cap, calls, ms, bytes, nullptr);
 }
 
 }  // extern "C"

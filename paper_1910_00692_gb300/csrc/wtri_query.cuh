@@ -98,7 +98,33 @@ struct Query {
     // Wedges an edge's thread scans before deferring the rest to a block (the
     // boundary between the short-list and long-list strategies).
     int32_t t_short;
+    // Instrumented run: bytes of the adjacency loads are added here (null:
+    // no counting).
+    unsigned long long* qbytes;
+    // The value of p for P_GEN queries.
+    double gp;
+    // Polls of the first wait for a staged row (WAIT_LIMIT in production;
+    // tests lower it to take the timeout path).
+    uint32_t wait_first;
 };
+
+// Bytes of adjacency loads issued by one thread (instrumented runs only).
+struct Tally {
+    unsigned long long n = 0;
+    bool on = false;
+    __device__ __forceinline__ void add(uint32_t b) {
+        if (on) n += b;
+    }
+};
+
+// Adds every lane's tally to the query's counter (one atomic per warp).
+__device__ __forceinline__ void flush_tally(const Query& q, const Tally& t) {
+    if (!q.qbytes) return;
+    unsigned long long v = t.n;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(q.qbytes, v);
+}
 
 constexpr int SHARD_SHIFT = 10;  // 1024-edge chunks of the edge order, dealt round-robin
 
@@ -116,14 +142,44 @@ __device__ __forceinline__ bool owns(const Query& q, int32_t r, int32_t rxc, int
     return !(rxc < r && drawn(q, rxc)) && !(ryc < r && drawn(q, ryc));
 }
 
+// m_p of Eq. 1 in fp64 for a finite p outside {0, 1, 2}: the weights in
+// ascending order (equal multisets give equal bits), scaled by the largest
+// (p > 0) or the smallest (p < 0) so that no power overflows:
+//   m_p = s * (((a/s)^p + (b/s)^p + (c/s)^p) / 3)^(1/p).
+__device__ __forceinline__ double general_mean(double p, uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t t;
+    if (a > b) { t = a; a = b; b = t; }
+    if (b > c) { t = b; b = c; c = t; }
+    if (a > b) { t = a; a = b; b = t; }
+    const double s = p > 0 ? (double)c : (double)a;
+    const double m = (pow((double)a / s, p) + pow((double)b / s, p) + pow((double)c / s, p)) / 3.0;
+    return s * pow(m, 1.0 / p);
+}
+
+// Ranking key of a triangle with edge weights a, b, c: exact integers for
+// p in {-inf, 0, 1, 2, +inf}; the mean's fp64 bit pattern for P_GEN.
 template <int P>
-__device__ __forceinline__ unsigned long long keyof(uint32_t a, uint32_t b, uint32_t c) {
+__device__ __forceinline__ unsigned long long keyof(uint32_t a, uint32_t b, uint32_t c,
+                                                    double gp = 0.0) {
     if (P == P_ONE) return (unsigned long long)a + b + c;
     if (P == P_TWO)
         return (unsigned long long)a * a + (unsigned long long)b * b + (unsigned long long)c * c;
     if (P == P_MAX) return (unsigned long long)max(a, max(b, c));
     if (P == P_GEO) return (unsigned long long)a * b * c;  // weights < 2^21: below 2^63
+    if (P == P_GEN) return (unsigned long long)__double_as_longlong(general_mean(gp, a, b, c));
     return (unsigned long long)min(a, min(b, c));
+}
+
+// Upper bound used for pruning: the key itself for the exact keys; for
+// P_GEN the mean raised by a relative 1e-12, far above fp64 rounding, so
+// that a bound computed for larger weights is never below a key computed
+// for smaller ones.
+template <int P>
+__device__ __forceinline__ unsigned long long boundof(uint32_t a, uint32_t b, uint32_t c,
+                                                      double gp = 0.0) {
+    if (P == P_GEN)
+        return (unsigned long long)__double_as_longlong(general_mean(gp, a, b, c) * (1.0 + 1e-12));
+    return keyof<P>(a, b, c);
 }
 
 __device__ __forceinline__ void sort3(int32_t& a, int32_t& b, int32_t& c) {
@@ -137,16 +193,18 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
     return *(volatile const unsigned long long*)p;
 }
 
-// Position just after edge r's own entry in x's weight-sorted list.
-__device__ __forceinline__ int64_t suffix_start(const DevGraph& G, int32_t x, int32_t r,
-                                                uint32_t* err) {
-    int64_t lo = G.rowptr[x], hi = G.rowptr[x + 1];
+// Position just after edge r's own entry in x's weight-sorted list
+// [lo, hi) (x's row).
+__device__ __forceinline__ int64_t suffix_start(const DevGraph& G, int64_t lo, int64_t hi, int32_t r,
+                                                uint32_t* err, Tally& tb) {
     const int64_t end = hi;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
+        tb.add(4);
         if (__ldg(G.wrk + mid) < r) lo = mid + 1;
         else hi = mid;
     }
+    tb.add(4);
     if (lo >= end || __ldg(G.wrk + lo) != r) {
         atomicOr(err, DEV_ERR_INTERNAL);
         return end;
@@ -155,23 +213,27 @@ __device__ __forceinline__ int64_t suffix_start(const DevGraph& G, int32_t x, in
 }
 
 // Closing edge (y, c) in the oriented lists: stored once, at the endpoint of
-// lower (degree, id) rank, rows ascending by id (row s starts at rowptr[s]
-// and holds odeg[s] entries).
-__device__ __forceinline__ bool probe_oriented(const DevGraph& G, int32_t y, int32_t dy, int32_t c,
-                                               int32_t& wyc, int32_t& ryc) {
-    const int32_t dc = __ldg(G.deg + c);
+// lower (degree, id) rank, rows ascending by id (row s at
+// [orowptr[s], orowptr[s+1])).
+__device__ __forceinline__ bool probe_oriented(const DevGraph& G, int32_t y, int64_t dy, int32_t c,
+                                               int32_t& wyc, int32_t& ryc, Tally& tb) {
+    const int64_t dc = __ldg(G.rowptr + c + 1) - __ldg(G.rowptr + c);
     const bool ylow = dy < dc || (dy == dc && y < c);
     const int32_t s = ylow ? y : c, t = ylow ? c : y;
-    int64_t lo = __ldg(G.rowptr + s), hi = lo + __ldg(G.odeg + s);
+    int64_t lo = __ldg(G.orowptr + s), hi = __ldg(G.orowptr + s + 1);
     const int64_t end = hi;
+    tb.add(32);
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
+        tb.add(4);
         if (__ldg(G.ocol + mid) < t) lo = mid + 1;
         else hi = mid;
     }
+    if (lo < end) tb.add(4);
     if (lo < end && __ldg(G.ocol + lo) == t) {
         wyc = __ldg(G.owt + lo);
         ryc = __ldg(G.ork + lo);
+        tb.add(8);
         return true;
     }
     return false;
@@ -203,20 +265,22 @@ __device__ __forceinline__ void append(const Query& q, unsigned long long key, i
 template <int P, bool SAMPLED>
 __device__ __forceinline__ void scan_wedges(const DevGraph& G, const Query& q,
                                             unsigned long long tau, int32_t r, uint32_t w,
-                                            int32_t x, int32_t y, int32_t dy, uint32_t ymax,
-                                            int64_t& j, int64_t jstop, bool& done) {
+                                            int32_t x, int32_t y, int64_t dy, uint32_t ymax,
+                                            int64_t& j, int64_t jstop, bool& done, Tally& tb) {
     for (; j < jstop; j++) {
         const uint32_t wxc = (uint32_t)__ldg(G.wwt + j);
-        if (keyof<P>(w, wxc, ymax) < tau) {  // wedge bound, non-increasing along the list
+        tb.add(4);
+        if (boundof<P>(w, wxc, ymax, q.gp) < tau) {  // wedge bound, non-increasing along the list
             done = true;
             return;
         }
         const int32_t c = __ldg(G.wcol + j);
+        tb.add(4);
         if (SAMPLED && c == y) continue;  // the edge itself (full rows in sampled mode)
         int32_t wyc, ryc;
-        if (probe_oriented(G, y, dy, c, wyc, ryc) &&
-            owns<SAMPLED>(q, r, __ldg(G.wrk + j), ryc)) {
-            const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc);
+        if (probe_oriented(G, y, dy, c, wyc, ryc, tb) &&
+            (tb.add(4), owns<SAMPLED>(q, r, __ldg(G.wrk + j), ryc))) {
+            const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc, q.gp);
             if (key >= tau) {
                 int32_t a = x, b = y, cc = c;
                 sort3(a, b, cc);
@@ -230,10 +294,11 @@ __device__ __forceinline__ void scan_wedges(const DevGraph& G, const Query& q,
 // edge's).
 template <int P, bool SAMPLED>
 __device__ __forceinline__ bool process_edge(const DevGraph& G, const Query& q,
-                                             unsigned long long tau, int32_t idx) {
+                                             unsigned long long tau, int32_t idx, Tally& tb) {
     const int32_t r = SAMPLED ? __ldg(q.slist + idx) : idx;
     const uint32_t w = (uint32_t)__ldg(G.ord_w + r);
-    if (!SAMPLED && keyof<P>(w, w, w) < tau) {
+    tb.add(4);
+    if (!SAMPLED && boundof<P>(w, w, w, q.gp) < tau) {
         // every later edge has a bound no larger: record the first such edge
         atomicMax(&q.st->stop_rev, STOP_NONE - (uint32_t)r);
         return false;
@@ -242,24 +307,27 @@ __device__ __forceinline__ bool process_edge(const DevGraph& G, const Query& q,
         (int32_t)(((uint32_t)r >> SHARD_SHIFT) % (uint32_t)q.nshards) != q.shard)
         return true;  // owned by another shard
     const int32_t u = __ldg(G.ord_u + r), v = __ldg(G.ord_v + r);
+    const int64_t bu = __ldg(G.rowptr + u), eu = __ldg(G.rowptr + u + 1);
+    const int64_t bv = __ldg(G.rowptr + v), ev = __ldg(G.rowptr + v + 1);
+    tb.add(40);
     // Exact mode scans what comes after r in each list; sampled mode scans
     // whole lists (the other two edges may be heavier than a drawn edge).
-    const int64_t su = SAMPLED ? __ldg(G.rowptr + u) : suffix_start(G, u, r, &q.st->err);
-    const int64_t sv = SAMPLED ? __ldg(G.rowptr + v) : suffix_start(G, v, r, &q.st->err);
-    const int64_t eu = __ldg(G.rowptr + u + 1), ev = __ldg(G.rowptr + v + 1);
+    const int64_t su = SAMPLED ? bu : suffix_start(G, bu, eu, r, &q.st->err, tb);
+    const int64_t sv = SAMPLED ? bv : suffix_start(G, bv, ev, r, &q.st->err, tb);
     if (su >= eu || sv >= ev) return true;  // no edge after r on one side: owns nothing
     const uint32_t umax = (uint32_t)__ldg(G.wwt + su), vmax = (uint32_t)__ldg(G.wwt + sv);
-    if (keyof<P>(w, umax, vmax) < tau) return true;  // edge bound
+    tb.add(8);
+    if (boundof<P>(w, umax, vmax, q.gp) < tau) return true;  // edge bound
     // Scan the shorter suffix; probe the other endpoint.
     const bool xu = (eu - su) <= (ev - sv);
     const int32_t x = xu ? u : v, y = xu ? v : u;
     const int64_t sx = xu ? su : sv, ex = xu ? eu : ev;
     const uint32_t ymax = xu ? vmax : umax;
-    const int32_t dy = __ldg(G.deg + y);
+    const int64_t dy = xu ? ev - bv : eu - bu;
     int64_t j = sx;
     bool done = false;
     scan_wedges<P, SAMPLED>(G, q, tau, r, w, x, y, dy, ymax, j, min(ex, sx + (int64_t)q.t_short),
-                            done);
+                            done, tb);
     if (!done && j < ex) {
         const uint32_t slot = atomicAdd(q.long_count, 1u);
         if (slot < q.long_cap) {
@@ -275,7 +343,7 @@ __device__ __forceinline__ bool process_edge(const DevGraph& G, const Query& q,
             q.longs[slot] = it;
         } else {
             // Deferred list full: finish the scan here.
-            scan_wedges<P, SAMPLED>(G, q, tau, r, w, x, y, dy, ymax, j, ex, done);
+            scan_wedges<P, SAMPLED>(G, q, tau, r, w, x, y, dy, ymax, j, ex, done, tb);
         }
     }
     return true;
@@ -289,10 +357,13 @@ __global__ void __launch_bounds__(RBLK) k_round(DevGraph G, Query q, int64_t lo,
     if (lo >= (int64_t)(STOP_NONE - *stop_rev)) return;
     const unsigned long long tau = ld_volatile_u64(&q.st->tau);
     const int64_t stride = (int64_t)gridDim.x * RBLK;
+    Tally tb;
+    tb.on = q.qbytes != nullptr;
     for (int64_t r64 = lo + (int64_t)blockIdx.x * RBLK + threadIdx.x; r64 < hi; r64 += stride) {
         if (r64 >= (int64_t)(STOP_NONE - *stop_rev)) break;
-        if (!process_edge<P, SAMPLED>(G, q, tau, (int32_t)r64)) break;
+        if (!process_edge<P, SAMPLED>(G, q, tau, (int32_t)r64, tb)) break;
     }
+    flush_tally(q, tb);
 }
 
 // Grid of a round: a few resident blocks per SM, striding over the range.
@@ -341,10 +412,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
 }
 
 // Stages y's id-sorted row in shared memory with one bulk copy (bounded
-// wait).  Returns false if the wait ran out (error recorded).
+// wait: at most `limit` polls; a limit of 0 does not wait at all, which
+// tests use to take the timeout path on purpose).  Returns false if the
+// wait ran out (error recorded); the copy in flight is then drained with the
+// full WAIT_LIMIT before the block goes on, so no copy outlives its block.
 __device__ __forceinline__ bool stage_row(const DevGraph& G, int64_t ybeg, int32_t dy,
                                           int32_t* srow, uint64_t* bar, uint32_t& phase,
-                                          int32_t& off, uint32_t* err, int* timed_out) {
+                                          int32_t& off, uint32_t* err, int* timed_out,
+                                          uint32_t limit) {
     // 16-byte aligned source: round the start down, the size up (the id
     // array has 16 bytes of slack after its end).
     const int64_t a0 = ybeg & ~int64_t(3);
@@ -355,20 +430,23 @@ __device__ __forceinline__ bool stage_row(const DevGraph& G, int64_t ybeg, int32
         mbar_expect_tx(bar, bytes);
         bulk_g2s(srow, G.scol + a0, bytes, bar);
     }
-    uint32_t spins = 0;
-    while (!mbar_try_wait(bar, phase)) {
-        if (++spins >= WAIT_LIMIT) {
-            atomicOr(err, DEV_ERR_TIMEOUT);
-            *timed_out = 1;
+    bool landed = false;
+    for (uint32_t spins = 0; spins < limit; spins++) {
+        if (mbar_try_wait(bar, phase)) {
+            landed = true;
             break;
         }
     }
+    if (!landed) {
+        atomicOr(err, DEV_ERR_TIMEOUT);
+        *timed_out = 1;
+    }
+    const uint32_t cur = phase;
     phase ^= 1u;
     __syncthreads();
     if (*timed_out) {
-        // Give the copy a second bounded chance to land before exit.
         uint32_t s2 = 0;
-        while (!mbar_try_wait(bar, phase ^ 1u) && ++s2 < WAIT_LIMIT) {
+        while (!mbar_try_wait(bar, cur) && ++s2 < WAIT_LIMIT) {
         }
         return false;
     }
@@ -381,7 +459,7 @@ __device__ __forceinline__ bool stage_row(const DevGraph& G, int64_t ybeg, int32
 template <int P, bool SAMPLED>
 __device__ __forceinline__ void long_scan(const DevGraph& G, const Query& q, unsigned long long tau,
                                           const LongItem& item, const int32_t* srow, int32_t off,
-                                          int64_t ybeg, int32_t dy, bool staged) {
+                                          int64_t ybeg, int64_t dy, bool staged, Tally& tb) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t w = (uint32_t)item.w, ymax = (uint32_t)item.ymax;
     const int32_t x = item.x, y = item.y, r = item.r;
@@ -391,12 +469,14 @@ __device__ __forceinline__ void long_scan(const DevGraph& G, const Query& q, uns
         uint32_t wxc = 0;
         if (j < item.j1) {
             wxc = (uint32_t)__ldg(G.wwt + j);
-            live = keyof<P>(w, wxc, ymax) >= tau;
+            tb.add(4);
+            live = boundof<P>(w, wxc, ymax, q.gp) >= tau;
         }
         if (__ballot_sync(0xffffffffu, live) == 0) break;
         int32_t c = 0;
         if (live) {
             c = __ldg(G.wcol + j);
+            tb.add(4);
             if (SAMPLED && c == y) live = false;  // the edge itself
         }
         if (live) {
@@ -412,13 +492,21 @@ __device__ __forceinline__ void long_scan(const DevGraph& G, const Query& q, uns
                 if (lo < dy && srow[off + lo] == c) {
                     found = true;
                     wyc = __ldg(G.swt + ybeg + lo);
-                    ryc = __ldg(G.srk + ybeg + lo);
+                    tb.add(4);
+                    // (y, c) lighter than r comes after r in the edge order;
+                    // otherwise its position decides, from the oriented row
+                    if ((uint32_t)wyc < w) {
+                        ryc = INT32_MAX;
+                    } else {
+                        int32_t w2 = 0;
+                        probe_oriented(G, y, dy, c, w2, ryc, tb);
+                    }
                 }
             } else {
-                found = probe_oriented(G, y, dy, c, wyc, ryc);
+                found = probe_oriented(G, y, dy, c, wyc, ryc, tb);
             }
-            if (found && owns<SAMPLED>(q, r, __ldg(G.wrk + j), ryc)) {
-                const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc);
+            if (found && (tb.add(4), owns<SAMPLED>(q, r, __ldg(G.wrk + j), ryc))) {
+                const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc, q.gp);
                 if (key >= tau) {
                     int32_t a = x, b = y, cc = c;
                     sort3(a, b, cc);
@@ -463,17 +551,22 @@ __global__ void __launch_bounds__(LBLK) k_long(DevGraph G, Query q) {
     }
     __syncthreads();
     uint32_t phase = 0;
+    Tally tb;
+    tb.on = q.qbytes != nullptr;
     for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
         const LongItem item = q.longs[it];
         const int64_t ybeg = __ldg(G.rowptr + item.y), yend = __ldg(G.rowptr + item.y + 1);
         const int32_t dy = (int32_t)(yend - ybeg);
         const bool staged = dy <= STAGE_MAX;
         int32_t off = 0;
-        if (staged && !stage_row(G, ybeg, dy, srow, &bar, phase, off, &q.st->err, &timed_out))
-            return;
-        long_scan<P, SAMPLED>(G, q, tau, item, srow, off, ybeg, dy, staged);
+        if (staged && !stage_row(G, ybeg, dy, srow, &bar, phase, off, &q.st->err, &timed_out,
+                                 q.wait_first))
+            break;
+        if (staged && threadIdx.x == 0) tb.add((uint32_t)dy * 4u);  // the staged row
+        long_scan<P, SAMPLED>(G, q, tau, item, srow, off, ybeg, dy, staged, tb);
         __syncthreads();  // the staged row is reused by the next item
     }
+    flush_tally(q, tb);
 }
 
 // ---------------------------------------------------------------------------
@@ -791,6 +884,7 @@ __device__ __forceinline__ void rank_one(const Query& q, uint32_t i, wtri_tri* o
         if (P == P_ONE) val = (double)ki / 3.0;
         else if (P == P_TWO) val = sqrt((double)ki / 3.0);
         else if (P == P_GEO) val = cbrt((double)ki);
+        else if (P == P_GEN) val = __longlong_as_double((long long)ki);
         else val = (double)ki;
         out_w[rank] = val;
         if (out_key) out_key[rank] = ki;

@@ -17,7 +17,16 @@
 //           uint4 grec(int64_t i)       from global memory
 //           uint32_t key(int64_t i)     (first-pass histogram)
 //           bool tma_ok()               sources 16-byte aligned
-//   Storer: void store(int64_t p, const uint4& rec); double rec_bytes()
+//   Storer: void store(int64_t p, const uint4& rec); double rec_bytes();
+//           void prepare()          once per CTA before the first store
+//
+// Gating: every kernel of a pass first reads the device status word and
+// returns at once if an earlier step reported an error, so a build needs no
+// host round trip between its steps.  A pass may also be conditional on the
+// largest key: with g.glo > 0 it runs only if some key has a bit at or above
+// g.glo (bit length of *g.gwmax), which lets a sort over keys whose width is
+// only known on the device launch the widest plan and skip the passes it
+// does not need.
 //
 // Three kernels per pass: per-chunk digit histograms (upsweep), a per-digit
 // scan over chunks, and the scatter.  The scatter streams its chunk tile by
@@ -102,7 +111,20 @@ struct PassGeom {
     int bins;         // 1 << digit bits
     int bits;
     uint32_t mask;
+    const uint32_t* gerr;   // status word: nonzero -> skip (may be null)
+    const int32_t* gwmax;   // largest key value (conditional passes; may be null)
+    int glo;                // conditional pass: runs iff bit_length(*gwmax) > glo
 };
+
+__device__ __forceinline__ bool pass_closed(const PassGeom& g) {
+    if (g.gerr && *(volatile const uint32_t*)g.gerr) return true;
+    if (g.glo > 0 && g.gwmax) {
+        const int32_t wm = *(volatile const int32_t*)g.gwmax;
+        const int B = wm > 0 ? 32 - __clz(wm) : 0;
+        if (g.glo >= B) return true;
+    }
+    return false;
+}
 
 // ---- histogram sources ------------------------------------------------------
 template <class Loader>
@@ -125,6 +147,7 @@ struct StoredDigits {  // later passes: 16-bit digits written by the previous sc
 // Stored digits are read eight at a time (one 16-byte load).
 template <class Dig>
 __global__ void __launch_bounds__(NT) k_upsweep(Dig dg, PassGeom g, uint32_t* counts) {
+    if (pass_closed(g)) return;
     __shared__ uint32_t hist[NW][MAX_BINS];
     const int w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < NW * MAX_BINS; i += NT) (&hist[0][0])[i] = 0;
@@ -173,7 +196,9 @@ __global__ void __launch_bounds__(NT) k_upsweep(Dig dg, PassGeom g, uint32_t* co
 }
 
 // Block d: exclusive scan of counts[d][0..G) in place; totals[d] = sum.
-__global__ void __launch_bounds__(NT) k_digit_scan(uint32_t* counts, int chunks, uint32_t* totals) {
+__global__ void __launch_bounds__(NT) k_digit_scan(uint32_t* counts, int chunks, uint32_t* totals,
+                                                   PassGeom g) {
+    if (pass_closed(g)) return;
     __shared__ uint32_t warp_tot[NW];
     __shared__ uint32_t tot;
     uint32_t* c = counts + (int64_t)blockIdx.x * chunks;
@@ -408,11 +433,14 @@ __device__ __forceinline__ void scatter_tile(const uint4 (&rec)[IT], int tcount,
 // loads.  Waits are bounded: on timeout the pass sets DEV_ERR_TIMEOUT, gives
 // copies in flight a bounded chance to land and the CTA returns.
 template <class Loader, class Storer, bool USE_BULK>
-__global__ void __launch_bounds__(NT, CTAS_PER_SM) k_scatter(Loader ld, Storer st, PassGeom g,
+__global__ void __launch_bounds__(NT, CTAS_PER_SM) k_scatter(Loader ld, Storer st_in, PassGeom g,
                                                            const uint32_t* counts,
                                                            const uint32_t* totals, uint32_t* err) {
+    if (pass_closed(g)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(smem_raw);
+    Storer st = st_in;
+    st.prepare();
     uint32_t run[DPT];
     {   // global start of this chunk's records of each digit
         uint32_t t[DPT], sum = 0;
@@ -515,9 +543,32 @@ struct AosStorer {
     int next_shift;
     uint32_t next_mask;
     __host__ __device__ double rec_bytes() const { return 18.0; }
+    __device__ __forceinline__ void prepare() {}
     __device__ __forceinline__ void store(int64_t p, const uint4& x) const {
         r[p] = x;
         dig[p] = (uint16_t)((x.x >> next_shift) & next_mask);
+    }
+};
+
+// A pass whose output is either the final arrays or the next pass's records:
+// final iff the following pass is skipped (see PassGeom::glo), decided once
+// per CTA from the device-side key width.
+template <class Final>
+struct SwitchStorer {
+    Final fin;
+    AosStorer mid;
+    const int32_t* gwmax;
+    int next_lo;   // lowest key bit of the following pass
+    bool is_final;
+    __host__ __device__ double rec_bytes() const { return mid.rec_bytes(); }
+    __device__ __forceinline__ void prepare() {
+        const int32_t wm = *(volatile const int32_t*)gwmax;
+        const int B = wm > 0 ? 32 - __clz(wm) : 0;
+        is_final = next_lo >= B;
+    }
+    __device__ __forceinline__ void store(int64_t p, const uint4& x) const {
+        if (is_final) fin.store(p, x);
+        else mid.store(p, x);
     }
 };
 
@@ -538,6 +589,9 @@ inline PassGeom make_geom(int64_t n, int shift, int bits) {
     g.bins = 1 << bits;
     g.bits = bits;
     g.mask = (uint32_t)g.bins - 1u;
+    g.gerr = nullptr;
+    g.gwmax = nullptr;
+    g.glo = 0;
     return g;
 }
 
@@ -570,23 +624,25 @@ inline int pass_shift(int bits, int p) {
     return s;
 }
 
+// alg_bytes: this pass's share of the sort's algorithmic bytes (the
+// scatter's phase timer; histograms and scans declare none).
 template <class Dig, class Loader, class Storer>
 int run_pass(const Dig& dg, const Loader& ld, const Storer& st, const PassGeom& g, uint32_t* scratch,
-             cudaStream_t s, uint32_t* err, double hist_bytes) {
+             cudaStream_t s, uint32_t* err, double hist_bytes, double alg_bytes) {
     if (g.n <= 0) return WTRI_OK;
     uint32_t* counts = scratch;
     uint32_t* totals = scratch + (size_t)MAX_BINS * g.chunks;
     {
-        ProfScope ps("radix_upsweep", s, hist_bytes * (double)g.n + 4.0 * g.bins * g.chunks, 1);
+        ProfScope ps("radix_upsweep", s, 0.0, 1, hist_bytes * (double)g.n + 4.0 * g.bins * g.chunks);
         WTRI_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)g.bins * g.chunks, s));
         k_upsweep<Dig><<<g.chunks * UP_SPLIT, NT, 0, s>>>(dg, g, counts);
     }
     {
-        ProfScope ps("radix_digit_scan", s, 8.0 * g.bins * g.chunks, 1);
-        k_digit_scan<<<g.bins, NT, 0, s>>>(counts, g.chunks, totals);
+        ProfScope ps("radix_digit_scan", s, 0.0, 1, 8.0 * g.bins * g.chunks);
+        k_digit_scan<<<g.bins, NT, 0, s>>>(counts, g.chunks, totals, g);
     }
     const size_t smem = sizeof(ScatterSmem);
-    ProfScope ps("radix_downsweep", s, (double)g.n * (Loader::REC_BYTES + st.rec_bytes()), 1);
+    ProfScope ps("radix_downsweep", s, alg_bytes, 1, (double)g.n * (Loader::REC_BYTES + st.rec_bytes()));
     if (bulk_enabled() && ld.tma_ok()) {
         static std::atomic<uint64_t> done{0};  // per instantiation and device
         WTRI_TRY(smem_optin((const void*)k_scatter<Loader, Storer, true>, (int)smem, done));
@@ -603,16 +659,20 @@ int run_pass(const Dig& dg, const Loader& ld, const Storer& st, const PassGeom& 
 // Full stable LSD sort of n records over 'bits' key bits: first pass from
 // 'first', middle passes through the 16-byte record buffers rec_a / rec_b
 // (n records each) with digits in 'dig' (n 16-bit words), last pass into
-// 'last'.
+// 'last'.  alg_total: the sort's algorithmic bytes (one read and one write
+// of its payload), spread evenly over its passes' scatters.  Every kernel
+// returns at once while *err is nonzero.
 template <class First, class Last>
 int lsd_sort(const First& first, const Last& last, int64_t n, int bits, uint4* rec_a, uint4* rec_b,
-             uint16_t* dig, uint32_t* scratch, cudaStream_t s, uint32_t* err) {
+             uint16_t* dig, uint32_t* scratch, cudaStream_t s, uint32_t* err, double alg_total) {
     const int passes = pass_count(bits);
     if (passes == 0) return set_error(WTRI_EINVAL, "internal: zero-pass sort");
+    const double alg = alg_total / passes;
     uint4* cur = rec_a;
     uint4* nxt = rec_b;
     for (int p = 0; p < passes; p++) {
-        const PassGeom g = make_geom(n, pass_shift(bits, p), pass_bits(bits, p));
+        PassGeom g = make_geom(n, pass_shift(bits, p), pass_bits(bits, p));
+        g.gerr = err;
         AosStorer as{nxt, dig, 0, 0u};
         if (p + 1 < passes) {
             as.next_shift = pass_shift(bits, p + 1);
@@ -623,16 +683,65 @@ int lsd_sort(const First& first, const Last& last, int64_t n, int bits, uint4* r
         if (p == 0) {
             KeyDigits<First> kd{first, g.shift, g.mask};
             if (passes == 1) {
-                WTRI_TRY(run_pass(kd, first, last, g, scratch, s, err, 4.0));
+                WTRI_TRY(run_pass(kd, first, last, g, scratch, s, err, 4.0, alg));
             } else {
-                WTRI_TRY(run_pass(kd, first, as, g, scratch, s, err, 4.0));
+                WTRI_TRY(run_pass(kd, first, as, g, scratch, s, err, 4.0, alg));
             }
         } else if (p == passes - 1) {
-            WTRI_TRY(run_pass(sd, al, last, g, scratch, s, err, 2.0));
+            WTRI_TRY(run_pass(sd, al, last, g, scratch, s, err, 2.0, alg));
         } else {
-            WTRI_TRY(run_pass(sd, al, as, g, scratch, s, err, 2.0));
+            WTRI_TRY(run_pass(sd, al, as, g, scratch, s, err, 2.0, alg));
         }
         if (p + 1 < passes) std::swap(cur, nxt);
+    }
+    return WTRI_OK;
+}
+
+// The same sort for keys whose width is known only on the device: the key's
+// largest value is *wmax (written by an earlier kernel on the stream).  The
+// plan covers max_bits in digits of MAX_BITS (pass p: bits [10p, 10p+10));
+// pass p > 0 runs only if a key has a bit at or above 10p, and each pass
+// writes the final arrays when the next one will not run.  alg_total is
+// spread over the passes the widest keys need (the phase timers see what
+// runs).
+template <class First, class Last>
+int lsd_sort_device_width(const First& first, const Last& last, int64_t n, int max_bits,
+                          const int32_t* wmax, uint4* rec_a, uint4* rec_b, uint16_t* dig,
+                          uint32_t* scratch, cudaStream_t s, uint32_t* err, double alg_total,
+                          int expected_passes) {
+    const int passes = (max_bits + MAX_BITS - 1) / MAX_BITS;
+    const double alg = alg_total / std::max(1, expected_passes);
+    uint4* cur = rec_a;
+    uint4* nxt = rec_b;
+    for (int p = 0; p < passes; p++) {
+        const int shift = p * MAX_BITS;
+        const int bits = std::min(MAX_BITS, max_bits - shift);
+        PassGeom g = make_geom(n, shift, bits);
+        g.gerr = err;
+        g.gwmax = wmax;
+        g.glo = shift;  // pass 0 always runs (glo = 0)
+        AosStorer as{nxt, dig, 0, 0u};
+        if (p + 1 < passes) {
+            as.next_shift = shift + MAX_BITS;
+            as.next_mask = (1u << std::min(MAX_BITS, max_bits - shift - MAX_BITS)) - 1u;
+        }
+        SwitchStorer<Last> sw{last, as, wmax, shift + MAX_BITS, false};
+        AosLoader al{cur};
+        StoredDigits sd{dig};
+        const double a = p < expected_passes ? alg : 0.0;
+        if (p == 0) {
+            KeyDigits<First> kd{first, g.shift, g.mask};
+            if (passes == 1) {
+                WTRI_TRY(run_pass(kd, first, last, g, scratch, s, err, 4.0, a));
+            } else {
+                WTRI_TRY(run_pass(kd, first, sw, g, scratch, s, err, 4.0, a));
+            }
+        } else if (p == passes - 1) {
+            WTRI_TRY(run_pass(sd, al, last, g, scratch, s, err, 2.0, a));
+        } else {
+            WTRI_TRY(run_pass(sd, al, sw, g, scratch, s, err, 2.0, a));
+        }
+        std::swap(cur, nxt);
     }
     return WTRI_OK;
 }

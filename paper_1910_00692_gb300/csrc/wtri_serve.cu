@@ -16,7 +16,10 @@
 // answered by one query at their largest k: under the total order (weight
 // desc, triple asc) the top-k is exactly the first k of the top-k' for any
 // k' >= k, so each request gets the prefix it asked for, identical to the
-// result of its own query.  WTRI_SERVE_COALESCE=0 runs one query per request.
+// result of its own query.  wtri_server_set_option(WTRI_SERVER_COALESCE, 0)
+// (or WTRI_SERVE_COALESCE=0 in the environment at creation) runs one query
+// per request.
+#include <atomic>
 #include <chrono>
 #include <cstdlib>
 #include <condition_variable>
@@ -63,7 +66,8 @@ struct InFlight {
     std::vector<int> query_of;  // request i is answered by query query_of[i] of the plan
 };
 
-bool coalesce_enabled() {
+// Default of a new server's coalescing option (environment, read once).
+bool coalesce_default() {
     static const bool on = [] {
         const char* e = getenv("WTRI_SERVE_COALESCE");
         return !(e && e[0] == '0');
@@ -98,6 +102,7 @@ struct wtri_server {
     bool stream_busy[wtri::WORKER_STREAMS] = {};
     std::vector<wtri::InFlight> inflight;  // touched by the worker only
     uint64_t batches = 0, admitted = 0, retries = 0;
+    std::atomic<bool> coalesce{true};  // same-(graph, p) requests of a micro-batch share a query
 };
 
 namespace wtri {
@@ -162,7 +167,7 @@ void launch_batch(wtri_server* S, std::vector<std::shared_ptr<Request>>& reqs, i
     std::vector<int32_t> pc, ks;
     std::unordered_map<int64_t, int> group;
     f.query_of.resize(reqs.size());
-    const bool merge = coalesce_enabled();
+    const bool merge = S->coalesce.load(std::memory_order_relaxed);
     for (size_t i = 0; i < reqs.size(); i++) {
         const int64_t key = (int64_t)reqs[i]->graph_id * 8 + reqs[i]->pcode;
         auto it = merge ? group.find(key) : group.end();
@@ -285,6 +290,7 @@ WTRI_API int wtri_server_create(uint64_t hbm_budget_bytes, int32_t max_slots, wt
     if (!S) return set_error(WTRI_ENOMEM, "host allocation failed");
     S->budget = hbm_budget_bytes;
     S->max_slots = max_slots;
+    S->coalesce.store(coalesce_default());
     if (cudaGetDevice(&S->device) != cudaSuccess) {
         delete S;
         return set_error(WTRI_ECUDA, "no current device");
@@ -323,6 +329,9 @@ WTRI_API int wtri_submit(wtri_server* S, int32_t graph_id, double p, int32_t k, 
     if (!S || !ticket) return set_error(WTRI_EINVAL, "NULL argument");
     int code = 0;
     WTRI_TRY(p_to_code(p, &code));
+    if (code == P_GEN)
+        return set_error(WTRI_EUNSUPPORTED,
+                         "the server takes p in {-inf, 0, 1, 2, +inf}; other p through wtri_topk");
     if (k <= 0) return set_error(WTRI_EINVAL, "k must be positive");
     if (k > 65536) return set_error(WTRI_EUNSUPPORTED, "k above 65536");
     auto r = std::make_shared<Request>();
@@ -406,3 +415,15 @@ WTRI_API void wtri_server_free(wtri_server* S) {
 }
 
 }  // extern "C"
+
+extern "C" WTRI_API int wtri_server_set_option(wtri_server* S, int option, int64_t value) {
+    using namespace wtri;
+    if (!S) return set_error(WTRI_EINVAL, "server is NULL");
+    switch (option) {
+        case WTRI_SERVER_COALESCE:
+            S->coalesce.store(value != 0);
+            return WTRI_OK;
+        default:
+            return set_error(WTRI_EINVAL, "unknown server option");
+    }
+}

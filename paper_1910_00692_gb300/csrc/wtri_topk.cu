@@ -7,9 +7,15 @@
 namespace wtri {
 namespace {
 
+// First-wait poll limit of the long-scan kernel's row staging (a test hook
+// lowers it; see wtri_debug_set_wait_limit).
+std::atomic<uint32_t> g_stage_wait{WAIT_LIMIT};
+uint32_t stage_wait_limit() { return g_stage_wait.load(std::memory_order_relaxed); }
+
 template <int P>
 int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight, int32_t* d_count,
-              cudaStream_t s, int scale, int shard, int nshards, unsigned long long* d_keys) {
+              cudaStream_t s, int scale, int shard, int nshards, unsigned long long* d_keys,
+              double gp) {
     const DevGraph& G = g->d;
     const int64_t m = G.m;
     const uint32_t cap = (uint32_t)std::min<int64_t>(
@@ -43,6 +49,9 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
     q.shard = shard;
     q.nshards = nshards;
     q.t_short = g->tune.t_short;
+    q.qbytes = query_bytes_on() ? query_bytes_counter() : nullptr;
+    q.gp = gp;
+    q.wait_first = stage_wait_limit();
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
 
     const size_t lsmem = LONG_SMEM;
@@ -146,7 +155,9 @@ __global__ void __launch_bounds__(1024) k_class_mass(const int64_t* __restrict__
         u128 x = 0;
         if (c < nc) {
             const u128 wv = (u128)(uint64_t)__ldg(ow + cstart[c]);
-            x = (u128)(uint64_t)(cstart[c + 1] - cstart[c]) * (P == P_TWO ? wv * wv : wv);
+            // w^p: p = 2 squares, p = 1 keeps, p = 0 gives 1 (uniform draws)
+            x = (u128)(uint64_t)(cstart[c + 1] - cstart[c]) *
+                (P == P_TWO ? wv * wv : (P == P_GEO ? (u128)1 : wv));
         }
         u128 inc = x;
 #pragma unroll
@@ -191,7 +202,7 @@ __global__ void k_draw(int64_t nsamples, uint64_t seed, const int64_t* __restric
         }
         const u128 prev = lo > 0 ? cmass[lo - 1] : (u128)0;
         const u128 wv = (u128)(uint64_t)__ldg(ow + cstart[lo]);
-        const u128 wp = P == P_TWO ? wv * wv : wv;
+        const u128 wp = P == P_TWO ? wv * wv : (P == P_GEO ? (u128)1 : wv);
         const int64_t r = cstart[lo] + (int64_t)((t - prev) / wp);
         atomicOr(mark + (r >> 5), 1u << (r & 31));
     }
@@ -310,8 +321,11 @@ int run_sample(const wtri_graph* g, int32_t k, int64_t nsamples, uint64_t seed, 
     q.shard = 0;
     q.nshards = 1;
     q.t_short = g->tune.t_short;
+    q.qbytes = nullptr;
+    q.gp = 0.0;
+    q.wait_first = stage_wait_limit();
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
-    ProfScope whole(P == P_ONE ? "sample_p=1" : "sample_p=2", s, 0.0, 0);
+    ProfScope whole(P == P_ONE ? "sample_p=1" : (P == P_TWO ? "sample_p=2" : "sample_p=0"), s, 0.0, 0);
     WTRI_TRY(draw_samples<P>(g, nsamples, seed, mark, s));
     {
         ProfScope ps("sample_compact", s, 8.0 * words, 2);
@@ -358,18 +372,20 @@ int run_sample(const wtri_graph* g, int32_t k, int64_t nsamples, uint64_t seed, 
 
 int topk_device(const wtri_graph* g, int pcode, int32_t k, wtri_tri* d_tris, double* d_weight,
                 int32_t* d_count, cudaStream_t stream, int retry_scale, int shard, int nshards,
-                unsigned long long* d_keys) {
+                unsigned long long* d_keys, double gp) {
     switch (pcode) {
         case P_MIN:
-            return run_query<P_MIN>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys);
+            return run_query<P_MIN>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys, gp);
         case P_ONE:
-            return run_query<P_ONE>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys);
+            return run_query<P_ONE>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys, gp);
         case P_TWO:
-            return run_query<P_TWO>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys);
+            return run_query<P_TWO>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys, gp);
         case P_GEO:
-            return run_query<P_GEO>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys);
+            return run_query<P_GEO>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys, gp);
+        case P_GEN:
+            return run_query<P_GEN>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys, gp);
         default:
-            return run_query<P_MAX>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys);
+            return run_query<P_MAX>(g, k, d_tris, d_weight, d_count, stream, retry_scale, shard, nshards, d_keys, gp);
     }
 }
 
@@ -431,7 +447,7 @@ int noalloc_scratch(void** out) {
 
 template <int P>
 int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight,
-                      int32_t* d_count, cudaStream_t s) {
+                      int32_t* d_count, cudaStream_t s, double gp) {
     const DevGraph& G = g->d;
     const int64_t m = G.m;
     void* base = nullptr;
@@ -452,6 +468,9 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
     q.shard = 0;
     q.nshards = 1;
     q.t_short = g->tune.t_short;
+    q.qbytes = nullptr;
+    q.gp = gp;
+    q.wait_first = stage_wait_limit();
     // The array keeps the previous call's contents: reset the status word
     // (counters, threshold, stop flag, error bits).
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
@@ -483,12 +502,15 @@ int sample_topk_device(const wtri_graph* g, int pcode, int32_t k, int64_t nsampl
                        int retry_scale) {
     if (pcode == P_ONE)
         return run_sample<P_ONE>(g, k, nsamples, seed, d_tris, d_weight, d_count, stream, retry_scale);
+    if (pcode == P_GEO)
+        return run_sample<P_GEO>(g, k, nsamples, seed, d_tris, d_weight, d_count, stream, retry_scale);
     return run_sample<P_TWO>(g, k, nsamples, seed, d_tris, d_weight, d_count, stream, retry_scale);
 }
 
 int sample_edges_device(const wtri_graph* g, int pcode, int64_t nsamples, uint64_t seed,
                         uint32_t* d_mark, cudaStream_t stream) {
     if (pcode == P_ONE) return draw_samples<P_ONE>(g, nsamples, seed, d_mark, stream);
+    if (pcode == P_GEO) return draw_samples<P_GEO>(g, nsamples, seed, d_mark, stream);
     return draw_samples<P_TWO>(g, nsamples, seed, d_mark, stream);
 }
 
@@ -511,11 +533,58 @@ extern "C" WTRI_API int wtri_topk_device_noalloc(const wtri_graph* g, double p, 
         return WTRI_OK;
     }
     switch (code) {
-        case P_MIN: return run_query_noalloc<P_MIN>(g, k, d_tris, d_weight, d_count, s);
-        case P_ONE: return run_query_noalloc<P_ONE>(g, k, d_tris, d_weight, d_count, s);
-        case P_TWO: return run_query_noalloc<P_TWO>(g, k, d_tris, d_weight, d_count, s);
-        case P_GEO: return run_query_noalloc<P_GEO>(g, k, d_tris, d_weight, d_count, s);
-        default: return run_query_noalloc<P_MAX>(g, k, d_tris, d_weight, d_count, s);
+        case P_MIN: return run_query_noalloc<P_MIN>(g, k, d_tris, d_weight, d_count, s, p);
+        case P_ONE: return run_query_noalloc<P_ONE>(g, k, d_tris, d_weight, d_count, s, p);
+        case P_TWO: return run_query_noalloc<P_TWO>(g, k, d_tris, d_weight, d_count, s, p);
+        case P_GEO: return run_query_noalloc<P_GEO>(g, k, d_tris, d_weight, d_count, s, p);
+        case P_GEN: return run_query_noalloc<P_GEN>(g, k, d_tris, d_weight, d_count, s, p);
+        default: return run_query_noalloc<P_MAX>(g, k, d_tris, d_weight, d_count, s, p);
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Instrumented query byte counter (one per device).
+// ---------------------------------------------------------------------------
+namespace wtri {
+namespace {
+__device__ unsigned long long g_query_bytes;
+std::atomic<int> g_query_bytes_on{0};
+std::mutex g_qb_mu;
+unsigned long long* g_qb_ptr[64] = {};
+}  // namespace
+
+bool query_bytes_on() { return g_query_bytes_on.load(std::memory_order_relaxed) != 0; }
+
+unsigned long long* query_bytes_counter() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_qb_mu);
+    if (!g_qb_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_query_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_qb_ptr[dev] = (unsigned long long*)p;
+    }
+    return g_qb_ptr[dev];
+}
+
+}  // namespace wtri
+
+extern "C" WTRI_API int wtri_query_bytes(int on, int reset, unsigned long long* bytes) {
+    using namespace wtri;
+    unsigned long long* d = query_bytes_counter();
+    if (!d) return set_error(WTRI_ECUDA, "query byte counter unavailable on this device");
+    WTRI_CUDA(cudaDeviceSynchronize());
+    if (bytes) WTRI_CUDA(cudaMemcpy(bytes, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    if (reset) WTRI_CUDA(cudaMemset(d, 0, sizeof(unsigned long long)));
+    g_query_bytes_on.store(on ? 1 : 0);
+    return WTRI_OK;
+}
+
+extern "C" WTRI_API int wtri_debug_set_wait_limit(int64_t polls) {
+    wtri::g_stage_wait.store(polls < 0 ? wtri::WAIT_LIMIT : (uint32_t)std::min<int64_t>(polls, UINT32_MAX));
+    return WTRI_OK;
+}

@@ -101,6 +101,8 @@ def lib():
     L.wtri_sample_topk.argtypes = [vp, f64, i32, i64, ctypes.c_uint64, ctypes.POINTER(_Result)]
     L.wtri_graph_copy_array.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
     L.wtri_sample_edges.argtypes = [vp, f64, i64, ctypes.c_uint64, vp, i64]
+    L.wtri_wedge_topk.argtypes = [vp, f64, i32, i64, ctypes.c_uint64, ctypes.POINTER(_Result)]
+    L.wtri_sample_wedges.argtypes = [vp, f64, i64, ctypes.c_uint64, vp, vp, vp, vp]
     L.wtri_topk_batch.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_Result)]
     L.wtri_topk_shard.argtypes = [vp, f64, i32, i32, i32, ctypes.POINTER(_Result), vp]
     L.wtri_autotune.argtypes = [vp, i32, i32, ctypes.POINTER(_TuneInfo)]
@@ -114,6 +116,10 @@ def lib():
     L.wtri_poll_timed.argtypes = [vp, u64, ctypes.POINTER(_Result), ctypes.POINTER(f64)]
     L.wtri_server_stats.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(i32),
                                     ctypes.POINTER(i32), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    L.wtri_debug_set_wait_limit.argtypes = [i64]
+    L.wtri_debug_set_wait_limit.restype = ctypes.c_int
+    L.wtri_server_set_option.argtypes = [vp, ctypes.c_int, i64]
+    L.wtri_server_set_option.restype = ctypes.c_int
     L.wtri_server_free.argtypes = [vp]
     L.wtri_server_free.restype = None
     L.wtri_last_error.restype = ctypes.c_char_p
@@ -124,7 +130,8 @@ def lib():
               L.wtri_sample_topk, L.wtri_graph_copy_array, L.wtri_sample_edges,
               L.wtri_topk_batch, L.wtri_server_create, L.wtri_server_add_graph, L.wtri_submit,
               L.wtri_poll, L.wtri_poll_timed, L.wtri_server_stats, L.wtri_topk_shard,
-              L.wtri_merge_topk, L.wtri_autotune, L.wtri_set_tune):
+              L.wtri_merge_topk, L.wtri_autotune, L.wtri_set_tune, L.wtri_wedge_topk,
+              L.wtri_sample_wedges):
         f.restype = ctypes.c_int
     _lib = L
     return L
@@ -264,6 +271,26 @@ def sample_topk(g: Graph, p: float, k: int, nsamples: int, seed: int):
                        int(k))
 
 
+def wedge_topk(g: Graph, p: float, k: int, nsamples: int, seed: int):
+    """wtri_wedge_topk: top-k of Algorithm 4's triangle set (host results)."""
+    return _host_query(lambda r: lib().wtri_wedge_topk(g.handle, float(p), int(k), int(nsamples),
+                                                        ctypes.c_uint64(seed & (2**64 - 1)), r),
+                       int(k))
+
+
+def sample_wedges(g: Graph, p: float, nsamples: int, seed: int):
+    """wtri_sample_wedges: (center, jb, jc, tri) of each draw of Algorithm 4."""
+    ns = int(nsamples)
+    center = np.zeros(max(ns, 1), np.int32)
+    jb = np.zeros(max(ns, 1), np.int32)
+    jc = np.zeros(max(ns, 1), np.int32)
+    tri = np.zeros(3 * max(ns, 1), np.int32)
+    _check(lib().wtri_sample_wedges(g.handle, float(p), ns, ctypes.c_uint64(int(seed) & (2**64 - 1)),
+                                    center.ctypes.data_as(ctypes.c_void_p), jb.ctypes.data_as(ctypes.c_void_p),
+                                    jc.ctypes.data_as(ctypes.c_void_p), tri.ctypes.data_as(ctypes.c_void_p)))
+    return center[:ns], jb[:ns], jc[:ns], tri[: 3 * ns].reshape(ns, 3)
+
+
 def topk_shard(g: Graph, p: float, k: int, shard: int, nshards: int):
     """wtri_topk_shard: exact top-k of the triangles owned by one shard.
     Returns (tris, weights, keys)."""
@@ -365,6 +392,10 @@ class Server:
         return {"batches": b.value, "admitted": a.value, "waiting": wq.value, "running": rn.value,
                 "scratch_bytes": sc.value, "retries": rt.value}
 
+    def set_coalesce(self, on: bool):
+        """WTRI_SERVER_COALESCE: same-(graph, p) requests of a micro-batch share one query."""
+        _check(lib().wtri_server_set_option(self._h, 1, 1 if on else 0))
+
     def free(self):
         if self._h:
             lib().wtri_server_free(self._h)
@@ -388,6 +419,13 @@ def sample_edges(g: Graph, p: float, nsamples: int, seed: int) -> np.ndarray:
                                    out.ctypes.data_as(ctypes.c_void_p), words))
     bits = np.unpackbits(out.view(np.uint8), bitorder="little")
     return bits[:m].astype(bool)
+
+
+def debug_set_wait_limit(polls: int):
+    """wtri_debug_set_wait_limit: fault injection for tests (polls of the
+    long-scan kernel's first bounded wait; 0: every staged wait times out;
+    negative: the default)."""
+    _check(lib().wtri_debug_set_wait_limit(int(polls)))
 
 
 def p_values():

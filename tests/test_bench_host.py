@@ -81,19 +81,21 @@ def test_measured_peak_reads_the_file():
         assert kind == "fallback" and peak == b.FALLBACK_HBM_GBS
 
 
-def test_ncu_traffic_tracks_the_sources():
-    b = _bench()
-    path = os.path.join(ROOT, "profiles", "radix_scatter_traffic_quarter.txt")
-    fields = dict(line.split(":", 1) for line in open(path) if ":" in line)
-    traffic, why = b.ncu_traffic()
+def test_ncu_traffic_tracks_the_sources(tmp_path):
     import hashlib
-    h = hashlib.sha256()
-    for f in fields["sources"].split():
-        h.update(open(os.path.join(ROOT, f), "rb").read())
-    if h.hexdigest() == fields["source_sha256"].strip():
-        assert traffic == float(fields["dram_bytes_per_launch_mid"])
-    else:
-        assert traffic is None and "changed" in why
+    b = _bench()
+    src = "bench.py"
+    digest = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+    cap = tmp_path / "radix_downsweep_traffic_large.txt"
+    cap.write_text(f"how: test capture\ndram_bytes_per_launch: 123.0\nsources: {src}\n"
+                   f"source_sha256: {digest}\n")
+    traffic, why = b.ncu_traffic("radix_downsweep", "large", str(tmp_path))
+    assert traffic == 123.0 and why == "test capture"
+    cap.write_text(f"dram_bytes_per_launch: 123.0\nsources: {src}\nsource_sha256: {'0' * 64}\n")
+    traffic, why = b.ncu_traffic("radix_downsweep", "large", str(tmp_path))
+    assert traffic is None and "changed" in why
+    traffic, why = b.ncu_traffic("radix_downsweep", "mid", str(tmp_path))
+    assert traffic is None and "no capture" in why
 
 
 def test_host_arrays_prefix():

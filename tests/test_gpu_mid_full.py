@@ -1,11 +1,11 @@
 """GPU parity at the full mid workload size (Chung-Lu n=1e6, m=2e7, exponent
 2.1, d_max 5e4, Zipf(2) weights capped at 1e6; k=1000 at every supported p), the
-configuration bench.py times: every output element against the oracle."""
+configuration of the mid bench workload: every output element against the oracle."""
 import pytest
 
 import oracle
 import synth
-from wtri_testutil import PS, assert_topk_equal
+from wtri_testutil import PS, assert_topk_equal, check_structures
 
 pytestmark = pytest.mark.gpu
 
@@ -28,25 +28,8 @@ def test_mid_full_k1000(mid, p):
     assert_topk_equal(tris, wts, want, p, f"mid p={p}")
 
 
-def test_mid_structure_sample(mid):
-    """Sampled checks of the device structures at full size (properties that
-    hold at any size, plus exact rows for a few vertices)."""
-    import numpy as np
+def test_mid_structures_whole(mid):
+    """Every device structure of the full mid build (2e7 edges, rows up to
+    ~35,000 entries) against the oracle's construction, whole arrays."""
     g, d = mid
-    ow = d.array("order_w")
-    assert np.all(np.diff(ow) <= 0)
-    assert np.array_equal(np.sort(ow), np.sort(g.w))
-    rowptr = d.array("rowptr")
-    deg = np.bincount(np.concatenate([g.u, g.v]), minlength=g.n)
-    assert np.array_equal(np.diff(rowptr), deg)
-    scol, wwt, wrk = d.array("scol"), d.array("wwt"), d.array("wrank")
-    rng = np.random.default_rng(0)
-    for x in list(rng.integers(0, g.n, 200)) + [int(np.argmax(deg))]:
-        s, e = rowptr[x], rowptr[x + 1]
-        assert np.all(np.diff(scol[s:e]) > 0)
-        assert np.all(np.diff(wrk[s:e]) > 0)
-        assert np.all(np.diff(wwt[s:e]) <= 0)
-        nb = np.sort(np.concatenate([g.v[g.u == x], g.u[g.v == x]]))
-        assert np.array_equal(scol[s:e], nb)
-    orow = d.array("orowptr")
-    assert orow[-1] == g.m
+    check_structures(g, d)

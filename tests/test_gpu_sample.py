@@ -28,7 +28,7 @@ def graphs():
 
 
 @pytest.mark.parametrize("name", ["tiny", "scaled"])
-@pytest.mark.parametrize("p", [1.0, 2.0])
+@pytest.mark.parametrize("p", [1.0, 2.0, 0.0])
 @pytest.mark.parametrize("nsamples,seed", [(1, 0), (1000, 7), (200_000, 7), (50_000, 2**64 - 1)])
 def test_draws_bit_identical(graphs, name, p, nsamples, seed):
     g, d = graphs[0][name], graphs[1][name]
@@ -38,7 +38,7 @@ def test_draws_bit_identical(graphs, name, p, nsamples, seed):
 
 
 @pytest.mark.parametrize("name", ["tiny", "scaled"])
-@pytest.mark.parametrize("p", [1.0, 2.0])
+@pytest.mark.parametrize("p", [1.0, 2.0, 0.0])
 @pytest.mark.parametrize("k,nsamples", [(10, 500), (100, 20_000), (1000, 300_000)])
 def test_sample_topk_vs_oracle(graphs, name, p, k, nsamples):
     g, d = graphs[0][name], graphs[1][name]
@@ -49,7 +49,7 @@ def test_sample_topk_vs_oracle(graphs, name, p, k, nsamples):
 
 def test_sample_errors(graphs):
     d = graphs[1]["tiny"]
-    for p in (math.inf, -math.inf):
+    for p in (math.inf, -math.inf, -1.0, 3.0):
         with pytest.raises(wt.WtriError) as ei:
             d.sample_topk(p, 10, 100, 1)
         assert ei.value.code == -5

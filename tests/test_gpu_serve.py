@@ -97,12 +97,15 @@ def test_burst_and_waves_equal_alone(graphs):
     srv.free()
 
 
-def test_same_graph_and_p_share_a_query(graphs):
+@pytest.mark.parametrize("coalesce", [True, False])
+def test_same_graph_and_p_share_a_query(graphs, coalesce):
     """Requests on one graph with one p and many k (some above the number of
     triangles) submitted together: each gets exactly its own top-k, the
-    prefix of the shared query's answer."""
+    prefix of the shared query's answer -- or, with coalescing off
+    (WTRI_SERVER_COALESCE = 0), the answer of its own query."""
     gs, ds = graphs
     srv = wt.Server(8 << 30, 256)
+    srv.set_coalesce(coalesce)
     gid = srv.add_graph(ds[0])
     ntri = len(ds[0].topk(1.0, 60000)[0])
     assert ntri < 20000

@@ -35,3 +35,20 @@ def test_shards(n, m, seed, nshards):
             assert np.array_equal(mt, ft) and np.array_equal(mw, fw)
     finally:
         d.free()
+
+
+def test_shard_rule_hand_built():
+    """wtri_topk_shard gives each shard exactly the triangles the hand-built
+    pin lists (ownership by the first edge's 1024-position chunk)."""
+    import shard_pin
+    n, u, v, w = shard_pin.graph()
+    d = wt.build_csr(n, u, v, w)
+    try:
+        for nsh, want in shard_pin.EXPECTED.items():
+            for sh in range(nsh):
+                for p in PS:
+                    t, _, _ = wt.topk_shard(d, p, 100, sh, nsh)
+                    got = sorted(tuple(int(x) for x in row) for row in t)
+                    assert got == sorted(want[sh]), (nsh, sh, p, got)
+    finally:
+        d.free()

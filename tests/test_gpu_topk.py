@@ -12,7 +12,7 @@ import pytest
 import oracle
 import synth
 from golden_io import P_OF, closed_form, load_all
-from wtri_testutil import PS, assert_topk_equal
+from wtri_testutil import PS, assert_topk_equal, check_structures
 
 pytestmark = pytest.mark.gpu
 
@@ -54,32 +54,12 @@ def test_tiny_vs_oracle(tiny, tiny_dev, p, k):
     assert_topk_equal(tris, wts, want, p, f"tiny p={p} k={k}")
 
 
-def _check_structures(g, d):
-    perm = oracle.edge_order(g.w)
-    assert np.array_equal(d.array("order_w"), g.w[perm])
-    ou, ov = d.array("order_u"), d.array("order_v")
-    assert np.array_equal(ou, g.u[perm]) and np.array_equal(ov, g.v[perm])
-    rowptr, col, wtt, eid = oracle.sym_csr(g.n, g.u, g.v, g.w)
-    assert np.array_equal(d.array("rowptr"), rowptr)
-    assert np.array_equal(d.array("degree"), np.diff(rowptr).astype(np.int32))
-    assert np.array_equal(d.array("scol"), col)
-    assert np.array_equal(d.array("swt"), wtt)
-    rank = np.empty(g.m, np.int64)
-    rank[perm] = np.arange(g.m)
-    assert np.array_equal(d.array("srank"), rank[eid])
-    wrp, wcol, wwt, wrk = oracle.weight_sorted_rows(g.n, g.u, g.v, g.w)
-    assert np.array_equal(d.array("wcol"), wcol)
-    assert np.array_equal(d.array("wwt"), wwt)
-    assert np.array_equal(d.array("wrank"), wrk)
-    orow, ocol, owt, oeid = oracle.oriented_csr(g.n, g.u, g.v, g.w)
-    assert np.array_equal(d.array("orowptr"), orow)
-    assert np.array_equal(d.array("ocol"), ocol)
-    assert np.array_equal(d.array("owt"), owt)
-    assert np.array_equal(d.array("orank"), rank[oeid])
-
-
 def test_tiny_structures(tiny, tiny_dev):
-    _check_structures(tiny, tiny_dev)
+    check_structures(tiny, tiny_dev)
+    # the id-sorted rows keep no edge ranks (the oriented rows carry them)
+    with pytest.raises(wt.WtriError) as ei:
+        tiny_dev.array("srank")
+    assert ei.value.code == -5
 
 
 @pytest.mark.parametrize("n,m,seed", [(20000, 200000, 11), (100000, 1000000, 12)])
@@ -88,9 +68,71 @@ def test_scaled_structures(n, m, seed):
     g = synth.scaled_mid_graph(n, m, seed=seed)
     d = wt.build_csr(g.n, g.u, g.v, g.w)
     try:
-        _check_structures(g, d)
+        check_structures(g, d)
     finally:
         d.free()
+
+
+def _hubs_graph(degrees, seed):
+    """Hub vertices 0..len(degrees)-1 of the given degrees to distinct
+    leaves, leaves joined in pairs (triangles through every hub), random
+    weights 1..9: rows of every size class of the per-row sort."""
+    rng = np.random.default_rng(seed)
+    us, vs = [], []
+    nxt = len(degrees)
+    for h, dgr in enumerate(degrees):
+        leaves = np.arange(nxt, nxt + dgr, dtype=np.int64)
+        nxt += dgr
+        us.append(np.full(dgr, h, np.int64))
+        vs.append(leaves)
+        us.append(leaves[0:dgr - 1:2])
+        vs.append(leaves[1:dgr:2])
+    # hub-hub edges so hub rows also hold other hubs
+    for a in range(len(degrees)):
+        for b in range(a + 1, len(degrees)):
+            us.append(np.array([a]))
+            vs.append(np.array([b]))
+    u = np.concatenate(us)
+    v = np.concatenate(vs)
+    perm = rng.permutation(u.shape[0])
+    u, v = u[perm], v[perm]
+    flip = rng.random(u.shape[0]) < 0.5
+    u2 = np.where(flip, v, u).astype(np.int32)
+    v2 = np.where(flip, u, v).astype(np.int32)
+    w = rng.integers(1, 10, u.shape[0]).astype(np.int32)
+    return synth.Graph(n=int(nxt), u=u2, v=v2, w=w, name="hubs")
+
+
+@pytest.mark.parametrize("degrees", [[5, 12, 30, 33, 500, 1024], [1025, 4000, 8192], [8193, 20000]],
+                         ids=["small-warp", "block-smem", "block-global"])
+def test_hub_rows_structures(degrees):
+    """Rows at the boundaries of the per-row sort's size classes (8/16/32
+    lanes, one warp up to 1024, one block up to 8192 in shared memory,
+    global scratch beyond): structures and the top-k against the oracle."""
+    g = _hubs_graph(degrees, seed=sum(degrees))
+    d = wt.build_csr(g.n, g.u, g.v, g.w)
+    try:
+        check_structures(g, d)
+        for p in PS:
+            want = oracle.topk(g.n, g.u, g.v, g.w, p, 300)
+            tris, wts = d.topk(p, 300)
+            assert_topk_equal(tris, wts, want, p, f"hubs {degrees} p={p}")
+    finally:
+        d.free()
+
+
+@pytest.mark.parametrize("dgr", [6, 14, 27, 200, 3000, 12000])
+def test_repeated_pair_in_long_row(dgr):
+    """A repeated undirected pair inside a row of each size class is
+    rejected (WTRI_EINVAL naming the neighbour)."""
+    g = _hubs_graph([dgr], seed=dgr)
+    u = np.concatenate([g.u, np.array([dgr // 2 + 1], np.int32)])  # hub 0 - leaf again, flipped
+    v = np.concatenate([g.v, np.array([0], np.int32)])
+    w = np.concatenate([g.w, np.array([3], np.int32)])
+    with pytest.raises(wt.WtriError) as ei:
+        wt.build_csr(g.n, u, v, w)
+    assert ei.value.code == -1
+    assert "repeated" in str(ei.value) and str(dgr // 2 + 1) in str(ei.value)
 
 
 @pytest.mark.parametrize("seed", range(24))
@@ -179,8 +221,8 @@ def test_bad_queries(tiny_dev):
         tiny_dev.topk(float("nan"), 10)
     assert ei.value.code == -1
     with pytest.raises(wt.WtriError) as ei:
-        tiny_dev.topk(0.5, 10)
-    assert ei.value.code == -5
+        tiny_dev.topk(float("inf") * 0.0, 10)  # NaN again, by arithmetic
+    assert ei.value.code == -1
     with pytest.raises(wt.WtriError) as ei:
         tiny_dev.topk(1.0, 0)
     assert ei.value.code == -1
@@ -316,3 +358,59 @@ def test_complete_graph_closed_form():
         np.testing.assert_array_equal(wts, (2 * sums + 3) / 3.0)
     finally:
         d.free()
+
+
+@pytest.mark.parametrize("p", [-1.0, -2.0, 0.5, 3.0])
+@pytest.mark.parametrize("k", [1, 100, 2000])
+def test_general_p_tiny(tiny, tiny_dev, p, k):
+    """Finite p outside {0, 1, 2}: ranked by the fp64 mean; the GPU answer
+    equals the oracle's under the fp64 rule (values within 1e-12 relative,
+    membership may differ only within 1e-12 of the k-th value)."""
+    from wtri_testutil import assert_topk_close
+    want = oracle.topk(tiny.n, tiny.u, tiny.v, tiny.w, p, k)
+    tris, wts = tiny_dev.topk(p, k)
+    assert_topk_close(tris, wts, want["tri"], want["value"], f"tiny p={p} k={k}")
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_general_p_random_small(seed):
+    from wtri_testutil import assert_topk_close
+    rng = np.random.default_rng(7000 + seed)
+    n = int(rng.integers(4, 60))
+    g = synth.random_small_graph(n, float(rng.uniform(0.1, 0.9)), int(rng.integers(1, 9)), seed)
+    if g.m == 0:
+        return
+    d = wt.build_csr(g.n, g.u, g.v, g.w)
+    try:
+        for p in (-1.0, -3.0, 0.5, 3.0):
+            for k in (1, 7, 200):
+                want = oracle.topk(g.n, g.u, g.v, g.w, p, k)
+                tris, wts = d.topk(p, k)
+                assert_topk_close(tris, wts, want["tri"], want["value"], f"seed={seed} p={p} k={k}")
+    finally:
+        d.free()
+
+
+@pytest.mark.parametrize("p", [-1.0, 3.0])
+def test_general_p_scaled(p):
+    """A 1e6-edge Chung-Lu graph with Zipf(2) weights up to 1e6."""
+    from wtri_testutil import assert_topk_close
+    g = synth.scaled_mid_graph(100000, 1000000, seed=12)
+    d = wt.build_csr(g.n, g.u, g.v, g.w)
+    try:
+        for k in (1000, 5000):
+            want = oracle.topk(g.n, g.u, g.v, g.w, p, k)
+            tris, wts = d.topk(p, k)
+            assert_topk_close(tris, wts, want["tri"], want["value"], f"scaled p={p} k={k}")
+    finally:
+        d.free()
+
+
+def test_general_p_refused_where_not_offered(tiny_dev):
+    """The samplers and the batched call take the exact-key p only."""
+    with pytest.raises(wt.WtriError) as ei:
+        tiny_dev.sample_topk(-1.0, 10, 1000, 1)
+    assert ei.value.code == -5
+    with pytest.raises(wt.WtriError) as ei:
+        wt.topk_batch([tiny_dev], [-1.0], [10])
+    assert ei.value.code == -5

@@ -70,3 +70,42 @@ def test_noalloc_rejects_k_above_limit():
         assert "16384" in str(ei.value)
     finally:
         d.free()
+
+
+def test_noalloc_overflow_reports_enomem_then_recovers():
+    """K_300 with equal weights: every one of its 4,455,100 triangles ties at
+    the k-th key, so a top-16384 query needs more candidate slots than the
+    fixed array's 1,048,576.  The status word reports WTRI_ENOMEM (-2)
+    instead of writing past the array; the call allocates no device memory;
+    and the next call, on another graph, is correct."""
+    dev = torch.device("cuda:0")
+    s = torch.cuda.Stream(device=dev)
+    n = 300
+    iu, iv = np.triu_indices(n, 1)
+    u, v = iu.astype(np.int32), iv.astype(np.int32)
+    w = np.ones(u.shape[0], np.int32)
+    dense = wt.build_csr(n, u, v, w, stream=s)
+    g = synth.tiny_graph(0)
+    d = wt.build_csr(g.n, g.u, g.v, g.w, stream=s)
+    try:
+        out = _outputs(16384, dev)
+        wt.topk_device_noalloc(dense, 1.0, 16384, *out, stream=s)  # first call on the device
+        s.synchronize()
+        assert int(out[2].item()) == -2
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        wt.topk_device_noalloc(dense, 1.0, 16384, *out, stream=s)
+        s.synchronize()
+        free1 = torch.cuda.mem_get_info(dev)[0]
+        assert int(out[2].item()) == -2
+        assert free1 == free0, (free0, free1)
+        ref = _outputs(1000, dev)
+        wt.topk_device(d, 1.0, 1000, *ref, stream=s)
+        got = _outputs(1000, dev)
+        wt.topk_device_noalloc(d, 1.0, 1000, *got, stream=s)
+        s.synchronize()
+        rt, rw = _read(*ref)
+        gt, gw = _read(*got)
+        assert np.array_equal(gt, rt) and np.array_equal(gw, rw)
+    finally:
+        dense.free()
+        d.free()
