@@ -316,20 +316,14 @@ def bench_batch_full(wt, count=4096, n_hi=200_000, reps=3):
         for i in range(8):
             ds[i].topk(ps[i], int(ks[i]))
         res, plain, times, t_plain = measure()
-        # the query schedule autotuned per size bucket: the largest graph of
-        # each power-of-two edge-count bucket is tuned and its setting applies
-        # to every graph of the bucket
+        # the query schedule autotuned per size bucket in the library
+        # (wtri_autotune_buckets: the largest graph of each power-of-two
+        # edge-count bucket is tuned, its setting applies to the bucket; the
+        # batched call runs every query with its own graph's schedule)
         t0 = time.perf_counter()
-        buckets = {}
-        for i, m_ in enumerate(ms):
-            buckets.setdefault(int(m_).bit_length(), []).append(i)
-        chosen = {}
-        for bkt, idx in sorted(buckets.items()):
-            info = ds[max(idx, key=lambda i: ms[i])].autotune(k=1000, reps=2)
-            chosen[bkt] = (info["first_round"], info["growth"], info["t_short"])
-            for i in idx:
-                ds[i].set_tune(*chosen[bkt])
+        nb = wt.autotune_buckets(ds, k=1000, reps=2)
         t_tune = time.perf_counter() - t0
+        chosen = {"buckets": nb}
         res_t, plain_t, times_t, t_plain_t = measure()
         same = all(np.array_equal(r[i][0], plain[i][0]) and np.array_equal(r[i][1], plain[i][1])
                    for r in (res, res_t, plain_t) for i in range(count))
@@ -339,8 +333,7 @@ def bench_batch_full(wt, count=4096, n_hi=200_000, reps=3):
                 "default_schedule": {"batched_ms": 1e3 * t_batch, "plain_calls_ms": 1e3 * t_plain,
                                      "speedup": t_plain / t_batch},
                 "bucket_tuned": {"batched_ms": 1e3 * t_batch_t, "plain_calls_ms": 1e3 * t_plain_t,
-                                 "speedup": t_plain_t / t_batch_t, "tuning_s": t_tune,
-                                 "settings": {f"m<2^{b_}": list(v) for b_, v in chosen.items()}},
+                                 "speedup": t_plain_t / t_batch_t, "tuning_s": t_tune, **chosen},
                 "plain_calls_ms": 1e3 * min(t_plain, t_plain_t),
                 "speedup": min(t_plain, t_plain_t) / min(t_batch, t_batch_t),
                 "results_identical": bool(same), "build_all_ms": 1e3 * t_build,

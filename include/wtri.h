@@ -290,6 +290,17 @@ typedef struct {
 } wtri_tune_info;
 
 WTRI_API int wtri_autotune(wtri_graph* g, int32_t k, int32_t reps, wtri_tune_info* info);
+
+/*
+ * Tuning for a collection of graphs (e.g. the graphs of a batch): graphs
+ * are grouped by size (the bit length of their edge count); the largest
+ * graph of each group is tuned with wtri_autotune and its setting applied
+ * to every graph of the group.  The batched call runs each query with its
+ * own graph's schedule, so one batch mixes the settings of all its groups.
+ * *buckets_tuned (may be NULL) receives the number of groups.
+ */
+WTRI_API int wtri_autotune_buckets(wtri_graph* const* gs, int32_t ngraphs, int32_t k, int32_t reps,
+                                   int32_t* buckets_tuned);
 WTRI_API int wtri_set_tune(wtri_graph* g, int64_t first_round, int32_t growth, int32_t t_short);
 
 /*

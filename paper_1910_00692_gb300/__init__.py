@@ -14,6 +14,7 @@ from .wtri import (  # noqa: F401
     Server,
     WtriError,
     WtriUnavailable,
+    autotune_buckets,
     build_csr,
     debug_set_wait_limit,
     lib,
@@ -30,7 +31,7 @@ from .wtri import (  # noqa: F401
     wedge_topk,
 )
 
-__all__ = ["ARRAYS", "Graph", "Server", "WtriError", "WtriUnavailable", "build_csr",
+__all__ = ["ARRAYS", "Graph", "Server", "WtriError", "WtriUnavailable", "autotune_buckets", "build_csr",
            "debug_set_wait_limit", "lib", "lib_path", "merge_topk", "topk_shard",
            "sample_edges", "sample_topk", "sample_wedges", "topk", "topk_batch", "topk_device",
            "topk_device_noalloc", "wedge_topk"]

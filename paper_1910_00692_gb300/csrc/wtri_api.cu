@@ -352,6 +352,35 @@ WTRI_API int wtri_autotune(wtri_graph* g, int32_t k, int32_t reps, wtri_tune_inf
     return WTRI_OK;
 }
 
+WTRI_API int wtri_autotune_buckets(wtri_graph* const* gs, int32_t ngraphs, int32_t k, int32_t reps,
+                                   int32_t* buckets_tuned) {
+    if (ngraphs < 0 || (ngraphs > 0 && !gs)) return set_error(WTRI_EINVAL, "bad graph array");
+    // size buckets: graphs whose edge counts have the same bit length
+    std::vector<int> best(65, -1);
+    for (int32_t i = 0; i < ngraphs; i++) {
+        if (!gs[i]) return set_error(WTRI_EINVAL, "graph " + std::to_string(i) + " is NULL");
+        int b = 0;
+        for (uint64_t m = (uint64_t)gs[i]->d.m; m; m >>= 1) b++;
+        if (best[(size_t)b] < 0 || gs[i]->d.m > gs[(size_t)best[(size_t)b]]->d.m) best[(size_t)b] = i;
+    }
+    int32_t tuned = 0;
+    std::vector<wtri::Tune> setting(65);
+    for (int b = 0; b <= 64; b++) {
+        if (best[(size_t)b] < 0) continue;
+        wtri_graph* g = gs[(size_t)best[(size_t)b]];
+        WTRI_TRY(wtri_autotune(g, k, reps, nullptr));
+        setting[(size_t)b] = g->tune;
+        tuned++;
+    }
+    for (int32_t i = 0; i < ngraphs; i++) {
+        int b = 0;
+        for (uint64_t m = (uint64_t)gs[i]->d.m; m; m >>= 1) b++;
+        gs[i]->tune = setting[(size_t)b];
+    }
+    if (buckets_tuned) *buckets_tuned = tuned;
+    return WTRI_OK;
+}
+
 WTRI_API int wtri_topk_device(const wtri_graph* g, double p, int32_t k, wtri_tri* d_tris,
                               double* d_weight, int32_t* d_count, void* stream) {
     int code = 0;

@@ -233,13 +233,21 @@ BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes,
         P->caps[(size_t)i] = batch_query_cap(ks[i], gs[i]->d.m);
         P->cand_total += P->caps[(size_t)i];
     }
-    // Round schedule (same as a single query), per query clipped to its m.
-    std::vector<int64_t> r_lo, r_hi;
-    for (int64_t lo = 0, size = FIRST_ROUND; lo < mmax; lo += size, size *= ROUND_GROWTH) {
-        r_lo.push_back(lo);
-        r_hi.push_back(std::min(mmax, lo + size));
+    // Round schedules: each query follows its own graph's schedule (first
+    // round, growth: the graph's tune, as a single query would); round r of
+    // the batch runs round r of every query (empty once a query's schedule
+    // has covered its edges).
+    (void)mmax;
+    int R = 0;
+    std::vector<std::vector<int64_t>> his((size_t)nq);
+    for (int i = 0; i < nq; i++) {
+        const int64_t m = gs[i]->d.m;
+        const int64_t first = std::max<int64_t>(1, gs[i]->tune.first_round);
+        const int64_t growth = std::max<int32_t>(2, gs[i]->tune.growth);
+        for (int64_t lo = 0, size = first; lo < m; lo += size, size *= growth)
+            his[(size_t)i].push_back(std::min(m, lo + size));
+        R = std::max<int>(R, (int)his[(size_t)i].size());
     }
-    const int R = (int)r_lo.size();
     P->R = R;
     // offs: per round, the query ranges' hi ends (the device computes the
     // live offsets from them and the stop points); totals bound the grids.
@@ -249,8 +257,10 @@ BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes,
     for (int r = 0; r < R; r++) {
         int64_t acc = 0;
         for (int i = 0; i < nq; i++) {
+            const auto& h = his[(size_t)i];
             const int64_t m = gs[i]->d.m;
-            const int64_t a = std::min(m, r_lo[(size_t)r]), b = std::min(m, r_hi[(size_t)r]);
+            const int64_t a = r == 0 ? 0 : (r - 1 < (int)h.size() ? h[(size_t)r - 1] : m);
+            const int64_t b = r < (int)h.size() ? h[(size_t)r] : m;
             P->offs[(size_t)r * nq + i] = b;
             P->los[(size_t)r * nq + i] = a;
             acc += b - a;
@@ -285,6 +295,20 @@ BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes,
 size_t batch_plan_bytes(const BatchPlan* P) { return P->bytes; }
 
 void batch_plan_destroy(BatchPlan* P) { delete P; }
+
+// The last instantiated batch graph of this thread on each device.
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t stream = nullptr;
+    uint64_t instantiations = 0, updates = 0;
+};
+
+GraphCache& graph_cache() {
+    static thread_local GraphCache cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    return cache[dev];
+}
 
 // Uploads the descriptors (small, from pageable memory: the call returns
 // once they are staged) and enqueues every kernel of the batch on s.
@@ -368,17 +392,41 @@ int batch_plan_launch(BatchPlan* P, void* dbuf, cudaStream_t s, int use_graph) {
     if (use_graph) {
         // The descriptors must have landed before the captured work refers
         // to them only through device pointers: that holds, the copies are
-        // ordered on s before the graph launch.
+        // ordered on s before the graph launch.  The instantiated graph is
+        // kept (per thread and device) and refreshed with
+        // cudaGraphExecUpdate when the next batch has the same launch
+        // topology (same number of rounds), so a repeated batch shape is
+        // instantiated once.
         cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             launch_all();
             e = cudaStreamEndCapture(s, &graph);  // always leave capture mode
         }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) {
+            GraphCache& gc = graph_cache();
+            if (gc.exec && gc.stream == s) {
+                cudaGraphExecUpdateResultInfo info;
+                if (cudaGraphExecUpdate(gc.exec, graph, &info) == cudaSuccess) {
+                    exec = gc.exec;
+                    gc.updates++;
+                } else {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(gc.exec);
+                    gc.exec = nullptr;
+                }
+            }
+            if (!exec) {
+                e = cudaGraphInstantiate(&exec, graph, 0);
+                if (e == cudaSuccess) {
+                    gc.exec = exec;
+                    gc.stream = s;
+                    gc.instantiations++;
+                }
+            }
+        }
         if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
-        if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) rc = cuda_error(e, "batch graph", __FILE__, __LINE__);
     } else {

@@ -355,6 +355,7 @@ __global__ void __launch_bounds__(RBLK) k_round(DevGraph G, Query q, int64_t lo,
     // before it has failed its bound (all later edges have no larger bound).
     const volatile uint32_t* stop_rev = &q.st->stop_rev;
     if (lo >= (int64_t)(STOP_NONE - *stop_rev)) return;
+    if (*(volatile const uint32_t*)&q.st->err) return;  // the query has already failed
     const unsigned long long tau = ld_volatile_u64(&q.st->tau);
     const int64_t stride = (int64_t)gridDim.x * RBLK;
     Tally tb;
@@ -543,6 +544,7 @@ __global__ void __launch_bounds__(LBLK) k_long(DevGraph G, Query q) {
     __shared__ int timed_out;
     const uint32_t n_items = min(*(volatile const uint32_t*)q.long_count, q.long_cap);
     if (blockIdx.x >= n_items) return;
+    if (*(volatile const uint32_t*)&q.st->err) return;  // the query has already failed
     const unsigned long long tau = ld_volatile_u64(&q.st->tau);
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
@@ -863,9 +865,11 @@ __device__ __forceinline__ void rank_one(const Query& q, uint32_t i, wtri_tri* o
     const uint32_t n = min(*(volatile uint32_t*)&q.st->count, q.cap);
     const int lane = threadIdx.x & 31;
     if (i == 0 && lane == 0) {
+        // a timeout first: it stops the per-round compaction, so a buffer
+        // overflow that follows it is its consequence, not the cause
         int32_t status = (int32_t)n;
-        if (err & DEV_ERR_OVERFLOW) status = WTRI_ENOMEM;
-        else if (err & DEV_ERR_TIMEOUT) status = WTRI_ETIMEOUT;
+        if (err & DEV_ERR_TIMEOUT) status = WTRI_ETIMEOUT;
+        else if (err & DEV_ERR_OVERFLOW) status = WTRI_ENOMEM;
         else if (err) status = WTRI_ECUDA;
         *out_count = status;
     }

@@ -462,10 +462,11 @@ struct BlockSmem {
 };
 
 // Sorts keys [base, base + cnt) of a row (cnt <= SB) into one run in
-// S.buf[returned index]; also stages the slice's weights and ranks by
-// position.  nw = the power of two of 1024-key slices covering cnt; warp
-// w < nw sorts slice w in registers; log2(nw) merge-path levels in shared
-// memory make one run of nw * 1024 keys (the padding sorts last).
+// S.buf[returned index] (element p at swz(p)); also stages the slice's
+// weights and ranks by position.  nw = the power of two of 1024-key slices
+// covering cnt; warp w < nw sorts slice w in registers; log2(nw) merge-path
+// levels in shared memory make one run of nw * 1024 keys (the padding sorts
+// last).
 __device__ __forceinline__ int block_sort_run(const RowsOut& R, int64_t s, int64_t base, int cnt,
                                               BlockSmem& S) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -485,31 +486,26 @@ __device__ __forceinline__ int block_sort_run(const RowsOut& R, int64_t s, int64
         }
         warp_bitonic<32>(k);
 #pragma unroll
-        for (int i = 0; i < 32; i++) S.buf[0][wid * 1024 + swz(lane * 32 + i)] = k[i];
+        for (int i = 0; i < 32; i++) S.buf[0][swz(wid * 1024 + lane * 32 + i)] = k[i];
     }
     __syncthreads();
+    // Every access below goes through swz (a bijection inside each group of
+    // 32 keys): the merge path writes 4..32 consecutive keys per thread, which
+    // unswizzled would put every lane of a warp on the same bank.
     int cur = 0;
     const int total = nw * 1024;
     const int per = total / NT;  // outputs per thread: 4 .. 32
     for (int len = 1024; len < total; len <<= 1) {
         const unsigned long long* src = S.buf[cur];
         unsigned long long* dst = S.buf[cur ^ 1];
-        // levels above the warp runs keep plain (unswizzled) indices
-        const bool sw_in = len == 1024;
-        auto rd = [&](int p) { return src[sw_in ? (p & ~1023) + swz(p & 1023) : p]; };
         const int q0 = threadIdx.x * per;
         const int pair = q0 / (2 * len), pb = pair * 2 * len;
-        auto A = [&](int64_t i) { return rd(pb + (int)i); };
-        auto B = [&](int64_t i) { return rd(pb + len + (int)i); };
-        merge_out(A, len, B, len, q0 - pb, per, [&](int64_t q, unsigned long long v) { dst[pb + q] = v; });
+        auto A = [&](int64_t i) { return src[swz(pb + (int)i)]; };
+        auto B = [&](int64_t i) { return src[swz(pb + len + (int)i)]; };
+        merge_out(A, len, B, len, q0 - pb, per,
+                  [&](int64_t q, unsigned long long v) { dst[swz(pb + (int)q)] = v; });
         __syncthreads();
         cur ^= 1;
-    }
-    if (nw == 1) {
-        // a single warp run: unswizzle into the other buffer
-        for (int p = threadIdx.x; p < 1024; p += NT) S.buf[1][p] = S.buf[0][swz(p)];
-        __syncthreads();
-        cur = 1;
     }
     return cur;
 }
@@ -577,7 +573,7 @@ __global__ void __launch_bounds__(NT) k_rows_block(RowsOut R, unsigned long long
             const int cnt = (int)min((int64_t)SB, d - base);
             const int b = block_sort_run(R, s, base, cnt, S);
             if (d <= SB) {
-                block_epilogue(R, s, 0, cnt, [&](int p) { return S.buf[b][p]; },
+                block_epilogue(R, s, 0, cnt, [&](int p) { return S.buf[b][swz(p)]; },
                                [&](unsigned long long kk, int32_t& w, int32_t& rk) {
                                    const uint32_t src = key_pos(kk);
                                    w = S.wv[src];
@@ -588,7 +584,7 @@ __global__ void __launch_bounds__(NT) k_rows_block(RowsOut R, unsigned long long
                 // positions in the key are relative to the slice: make them
                 // row positions for the merges and the final epilogue
                 for (int j = threadIdx.x; j < cnt; j += NT)
-                    g0[s + base + j] = S.buf[b][j] + (unsigned long long)base;
+                    g0[s + base + j] = S.buf[b][swz(j)] + (unsigned long long)base;
             }
             __syncthreads();
         }

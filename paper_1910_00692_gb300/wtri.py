@@ -107,6 +107,8 @@ def lib():
     L.wtri_topk_shard.argtypes = [vp, f64, i32, i32, i32, ctypes.POINTER(_Result), vp]
     L.wtri_autotune.argtypes = [vp, i32, i32, ctypes.POINTER(_TuneInfo)]
     L.wtri_set_tune.argtypes = [vp, i64, i32, i32]
+    L.wtri_autotune_buckets.argtypes = [vp, i32, i32, i32, ctypes.POINTER(i32)]
+    L.wtri_autotune_buckets.restype = ctypes.c_int
     L.wtri_merge_topk.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(_Result), vp]
     u64 = ctypes.c_uint64
     L.wtri_server_create.argtypes = [u64, i32, ctypes.POINTER(vp)]
@@ -324,6 +326,17 @@ def merge_topk(parts, k: int):
                                  ctypes.byref(res), keys.ctypes.data_as(ctypes.c_void_p)))
     c = res.count
     return tris[:c].copy(), wts[:c].copy(), keys[:c].copy()
+
+
+def autotune_buckets(graphs, k: int = 1000, reps: int = 2) -> int:
+    """wtri_autotune_buckets: tunes the largest graph of each size group and
+    applies its schedule to the group; returns the number of groups."""
+    n = len(graphs)
+    handles = (ctypes.c_void_p * max(n, 1))(*[g.handle.value for g in graphs])
+    out = ctypes.c_int32()
+    _check(lib().wtri_autotune_buckets(ctypes.cast(handles, ctypes.c_void_p), n, int(k), int(reps),
+                                       ctypes.byref(out)))
+    return out.value
 
 
 def topk_batch(graphs, ps, ks):
