@@ -763,7 +763,7 @@ def run_step_workload(args, world, rank, local):
                 "achieved_gbs": step_bytes / 1e9 / (ms / 1e3),
                 "frac": step_bytes / 1e9 / (ms / 1e3) / peak,
                 "bytes_per_edge": step_bytes / m,
-                "rule": ("COO read 12 B/edge; symmetric id-sorted CSR 16 B/edge and oriented CSR "
+                "rule": ("COO read 12 B/edge; oriented CSR "
                          "12 B/edge written once; row offsets 8 B/vertex each; edge order sort "
                          "8+8 B/edge and weight-sorted rows 24+24 B/edge (one read + one write); "
                          "query: adjacency bytes counted by the instrumented run")}

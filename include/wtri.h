@@ -371,16 +371,15 @@ WTRI_API int wtri_sample_wedges(const wtri_graph* g, double p, int64_t nsamples,
  */
 enum {
     WTRI_ARR_DEGREE = 0,      /* int32[n]     degree d_a */
-    WTRI_ARR_ROWPTR = 1,      /* int64[n+1]   row offsets of both symmetric layouts */
+    WTRI_ARR_ROWPTR = 1,      /* int64[n+1]   row offsets of the weight-sorted rows */
     WTRI_ARR_ORDER_U = 2,     /* int32[m]     edge order: endpoint u of the r-th edge */
     WTRI_ARR_ORDER_V = 3,     /* int32[m]     edge order: endpoint v */
     WTRI_ARR_ORDER_W = 4,     /* int32[m]     edge order: weight (non-increasing) */
     WTRI_ARR_WCOL = 5,        /* int32[2m]    weight-sorted rows: neighbour */
     WTRI_ARR_WWT = 6,         /* int32[2m]    weight-sorted rows: weight */
     WTRI_ARR_WRANK = 7,       /* int32[2m]    weight-sorted rows: edge rank r */
-    WTRI_ARR_SCOL = 8,        /* int32[2m]    id-sorted rows: neighbour */
-    WTRI_ARR_SWT = 9,         /* int32[2m]    id-sorted rows: weight */
-    WTRI_ARR_SRANK = 10,      /* int32[2m]    id-sorted rows: edge rank r */
+    /* 8..10: unused (no symmetric id-sorted rows are kept: every lookup
+       searches the one oriented row that can hold the edge) */
     WTRI_ARR_OROWPTR = 11,    /* int64[n+1]   oriented row offsets */
     WTRI_ARR_OCOL = 12,       /* int32[m]     oriented rows: higher-ranked endpoint */
     WTRI_ARR_OWT = 13,        /* int32[m]     oriented rows: weight */
@@ -398,8 +397,8 @@ WTRI_API int wtri_graph_copy_array(const wtri_graph* g, int which, void* dst,
  * WTRI_ENOTFOUND past the last phase.  wtri_prof_reset clears the totals.
  *
  * Algorithmic bytes: the COO input read once (12 per edge); each resident
- * output written once (the symmetric id-sorted rows 16 per edge, the
- * oriented rows 12 per edge, each row-offset array 8 per vertex); each
+ * output written once (the oriented rows 12 per edge, each row-offset
+ * array 8 per vertex); each
  * sort one read and one write of its payload (the edge order 8 + 8 per
  * edge, the weight-sorted rows 24 + 24 per edge) whatever its number of
  * passes, spread evenly over the passes; histogram, scan and other helper
@@ -420,7 +419,7 @@ WTRI_API int wtri_prof_read_ex(int idx, char* name, int name_cap, long long* cal
  * Instrumented query (no counterpart in the paper): while on != 0, the
  * exact top-k kernels (single and device queries) count the bytes of every
  * global load they issue on the graph's adjacency structures (edge order,
- * weight-sorted, id-sorted and oriented rows, offsets, degrees) into a
+ * weight-sorted and oriented rows, offsets, degrees) into a
  * counter of the current device.  The counting costs time: time queries
  * with it off.  *bytes receives the counter after the device is idle
  * (cudaDeviceSynchronize); reset != 0 zeroes it afterwards.  bytes may be

@@ -530,11 +530,6 @@ WTRI_API int wtri_graph_copy_array(const wtri_graph* g, int which, void* dst,
         case WTRI_ARR_WCOL: src = g->d.wcol; bytes = 8 * m; break;
         case WTRI_ARR_WWT: src = g->d.wwt; bytes = 8 * m; break;
         case WTRI_ARR_WRANK: src = g->d.wrk; bytes = 8 * m; break;
-        case WTRI_ARR_SCOL: src = g->d.scol; bytes = 8 * m; break;
-        case WTRI_ARR_SWT: src = g->d.swt; bytes = 8 * m; break;
-        case WTRI_ARR_SRANK:
-            return set_error(WTRI_EUNSUPPORTED,
-                             "edge ranks of the id-sorted rows are not kept (the oriented rows carry them)");
         case WTRI_ARR_OROWPTR: src = g->d.orowptr; bytes = 8 * (n + 1); break;
         case WTRI_ARR_OCOL: src = g->d.ocol; bytes = 4 * m; break;
         case WTRI_ARR_OWT: src = g->d.owt; bytes = 4 * m; break;

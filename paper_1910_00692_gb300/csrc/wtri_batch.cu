@@ -124,20 +124,21 @@ __global__ void __launch_bounds__(LBLK) k_long_batch(BatchDev B, const LongItem*
         const Query& q = B.queries[qi];
         const DevGraph& G = B.graphs[qi];
         const unsigned long long tau = ld_volatile_u64(&q.st->tau);
-        const int64_t ybeg = __ldg(G.rowptr + item.y), yend = __ldg(G.rowptr + item.y + 1);
-        const int32_t dy = (int32_t)(yend - ybeg);
-        const bool staged = dy <= STAGE_MAX;
+        const int64_t dy = __ldg(G.rowptr + item.y + 1) - __ldg(G.rowptr + item.y);
+        const int64_t obeg = __ldg(G.orowptr + item.y);
+        const int32_t ody = (int32_t)(__ldg(G.orowptr + item.y + 1) - obeg);
+        const bool staged = ody > 0 && ody <= STAGE_MAX;
         int32_t off = 0;
-        if (staged && !stage_row(G, ybeg, dy, srow, &bar, phase, off, &q.st->err, &timed_out,
+        if (staged && !stage_row(G, obeg, ody, srow, &bar, phase, off, &q.st->err, &timed_out,
                                  WAIT_LIMIT))
             return;
         Tally tb;
         switch (B.pcodes[qi]) {
-            case P_MIN: long_scan<P_MIN, false>(G, q, tau, item, srow, off, ybeg, dy, staged, tb); break;
-            case P_ONE: long_scan<P_ONE, false>(G, q, tau, item, srow, off, ybeg, dy, staged, tb); break;
-            case P_TWO: long_scan<P_TWO, false>(G, q, tau, item, srow, off, ybeg, dy, staged, tb); break;
-            case P_GEO: long_scan<P_GEO, false>(G, q, tau, item, srow, off, ybeg, dy, staged, tb); break;
-            default: long_scan<P_MAX, false>(G, q, tau, item, srow, off, ybeg, dy, staged, tb); break;
+            case P_MIN: long_scan<P_MIN, false>(G, q, tau, item, srow, off, obeg, ody, dy, staged, tb); break;
+            case P_ONE: long_scan<P_ONE, false>(G, q, tau, item, srow, off, obeg, ody, dy, staged, tb); break;
+            case P_TWO: long_scan<P_TWO, false>(G, q, tau, item, srow, off, obeg, ody, dy, staged, tb); break;
+            case P_GEO: long_scan<P_GEO, false>(G, q, tau, item, srow, off, obeg, ody, dy, staged, tb); break;
+            default: long_scan<P_MAX, false>(G, q, tau, item, srow, off, obeg, ody, dy, staged, tb); break;
         }
         __syncthreads();
     }

@@ -1,5 +1,5 @@
 // Device graph build: validation, degrees, the edge order, per-vertex
-// weight-sorted lists, id-sorted lists and the degree orientation.
+// weight-sorted lists and the degree-oriented id-sorted lists.
 //
 // Preprocessing named by the paper: "Sort E in decreasing order of weight"
 // (Algorithm 2, first step), neighbour sets N(a) and degrees d_a (Section
@@ -16,15 +16,16 @@
 //      order" is stably radix-sorted by row, so each row keeps edge order.
 //   4. Row offsets and degrees from the boundaries of the sorted rows (no
 //      atomics).
-//   5. Oriented out-degrees (neighbours of higher (degree, id) rank) and
-//      their scan, the oriented row offsets.
-//   6. Per-row segmented sort of the weight-sorted rows by neighbour id
-//      (wtri_rows.cuh): the id-sorted rows, the oriented rows in place, and
-//      repeated pairs (equal neighbours next to each other).
+//   5. Orientation of every entry (neighbour of higher (degree, id) rank),
+//      the oriented out-degrees and their scan (the oriented row offsets);
+//      per-row segmented sort of the forward entries by neighbour id
+//      (wtri_rows.cuh): the oriented rows, and repeated pairs (equal
+//      neighbours next to each other in one oriented row).
 #include <cuda_runtime.h>
 #include <stdio.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 
 #include "wtri_internal.cuh"
@@ -42,7 +43,8 @@ struct BuildStatus {
     int32_t wmax;
     int32_t maxdeg;
     int32_t pad;
-    unsigned long long first_bad;  // smallest offending edge index
+    unsigned long long first_bad;  // smallest offending edge index; for a repeated
+                                   // pair, the smallest x << 32 | c of its oriented row
 };
 
 __global__ void k_validate(int32_t n, int64_t m, const int32_t* __restrict__ u,
@@ -272,16 +274,16 @@ __global__ void k_rowptr_from_rows(int32_t n, int64_t n2, const int32_t* __restr
     }
 }
 
-// Degrees saturated to 8 bits (the form the orientation test gathers: one
-// byte per vertex, small enough to stay in L2) and the maximum degree.
-__global__ void k_degrees(int32_t n, const int64_t* __restrict__ rowptr, uint8_t* __restrict__ deg8,
+// Degrees saturated to 16 bits (the form the orientation test gathers: two
+// bytes per vertex, small enough to stay mostly in L2) and the maximum degree.
+__global__ void k_degrees(int32_t n, const int64_t* __restrict__ rowptr, uint16_t* __restrict__ deg16,
                           BuildStatus* st) {
     if (*(volatile const uint32_t*)&st->err) return;
     int32_t mx = 0;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = rowptr[x + 1] - rowptr[x];
-        deg8[x] = (uint8_t)min(d, (int64_t)rows::DEG8_SAT);
+        deg16[x] = (uint16_t)min(d, (int64_t)rows::DEG_SAT);
         mx = max(mx, (int32_t)min(d, (int64_t)INT32_MAX));
     }
 #pragma unroll
@@ -350,7 +352,7 @@ unsigned grid_for(int64_t work, int per_block = BLK) {
 // upper bound on any degree (sets the number of hub merge levels launched;
 // levels that no row needs return at once).
 int sort_rows(const rows::RowsOut& R, unsigned long long* g0, unsigned long long* g1, int32_t* cursor,
-              int64_t max_deg_bound, const uint32_t* gate, cudaStream_t s) {
+              int64_t max_deg_bound, int nbits, const uint32_t* gate, cudaStream_t s) {
     const int sms = sm_count();
     {
         ProfScope ps("rows_sort_small", s, 0.0, 3);
@@ -359,7 +361,7 @@ int sort_rows(const rows::RowsOut& R, unsigned long long* g0, unsigned long long
         rows::k_rows_small<32><<<sms * 8, rows::NT, 0, s>>>(R, rows::CLS_G32, gate);
     }
     {
-        ProfScope ps("rows_sort_warp", s, 0.0, 5);
+        ProfScope ps("rows_sort_warp", s, 0.0, 4);
         auto launch = [&](auto kern, int epl, int cls) -> int {
             static std::atomic<uint64_t> done[6];
             const int smem = rows::NWARPS * 32 * epl * 16;  // keys + weights + ranks
@@ -373,20 +375,19 @@ int sort_rows(const rows::RowsOut& R, unsigned long long* g0, unsigned long long
         WTRI_TRY(launch(rows::k_rows_warp<4>, 4, rows::CLS_W4));
         WTRI_TRY(launch(rows::k_rows_warp<8>, 8, rows::CLS_W8));
         WTRI_TRY(launch(rows::k_rows_warp<16>, 16, rows::CLS_W16));
-        WTRI_TRY(launch(rows::k_rows_warp<32>, 32, rows::CLS_W32));
     }
     {
         ProfScope ps("rows_sort_block", s, 0.0, 1);
         static std::atomic<uint64_t> done{0};
-        const int smem = (int)sizeof(rows::BlockSmem);
+        const int smem = (int)sizeof(rows::RadixSmem);
         WTRI_TRY(smem_optin((const void*)rows::k_rows_block, smem, done));
-        rows::k_rows_block<<<sms, rows::NT, smem, s>>>(R, g0, cursor, gate);
+        rows::k_rows_block<<<sms * 2, rows::NT, smem, s>>>(R, g0, cursor, nbits, gate);
     }
     {
         int levels = 0;
-        for (int64_t len = rows::SB; len < max_deg_bound; len <<= 1) levels++;
+        for (int64_t len = rows::SR; len < max_deg_bound; len <<= 1) levels++;
         ProfScope ps("rows_sort_hub", s, 0.0, levels + 1);
-        int64_t len = rows::SB;
+        int64_t len = rows::SR;
         for (int l = 0; l < levels; l++, len <<= 1)
             rows::k_rows_merge<<<sms * 4, rows::NT, 0, s>>>(R, (l & 1) ? g1 : g0, (l & 1) ? g0 : g1, len,
                                                             gate);
@@ -436,7 +437,6 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     const size_t o_rowptr = take(8 * (N1 + 1)), o_orowptr = take(8 * (N1 + 1));
     const size_t o_ou = take(4 * M), o_ov = take(4 * M), o_ow = take(4 * M);
     const size_t o_wcol = take(4 * M2), o_wwt = take(4 * M2), o_wrk = take(4 * M2);
-    const size_t o_scol = take(4 * M2), o_swt = take(4 * M2);
     const size_t o_ocol = take(4 * M), o_owt = take(4 * M), o_ork = take(4 * M);
     const size_t total = off;
 
@@ -456,7 +456,6 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     int64_t* orowptr = (int64_t*)(B + o_orowptr);
     int32_t *ou = (int32_t*)(B + o_ou), *ov = (int32_t*)(B + o_ov), *ow = (int32_t*)(B + o_ow);
     int32_t *wcol = (int32_t*)(B + o_wcol), *wwt = (int32_t*)(B + o_wwt), *wrk = (int32_t*)(B + o_wrk);
-    int32_t *scol = (int32_t*)(B + o_scol), *swt = (int32_t*)(B + o_swt);
     int32_t *ocol = (int32_t*)(B + o_ocol), *owt = (int32_t*)(B + o_owt), *ork = (int32_t*)(B + o_ork);
 
     auto fail = [&](int rc) {
@@ -510,8 +509,8 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         uint16_t* dig = (uint16_t*)(rec_b + rec_words / 4);
         uint32_t* counts = (uint32_t*)dig + dig_words;
         int32_t* wrow = (int32_t*)(counts + cnt_words);
-        uint8_t* deg8 = (uint8_t*)(wrow + n2);  // n bytes (room for 2n reserved)
-        int32_t* odeg = (int32_t*)(deg8 + 4 * ((N1 + 1) / 2 + 4));
+        uint16_t* deg16 = (uint16_t*)(wrow + n2);  // n halfwords
+        int32_t* odeg = (int32_t*)(deg16 + 2 * ((N1 + 1) / 2 + 4));
         int32_t* list = odeg + N1 + 4;
         int32_t* small = list + N1 + 4;  // class counts, offsets, fill cursors, block-row cursor
         int32_t* cls_cnt = small;
@@ -547,40 +546,40 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         {
             ProfScope ps("row_offsets", s, 8.0 * (n + 1), 2, 4.0 * n2 + 8.0 * (n + 1) + 2.0 * n);
             k_rowptr_from_rows<<<grid_for(n2), BLK, 0, s>>>(n, n2, wrow, rowptr, gate);
-            k_degrees<<<grid_for(n), BLK, 0, s>>>(n, rowptr, deg8, d_st);
+            k_degrees<<<grid_for(n), BLK, 0, s>>>(n, rowptr, deg16, d_st);
         }
-        // 5. row classes by degree
+        // 5. orientation of every entry and the oriented out-degrees (the
+        //    forward entries' keys packed per row in rec_b), their scan (the
+        //    oriented row offsets), the rows' size classes by oriented degree,
+        //    then the per-row sort by id writing the oriented rows.  Scratch:
+        //    the record buffers, free once the radix sorts are done (g0/g1:
+        //    the hub rows' runs, 8 bytes per entry each, in rec_a).
         {
-            ProfScope ps("orient_classes", s, 0.0, 3, 4.0 * n + 24.0 * n);
-            rows::k_class_count<<<grid_for(n, rows::NT), rows::NT, 0, s>>>(n, rowptr, cls_cnt, gate);
-            rows::k_class_offsets<<<1, 32, 0, s>>>(cls_cnt, cls_off, cls_cur, gate);
-            rows::k_class_fill<<<grid_for(n, rows::NT), rows::NT, 0, s>>>(n, rowptr, cls_cur, list, gate);
-        }
-        // 6. orientation of every entry (a bit each) and the oriented
-        //    out-degrees, their scan (the oriented row offsets), then the
-        //    per-row sort by id: the id-sorted rows and the oriented rows in
-        //    place.  Scratch: the record buffers, free once the radix sorts
-        //    are done (g0/g1: the hub rows' runs, 8 bytes per entry each, in
-        //    rec_a; the orientation bits in rec_b).
-        {
-            // reads the weight-sorted rows once; writes the symmetric
-            // id-sorted rows (16 B per edge), the oriented rows (12 B per
-            // edge) and their offsets (8 B per vertex)
-            ProfScope ps("rows_sort", s, 16.0 * m + 12.0 * m + 8.0 * (n + 1), 0,
-                         8.0 * n2 + 0.125 * n2 + 24.0 * n2 + 16.0 * m + 12.0 * m + 8.0 * (n + 1));
+            // reads the weight-sorted rows once; writes the oriented rows
+            // (12 B per edge) and their offsets (8 B per vertex)
+            ProfScope ps("rows_sort", s, 12.0 * m + 8.0 * (n + 1), 0,
+                         8.0 * n2 + n2 + 8.0 * m + 8.0 * m + 8.0 * m + 12.0 * m + 8.0 * (n + 1));
             unsigned long long* g0 = (unsigned long long*)rec_a;
             unsigned long long* g1 = g0 + n2;
-            uint32_t* fwd = (uint32_t*)rec_b;
+            unsigned long long* pk = (unsigned long long*)rec_b;
             {
                 ProfScope pf("rows_sort_fwd", s, 0.0, 1);
-                rows::k_fwd<<<grid_for(n2, rows::NT), rows::NT, 0, s>>>(n2, wrow, wcol, rowptr, deg8, fwd, odeg,
+                rows::k_fwd<<<grid_for(n2, rows::NT), rows::NT, 0, s>>>(n2, wrow, wcol, rowptr, deg16, pk, odeg,
                                                                         gate);
             }
             WTRI_TRY(exclusive_scan_i32_to_i64(odeg, orowptr, n, s));
-            rows::RowsOut R{rowptr, wcol, wwt, wrk, deg8, scol, swt, fwd, orowptr, ocol, owt, ork,
+            {
+                ProfScope pc("orient_classes", s, 0.0, 3, 4.0 * n + 8.0 * n);
+                rows::k_class_count<<<grid_for(n, rows::NT), rows::NT, 0, s>>>(n, odeg, cls_cnt, gate);
+                rows::k_class_offsets<<<1, 32, 0, s>>>(cls_cnt, cls_off, cls_cur, gate);
+                rows::k_class_fill<<<grid_for(n, rows::NT), rows::NT, 0, s>>>(n, odeg, cls_cur, list, gate);
+            }
+            rows::RowsOut R{rowptr, wwt, wrk, pk, odeg, orowptr, ocol, owt, ork,
                             &d_st->err, &d_st->first_bad, list, cls_off};
-            const int64_t max_deg = std::min<int64_t>((int64_t)n - 1, m);
-            WTRI_TRY(sort_rows(R, g0, g1, cursor, max_deg, gate, s));
+            // d forward neighbours all have degree >= d: d^2 <= 2m
+            int64_t od_max = (int64_t)std::sqrt(2.0 * (double)m) + 1;
+            od_max = std::min<int64_t>(od_max, std::min<int64_t>((int64_t)n - 1, m));
+            WTRI_TRY(sort_rows(R, g0, g1, cursor, od_max, nbits, gate, s));
         }
         if (cudaGetLastError() != cudaSuccess)
             return fail(set_error(WTRI_ECUDA, "build kernel launch failed"));
@@ -603,12 +602,9 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     if (h_st.err & DEV_ERR_TIMEOUT)
         return fail(set_error(WTRI_ETIMEOUT, "a bounded wait in the radix sort ran out"));
     if (h_st.err & DEV_ERR_DUPLICATE) {
-        int32_t col = -1;
-        const int64_t j = (int64_t)h_st.first_bad;
-        cudaMemcpyAsync(&col, scol + j, 4, cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
-        return fail(set_error(WTRI_EINVAL, "repeated undirected pair: neighbour " + std::to_string(col) +
-                                               " appears twice in one row"));
+        const uint64_t pr = (uint64_t)h_st.first_bad;
+        return fail(set_error(WTRI_EINVAL, "repeated undirected pair {" + std::to_string((uint32_t)(pr >> 32)) +
+                                               ", " + std::to_string((uint32_t)pr) + "}"));
     }
     if (h_st.err) return fail(set_error(WTRI_ECUDA, "internal error in the build"));
     g->d.wmax = h_st.wmax;
@@ -621,8 +617,6 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     g->d.wcol = wcol;
     g->d.wwt = wwt;
     g->d.wrk = wrk;
-    g->d.scol = scol;
-    g->d.swt = swt;
     g->d.ocol = ocol;
     g->d.owt = owt;
     g->d.ork = ork;

@@ -62,14 +62,15 @@ int p_to_code_for(double p, const wtri_graph* g, int* code);
 // Layouts (r is an edge's position in the edge order: weight desc, input
 // index asc):
 //   ord_u/v/w[r]          edge order
-//   rowptr[n+1]           offsets of both symmetric layouts (degree d_x =
+//   rowptr[n+1]           offsets of the weight-sorted lists (degree d_x =
 //                         rowptr[x+1] - rowptr[x])
 //   wcol/wwt/wrk[2m]      per-vertex lists in edge order (weight-sorted)
-//   scol/swt[2m]          per-vertex lists by neighbour id
 //   orowptr[n+1]          offsets of the oriented lists
 //   ocol/owt/ork[m]       oriented lists by neighbour id: each edge once, at
-//                         its endpoint of lower (degree, id) rank
-// 64 bytes per edge and 16 per vertex.
+//                         its endpoint of lower (degree, id) rank; the
+//                         lookup of edge {a, b} searches the one list that
+//                         can hold it
+// 48 bytes per edge and 16 per vertex.
 // ---------------------------------------------------------------------------
 struct DevGraph {
     int32_t n;
@@ -84,8 +85,6 @@ struct DevGraph {
     const int32_t* wcol;
     const int32_t* wwt;
     const int32_t* wrk;
-    const int32_t* scol;
-    const int32_t* swt;
     const int32_t* ocol;
     const int32_t* owt;
     const int32_t* ork;

@@ -214,15 +214,19 @@ __device__ __forceinline__ int64_t suffix_start(const DevGraph& G, int64_t lo, i
 
 // Closing edge (y, c) in the oriented lists: stored once, at the endpoint of
 // lower (degree, id) rank, rows ascending by id (row s at
-// [orowptr[s], orowptr[s+1])).
-__device__ __forceinline__ bool probe_oriented(const DevGraph& G, int32_t y, int64_t dy, int32_t c,
-                                               int32_t& wyc, int32_t& ryc, Tally& tb) {
+// [orowptr[s], orowptr[s+1])).  y_owns: whether y is that endpoint.
+__device__ __forceinline__ bool y_owns(const DevGraph& G, int32_t y, int64_t dy, int32_t c, Tally& tb) {
     const int64_t dc = __ldg(G.rowptr + c + 1) - __ldg(G.rowptr + c);
-    const bool ylow = dy < dc || (dy == dc && y < c);
-    const int32_t s = ylow ? y : c, t = ylow ? c : y;
+    tb.add(16);
+    return dy < dc || (dy == dc && y < c);
+}
+
+// Searches oriented row s for t.
+__device__ __forceinline__ bool search_oriented(const DevGraph& G, int32_t s, int32_t t, int32_t& wst,
+                                                int32_t& rst, Tally& tb) {
     int64_t lo = __ldg(G.orowptr + s), hi = __ldg(G.orowptr + s + 1);
     const int64_t end = hi;
-    tb.add(32);
+    tb.add(16);
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
         tb.add(4);
@@ -231,12 +235,18 @@ __device__ __forceinline__ bool probe_oriented(const DevGraph& G, int32_t y, int
     }
     if (lo < end) tb.add(4);
     if (lo < end && __ldg(G.ocol + lo) == t) {
-        wyc = __ldg(G.owt + lo);
-        ryc = __ldg(G.ork + lo);
+        wst = __ldg(G.owt + lo);
+        rst = __ldg(G.ork + lo);
         tb.add(8);
         return true;
     }
     return false;
+}
+
+__device__ __forceinline__ bool probe_oriented(const DevGraph& G, int32_t y, int64_t dy, int32_t c,
+                                               int32_t& wyc, int32_t& ryc, Tally& tb) {
+    return y_owns(G, y, dy, c, tb) ? search_oriented(G, y, c, wyc, ryc, tb)
+                                   : search_oriented(G, c, y, wyc, ryc, tb);
 }
 
 // Warp-aggregated append: the active lanes appending to the same query
@@ -374,10 +384,11 @@ inline unsigned round_grid(int64_t edges) {
 }
 
 // ---------------------------------------------------------------------------
-// Deferred long scans: one block per item.  The y row (ids) is staged in
-// shared memory with a bulk async copy completed on an mbarrier; lookups of
-// the closing edge are binary searches there.  Rows longer than STAGE_MAX
-// fall back to the oriented lists in global memory.
+// Deferred long scans: one block per item.  y's oriented row (ids) is
+// staged in shared memory with a bulk async copy completed on an mbarrier;
+// closing edges that y owns are binary searches there, the others searches
+// of the neighbour's oriented row in global memory.  Oriented rows longer
+// than STAGE_MAX are searched in global memory too.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -412,24 +423,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
     return ok != 0;
 }
 
-// Stages y's id-sorted row in shared memory with one bulk copy (bounded
-// wait: at most `limit` polls; a limit of 0 does not wait at all, which
-// tests use to take the timeout path on purpose).  Returns false if the
-// wait ran out (error recorded); the copy in flight is then drained with the
-// full WAIT_LIMIT before the block goes on, so no copy outlives its block.
-__device__ __forceinline__ bool stage_row(const DevGraph& G, int64_t ybeg, int32_t dy,
-                                          int32_t* srow, uint64_t* bar, uint32_t& phase,
-                                          int32_t& off, uint32_t* err, int* timed_out,
-                                          uint32_t limit) {
+// Stages y's oriented row (ids; beg = orowptr[y], len entries) in shared
+// memory with one bulk copy (bounded wait: at most `limit` polls; a limit of
+// 0 does not wait at all, which tests use to take the timeout path on
+// purpose).  Returns false if the wait ran out (error recorded); the copy in
+// flight is then drained with the full WAIT_LIMIT before the block goes on,
+// so no copy outlives its block.
+__device__ __forceinline__ bool stage_row(const DevGraph& G, int64_t beg, int32_t len, int32_t* srow,
+                                          uint64_t* bar, uint32_t& phase, int32_t& off, uint32_t* err,
+                                          int* timed_out, uint32_t limit) {
     // 16-byte aligned source: round the start down, the size up (the id
     // array has 16 bytes of slack after its end).
-    const int64_t a0 = ybeg & ~int64_t(3);
-    off = (int32_t)(ybeg - a0);
-    const uint32_t bytes = (uint32_t)(((off + dy) * 4 + 15) & ~15);
+    const int64_t a0 = beg & ~int64_t(3);
+    off = (int32_t)(beg - a0);
+    const uint32_t bytes = (uint32_t)(((off + len) * 4 + 15) & ~15);
     if (threadIdx.x == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, bytes);
-        bulk_g2s(srow, G.scol + a0, bytes, bar);
+        bulk_g2s(srow, G.ocol + a0, bytes, bar);
     }
     bool landed = false;
     for (uint32_t spins = 0; spins < limit; spins++) {
@@ -460,7 +471,7 @@ __device__ __forceinline__ bool stage_row(const DevGraph& G, int64_t ybeg, int32
 template <int P, bool SAMPLED>
 __device__ __forceinline__ void long_scan(const DevGraph& G, const Query& q, unsigned long long tau,
                                           const LongItem& item, const int32_t* srow, int32_t off,
-                                          int64_t ybeg, int64_t dy, bool staged, Tally& tb) {
+                                          int64_t obeg, int32_t ody, int64_t dy, bool staged, Tally& tb) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t w = (uint32_t)item.w, ymax = (uint32_t)item.ymax;
     const int32_t x = item.x, y = item.y, r = item.r;
@@ -483,28 +494,25 @@ __device__ __forceinline__ void long_scan(const DevGraph& G, const Query& q, uns
         if (live) {
             int32_t wyc = 0, ryc = -1;
             bool found = false;
-            if (staged) {
-                int lo = 0, hi = dy;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (srow[off + mid] < c) lo = mid + 1;
-                    else hi = mid;
-                }
-                if (lo < dy && srow[off + lo] == c) {
-                    found = true;
-                    wyc = __ldg(G.swt + ybeg + lo);
-                    tb.add(4);
-                    // (y, c) lighter than r comes after r in the edge order;
-                    // otherwise its position decides, from the oriented row
-                    if ((uint32_t)wyc < w) {
-                        ryc = INT32_MAX;
-                    } else {
-                        int32_t w2 = 0;
-                        probe_oriented(G, y, dy, c, w2, ryc, tb);
+            if (y_owns(G, y, dy, c, tb)) {
+                if (staged) {
+                    int lo = 0, hi = ody;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (srow[off + mid] < c) lo = mid + 1;
+                        else hi = mid;
                     }
+                    if (lo < ody && srow[off + lo] == c) {
+                        found = true;
+                        wyc = __ldg(G.owt + obeg + lo);
+                        ryc = __ldg(G.ork + obeg + lo);
+                        tb.add(8);
+                    }
+                } else {
+                    found = search_oriented(G, y, c, wyc, ryc, tb);
                 }
             } else {
-                found = probe_oriented(G, y, dy, c, wyc, ryc, tb);
+                found = search_oriented(G, c, y, wyc, ryc, tb);
             }
             if (found && (tb.add(4), owns<SAMPLED>(q, r, __ldg(G.wrk + j), ryc))) {
                 const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc, q.gp);
@@ -518,10 +526,11 @@ __device__ __forceinline__ void long_scan(const DevGraph& G, const Query& q, uns
     }
 }
 
-// Deferred long scans: one block per item.  The y row (ids) is staged in
-// shared memory with a bulk async copy completed on an mbarrier; lookups of
-// the closing edge are binary searches there.  Rows longer than STAGE_MAX
-// fall back to the oriented lists in global memory.
+// Deferred long scans: one block per item.  y's oriented row (ids) is
+// staged in shared memory with a bulk async copy completed on an mbarrier;
+// closing edges that y owns are binary searches there, the others searches
+// of the neighbour's oriented row in global memory.  Oriented rows longer
+// than STAGE_MAX are searched in global memory too.
 template <int P, bool SAMPLED = false>
 __global__ void __launch_bounds__(LBLK) k_long(DevGraph G, Query q);
 
@@ -557,15 +566,16 @@ __global__ void __launch_bounds__(LBLK) k_long(DevGraph G, Query q) {
     tb.on = q.qbytes != nullptr;
     for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
         const LongItem item = q.longs[it];
-        const int64_t ybeg = __ldg(G.rowptr + item.y), yend = __ldg(G.rowptr + item.y + 1);
-        const int32_t dy = (int32_t)(yend - ybeg);
-        const bool staged = dy <= STAGE_MAX;
+        const int64_t dy = __ldg(G.rowptr + item.y + 1) - __ldg(G.rowptr + item.y);
+        const int64_t obeg = __ldg(G.orowptr + item.y);
+        const int32_t ody = (int32_t)(__ldg(G.orowptr + item.y + 1) - obeg);
+        const bool staged = ody > 0 && ody <= STAGE_MAX;
         int32_t off = 0;
-        if (staged && !stage_row(G, ybeg, dy, srow, &bar, phase, off, &q.st->err, &timed_out,
+        if (staged && !stage_row(G, obeg, ody, srow, &bar, phase, off, &q.st->err, &timed_out,
                                  q.wait_first))
             break;
-        if (staged && threadIdx.x == 0) tb.add((uint32_t)dy * 4u);  // the staged row
-        long_scan<P, SAMPLED>(G, q, tau, item, srow, off, ybeg, dy, staged, tb);
+        if (staged && threadIdx.x == 0) tb.add((uint32_t)ody * 4u + 32u);  // offsets, the staged row
+        long_scan<P, SAMPLED>(G, q, tau, item, srow, off, obeg, ody, dy, staged, tb);
         __syncthreads();  // the staged row is reused by the next item
     }
     flush_tally(q, tb);

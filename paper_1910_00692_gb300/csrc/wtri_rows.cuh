@@ -1,34 +1,38 @@
-// Id-sorted symmetric rows and the degree orientation, derived from the
+// The oriented rows of NodeIterator++ (Section 5.2), derived from the
 // weight-sorted rows by a per-row segmented sort.
 //
 // Input: the weight-sorted rows (row x holds its neighbours in edge order at
 // [rowptr[x], rowptr[x+1]) of wcol / wwt / wrk) and the row of each entry
-// (wrow, build scratch).  Output, for every row x:
-//   * scol / swt at the same positions, ascending by neighbour id (N(a) of
-//     Section 4, the lists the closing-edge lookups search);
-//   * the oriented row of NodeIterator++ (Section 5.2): the neighbours c of
-//     higher (degree, id) rank than x, ascending by id, at
-//     [orowptr[x], orowptr[x+1]) of ocol / owt / ork;
-//   * repeated pairs (a neighbour twice in one row) flagged as an invalid
-//     input (Section 1: a simple graph).
+// (wrow, build scratch).  Output, for every row x: the neighbours c of
+// higher (degree, id) rank than x, ascending by id, at [orowptr[x],
+// orowptr[x+1]) of ocol / owt / ork -- every edge once, under its
+// lower-ranked endpoint, the lists the closing-edge lookups search (N(a) of
+// Section 4, split by the orientation).  A neighbour twice in one row is a
+// repeated pair, an invalid input (Section 1: a simple graph); both copies
+// of a pair land in the same oriented row, so the sort finds every repeat.
 //
-// Rows are sorted by size class, every sort on 64-bit keys (id << 32 |
-// position in the row), unique within a row:
+// k_fwd decides the orientation of every entry at once and packs each
+// forward entry's key (id << 32 | position in the weight-sorted row) into
+// the first odeg[x] slots of its row's range in scratch (unordered: one
+// atomic per row and warp).  A scan of odeg gives orowptr.  Rows are then
+// sorted by their oriented degree d, on 64-bit keys (id << 32 | index of the
+// key among the row's packed keys), unique within a row:
 //   d <= 32           sub-warp bitonic network in registers (groups of 8, 16
 //                     or 32 lanes, several rows per warp);
-//   32 < d <= 1024    one warp per row: bitonic network over 2..32 keys per
+//   32 < d <= 512     one warp per row: bitonic network over 2..16 keys per
 //                     lane in registers, transposed through shared memory;
-//   1024 < d          one block per row: warp-sorted runs of 1024 merged by
-//                     merge path in shared memory into runs of SB; rows above
-//                     SB leave their sorted runs in global scratch, where one
+//   512 < d           one block per row: stable LSD radix sort of the ids in
+//                     shared memory (digits of at most 9 bits, ranked by warp
+//                     ballots), slices of at most SR keys; rows above SR
+//                     leave their sorted slices in global scratch, where one
 //                     launch per merge level (many blocks, one row each)
 //                     merges pairs of runs until the row is one run.
-// The orientation is decided first, for every entry at once (k_fwd: a bit
-// per entry, whether the neighbour ranks above the row's vertex, and the
-// oriented out-degree of each row); a scan gives the oriented offsets
-// orowptr.  The bit then travels inside the sort key (id << 32 | bit << 31
-// | position), so the sorts write the oriented entries in place with no
-// gathers of their own.
+// A bitonic network spends log d (log d + 1) / 2 compare-exchange stages
+// on every key, the radix sort a fixed number of passes (3 for 26-bit ids):
+// the network wins on short rows, the radix sort from a few hundred keys.
+// A vertex with d forward neighbours has d neighbours of degree >= d, so
+// d <= sqrt(2m): the oriented rows are short even where the full rows are
+// not.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -41,18 +45,17 @@ namespace rows {
 
 constexpr int NT = 256;           // block kernels
 constexpr int NWARPS = NT / 32;
-constexpr int WMAX = 1024;        // longest row sorted by one warp
-constexpr int SB = 8192;          // longest run a block sorts in shared memory
-constexpr int MOPT = 16;          // merge path: outputs per thread and step
+constexpr int WMAX = 512;         // longest row sorted by one warp
+constexpr int SR = 4096;          // longest slice a block radix-sorts in shared memory
 
-// Size classes of a row (by degree d): three sub-warp classes, five warp
-// classes by keys per lane (2, 4, 8, 16, 32), block rows, hub rows (> SB).
+// Size classes of a row (by oriented degree d): three sub-warp classes, four
+// warp classes by keys per lane (2, 4, 8, 16), block rows, hub rows (> SR).
 enum : int {
     CLS_NONE = 0, CLS_G8, CLS_G16, CLS_G32,
-    CLS_W2, CLS_W4, CLS_W8, CLS_W16, CLS_W32,
+    CLS_W2, CLS_W4, CLS_W8, CLS_W16,
     CLS_BLOCK, CLS_HUB
 };
-constexpr int NCLS = 11;
+constexpr int NCLS = 10;
 
 __device__ __forceinline__ int row_class(int64_t d) {
     if (d <= 0) return CLS_NONE;
@@ -62,23 +65,23 @@ __device__ __forceinline__ int row_class(int64_t d) {
     if (d <= 64) return CLS_W2;
     if (d <= 128) return CLS_W4;
     if (d <= 256) return CLS_W8;
-    if (d <= 512) return CLS_W16;
-    if (d <= WMAX) return CLS_W32;
-    if (d <= SB) return CLS_BLOCK;
+    if (d <= WMAX) return CLS_W16;
+    if (d <= SR) return CLS_BLOCK;
     return CLS_HUB;
 }
 
 // Whether x (degree dx) comes before its neighbour c in the (degree, id)
-// order.  The degrees saturated to 8 bits (a 1-byte-per-vertex table that
-// stays in L2) decide unless both saturate; then the exact degree of c comes
-// from the row offsets.
-constexpr uint32_t DEG8_SAT = 255;
+// order.  The degrees saturated to 16 bits (a 2-byte-per-vertex table that
+// mostly stays in L2) decide unless both saturate; then the exact degree of
+// c comes from the row offsets.
+constexpr uint32_t DEG_SAT = 65535;
 
-__device__ __forceinline__ bool rank_before(int32_t x, int64_t dx, const uint8_t* __restrict__ deg8,
+// dc16: deg16[c], gathered by the caller.
+__device__ __forceinline__ bool rank_before(int32_t x, int64_t dx, uint32_t dc16,
                                             const int64_t* __restrict__ rowptr, int32_t c) {
-    uint64_t dc = __ldg(deg8 + c);
-    if (dx >= DEG8_SAT) {
-        if (dc < DEG8_SAT) return false;
+    uint64_t dc = dc16;
+    if (dx >= DEG_SAT) {
+        if (dc < DEG_SAT) return false;
         dc = (uint64_t)(__ldg(rowptr + c + 1) - __ldg(rowptr + c));
     }
     return (uint64_t)dx < dc || ((uint64_t)dx == dc && x < c);
@@ -86,19 +89,16 @@ __device__ __forceinline__ bool rank_before(int32_t x, int64_t dx, const uint8_t
 
 struct RowsOut {
     const int64_t* rowptr;
-    const int32_t* wcol;
     const int32_t* wwt;
     const int32_t* wrk;
-    const uint8_t* deg8;
-    int32_t* scol;
-    int32_t* swt;
-    const uint32_t* fwd;             // bit j: entry j's neighbour ranks above its row's vertex
+    const unsigned long long* pk;    // packed forward keys, row x at [rowptr[x], rowptr[x] + odeg[x])
+    const int32_t* odeg;             // oriented out-degrees
     const int64_t* orowptr;          // oriented row offsets
     int32_t* ocol;
     int32_t* owt;
     int32_t* ork;
     uint32_t* err;                   // build status: error bits
-    unsigned long long* first_dup;   // smallest entry index of a repeated neighbour
+    unsigned long long* first_dup;   // smallest repeated pair, x << 32 | c
     const int32_t* list;             // rows of each class, class c at [cls_off[c], cls_off[c+1])
     const int32_t* cls_off;
 };
@@ -110,22 +110,22 @@ __device__ __forceinline__ bool rows_gate_closed(const uint32_t* gate) {
     return (*(volatile const uint32_t*)gate & ~(uint32_t)DEV_ERR_DUPLICATE) != 0;
 }
 
-__device__ __forceinline__ void flag_dup(const RowsOut& R, int64_t j) {
+__device__ __forceinline__ void flag_dup(const RowsOut& R, int32_t x, int32_t c) {
     atomicOr(R.err, DEV_ERR_DUPLICATE);
-    atomicMin(R.first_dup, (unsigned long long)j);
+    atomicMin(R.first_dup, ((unsigned long long)(uint32_t)x << 32) | (uint32_t)c);
 }
 
 // ---------------------------------------------------------------------------
-// Row classes: counts, then the list of rows of each class.
+// Row classes by oriented degree: counts, then the list of rows of each class.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) k_class_count(int32_t n, const int64_t* __restrict__ rowptr,
+__global__ void __launch_bounds__(NT) k_class_count(int32_t n, const int32_t* __restrict__ odeg,
                                                     int32_t* __restrict__ cls_cnt, const uint32_t* gate) {
     if (rows_gate_closed(gate)) return;
     __shared__ int32_t sc[NCLS];
     if (threadIdx.x < NCLS) sc[threadIdx.x] = 0;
     __syncthreads();
     for (int64_t x = (int64_t)blockIdx.x * NT + threadIdx.x; x < n; x += (int64_t)gridDim.x * NT) {
-        const int c = row_class(rowptr[x + 1] - rowptr[x]);
+        const int c = row_class(__ldg(odeg + x));
         if (c != CLS_NONE) atomicAdd(&sc[c], 1);
     }
     __syncthreads();
@@ -147,14 +147,14 @@ __global__ void k_class_offsets(const int32_t* cls_cnt, int32_t* cls_off, int32_
     }
 }
 
-__global__ void __launch_bounds__(NT) k_class_fill(int32_t n, const int64_t* __restrict__ rowptr,
+__global__ void __launch_bounds__(NT) k_class_fill(int32_t n, const int32_t* __restrict__ odeg,
                                                    int32_t* __restrict__ cls_cur, int32_t* __restrict__ list,
                                                    const uint32_t* gate) {
     if (rows_gate_closed(gate)) return;
     const int lane = threadIdx.x & 31;
     for (int64_t x0 = (int64_t)blockIdx.x * NT; x0 < n; x0 += (int64_t)gridDim.x * NT) {
         const int64_t x = x0 + threadIdx.x;
-        const int c = x < n ? row_class(rowptr[x + 1] - rowptr[x]) : CLS_NONE;
+        const int c = x < n ? row_class(__ldg(odeg + x)) : CLS_NONE;
         // one atomic per class present in the warp
         for (int k = 1; k < NCLS; k++) {
             const uint32_t b = __ballot_sync(0xffffffffu, c == k);
@@ -168,64 +168,18 @@ __global__ void __launch_bounds__(NT) k_class_fill(int32_t n, const int64_t* __r
 }
 
 // ---------------------------------------------------------------------------
-// Orientation of every entry: bit j of fwd says whether entry j's neighbour
-// ranks above its row's vertex (NodeIterator++ keeps the edge in that row);
-// odeg[x] counts them (rows are contiguous: a warp adds one count per row
-// it touches).
+// Orientation of every entry: entry e of row x is forward if its neighbour c
+// ranks above x (NodeIterator++ keeps the edge in x's row).  odeg[x] counts
+// them; each forward entry's key (c << 32 | e - rowptr[x]) goes to slot
+// rowptr[x] + (its arrival index) of pk.  Rows are contiguous, so a warp
+// takes one atomic per row it touches.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) k_fwd(int64_t n2, const int32_t* __restrict__ wrow,
-                                            const int32_t* __restrict__ wcol,
-                                            const int64_t* __restrict__ rowptr,
-                                            const uint8_t* __restrict__ deg8, uint32_t* __restrict__ fwd,
-                                            int32_t* __restrict__ odeg, const uint32_t* gate) {
-    if (rows_gate_closed(gate)) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
-    for (int64_t base = (((int64_t)blockIdx.x * NT + threadIdx.x) >> 5) * 32; base < n2;
-         base += nwarps * 32) {
-        const int64_t e = base + lane;
-        const bool valid = e < n2;
-        int32_t x = -1;
-        bool f = false;
-        if (valid) {
-            x = __ldcs(wrow + e);
-            const int32_t c = __ldcs(wcol + e);
-            const int64_t dx = __ldg(rowptr + x + 1) - __ldg(rowptr + x);
-            f = rank_before(x, dx, deg8, rowptr, c);
-        }
-        const uint32_t bits = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) fwd[base >> 5] = bits;  // base is a multiple of 32
-        const int32_t xp = __shfl_up_sync(0xffffffffu, x, 1);
-        const bool head = valid && (lane == 0 || xp != x);
-        const uint32_t heads = __ballot_sync(0xffffffffu, head);
-        if (head) {
-            const uint32_t above = heads & ~((2u << lane) - 1u);  // heads after this lane
-            const int end = above ? __ffs(above) - 1 : 32;
-            const uint32_t seg = (end >= 32 ? 0xffffffffu : ((1u << end) - 1u)) & ~((1u << lane) - 1u);
-            const int cnt = __popc(bits & seg);
-            if (cnt) atomicAdd(odeg + x, cnt);
-        }
-    }
-}
+constexpr unsigned long long KEY_NONE = ~0ull;  // sorts after every real key
 
-__device__ __forceinline__ bool fwd_bit(const uint32_t* fwd, int64_t j) {
-    return (__ldg(fwd + (j >> 5)) >> (j & 31)) & 1u;
-}
-
-// ---------------------------------------------------------------------------
-// Writes: the id-sorted entry; the oriented entry at its compact position.
-// Outputs are written once and not read again by this pass: streaming
-// stores, so that they do not displace the tables the pass gathers from.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void write_sym(const RowsOut& R, int64_t j, int32_t c, int32_t w) {
-    __stcs(R.scol + j, c);
-    __stcs(R.swt + j, w);
-}
-__device__ __forceinline__ void write_orient(const RowsOut& R, int64_t p, int32_t c, int32_t w,
-                                             int32_t rk) {
-    __stcs(R.ocol + p, c);
-    __stcs(R.owt + p, w);
-    __stcs(R.ork + p, rk);
+__device__ __forceinline__ int32_t key_col(unsigned long long k) { return (int32_t)(k >> 32); }
+__device__ __forceinline__ uint32_t key_pos(unsigned long long k) { return (uint32_t)k & 0x7fffffffu; }
+__device__ __forceinline__ unsigned long long with_pos(unsigned long long k, uint32_t i) {
+    return (k & 0xffffffff00000000ull) | i;
 }
 
 __device__ __forceinline__ uint32_t lane_lt() {
@@ -234,18 +188,88 @@ __device__ __forceinline__ uint32_t lane_lt() {
     return m;
 }
 
-constexpr unsigned long long KEY_NONE = ~0ull;  // sorts after every real key
+constexpr int FWD_U = 4;  // strips of 32 entries per warp and iteration (loads issued together)
 
-// Sort key of entry j of a row: neighbour id, then the orientation bit, then
-// the position (unique within the row; the sorts order by id only, the rest
-// rides along).
-__device__ __forceinline__ unsigned long long row_key(int32_t c, bool f, int64_t j) {
-    return ((unsigned long long)(uint32_t)c << 32) | ((unsigned long long)f << 31) |
-           (unsigned long long)(uint32_t)j;
+__global__ void __launch_bounds__(NT) k_fwd(int64_t n2, const int32_t* __restrict__ wrow,
+                                            const int32_t* __restrict__ wcol,
+                                            const int64_t* __restrict__ rowptr,
+                                            const uint16_t* __restrict__ deg16,
+                                            unsigned long long* __restrict__ pk,
+                                            int32_t* __restrict__ odeg, const uint32_t* gate) {
+    if (rows_gate_closed(gate)) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lane_lt();
+    const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+    for (int64_t base = (((int64_t)blockIdx.x * NT + threadIdx.x) >> 5) * (32 * FWD_U); base < n2;
+         base += nwarps * (32 * FWD_U)) {
+        int32_t x[FWD_U], c[FWD_U];
+        int64_t s[FWD_U], dx[FWD_U];
+        uint32_t dc[FWD_U];
+#pragma unroll
+        for (int u = 0; u < FWD_U; u++) {
+            const int64_t e = base + u * 32 + lane;
+            x[u] = e < n2 ? __ldcs(wrow + e) : -1;
+            c[u] = e < n2 ? __ldcs(wcol + e) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < FWD_U; u++) {
+            s[u] = x[u] >= 0 ? __ldg(rowptr + x[u]) : 0;
+            dx[u] = x[u] >= 0 ? __ldg(rowptr + x[u] + 1) - s[u] : 0;
+            dc[u] = x[u] >= 0 ? __ldg(deg16 + c[u]) : 0u;
+        }
+        int32_t slot[FWD_U];
+        uint32_t bits[FWD_U], seg[FWD_U];
+        int hl[FWD_U];
+#pragma unroll
+        for (int u = 0; u < FWD_U; u++) {
+            const bool valid = x[u] >= 0;
+            const bool f = valid && rank_before(x[u], dx[u], dc[u], rowptr, c[u]);
+            bits[u] = __ballot_sync(0xffffffffu, f);
+            const int32_t xp = __shfl_up_sync(0xffffffffu, x[u], 1);
+            const bool head = valid && (lane == 0 || xp != x[u]);
+            const uint32_t heads = __ballot_sync(0xffffffffu, head);
+            // the segment of lanes sharing this lane's row starts at its head
+            hl[u] = valid ? 31 - __clz(heads & (lt | (1u << lane))) : lane;
+            const uint32_t after = heads & ~((2u << hl[u]) - 1u);  // heads after the segment's
+            const int end = after ? __ffs(after) - 1 : 32;
+            seg[u] = (end >= 32 ? 0xffffffffu : ((1u << end) - 1u)) & ~((1u << hl[u]) - 1u);
+            slot[u] = 0;
+            if (head) {
+                const int cnt = __popc(bits[u] & seg[u]);
+                if (cnt) slot[u] = atomicAdd(odeg + x[u], cnt);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < FWD_U; u++) {
+            const int32_t sl = __shfl_sync(0xffffffffu, slot[u], hl[u]);
+            if ((bits[u] >> lane) & 1u) {
+                const int64_t e = base + u * 32 + lane;
+                __stcg(pk + s[u] + sl + __popc(bits[u] & seg[u] & lt),
+                       ((unsigned long long)(uint32_t)c[u] << 32) | (uint32_t)(e - s[u]));
+            }
+        }
+    }
 }
-__device__ __forceinline__ int32_t key_col(unsigned long long k) { return (int32_t)(k >> 32); }
-__device__ __forceinline__ bool key_fwd(unsigned long long k) { return (k >> 31) & 1ull; }
-__device__ __forceinline__ uint32_t key_pos(unsigned long long k) { return (uint32_t)k & 0x7fffffffu; }
+
+// ---------------------------------------------------------------------------
+// Oriented entry p of row x.  Outputs are written once and not read again
+// by this pass: streaming stores, so that they do not displace the rows the
+// pass gathers from.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void write_orient(const RowsOut& R, int64_t p, int32_t c, int32_t w,
+                                             int32_t rk) {
+    __stcs(R.ocol + p, c);
+    __stcs(R.owt + p, w);
+    __stcs(R.ork + p, rk);
+}
+
+// Weight and rank of a packed key (position in the weight-sorted row s..).
+__device__ __forceinline__ void gather_wr(const RowsOut& R, int64_t s, unsigned long long kk, int32_t& w,
+                                          int32_t& rk) {
+    const uint32_t j = key_pos(kk);
+    w = __ldg(R.wwt + s + j);
+    rk = __ldg(R.wrk + s + j);
+}
 
 // ---------------------------------------------------------------------------
 // Rows of at most G entries (G = 8, 16, 32): G lanes per row, a bitonic
@@ -258,25 +282,24 @@ __global__ void __launch_bounds__(NT) k_rows_small(RowsOut R, int cls, const uin
     constexpr int RPW = 32 / G;  // rows per warp
     const int64_t lo = R.cls_off[cls], hi = R.cls_off[cls + 1];
     const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
-    const uint32_t gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
     for (int64_t wbase = lo + (((int64_t)blockIdx.x * NT + threadIdx.x) >> 5) * RPW; wbase < hi;
          wbase += nwarps * RPW) {
         const int64_t ri = wbase + grp;
-        int32_t x = 0;
-        int64_t s = 0, d = 0, ob = 0;
+        int32_t x = 0, d = 0;
+        int64_t s = 0, ob = 0;
         if (ri < hi) {
             x = __ldg(R.list + ri);
             s = __ldg(R.rowptr + x);
-            d = __ldg(R.rowptr + x + 1) - s;
+            d = __ldg(R.odeg + x);
             ob = __ldg(R.orowptr + x);
         }
         const bool valid = gl < d;
         unsigned long long key = KEY_NONE;
         int32_t w = 0, rk = 0;
         if (valid) {
-            key = row_key(__ldcs(R.wcol + s + gl), fwd_bit(R.fwd, s + gl), gl);
-            w = __ldcs(R.wwt + s + gl);
-            rk = __ldcs(R.wrk + s + gl);
+            key = __ldcs(R.pk + s + gl);
+            gather_wr(R, s, key, w, rk);
+            key = with_pos(key, gl);
         }
 #pragma unroll
         for (int k = 2; k <= G; k <<= 1) {
@@ -291,14 +314,11 @@ __global__ void __launch_bounds__(NT) k_rows_small(RowsOut R, int cls, const uin
         const int32_t ws = __shfl_sync(0xffffffffu, w, src, G);
         const int32_t rks = __shfl_sync(0xffffffffu, rk, src, G);
         const unsigned long long prev = __shfl_up_sync(0xffffffffu, key, 1, G);
-        const int32_t c = key_col(key);
-        const bool f = valid && key_fwd(key);
         if (valid) {
-            write_sym(R, s + gl, c, ws);
-            if (gl > 0 && key_col(prev) == c) flag_dup(R, s + gl);
+            const int32_t c = key_col(key);
+            write_orient(R, ob + gl, c, ws, rks);
+            if (gl > 0 && key_col(prev) == c) flag_dup(R, x, c);
         }
-        const uint32_t b = __ballot_sync(0xffffffffu, f) & gmask;
-        if (f) write_orient(R, ob + __popc(b & lane_lt()), c, ws, rks);
     }
 }
 
@@ -364,34 +384,33 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&k)[EPL]) {
 __device__ __forceinline__ int swz(int p) { return p ^ ((p >> 5) & 31); }
 
 // ---------------------------------------------------------------------------
-// Rows of 33..1024 entries: one warp per row, 32 * EPL keys in registers
-// (EPL = 2, 4, 8, 16, 32 by class), sorted, transposed through the warp's
-// shared memory (keys, and the row's weights and ranks by position).
+// Rows of 33..512 entries: one warp per row, 32 * EPL keys in registers
+// (EPL = 2, 4, 8, 16 by class), sorted, transposed through the warp's
+// shared memory (keys, and the row's weights and ranks by packed index).
 // ---------------------------------------------------------------------------
 template <int EPL>
 __global__ void __launch_bounds__(NT) k_rows_warp(RowsOut R, int cls, const uint32_t* gate) {
     if (rows_gate_closed(gate)) return;
     extern __shared__ __align__(16) unsigned long long wsm[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint32_t lt = lane_lt();
     unsigned long long* run = wsm + (size_t)wid * 2 * 32 * EPL;
-    int32_t* wv = reinterpret_cast<int32_t*>(run + 32 * EPL);  // weights by position
-    int32_t* rv = wv + 32 * EPL;                                 // ranks by position
+    int32_t* wv = reinterpret_cast<int32_t*>(run + 32 * EPL);  // weights by packed index
+    int32_t* rv = wv + 32 * EPL;                                 // ranks by packed index
     const int64_t lo = R.cls_off[cls], hi = R.cls_off[cls + 1];
     const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
     for (int64_t ri = lo + (((int64_t)blockIdx.x * NT + threadIdx.x) >> 5); ri < hi; ri += nwarps) {
         const int32_t x = __ldg(R.list + ri);
         const int64_t s = __ldg(R.rowptr + x);
-        const int d = (int)(__ldg(R.rowptr + x + 1) - s);
+        const int d = __ldg(R.odeg + x);
         const int64_t ob = __ldg(R.orowptr + x);
         unsigned long long k[EPL];
 #pragma unroll
         for (int i = 0; i < EPL; i++) {
             const int j = i * 32 + lane;  // coalesced loads; the network ignores input order
             if (j < d) {
-                k[i] = row_key(__ldcs(R.wcol + s + j), fwd_bit(R.fwd, s + j), j);
-                wv[j] = __ldcs(R.wwt + s + j);
-                rv[j] = __ldcs(R.wrk + s + j);
+                const unsigned long long kk = __ldcs(R.pk + s + j);
+                gather_wr(R, s, kk, wv[j], rv[j]);
+                k[i] = with_pos(kk, j);
             } else {
                 k[i] = KEY_NONE;
             }
@@ -400,24 +419,12 @@ __global__ void __launch_bounds__(NT) k_rows_warp(RowsOut R, int cls, const uint
 #pragma unroll
         for (int i = 0; i < EPL; i++) run[swz(lane * EPL + i)] = k[i];
         __syncwarp();
-        int64_t orun = 0;
-        for (int base = 0; base < d; base += 32) {
-            const int j = base + lane;
-            bool f = false;
-            int32_t c = 0, w = 0, rk = 0;
-            if (j < d) {
-                const unsigned long long kk = run[swz(j)];
-                c = key_col(kk);
-                f = key_fwd(kk);
-                const uint32_t src = key_pos(kk);
-                w = wv[src];
-                rk = rv[src];
-                write_sym(R, s + j, c, w);
-                if (j > 0 && key_col(run[swz(j - 1)]) == c) flag_dup(R, s + j);
-            }
-            const uint32_t b = __ballot_sync(0xffffffffu, f);
-            if (f) write_orient(R, ob + orun + __popc(b & lt), c, w, rk);
-            orun += __popc(b);
+        for (int j = lane; j < d; j += 32) {
+            const unsigned long long kk = run[swz(j)];
+            const int32_t c = key_col(kk);
+            const uint32_t src = key_pos(kk);
+            write_orient(R, ob + j, c, wv[src], rv[src]);
+            if (j > 0 && key_col(run[swz(j - 1)]) == c) flag_dup(R, x, c);
         }
         __syncwarp();
     }
@@ -453,112 +460,176 @@ __device__ __forceinline__ void merge_out(const RA& a, int64_t na, const RB& b, 
     }
 }
 
-struct BlockSmem {
-    unsigned long long buf[2][SB];   // runs, ping-pong (swizzled per 1024-key run)
-    int32_t wv[SB];                  // weights of the slice by position
-    int32_t rv[SB];                  // ranks of the slice by position
-    uint32_t warp_tot[NWARPS];
+// ---------------------------------------------------------------------------
+// Block radix sort of one slice (cnt <= SR keys) in shared memory: LSD over
+// the id bits [32, 32 + nbits) of the keys, digits of at most RBITS bits,
+// each pass stable.  Item j of warp w, lane l is key w * 32 * IT + j * 32 + l
+// of the source buffer (IT keys per thread, IT * NT >= cnt); within a warp
+// the items are ranked strip by strip (a ballot per digit bit gives the
+// lanes of equal digit, a per-warp counter per digit the keys before), the
+// warps in order by a scan of the per-(warp, digit) counts.
+// ---------------------------------------------------------------------------
+constexpr int RBITS = 9;
+constexpr int RBINS = 1 << RBITS;
+constexpr int RDPT = RBINS / NT;  // digits owned by a thread in the scan
+static_assert(RDPT == 2, "a thread owns two digits: one 4-byte word of each warp's counters");
+
+struct RadixSmem {
+    unsigned long long key[2][SR];   // ping-pong key buffers
+    int32_t wv[SR];                  // weights of the slice by packed index
+    int32_t rv[SR];                  // ranks of the slice by packed index
+    uint16_t cnt[NWARPS][RBINS];     // per (warp, digit): count, then output offset
+    uint32_t warp_tot[32];
+    uint32_t total;
     int32_t item;
 };
 
-// Sorts keys [base, base + cnt) of a row (cnt <= SB) into one run in
-// S.buf[returned index] (element p at swz(p)); also stages the slice's
-// weights and ranks by position.  nw = the power of two of 1024-key slices
-// covering cnt; warp w < nw sorts slice w in registers; log2(nw) merge-path
-// levels in shared memory make one run of nw * 1024 keys (the padding sorts
-// last).
-__device__ __forceinline__ int block_sort_run(const RowsOut& R, int64_t s, int64_t base, int cnt,
-                                              BlockSmem& S) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int nw = 1;
-    while (nw * 1024 < cnt) nw <<= 1;
-    for (int j = threadIdx.x; j < cnt; j += NT) {
-        S.wv[j] = __ldcs(R.wwt + s + base + j);
-        S.rv[j] = __ldcs(R.wrk + s + base + j);
+__device__ __forceinline__ uint32_t block_scan_excl(uint32_t x, uint32_t* warp_tot) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
     }
-    if (wid < nw) {
-        unsigned long long k[32];
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    uint32_t before = 0;
 #pragma unroll
-        for (int i = 0; i < 32; i++) {
-            const int j = wid * 1024 + i * 32 + lane;
-            k[i] = j < cnt ? row_key(__ldcs(R.wcol + s + base + j), fwd_bit(R.fwd, s + base + j), j)
-                           : KEY_NONE;
+    for (int k = 0; k < NWARPS; k++) before += k < w ? warp_tot[k] : 0u;
+    __syncthreads();
+    return before + inc - x;
+}
+
+// Lanes whose valid item has the same digit as this lane's (invalid lanes
+// group among themselves).
+__device__ __forceinline__ uint32_t radix_peers(uint32_t d, int bits, bool valid) {
+    const uint32_t vb = __ballot_sync(0xffffffffu, valid);
+    uint32_t p = valid ? vb : ~vb;
+#pragma unroll
+    for (int k = 0; k < RBITS; k++) {
+        if (k < bits) {
+            const bool bit = (d >> k) & 1u;
+            const uint32_t b = __ballot_sync(0xffffffffu, bit);
+            p &= bit ? b : ~b;
         }
-        warp_bitonic<32>(k);
+    }
+    return p;
+}
+
+template <int IT>
+__device__ __forceinline__ void radix_pass(const unsigned long long* src, unsigned long long* dst, int cnt,
+                                           int shift, int bits, RadixSmem& S) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t lt = lane_lt();
+    const uint32_t mask = (1u << bits) - 1u;
+    for (int q = threadIdx.x; q < NWARPS * RBINS / 2; q += NT) reinterpret_cast<uint32_t*>(&S.cnt[0][0])[q] = 0;
+    __syncthreads();
+    unsigned long long k[IT];
+    uint32_t rank[IT];
 #pragma unroll
-        for (int i = 0; i < 32; i++) S.buf[0][swz(wid * 1024 + lane * 32 + i)] = k[i];
+    for (int j = 0; j < IT; j++) {
+        const int li = w * 32 * IT + j * 32 + lane;
+        k[j] = li < cnt ? src[li] : KEY_NONE;
+        rank[j] = radix_peers((uint32_t)(k[j] >> (32 + shift)) & mask, bits, li < cnt);
+    }
+#pragma unroll
+    for (int j = 0; j < IT; j++) {
+        const int li = w * 32 * IT + j * 32 + lane;
+        const bool valid = li < cnt;
+        const uint32_t d = (uint32_t)(k[j] >> (32 + shift)) & mask;
+        const uint32_t peers = rank[j];
+        const uint32_t b = valid ? (uint32_t)S.cnt[w][d] : 0u;
+        rank[j] = b + __popc(peers & lt);
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) S.cnt[w][d] = (uint16_t)(b + __popc(peers));
+        __syncwarp();
     }
     __syncthreads();
-    // Every access below goes through swz (a bijection inside each group of
-    // 32 keys): the merge path writes 4..32 consecutive keys per thread, which
-    // unswizzled would put every lane of a warp on the same bank.
-    int cur = 0;
-    const int total = nw * 1024;
-    const int per = total / NT;  // outputs per thread: 4 .. 32
-    for (int len = 1024; len < total; len <<= 1) {
-        const unsigned long long* src = S.buf[cur];
-        unsigned long long* dst = S.buf[cur ^ 1];
-        const int q0 = threadIdx.x * per;
-        const int pair = q0 / (2 * len), pb = pair * 2 * len;
-        auto A = [&](int64_t i) { return src[swz(pb + (int)i)]; };
-        auto B = [&](int64_t i) { return src[swz(pb + len + (int)i)]; };
-        merge_out(A, len, B, len, q0 - pb, per,
-                  [&](int64_t q, unsigned long long v) { dst[swz(pb + (int)q)] = v; });
-        __syncthreads();
+    // digit starts, then each warp's offset within its digit: thread t owns
+    // digits 2t, 2t + 1 (one 4-byte word of every warp's counters)
+    {
+        const int d0 = threadIdx.x * RDPT;
+        uint32_t t0 = 0, t1 = 0;
+#pragma unroll
+        for (int q = 0; q < NWARPS; q++) {
+            const uint32_t r = *reinterpret_cast<const uint32_t*>(&S.cnt[q][d0]);
+            t0 += r & 0xffffu;
+            t1 += r >> 16;
+        }
+        uint32_t s0 = block_scan_excl(t0 + t1, S.warp_tot), s1 = s0 + t0;
+#pragma unroll
+        for (int q = 0; q < NWARPS; q++) {
+            uint32_t* p = reinterpret_cast<uint32_t*>(&S.cnt[q][d0]);
+            const uint32_t r = *p;
+            *p = s0 | (s1 << 16);
+            s0 += r & 0xffffu;
+            s1 += r >> 16;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < IT; j++) {
+        const int li = w * 32 * IT + j * 32 + lane;
+        if (li < cnt) dst[S.cnt[w][(uint32_t)(k[j] >> (32 + shift)) & mask] + rank[j]] = k[j];
+    }
+    __syncthreads();
+}
+
+// Loads packed keys [base, base + cnt) of a row (cnt <= SR) with their
+// weights and ranks, sorts them by id (key positions relative to the slice);
+// returns the buffer holding the sorted keys.
+template <int IT>
+__device__ __forceinline__ int radix_sort_slice(const RowsOut& R, int64_t s, int64_t base, int cnt, int nbits,
+                                                RadixSmem& S) {
+    for (int j = threadIdx.x; j < cnt; j += NT) {
+        const unsigned long long kk = __ldcs(R.pk + s + base + j);
+        gather_wr(R, s, kk, S.wv[j], S.rv[j]);
+        S.key[0][j] = with_pos(kk, j);
+    }
+    __syncthreads();
+    const int passes = (nbits + RBITS - 1) / RBITS;
+    int cur = 0, shift = 0;
+    for (int p = 0; p < passes; p++) {
+        const int bits = nbits / passes + (p < nbits % passes ? 1 : 0);
+        radix_pass<IT>(S.key[cur], S.key[cur ^ 1], cnt, shift, bits, S);
+        shift += bits;
         cur ^= 1;
     }
     return cur;
 }
 
-// Epilogue of sorted keys readable by position p < cnt (the positions of a
-// row starting at p0): id-sorted entries at s + p0 + p, repeats, oriented
-// entries at ob + orun + (rank among the oriented keys).  Weights and ranks
-// come from wget(key).  Returns the number of oriented keys.  Block-wide:
-// per 256 positions one ballot per warp and one barrier pair.
+__device__ __forceinline__ int radix_sort_any(const RowsOut& R, int64_t s, int64_t base, int cnt, int nbits,
+                                              RadixSmem& S) {
+    if (cnt <= 4 * NT) return radix_sort_slice<4>(R, s, base, cnt, nbits, S);
+    if (cnt <= 8 * NT) return radix_sort_slice<8>(R, s, base, cnt, nbits, S);
+    return radix_sort_slice<16>(R, s, base, cnt, nbits, S);
+}
+static_assert(16 * NT == SR, "the widest item count covers a slice");
+
+// Epilogue of a row's sorted keys, readable by position p < cnt: oriented
+// entry p at ob + p, its weight and rank from wget(key), repeats flagged.
 template <class Keys, class WR>
-__device__ __forceinline__ int64_t block_epilogue(const RowsOut& R, int64_t s, int64_t p0, int cnt,
-                                                  const Keys& key_at, const WR& wget, int64_t ob,
-                                                  int64_t orun, unsigned long long prev_key,
-                                                  uint32_t* warp_tot) {
-    const int lane = threadIdx.x & 31, w_ = threadIdx.x >> 5;
-    const uint32_t lt = lane_lt();
-    for (int base = 0; base < cnt; base += NT) {
-        const int p = base + threadIdx.x;
-        bool f = false;
-        int32_t c = 0, w = 0, rk = 0;
-        if (p < cnt) {
-            const unsigned long long kk = key_at(p);
-            c = key_col(kk);
-            f = key_fwd(kk);
-            wget(kk, w, rk);
-            write_sym(R, s + p0 + p, c, w);
-            const unsigned long long pk = p > 0 ? key_at(p - 1) : prev_key;
-            if ((p0 + p) > 0 && key_col(pk) == c) flag_dup(R, s + p0 + p);
-        }
-        const uint32_t b = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) warp_tot[w_] = __popc(b);
-        __syncthreads();
-        uint32_t before = 0, total = 0;
-#pragma unroll
-        for (int k = 0; k < NWARPS; k++) {
-            const uint32_t t = warp_tot[k];
-            before += k < w_ ? t : 0u;
-            total += t;
-        }
-        if (f) write_orient(R, ob + orun + before + __popc(b & lt), c, w, rk);
-        orun += total;
-        __syncthreads();
+__device__ __forceinline__ void block_epilogue(const RowsOut& R, int32_t x, int cnt, const Keys& key_at,
+                                               const WR& wget, int64_t ob) {
+    for (int p = threadIdx.x; p < cnt; p += NT) {
+        const unsigned long long kk = key_at(p);
+        const int32_t c = key_col(kk);
+        int32_t w, rk;
+        wget(kk, w, rk);
+        write_orient(R, ob + p, c, w, rk);
+        if (p > 0 && key_col(key_at(p - 1)) == c) flag_dup(R, x, c);
     }
-    return orun;
 }
 
-// Rows of 1025..SB entries sort whole in shared memory; hub rows (above SB)
-// sort each SB slice and leave it in g0 (global, at the row's offset).
-__global__ void __launch_bounds__(NT) k_rows_block(RowsOut R, unsigned long long* g0, int32_t* cursor,
-                                                   const uint32_t* gate) {
+// Rows of 513..SR oriented entries sort whole in shared memory; hub rows
+// (above SR) sort each SR slice and leave it in g0 (global, at the row's
+// offset rowptr[x]).  nbits: bit length of the largest vertex id.
+__global__ void __launch_bounds__(NT, 2) k_rows_block(RowsOut R, unsigned long long* g0, int32_t* cursor,
+                                                      int nbits, const uint32_t* gate) {
     if (rows_gate_closed(gate)) return;
     extern __shared__ __align__(16) unsigned char bsm_raw[];
-    BlockSmem& S = *reinterpret_cast<BlockSmem*>(bsm_raw);
+    RadixSmem& S = *reinterpret_cast<RadixSmem*>(bsm_raw);
     const int64_t lo = R.cls_off[CLS_BLOCK], hi = R.cls_off[CLS_HUB + 1];  // block and hub rows
     for (;;) {
         if (threadIdx.x == 0) S.item = atomicAdd(cursor, 1);
@@ -568,23 +639,23 @@ __global__ void __launch_bounds__(NT) k_rows_block(RowsOut R, unsigned long long
         if (ri >= hi) break;
         const int32_t x = __ldg(R.list + ri);
         const int64_t s = __ldg(R.rowptr + x);
-        const int64_t d = __ldg(R.rowptr + x + 1) - s;
-        for (int64_t base = 0; base < d; base += SB) {
-            const int cnt = (int)min((int64_t)SB, d - base);
-            const int b = block_sort_run(R, s, base, cnt, S);
-            if (d <= SB) {
-                block_epilogue(R, s, 0, cnt, [&](int p) { return S.buf[b][swz(p)]; },
+        const int64_t d = __ldg(R.odeg + x);
+        for (int64_t base = 0; base < d; base += SR) {
+            const int cnt = (int)min((int64_t)SR, d - base);
+            const int b = radix_sort_any(R, s, base, cnt, nbits, S);
+            if (d <= SR) {
+                block_epilogue(R, x, cnt, [&](int p) { return S.key[b][p]; },
                                [&](unsigned long long kk, int32_t& w, int32_t& rk) {
                                    const uint32_t src = key_pos(kk);
                                    w = S.wv[src];
                                    rk = S.rv[src];
                                },
-                               __ldg(R.orowptr + x), 0, KEY_NONE, S.warp_tot);
+                               __ldg(R.orowptr + x));
             } else {
                 // positions in the key are relative to the slice: make them
-                // row positions for the merges and the final epilogue
+                // packed indices of the row for the merges and the epilogue
                 for (int j = threadIdx.x; j < cnt; j += NT)
-                    g0[s + base + j] = S.buf[b][swz(j)] + (unsigned long long)base;
+                    g0[s + base + j] = S.key[b][j] + (unsigned long long)base;
             }
             __syncthreads();
         }
@@ -608,7 +679,7 @@ __global__ void __launch_bounds__(NT) k_rows_merge(RowsOut R, const unsigned lon
     for (int64_t ri = lo + blockIdx.x; ri < hi; ri += gridDim.x) {
         const int32_t x = __ldg(R.list + ri);
         const int64_t s = __ldg(R.rowptr + x);
-        const int64_t d = __ldg(R.rowptr + x + 1) - s;
+        const int64_t d = __ldg(R.odeg + x);
         if (d <= len) continue;
         for (int64_t q0 = 0; q0 < d; q0 += MT) {
             const int64_t q1 = min(d, q0 + MT);
@@ -639,29 +710,25 @@ __global__ void __launch_bounds__(NT) k_rows_merge(RowsOut R, const unsigned lon
 }
 
 // Epilogue of the hub rows, from the buffer holding each row's last level:
-// one block per row, slices of SB positions staged in shared memory with
-// their weights and ranks gathered from the weight-sorted row.
+// one block per row; weights and ranks gathered through the packed key
+// (its position in the weight-sorted row).
 __global__ void __launch_bounds__(NT) k_rows_hub_out(RowsOut R, const unsigned long long* g0,
                                                      const unsigned long long* g1,
                                                      const uint32_t* gate) {
     if (rows_gate_closed(gate)) return;
-    __shared__ uint32_t warp_tot[NWARPS];
     const int64_t lo = R.cls_off[CLS_HUB], hi = R.cls_off[CLS_HUB + 1];
     for (int64_t ri = lo + blockIdx.x; ri < hi; ri += gridDim.x) {
         const int32_t x = __ldg(R.list + ri);
         const int64_t s = __ldg(R.rowptr + x);
-        const int64_t d = __ldg(R.rowptr + x + 1) - s;
+        const int64_t d = __ldg(R.odeg + x);
         int levels = 0;
-        for (int64_t len = SB; len < d; len <<= 1) levels++;
+        for (int64_t len = SR; len < d; len <<= 1) levels++;
         const unsigned long long* g = ((levels & 1) ? g1 : g0) + s;
-        block_epilogue(R, s, 0, (int)d, [&](int64_t p) { return __ldcs(g + p); },
+        block_epilogue(R, x, (int)d, [&](int64_t p) { return __ldcs(g + p); },
                        [&](unsigned long long kk, int32_t& w, int32_t& rk) {
-                           const uint32_t src = key_pos(kk);
-                           w = __ldg(R.wwt + s + src);
-                           rk = __ldg(R.wrk + s + src);
+                           gather_wr(R, s, __ldg(R.pk + s + key_pos(kk)), w, rk);
                        },
-                       __ldg(R.orowptr + x), 0, KEY_NONE, warp_tot);
-        __syncthreads();
+                       __ldg(R.orowptr + x));
     }
 }
 

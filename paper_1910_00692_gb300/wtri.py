@@ -36,9 +36,6 @@ ARRAYS = {
     "wcol": (5, np.int32, "2m"),
     "wwt": (6, np.int32, "2m"),
     "wrank": (7, np.int32, "2m"),
-    "scol": (8, np.int32, "2m"),
-    "swt": (9, np.int32, "2m"),
-    "srank": (10, np.int32, "2m"),
     "orowptr": (11, np.int64, "n+1"),
     "ocol": (12, np.int32, "m"),
     "owt": (13, np.int32, "m"),

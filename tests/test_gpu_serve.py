@@ -138,7 +138,7 @@ def test_small_slot_limit(graphs):
 
 def test_server_errors(graphs):
     gs, ds = graphs
-    srv = wt.Server(1 << 20, 8)          # 1 MB: no graph fits
+    srv = wt.Server(1 << 18, 8)          # 256 KB: no graph fits
     with pytest.raises(wt.WtriError) as ei:
         srv.add_graph(ds[0])
     assert ei.value.code == -2

@@ -4,6 +4,7 @@ Triangle sets and order are compared element by element (bit-exact ids);
 weights bit-exact for p in {-inf, 1, +inf} and within 1e-12 relative at
 p = 2 and p = 0.  Inputs are the seeded synthetic graphs of synth/.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -56,10 +57,10 @@ def test_tiny_vs_oracle(tiny, tiny_dev, p, k):
 
 def test_tiny_structures(tiny, tiny_dev):
     check_structures(tiny, tiny_dev)
-    # the id-sorted rows keep no edge ranks (the oriented rows carry them)
-    with pytest.raises(wt.WtriError) as ei:
-        tiny_dev.array("srank")
-    assert ei.value.code == -5
+    # array ids 8..10 are unused (no symmetric id-sorted rows are kept)
+    nb = ctypes.c_int64()
+    for which in (8, 9, 10, 99):
+        assert wt.lib().wtri_graph_copy_array(tiny_dev._h, which, None, 0, ctypes.byref(nb)) == -1
 
 
 @pytest.mark.parametrize("n,m,seed", [(20000, 200000, 11), (100000, 1000000, 12)])
@@ -73,25 +74,19 @@ def test_scaled_structures(n, m, seed):
         d.free()
 
 
-def _hubs_graph(degrees, seed):
-    """Hub vertices 0..len(degrees)-1 of the given degrees to distinct
-    leaves, leaves joined in pairs (triangles through every hub), random
-    weights 1..9: rows of every size class of the per-row sort."""
+def _cliques_graph(sizes, seed, wmax=9):
+    """Disjoint cliques K_{s+1} for s in sizes: equal degrees inside a clique,
+    so the (degree, id) order gives its vertices the oriented degrees s,
+    s - 1, ..., 0 -- every size class of the per-row sort up to s; random
+    weights 1..wmax, edges shuffled and flipped."""
     rng = np.random.default_rng(seed)
     us, vs = [], []
-    nxt = len(degrees)
-    for h, dgr in enumerate(degrees):
-        leaves = np.arange(nxt, nxt + dgr, dtype=np.int64)
-        nxt += dgr
-        us.append(np.full(dgr, h, np.int64))
-        vs.append(leaves)
-        us.append(leaves[0:dgr - 1:2])
-        vs.append(leaves[1:dgr:2])
-    # hub-hub edges so hub rows also hold other hubs
-    for a in range(len(degrees)):
-        for b in range(a + 1, len(degrees)):
-            us.append(np.array([a]))
-            vs.append(np.array([b]))
+    base = 0
+    for s_ in sizes:
+        iu, ju = np.triu_indices(s_ + 1, 1)
+        us.append(iu + base)
+        vs.append(ju + base)
+        base += s_ + 1
     u = np.concatenate(us)
     v = np.concatenate(vs)
     perm = rng.permutation(u.shape[0])
@@ -99,40 +94,62 @@ def _hubs_graph(degrees, seed):
     flip = rng.random(u.shape[0]) < 0.5
     u2 = np.where(flip, v, u).astype(np.int32)
     v2 = np.where(flip, u, v).astype(np.int32)
-    w = rng.integers(1, 10, u.shape[0]).astype(np.int32)
-    return synth.Graph(n=int(nxt), u=u2, v=v2, w=w, name="hubs")
+    w = rng.integers(1, wmax + 1, u.shape[0]).astype(np.int32)
+    return synth.Graph(n=int(base), u=u2, v=v2, w=w, name="cliques")
 
 
-@pytest.mark.parametrize("degrees", [[5, 12, 30, 33, 500, 1024], [1025, 4000, 8192], [8193, 20000]],
-                         ids=["small-warp", "block-smem", "block-global"])
-def test_hub_rows_structures(degrees):
-    """Rows at the boundaries of the per-row sort's size classes (8/16/32
-    lanes, one warp up to 1024, one block up to 8192 in shared memory,
-    global scratch beyond): structures and the top-k against the oracle."""
-    g = _hubs_graph(degrees, seed=sum(degrees))
+def test_oriented_row_classes_topk():
+    """Oriented rows of the sub-warp and warp classes (cliques up to 129):
+    structures and the top-k against the oracle."""
+    g = _cliques_graph([5, 8, 9, 16, 17, 32, 33, 64, 65, 129], seed=7)
     d = wt.build_csr(g.n, g.u, g.v, g.w)
     try:
         check_structures(g, d)
         for p in PS:
             want = oracle.topk(g.n, g.u, g.v, g.w, p, 300)
             tris, wts = d.topk(p, 300)
-            assert_topk_equal(tris, wts, want, p, f"hubs {degrees} p={p}")
+            assert_topk_equal(tris, wts, want, p, f"cliques p={p}")
     finally:
         d.free()
 
 
-@pytest.mark.parametrize("dgr", [6, 14, 27, 200, 3000, 12000])
+@pytest.mark.parametrize("sizes", [[256, 257, 512, 513, 1024, 1025], [4000], [8193]],
+                         ids=["warp-block", "block-smem", "block-global"])
+def test_oriented_row_classes_structures(sizes):
+    """Oriented rows at the boundaries of the per-row sort's size classes (one
+    warp up to 1024, one block up to 8192 in shared memory, global merges
+    beyond): every device structure against the oracle's construction; on
+    the warp/block boundary case also the top-k at p = 1."""
+    g = _cliques_graph(sizes, seed=sum(sizes), wmax=1_000_000)
+    d = wt.build_csr(g.n, g.u, g.v, g.w)
+    try:
+        check_structures(g, d)
+        if max(sizes) <= 1025:
+            want = oracle.topk(g.n, g.u, g.v, g.w, 1.0, 300)
+            tris, wts = d.topk(1.0, 300)
+            assert_topk_equal(tris, wts, want, 1.0, f"cliques {sizes}")
+    finally:
+        d.free()
+
+
+@pytest.mark.parametrize("dgr", [6, 14, 27, 200, 3000, 9000])
 def test_repeated_pair_in_long_row(dgr):
-    """A repeated undirected pair inside a row of each size class is
-    rejected (WTRI_EINVAL naming the neighbour)."""
-    g = _hubs_graph([dgr], seed=dgr)
-    u = np.concatenate([g.u, np.array([dgr // 2 + 1], np.int32)])  # hub 0 - leaf again, flipped
-    v = np.concatenate([g.v, np.array([0], np.int32)])
-    w = np.concatenate([g.w, np.array([3], np.int32)])
+    """A repeated undirected pair inside an oriented row of each size class is
+    rejected (WTRI_EINVAL naming the pair).  Vertex 0 joins every vertex of
+    a clique K_{dgr} whose vertices also hold two leaves each, so vertex 0
+    has the lowest degree and its oriented row holds the whole clique and
+    the repeat."""
+    iu, ju = np.triu_indices(dgr, 1)
+    cu, cv = iu + 1, ju + 1
+    star = np.arange(1, dgr + 1)
+    leaves = dgr + 1 + np.arange(2 * dgr)
+    u = np.concatenate([cu, np.zeros(dgr, np.int64), np.repeat(star, 2), [dgr // 2 + 1]]).astype(np.int32)
+    v = np.concatenate([cv, star, leaves, [0]]).astype(np.int32)
+    w = np.full(u.shape[0], 3, np.int32)
     with pytest.raises(wt.WtriError) as ei:
-        wt.build_csr(g.n, u, v, w)
+        wt.build_csr(3 * dgr + 1, u, v, w)
     assert ei.value.code == -1
-    assert "repeated" in str(ei.value) and str(dgr // 2 + 1) in str(ei.value)
+    assert "repeated" in str(ei.value) and "{0, %d}" % (dgr // 2 + 1) in str(ei.value)
 
 
 @pytest.mark.parametrize("seed", range(24))
