@@ -384,6 +384,84 @@ inline unsigned round_grid(int64_t edges) {
 }
 
 // ---------------------------------------------------------------------------
+// Round at p = -inf by NodeIterator++ over the degree order (Section 5.2):
+// one warp per edge r = {a, b}, a the endpoint of lower (degree, id) rank.
+// A triangle a < b < c in that order is found exactly once, from its edge
+// {a, b}, as c in N+(a) ∩ N+(b) (the oriented rows): the shorter row is
+// scanned and each c binary-searched in the other.  Its key min(w_ab, w_ac,
+// w_bc) is at most w_r, so the heavy-first stop of the sweep holds: once
+// w_r < tau no later edge can close a triangle that enters the top-k, and
+// entries lighter than tau are skipped before the search.  Every edge of a
+// qualifying triangle is at least tau, which is why this replaces the
+// weight-sorted scan (whose wedge bound prunes little at p = -inf) for the
+// unsampled, unsharded query.
+// ---------------------------------------------------------------------------
+constexpr int MIN_WARPS = RBLK / 32;
+
+__global__ void __launch_bounds__(RBLK) k_round_min(DevGraph G, Query q, int64_t lo, int64_t hi) {
+    const volatile uint32_t* stop_rev = &q.st->stop_rev;
+    if (lo >= (int64_t)(STOP_NONE - *stop_rev)) return;
+    if (*(volatile const uint32_t*)&q.st->err) return;  // the query has already failed
+    const unsigned long long tau = ld_volatile_u64(&q.st->tau);
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * MIN_WARPS;
+    Tally tb;
+    tb.on = q.qbytes != nullptr;
+    for (int64_t r = lo + (int64_t)blockIdx.x * MIN_WARPS + (threadIdx.x >> 5); r < hi; r += nwarps) {
+        if (r >= (int64_t)(STOP_NONE - *stop_rev)) break;
+        const uint32_t w = (uint32_t)__ldg(G.ord_w + r);
+        if (w < tau) {
+            // every later edge is lighter: record the first such edge
+            if (lane == 0) atomicMax(&q.st->stop_rev, STOP_NONE - (uint32_t)r);
+            break;
+        }
+        const int32_t u = __ldg(G.ord_u + r), v = __ldg(G.ord_v + r);
+        const int64_t du = __ldg(G.rowptr + u + 1) - __ldg(G.rowptr + u);
+        const int64_t dv = __ldg(G.rowptr + v + 1) - __ldg(G.rowptr + v);
+        const bool ua = du < dv || (du == dv && u < v);
+        const int32_t a = ua ? u : v, b = ua ? v : u;
+        const int64_t ab = __ldg(G.orowptr + a), ae = __ldg(G.orowptr + a + 1);
+        const int64_t bb = __ldg(G.orowptr + b), be = __ldg(G.orowptr + b + 1);
+        if (lane == 0) tb.add(12 + 32 + 32);
+        const bool as = (ae - ab) <= (be - bb);
+        const int64_t sb = as ? ab : bb, se = as ? ae : be;  // scanned row
+        const int64_t lb = as ? bb : ab, le = as ? be : ae;  // searched row
+        for (int64_t base = sb; base < se; base += 32) {
+            const int64_t j = base + lane;
+            if (j >= se) break;
+            const uint32_t wsc = (uint32_t)__ldg(G.owt + j);
+            tb.add(4);
+            if (wsc < tau) continue;
+            const int32_t c = __ldg(G.ocol + j);
+            tb.add(4);
+            int64_t l0 = lb, l1 = le;
+            while (l0 < l1) {
+                const int64_t mid = (l0 + l1) >> 1;
+                tb.add(4);
+                if (__ldg(G.ocol + mid) < c) l0 = mid + 1;
+                else l1 = mid;
+            }
+            if (l0 < le && (tb.add(4), __ldg(G.ocol + l0) == c)) {
+                const uint32_t wlc = (uint32_t)__ldg(G.owt + l0);
+                tb.add(4);
+                const unsigned long long key = keyof<P_MIN>(w, wsc, wlc);
+                if (key >= tau) {
+                    int32_t x = a, y = b, z = c;
+                    sort3(x, y, z);
+                    append(q, key, x, y, z);
+                }
+            }
+        }
+    }
+    flush_tally(q, tb);
+}
+
+inline unsigned round_grid_warps(int64_t edges) {
+    const int64_t cap = (int64_t)sm_count() * 8;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cap, (edges + MIN_WARPS - 1) / MIN_WARPS));
+}
+
+// ---------------------------------------------------------------------------
 // Deferred long scans: one block per item.  y's oriented row (ids) is
 // staged in shared memory with a bulk async copy completed on an mbarrier;
 // closing edges that y owns are binary searches there, the others searches

@@ -49,10 +49,13 @@ namespace radix {
 
 constexpr int MAX_BITS = 10;               // widest digit of a pass
 constexpr int MAX_BINS = 1 << MAX_BITS;
-constexpr int NT = 256;                    // threads of the histogram and scatter CTAs
+#ifndef WTRI_RADIX_NT
+#define WTRI_RADIX_NT 256
+#endif
+constexpr int NT = WTRI_RADIX_NT;          // threads of the histogram and scatter CTAs
 constexpr int NW = NT / 32;
 #ifndef WTRI_RADIX_IT
-#define WTRI_RADIX_IT 24
+#define WTRI_RADIX_IT (WTRI_RADIX_NT == 512 ? 11 : 24)  // the tiles, counters and staging fit 227 KB
 #endif
 #ifndef WTRI_RADIX_CTAS
 #define WTRI_RADIX_CTAS 1
@@ -62,9 +65,11 @@ constexpr int TT = NT * IT;                // records per tile
 constexpr int CTAS_PER_SM = WTRI_RADIX_CTAS;
 constexpr int DPT = MAX_BINS / NT;         // digits owned by a thread in the tile scan
 constexpr int UP_SPLIT = 8;                // histogram blocks per chunk
+constexpr int UNT = 256;                   // threads of a histogram block
+constexpr int UNW = UNT / 32;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;  // bounded mbarrier polling
 static_assert(TT % 16 == 0, "tiles are whole 16-byte lines of every source array");
-static_assert(DPT == 4, "a thread's digits are one 8-byte word of each warp's counters");
+static_assert(DPT == 2 || DPT == 4, "a thread's digits are one 4- or 8-byte word of each warp's counters");
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -146,11 +151,11 @@ struct StoredDigits {  // later passes: 16-bit digits written by the previous sc
 // zeroed per-chunk histogram; each warp counts into its own shared copy.
 // Stored digits are read eight at a time (one 16-byte load).
 template <class Dig>
-__global__ void __launch_bounds__(NT) k_upsweep(Dig dg, PassGeom g, uint32_t* counts) {
+__global__ void __launch_bounds__(UNT) k_upsweep(Dig dg, PassGeom g, uint32_t* counts) {
     if (pass_closed(g)) return;
-    __shared__ uint32_t hist[NW][MAX_BINS];
+    __shared__ uint32_t hist[UNW][MAX_BINS];
     const int w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < NW * MAX_BINS; i += NT) (&hist[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < UNW * MAX_BINS; i += UNT) (&hist[0][0])[i] = 0;
     __syncthreads();
     uint32_t* h = hist[w];
     const int chunk = blockIdx.x / UP_SPLIT, part = blockIdx.x % UP_SPLIT;
@@ -163,7 +168,7 @@ __global__ void __launch_bounds__(NT) k_upsweep(Dig dg, PassGeom g, uint32_t* co
     if constexpr (Dig::PACKED) {
         const int64_t nv = (end - beg) >> 3;  // whole groups of 8 (beg is a multiple of 8)
         const uint4* v = reinterpret_cast<const uint4*>(dg.d + beg);
-        for (int64_t q = threadIdx.x; q < nv; q += NT) {
+        for (int64_t q = threadIdx.x; q < nv; q += UNT) {
             const uint4 x = __ldg(v + q);
             atomicAdd(&h[x.x & 0xffffu], 1u);
             atomicAdd(&h[x.x >> 16], 1u);
@@ -177,20 +182,20 @@ __global__ void __launch_bounds__(NT) k_upsweep(Dig dg, PassGeom g, uint32_t* co
         i0 = beg + (nv << 3);
     } else {
         constexpr int U = 4;
-        for (; i0 + (int64_t)U * NT <= end; i0 += (int64_t)U * NT) {
+        for (; i0 + (int64_t)U * UNT <= end; i0 += (int64_t)U * UNT) {
             uint32_t d[U];
 #pragma unroll
-            for (int u = 0; u < U; u++) d[u] = dg.digit(i0 + (int64_t)u * NT + threadIdx.x);
+            for (int u = 0; u < U; u++) d[u] = dg.digit(i0 + (int64_t)u * UNT + threadIdx.x);
 #pragma unroll
             for (int u = 0; u < U; u++) atomicAdd(&h[d[u]], 1u);
         }
     }
-    for (int64_t i = i0 + threadIdx.x; i < end; i += NT) atomicAdd(&h[dg.digit(i)], 1u);
+    for (int64_t i = i0 + threadIdx.x; i < end; i += UNT) atomicAdd(&h[dg.digit(i)], 1u);
     __syncthreads();
-    for (int d = threadIdx.x; d < g.bins; d += NT) {
+    for (int d = threadIdx.x; d < g.bins; d += UNT) {
         uint32_t s = 0;
 #pragma unroll
-        for (int k = 0; k < NW; k++) s += hist[k][d];
+        for (int k = 0; k < UNW; k++) s += hist[k][d];
         if (s) atomicAdd(&counts[(int64_t)d * g.chunks + chunk], s);
     }
 }
@@ -321,6 +326,28 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d, int bits, bool valid
 }
 __device__ __forceinline__ uint32_t hi16(uint32_t x) { return x >> 16; }
 
+// A thread's DPT consecutive 16-bit counters as one 4- or 8-byte word.
+__device__ __forceinline__ void load_counts(const uint16_t* p, uint32_t (&c)[DPT]) {
+    if constexpr (DPT == 4) {
+        const uint2 r = *reinterpret_cast<const uint2*>(p);
+        c[0] = lo16(r.x);
+        c[1] = hi16(r.x);
+        c[2] = lo16(r.y);
+        c[3] = hi16(r.y);
+    } else {
+        const uint32_t r = *reinterpret_cast<const uint32_t*>(p);
+        c[0] = lo16(r);
+        c[1] = hi16(r);
+    }
+}
+__device__ __forceinline__ void store_counts(uint16_t* p, const uint32_t (&s)[DPT]) {
+    if constexpr (DPT == 4) {
+        *reinterpret_cast<uint2*>(p) = make_uint2(s[0] | (s[1] << 16), s[2] | (s[3] << 16));
+    } else {
+        *reinterpret_cast<uint32_t*>(p) = s[0] | (s[1] << 16);
+    }
+}
+
 // Rank, stage and write one tile of tcount <= TT records held in registers.
 // Item j of warp w, lane l is record w * 32 * IT + j * 32 + l of the tile;
 // ranking strips in order and warps in order keeps equal digits stable.
@@ -361,29 +388,31 @@ __device__ __forceinline__ void scatter_tile(const uint4 (&rec)[IT], int tcount,
     }
     __syncthreads();
     // 3. per digit: offsets of each warp, tile start, output delta.  Thread t
-    //    owns digits 4t..4t+3: one 8-byte word of each warp's counters.
+    //    owns digits DPT t .. DPT t + DPT - 1: one word of each warp's counters.
     {
         const int d0 = threadIdx.x * DPT;
         const bool mine = d0 < g.bins;
-        uint32_t tot[DPT] = {0, 0, 0, 0};
+        uint32_t tot[DPT];
+#pragma unroll
+        for (int i = 0; i < DPT; i++) tot[i] = 0;
         if (mine) {
 #pragma unroll
             for (int k = 0; k < NW; k++) {
-                const uint2 r = *reinterpret_cast<const uint2*>(&S.cnt[k][d0]);
-                tot[0] += lo16(r.x);
-                tot[1] += hi16(r.x);
-                tot[2] += lo16(r.y);
-                tot[3] += hi16(r.y);
+                uint32_t c[DPT];
+                load_counts(&S.cnt[k][d0], c);
+#pragma unroll
+                for (int i = 0; i < DPT; i++) tot[i] += c[i];
             }
         }
-        const uint32_t sum = tot[0] + tot[1] + tot[2] + tot[3];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int i = 0; i < DPT; i++) sum += tot[i];
         const uint32_t start = block_exclusive_scan<NT>(sum, S.warp_tot, &S.total);
         if (mine) {
             uint32_t s[DPT];
             s[0] = start;
-            s[1] = s[0] + tot[0];
-            s[2] = s[1] + tot[1];
-            s[3] = s[2] + tot[2];
+#pragma unroll
+            for (int i = 1; i < DPT; i++) s[i] = s[i - 1] + tot[i - 1];
 #pragma unroll
             for (int i = 0; i < DPT; i++) {
                 S.delta[d0 + i] = run[i] - s[i];
@@ -391,13 +420,11 @@ __device__ __forceinline__ void scatter_tile(const uint4 (&rec)[IT], int tcount,
             }
 #pragma unroll
             for (int k = 0; k < NW; k++) {
-                uint2* p = reinterpret_cast<uint2*>(&S.cnt[k][d0]);
-                const uint2 r = *p;
-                *p = make_uint2(s[0] | (s[1] << 16), s[2] | (s[3] << 16));
-                s[0] += lo16(r.x);
-                s[1] += hi16(r.x);
-                s[2] += lo16(r.y);
-                s[3] += hi16(r.y);
+                uint32_t c[DPT];
+                load_counts(&S.cnt[k][d0], c);
+                store_counts(&S.cnt[k][d0], s);
+#pragma unroll
+                for (int i = 0; i < DPT; i++) s[i] += c[i];
             }
         }
     }
@@ -635,7 +662,7 @@ int run_pass(const Dig& dg, const Loader& ld, const Storer& st, const PassGeom& 
     {
         ProfScope ps("radix_upsweep", s, 0.0, 1, hist_bytes * (double)g.n + 4.0 * g.bins * g.chunks);
         WTRI_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)g.bins * g.chunks, s));
-        k_upsweep<Dig><<<g.chunks * UP_SPLIT, NT, 0, s>>>(dg, g, counts);
+        k_upsweep<Dig><<<g.chunks * UP_SPLIT, UNT, 0, s>>>(dg, g, counts);
     }
     {
         ProfScope ps("radix_digit_scan", s, 0.0, 1, 8.0 * g.bins * g.chunks);

@@ -58,16 +58,23 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
     WTRI_TRY((long_optin<P, false>()));
     const int long_grid = sm_count() * 2;
     ProfScope whole(query_name(P), s, 0.0, 0);
+    // p = -inf on one shard: NodeIterator++ rounds (no deferred scans)
+    const bool oriented = P == P_MIN && nshards == 1;
     int64_t lo = 0, size = g->tune.first_round;
     while (lo < m) {
         const int64_t hi = std::min(m, lo + size);
-        {
-            ProfScope ps("topk_round", s, 0.0, 1);
-            k_round<P><<<round_grid(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
-        }
-        {
-            ProfScope ps("topk_long", s, 0.0, 1);
-            k_long<P><<<long_grid, LBLK, lsmem, s>>>(G, q);
+        if (oriented) {
+            ProfScope ps("topk_round_min", s, 0.0, 1);
+            k_round_min<<<round_grid_warps(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
+        } else {
+            {
+                ProfScope ps("topk_round", s, 0.0, 1);
+                k_round<P><<<round_grid(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
+            }
+            {
+                ProfScope ps("topk_long", s, 0.0, 1);
+                k_long<P><<<long_grid, LBLK, lsmem, s>>>(G, q);
+            }
         }
         {
             ProfScope ps("topk_select", s, 0.0, 1);
@@ -481,10 +488,16 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
     int64_t lo = 0, size = g->tune.first_round;
     while (lo < m) {
         const int64_t hi = std::min(m, lo + size);
-        k_round<P><<<round_grid(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
-        k_long<P><<<long_grid, LBLK, lsmem, s>>>(G, q);
+        if (P == P_MIN) {  // NodeIterator++ rounds, as in run_query
+            k_round_min<<<round_grid_warps(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
+            count_launches(1);
+        } else {
+            k_round<P><<<round_grid(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
+            k_long<P><<<long_grid, LBLK, lsmem, s>>>(G, q);
+            count_launches(2);
+        }
         k_select<<<1, SBLK, 0, s>>>(q);
-        count_launches(3);
+        count_launches(1);
         lo = hi;
         size *= g->tune.growth;
     }
