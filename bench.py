@@ -365,7 +365,7 @@ def run_batch_workload(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def serve_run(wt, ds, edges, rate, count, seq_count, note, seq_budget_s=1e9):
+def serve_run(wt, ds, edges, rate, count, seq_count, note, seq_budget_s=1e9, coalesce=True):
     """Poisson arrivals at `rate` req/s over the resident graphs `ds`, k ~
     U[10,1000], p ~ U{-inf,1,2,+inf}, through the continuous-batching server
     (latency = submission to completion, measured by the server).  Baseline:
@@ -379,6 +379,7 @@ def serve_run(wt, ds, edges, rate, count, seq_count, note, seq_budget_s=1e9):
     ks = rng.integers(10, 1001, size=count)
     ps = np.array(PS)[rng.integers(0, 4, size=count)]
     srv = wt.Server(120 << 30, 256)
+    srv.set_coalesce(coalesce)
     ids = [srv.add_graph(d) for d in ds]
     for i in range(16):  # warm-up
         t = srv.submit(ids[i % len(ds)], PS[i % 4], 100)
@@ -426,13 +427,14 @@ def serve_run(wt, ds, edges, rate, count, seq_count, note, seq_budget_s=1e9):
     out = {"requests": count, "rate_req_s": rate, "graphs_edges": [int(x) for x in edges],
            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
            "qps": count / t_last, "micro_batches": int(st["batches"]), "retries": int(st["retries"]),
-           "sequential_requests": seq_count,
-           "sequential_p50_ms": 1e3 * float(np.percentile(seq_lat, 50)),
-           "sequential_p99_ms": 1e3 * float(np.percentile(seq_lat, 99)),
-           "sequential_qps": seq_count / finish,
-           "sequential_mean_service_ms": 1e3 * float(service.mean()),
-           "budget_gb": 120, "note": note}
-    if seq_count < count:
+           "budget_gb": 120, "coalesce": bool(coalesce), "note": note}
+    if seq_count > 0:
+        out.update({"sequential_requests": seq_count,
+                    "sequential_p50_ms": 1e3 * float(np.percentile(seq_lat, 50)),
+                    "sequential_p99_ms": 1e3 * float(np.percentile(seq_lat, 99)),
+                    "sequential_qps": seq_count / finish,
+                    "sequential_mean_service_ms": 1e3 * float(service.mean())})
+    if 0 < seq_count < count:
         out["server_first_requests_p50_ms"] = 1e3 * float(np.percentile(head, 50))
         out["server_first_requests_p99_ms"] = 1e3 * float(np.percentile(head, 99))
     return out
@@ -445,10 +447,14 @@ def bench_serve(wt, g_mid, rate=2000.0, count=4000):
     gs = [g_mid, synth.scaled_mid_graph(200_000, 2_000_000, seed=5),
           synth.scaled_mid_graph(500_000, 5_000_000, seed=6)]
     ds = [wt.build_csr(x.n, x.u, x.v, x.w) for x in gs]
+    note = ("reduced pool: the bench graph and two Chung-Lu graphs instead of the "
+            "1e9- and 2e8-edge graphs (the full pool runs under --workload serve)")
     try:
-        return serve_run(wt, ds, [x.m for x in gs], rate, count, count,
-                         "reduced pool: the bench graph and two Chung-Lu graphs instead of the "
-                         "1e9- and 2e8-edge graphs (the full pool runs under --workload serve)")
+        r = serve_run(wt, ds, [x.m for x in gs], rate, count, count, note)
+        # every request runs its own query (no sharing of same-(graph, p) queries)
+        r["no_coalescing"] = serve_run(wt, ds, [x.m for x in gs], rate, count // 2, 0, note,
+                                       coalesce=False)
+        return r
     finally:
         for d in ds:
             d.free()
@@ -477,11 +483,17 @@ def run_serve_workload(args, world, rank, count=100_000, seq_count=20_000):
                       "full pool; sequential baseline over the first sequential_requests requests "
                       "(same arrivals, at most 150 s of sequential service), server figures over "
                       "all requests and over those", seq_budget_s=150.0)
+        # every request runs its own query (no sharing of same-(graph, p)
+        # queries): 20,000 requests at the same offered rate
+        r["no_coalescing"] = serve_run(wt, ds, edges, 2000.0, 20_000, 0,
+                                       "full pool, coalescing off, no sequential baseline",
+                                       coalesce=False)
+        resident = sum(d.info()["device_bytes"] for d in ds)
     finally:
         for d in ds:
             d.free()
     r["pool_draw_and_build_s"] = t_pool
-    r["resident_gb"] = 84 * sum(edges) / 1e9
+    r["resident_gb"] = resident / 1e9
     if rank != 0:
         return
     line = {
@@ -670,13 +682,23 @@ def run_step_workload(args, world, rank, local):
         tune = d0.autotune(k=k, reps=3)
         d0.free()
 
+    # N > 1: every rank builds its own replica of the graph and answers one
+    # shard of each query (the owning edges split across ranks); one NCCL
+    # all-gather of the shards' k best and the host merge give the answer.
+    from paper_1910_00692_gb300 import distributed as wdist
+
     def step():
         with torch.cuda.stream(stream):
             d = wt.build_csr(n, du, dv, dw, stream=stream)
             if tune:
                 d.set_tune(tune["first_round"], tune["growth"], tune["t_short"])
             for i, p in enumerate(ps_step):
-                wt.topk_device(d, p, k, out_t, out_w, out_c[i:i + 1], stream=stream)
+                if pg:
+                    local_part = wt.topk_shard(d, p, k, rank, world)
+                    tris_g, _, _ = wdist.merge_across_ranks(local_part, k)
+                    out_c[i:i + 1].fill_(tris_g.shape[0])
+                else:
+                    wt.topk_device(d, p, k, out_t, out_w, out_c[i:i + 1], stream=stream)
             d.free()
 
     for _ in range(args.warmup):
@@ -782,7 +804,10 @@ def run_step_workload(args, world, rank, local):
             if tune:
                 d.set_tune(tune["first_round"], tune["growth"], tune["t_short"])
             for p in ps_step:
-                tris, wts = d.topk(p, k)
+                if pg:
+                    tris, wts, _ = wdist.topk_distributed(d, p, k)
+                else:
+                    tris, wts = d.topk(p, k)
                 d2h += tris.nbytes + wts.nbytes + 4
             d.free()
         e2e_step()
@@ -843,7 +868,9 @@ def run_step_workload(args, world, rank, local):
             "config": {"workload": wl, "global_batch": world, "k": k,
                        "step": STEP_DEF if not large else
                        "wtri_build_csr from device COO + exact top-1000 at p = 1",
-                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "parallelism": (f"replicated build on {world} GPUs, each query sharded "
+                                       f"{world} ways (owning edges), NCCL all-gather of 1+5k "
+                                       f"int64 per rank + host merge") if world > 1 else "single",
                        "l2": (f"inputs larger than L2: COO {12 * m / 1e9:.2f} GB, resident graph "
                               f"{info['device_bytes'] / 1e9:.1f} GB per step")},
             "graph": info,

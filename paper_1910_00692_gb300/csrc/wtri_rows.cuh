@@ -275,49 +275,71 @@ __device__ __forceinline__ void gather_wr(const RowsOut& R, int64_t s, unsigned 
 // Rows of at most G entries (G = 8, 16, 32): G lanes per row, a bitonic
 // network across the group's lanes.
 // ---------------------------------------------------------------------------
+constexpr int SMALL_U = 4;  // rows per lane group and iteration (their loads issued together)
+
 template <int G>
 __global__ void __launch_bounds__(NT) k_rows_small(RowsOut R, int cls, const uint32_t* gate) {
     if (rows_gate_closed(gate)) return;
     const int lane = threadIdx.x & 31, gl = lane & (G - 1), grp = lane / G;
-    constexpr int RPW = 32 / G;  // rows per warp
+    constexpr int RPW = 32 / G;  // rows per warp and unrolled step
     const int64_t lo = R.cls_off[cls], hi = R.cls_off[cls + 1];
     const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
-    for (int64_t wbase = lo + (((int64_t)blockIdx.x * NT + threadIdx.x) >> 5) * RPW; wbase < hi;
-         wbase += nwarps * RPW) {
-        const int64_t ri = wbase + grp;
-        int32_t x = 0, d = 0;
-        int64_t s = 0, ob = 0;
-        if (ri < hi) {
-            x = __ldg(R.list + ri);
-            s = __ldg(R.rowptr + x);
-            d = __ldg(R.odeg + x);
-            ob = __ldg(R.orowptr + x);
+    for (int64_t wbase = lo + (((int64_t)blockIdx.x * NT + threadIdx.x) >> 5) * (RPW * SMALL_U); wbase < hi;
+         wbase += nwarps * (RPW * SMALL_U)) {
+        int32_t x[SMALL_U], d[SMALL_U];
+        int64_t s[SMALL_U], ob[SMALL_U];
+#pragma unroll
+        for (int u = 0; u < SMALL_U; u++) {
+            const int64_t ri = wbase + u * RPW + grp;
+            x[u] = ri < hi ? __ldg(R.list + ri) : -1;
         }
-        const bool valid = gl < d;
-        unsigned long long key = KEY_NONE;
-        int32_t w = 0, rk = 0;
-        if (valid) {
-            key = __ldcs(R.pk + s + gl);
-            gather_wr(R, s, key, w, rk);
-            key = with_pos(key, gl);
+#pragma unroll
+        for (int u = 0; u < SMALL_U; u++) {
+            s[u] = 0;
+            d[u] = 0;
+            ob[u] = 0;
+            if (x[u] >= 0) {
+                s[u] = __ldg(R.rowptr + x[u]);
+                d[u] = __ldg(R.odeg + x[u]);
+                ob[u] = __ldg(R.orowptr + x[u]);
+            }
+        }
+        unsigned long long key[SMALL_U];
+#pragma unroll
+        for (int u = 0; u < SMALL_U; u++) key[u] = gl < d[u] ? __ldcs(R.pk + s[u] + gl) : KEY_NONE;
+        int32_t w[SMALL_U], rk[SMALL_U];
+#pragma unroll
+        for (int u = 0; u < SMALL_U; u++) {
+            w[u] = 0;
+            rk[u] = 0;
+            if (gl < d[u]) {
+                gather_wr(R, s[u], key[u], w[u], rk[u]);
+                key[u] = with_pos(key[u], gl);
+            }
         }
 #pragma unroll
         for (int k = 2; k <= G; k <<= 1) {
 #pragma unroll
             for (int j = k >> 1; j > 0; j >>= 1) {
-                const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, j, G);
                 const bool up = (gl & k) == 0, lower = (gl & j) == 0;
-                key = (lower == up) ? (ok < key ? ok : key) : (ok > key ? ok : key);
+#pragma unroll
+                for (int u = 0; u < SMALL_U; u++) {
+                    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key[u], j, G);
+                    key[u] = (lower == up) ? (ok < key[u] ? ok : key[u]) : (ok > key[u] ? ok : key[u]);
+                }
             }
         }
-        const int src = (int)key_pos(key) & (G - 1);
-        const int32_t ws = __shfl_sync(0xffffffffu, w, src, G);
-        const int32_t rks = __shfl_sync(0xffffffffu, rk, src, G);
-        const unsigned long long prev = __shfl_up_sync(0xffffffffu, key, 1, G);
-        if (valid) {
-            const int32_t c = key_col(key);
-            write_orient(R, ob + gl, c, ws, rks);
-            if (gl > 0 && key_col(prev) == c) flag_dup(R, x, c);
+#pragma unroll
+        for (int u = 0; u < SMALL_U; u++) {
+            const int src = (int)key_pos(key[u]) & (G - 1);
+            const int32_t ws = __shfl_sync(0xffffffffu, w[u], src, G);
+            const int32_t rks = __shfl_sync(0xffffffffu, rk[u], src, G);
+            const unsigned long long prev = __shfl_up_sync(0xffffffffu, key[u], 1, G);
+            if (gl < d[u]) {
+                const int32_t c = key_col(key[u]);
+                write_orient(R, ob[u] + gl, c, ws, rks);
+                if (gl > 0 && key_col(prev) == c) flag_dup(R, x[u], c);
+            }
         }
     }
 }

@@ -24,6 +24,10 @@ class _FakeServer:
 
     def __init__(self, *_):
         self.n = 0
+        self.coalesce = True
+
+    def set_coalesce(self, on):
+        self.coalesce = on
 
     def add_graph(self, d):
         return 0
@@ -62,6 +66,15 @@ def test_serve_run_queue_arithmetic():
     assert r["sequential_p99_ms"] > r["sequential_p50_ms"] > 2.0
     assert r["sequential_qps"] < 1000.0
     assert r["server_first_requests_p50_ms"] == 1.0
+    json.dumps(r)
+
+
+def test_serve_run_without_coalescing_or_baseline():
+    b = _bench()
+    wt = types.SimpleNamespace(Server=_FakeServer)
+    r = b.serve_run(wt, [_FakeGraph(0.001)], [10], 5000.0, 100, 0, "test", coalesce=False)
+    assert r["coalesce"] is False and r["requests"] == 100
+    assert "sequential_requests" not in r and "server_first_requests_p50_ms" not in r
     json.dumps(r)
 
 

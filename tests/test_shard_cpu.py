@@ -89,3 +89,19 @@ def test_gloo_two_ranks(tmp_path):
                        start_method="spawn")
     for r in range(2):
         assert (tmp_path / f"rank{r}.txt").read_text() == "ok"
+
+
+def test_pack_roundtrip():
+    """The fixed-size exchange buffer carries counts, triples, fp64 weights
+    and 64-bit keys bit for bit, short parts padded."""
+    from paper_1910_00692_gb300 import distributed
+    t = np.array([[0, 1, 2], [5, 6, 7]], np.int32)
+    w = np.array([1.0 / 3.0, 2.0 ** -1074], np.float64)
+    kk = np.array([2 ** 64 - 1, 12], np.uint64)
+    buf = distributed.pack_part((t, w, kk), 4)
+    assert buf.shape == (21,) and buf.dtype == np.int64
+    t2, w2, k2 = distributed.unpack_part(buf, 4)
+    assert np.array_equal(t2, t) and np.array_equal(w2.view(np.int64), w.view(np.int64))
+    assert np.array_equal(k2, kk)
+    t3, w3, k3 = distributed.unpack_part(distributed.pack_part((t[:0], w[:0], kk[:0]), 4), 4)
+    assert t3.shape == (0, 3) and w3.shape == (0,) and k3.shape == (0,)
