@@ -96,9 +96,13 @@ def lib():
                                ctypes.c_int64, ctypes.c_double, i32p, u64p, f64p, I64P, i64p]
         L.dhl_alpha.argtypes = [ctypes.c_int, ctypes.c_double]
         L.dhl_alpha.restype = ctypes.c_double
+        L.or_clique_topk.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, i32p, u64p, f64p,
+                                     I64P, I64P]
         for f in (L.dhl_topk, L.or_validate, L.or_sym_csr, L.or_edge_order, L.or_oriented_csr,
                   L.or_score, L.or_topk, L.or_count_triangles, L.or_sample_edges,
-                  L.or_topk_of_sampled, L.or_topk_shard, L.or_wedge_samples, L.or_wedge_topk):
+                  L.or_topk_of_sampled, L.or_topk_shard, L.or_wedge_samples, L.or_wedge_topk,
+                  L.or_clique_topk):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -388,3 +392,44 @@ def wedge_topk(n, u, v, w, p, k, nsamples, seed):
     c = int(cnt.value)
     return {"tri": tri[: 3 * c].reshape(c, 3), "key": key[:c], "value": val[:c], "count": c,
             "ntri": int(ntri.value)}
+
+
+CLIQUE_P2_WMAX = 1 << 30  # p = 2 ranks cliques by the sum of ten squares: exact below 2^64
+
+
+def clique_topk(n, u, v, w, q, p, k, edge_sampled=None):
+    """Top-k q-cliques (q = 4, 5) by the p-mean of their edge weights (Section
+    4.5, Appendix A), p in {-inf, 1, 2, +inf}.  edge_sampled (one flag per
+    input edge, or None for every clique): only cliques with a flagged edge.
+    Returns dict(ids (count x q), key, value, count, ncliques)."""
+    u, v, w = _arr(u), _arr(v), _arr(w)
+    pc = pcode(p)
+    if pc > 3:
+        raise OracleError("cliques rank at p in {-inf, 1, 2, +inf}")
+    k = int(k)
+    ids = np.zeros(max(k, 1) * q, np.int32)
+    key = np.zeros(max(k, 1), np.uint64)
+    val = np.zeros(max(k, 1), np.float64)
+    cnt = ctypes.c_int64(0)
+    ncl = ctypes.c_int64(0)
+    flags = None
+    if edge_sampled is not None:
+        flags = np.ascontiguousarray(edge_sampled, dtype=np.uint8)
+        if flags.shape[0] != u.shape[0]:
+            raise OracleError("edge_sampled needs one flag per edge")
+    rc = lib().or_clique_topk(n, u.shape[0], u, v, w, int(q), pc,
+                              None if flags is None else flags.ctypes.data_as(ctypes.c_void_p),
+                              k, ids, key, val, ctypes.byref(cnt), ctypes.byref(ncl))
+    if rc != 0:
+        raise OracleError(f"or_clique_topk failed (rc={rc})")
+    c = cnt.value
+    return {"ids": ids[:c * q].reshape(-1, q), "key": key[:c], "value": val[:c], "count": c,
+            "ncliques": ncl.value}
+
+
+def sampled_edge_flags(w, p, nsamples, seed):
+    """One flag per input edge: drawn at least once by Algorithm 3's sampler."""
+    perm, hits = sample_edges(w, p, nsamples, seed)
+    flags = np.zeros(len(w), np.uint8)
+    flags[perm[hits > 0]] = 1
+    return flags

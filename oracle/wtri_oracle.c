@@ -1079,3 +1079,170 @@ int or_wedge_topk(int32_t n, int64_t m, const int32_t* u, const int32_t* v, cons
     free(ctr); free(st); free(rowp); free(col); free(wt); free(eid);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Top weighted cliques (Section 4.5, Appendix A).                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The weight of a q-clique is the generalized p-mean of the weights of its
+ * q(q-1)/2 edges (Appendix A).  Keys, exact and monotone in that mean, for
+ * p in {-inf, 1, 2, +inf} (codes 0..3): the minimum, the sum, the sum of
+ * squares (weights at most 2^30, so that ten squares fit 64 bits) and the
+ * maximum of the edge weights.  p = 0 and other finite p are not taken (the
+ * product of ten weights has no 64-bit key).  Value: min, sum / E,
+ * sqrt(sum of squares / E), max with E = q(q-1)/2.
+ */
+#define OR_CLIQUE_P2_WMAX (1 << 30)
+
+typedef struct {
+    uint64_t key;
+    int32_t t[5];
+} or_clq;
+
+static int g_clq_q;
+
+static int cmp_clq(const void* a, const void* b) {
+    const or_clq* x = (const or_clq*)a;
+    const or_clq* y = (const or_clq*)b;
+    if (x->key != y->key) return x->key > y->key ? -1 : 1;
+    for (int i = 0; i < g_clq_q; i++)
+        if (x->t[i] != y->t[i]) return x->t[i] < y->t[i] ? -1 : 1;
+    return 0;
+}
+
+/* Position of b in a's id-sorted row, or -1. */
+static int64_t row_find(const int64_t* rowptr, const int32_t* col, int32_t a, int32_t b) {
+    int64_t lo = rowptr[a], hi = rowptr[a + 1];
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (col[mid] < b) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < rowptr[a + 1] && col[lo] == b) ? lo : -1;
+}
+
+static uint64_t clique_key(int pcode, const int32_t* wts, int ne) {
+    uint64_t acc = (pcode == 0) ? UINT64_MAX : 0;
+    for (int i = 0; i < ne; i++) {
+        uint64_t x = (uint64_t)wts[i];
+        if (pcode == 0) acc = x < acc ? x : acc;
+        else if (pcode == 1) acc += x;
+        else if (pcode == 2) acc += x * x;
+        else acc = x > acc ? x : acc;
+    }
+    return acc;
+}
+
+static double clique_value(int pcode, uint64_t key, int ne) {
+    if (pcode == 1) return (double)key / (double)ne;
+    if (pcode == 2) return sqrt((double)key / (double)ne);
+    return (double)key;
+}
+
+/*
+ * Top-k q-cliques (q = 4 or 5) under (weight desc, sorted vertex tuple asc).
+ * edge_sampled == NULL: every clique of the graph; else only the cliques
+ * with at least one edge i with edge_sampled[i] != 0 -- the set that edge
+ * sampling enumerates (Section 4.5: sample edges, enumerate the cliques on
+ * them).  Every clique is listed once, as vertices a < b < c < d (< e) with
+ * every pair adjacent, then all of them are sorted.  ids receives q ids
+ * per clique, ascending; *nclq the number of cliques in the set.
+ */
+int or_clique_topk(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int32_t* w,
+                   int q, int pcode, const uint8_t* edge_sampled, int64_t k, int32_t* ids,
+                   uint64_t* key, double* value, int64_t* count, int64_t* nclq) {
+    *count = 0;
+    *nclq = 0;
+    if ((q != 4 && q != 5) || pcode < 0 || pcode > 3 || k <= 0) return OR_EINVAL;
+    if (pcode == 2)
+        for (int64_t i = 0; i < m; i++)
+            if (w[i] > OR_CLIQUE_P2_WMAX) return OR_EINVAL;
+    int64_t* rowptr = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    int32_t* col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
+    int32_t* wt = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
+    int64_t* eid = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * m + 1));
+    if (!rowptr || !col || !wt || !eid) {
+        free(rowptr); free(col); free(wt); free(eid);
+        return OR_ENOMEM;
+    }
+    int rc = or_sym_csr(n, m, u, v, w, rowptr, col, wt, eid);
+    const int ne = q * (q - 1) / 2;
+    int64_t cap = 1024, len = 0;
+    or_clq* all = (or_clq*)malloc(sizeof(or_clq) * (size_t)cap);
+    if (!all) rc = OR_ENOMEM;
+    int32_t t[5];
+    for (int32_t a = 0; a < n && rc == OR_OK; a++) {
+        t[0] = a;
+        /* extend t[0..depth) by neighbours of a above t[depth-1], adjacent to all */
+        int64_t pos[5];
+        int depth = 1;
+        pos[1] = rowptr[a];
+        while (depth > 0 && rc == OR_OK) {
+            if (depth == q) {
+                int32_t wts[10];
+                int sampled = edge_sampled == NULL;
+                int e = 0;
+                for (int i = 0; i < q; i++)
+                    for (int j = i + 1; j < q; j++) {
+                        int64_t p_ = row_find(rowptr, col, t[i], t[j]);
+                        wts[e++] = wt[p_];
+                        if (edge_sampled && edge_sampled[eid[p_]]) sampled = 1;
+                    }
+                if (sampled) {
+                    if (len == cap) {
+                        or_clq* grown = (or_clq*)realloc(all, sizeof(or_clq) * (size_t)(2 * cap));
+                        if (!grown) {
+                            rc = OR_ENOMEM;
+                            break;
+                        }
+                        all = grown;
+                        cap *= 2;
+                    }
+                    all[len].key = clique_key(pcode, wts, ne);
+                    for (int i = 0; i < 5; i++) all[len].t[i] = i < q ? t[i] : 0;
+                    len++;
+                }
+                depth--;
+                continue;
+            }
+            /* next candidate for slot `depth`: a neighbour of a above t[depth-1] */
+            int found = 0;
+            while (pos[depth] < rowptr[a + 1]) {
+                int32_t c = col[pos[depth]++];
+                if (c <= t[depth - 1]) continue;
+                int adj = 1;
+                for (int i = 1; i < depth && adj; i++) adj = row_find(rowptr, col, t[i], c) >= 0;
+                if (adj) {
+                    t[depth] = c;
+                    found = 1;
+                    break;
+                }
+            }
+            if (found) {
+                depth++;
+                if (depth < q) pos[depth] = pos[depth - 1];  /* the row is id-sorted */
+            } else {
+                depth--;
+            }
+        }
+    }
+    if (rc == OR_OK) {
+        g_clq_q = q;
+        qsort(all, (size_t)len, sizeof(or_clq), cmp_clq);
+        int64_t out = len < k ? len : k;
+        for (int64_t i = 0; i < out; i++) {
+            for (int j = 0; j < q; j++) ids[q * i + j] = all[i].t[j];
+            key[i] = all[i].key;
+            value[i] = clique_value(pcode, all[i].key, ne);
+        }
+        *count = out;
+        *nclq = len;
+    }
+    free(all);
+    free(rowptr);
+    free(col);
+    free(wt);
+    free(eid);
+    return rc;
+}
