@@ -363,6 +363,28 @@ WTRI_API int wtri_sample_wedges(const wtri_graph* g, double p, int64_t nsamples,
                                 int32_t* center, int32_t* jb, int32_t* jc, int32_t* tri);
 
 /*
+ * Top weighted q-cliques by edge sampling (Section 4.5: sample an edge and
+ * enumerate the cliques incident on it; Appendix A: a clique weighs the
+ * generalized p-mean of its edge weights, Eq. 1 over q(q-1)/2 weights).
+ * q = 4 or 5.  Edges are drawn exactly as wtri_sample_edges draws them
+ * (nsamples draws of Algorithm 3 at p, seed): p = 1 or 2.  nsamples < 0
+ * takes every edge instead: the exact top-k q-cliques, at any p in
+ * {-inf, 1, 2, +inf}.  Cliques rank by (weight desc, sorted vertex tuple
+ * asc) with exact integer keys (min, sum, sum of squares, max of the edge
+ * weights; p = 2 needs weights up to 2^30, else WTRI_EUNSUPPORTED).
+ * Outputs (host, caller-owned): cliques[q i .. q i + q-1] ascending ids,
+ * weights[i] the fp64 mean (min, sum / E, sqrt(sum of squares / E), max with
+ * E = q(q-1)/2), keys[i] the key (keys may be NULL), *count = min(k, number
+ * of cliques found).  k in [1, 65536].  WTRI_EUNSUPPORTED if a drawn edge
+ * has more than 1024 common neighbours; WTRI_ENOMEM past 2^23 cliques on
+ * the drawn edges.  No counterpart for the exact mode in the paper (its
+ * baseline enumerates cliques on the CPU).
+ */
+WTRI_API int wtri_sample_cliques(const wtri_graph* g, int32_t q, double p, int32_t k, int64_t nsamples,
+                                 uint64_t seed, int32_t* cliques, double* weights, uint64_t* keys,
+                                 int32_t* count);
+
+/*
  * Copies one internal array of a built graph to host memory, for tests that
  * compare the device structures with an independent construction.
  * which: one of the WTRI_ARR_* values.  dst must hold bytes_capacity bytes;

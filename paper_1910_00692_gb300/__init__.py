@@ -20,6 +20,7 @@ from .wtri import (  # noqa: F401
     lib,
     lib_path,
     merge_topk,
+    sample_cliques,
     sample_edges,
     sample_topk,
     sample_wedges,
@@ -33,5 +34,5 @@ from .wtri import (  # noqa: F401
 
 __all__ = ["ARRAYS", "Graph", "Server", "WtriError", "WtriUnavailable", "autotune_buckets", "build_csr",
            "debug_set_wait_limit", "lib", "lib_path", "merge_topk", "topk_shard",
-           "sample_edges", "sample_topk", "sample_wedges", "topk", "topk_batch", "topk_device",
+           "sample_cliques", "sample_edges", "sample_topk", "sample_wedges", "topk", "topk_batch", "topk_device",
            "topk_device_noalloc", "wedge_topk"]

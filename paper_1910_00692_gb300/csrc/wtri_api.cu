@@ -457,6 +457,26 @@ WTRI_API int wtri_sample_wedges(const wtri_graph* g, double p, int64_t nsamples,
     return wedge_draws_host(g, code, nsamples, seed, center, jb, jc, tri);
 }
 
+WTRI_API int wtri_sample_cliques(const wtri_graph* g, int32_t q, double p, int32_t k, int64_t nsamples,
+                                 uint64_t seed, int32_t* cliques, double* weights, uint64_t* keys,
+                                 int32_t* count) {
+    if (!g) return set_error(WTRI_EINVAL, "graph is NULL");
+    if (count) *count = 0;
+    if (q != 4 && q != 5) return set_error(WTRI_EINVAL, "clique size must be 4 or 5");
+    if (k <= 0 || k > 65536) return set_error(WTRI_EINVAL, "k must be in [1, 65536]");
+    if (!cliques || !weights || !count) return set_error(WTRI_EINVAL, "output arrays are NULL");
+    int code = 0;
+    WTRI_TRY(p_to_code(p, &code));
+    if (code != P_MIN && code != P_ONE && code != P_TWO && code != P_MAX)
+        return set_error(WTRI_EUNSUPPORTED, "cliques rank at p in {-inf, 1, 2, +inf}");
+    if (nsamples >= 0 && code != P_ONE && code != P_TWO)
+        return set_error(WTRI_EUNSUPPORTED, "edge draws need w^p with p = 1 or 2");
+    if (code == P_TWO && g->d.wmax > (1 << 30))
+        return set_error(WTRI_EUNSUPPORTED, "p = 2 ranks cliques by a sum of squares: weights up to 2^30");
+    if (g->d.m == 0) return WTRI_OK;
+    return clique_topk_host(g, q, code, k, nsamples, seed, cliques, weights, keys, count);
+}
+
 WTRI_API int wtri_topk_batch(const wtri_graph* const* gs, const double* p, const int32_t* k,
                              int32_t nq, wtri_result* outs) {
     if (nq < 0) return set_error(WTRI_EINVAL, "nq must be non-negative");

@@ -137,6 +137,10 @@ int sample_edges_device(const wtri_graph* g, int pcode, int64_t nsamples, uint64
 // Weighted wedge sampling (wtri_wedge.cu), p codes P_GEO, P_ONE, P_TWO.
 int wedge_topk_device(const wtri_graph* g, int pcode, int32_t k, int64_t nsamples, uint64_t seed,
                       wtri_tri* d_tris, double* d_weight, int32_t* d_count, cudaStream_t s);
+// Top-k q-cliques (q = 4, 5) on the edges drawn at p (every edge when
+// nsamples < 0); host outputs.
+int clique_topk_host(const wtri_graph* g, int q, int pcode, int32_t k, int64_t nsamples, uint64_t seed,
+                     int32_t* h_ids, double* h_w, uint64_t* h_keys, int32_t* h_count);
 int wedge_draws_host(const wtri_graph* g, int pcode, int64_t nsamples, uint64_t seed, int32_t* center,
                      int32_t* jb, int32_t* jc, int32_t* tri);
 

@@ -652,24 +652,27 @@ inline int pass_shift(int bits, int p) {
 }
 
 // alg_bytes: this pass's share of the sort's algorithmic bytes (the
-// scatter's phase timer; histograms and scans declare none).
+// scatter's phase timer; histograms and scans declare none).  expected:
+// whether the pass is expected to run (a conditional pass that the widest
+// expected keys skip declares no moved bytes either).
 template <class Dig, class Loader, class Storer>
 int run_pass(const Dig& dg, const Loader& ld, const Storer& st, const PassGeom& g, uint32_t* scratch,
-             cudaStream_t s, uint32_t* err, double hist_bytes, double alg_bytes) {
+             cudaStream_t s, uint32_t* err, double hist_bytes, double alg_bytes, bool expected = true) {
+    const double mv = expected ? 1.0 : 0.0;
     if (g.n <= 0) return WTRI_OK;
     uint32_t* counts = scratch;
     uint32_t* totals = scratch + (size_t)MAX_BINS * g.chunks;
     {
-        ProfScope ps("radix_upsweep", s, 0.0, 1, hist_bytes * (double)g.n + 4.0 * g.bins * g.chunks);
+        ProfScope ps("radix_upsweep", s, 0.0, 1, mv * (hist_bytes * (double)g.n + 4.0 * g.bins * g.chunks));
         WTRI_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)g.bins * g.chunks, s));
         k_upsweep<Dig><<<g.chunks * UP_SPLIT, UNT, 0, s>>>(dg, g, counts);
     }
     {
-        ProfScope ps("radix_digit_scan", s, 0.0, 1, 8.0 * g.bins * g.chunks);
+        ProfScope ps("radix_digit_scan", s, 0.0, 1, mv * 8.0 * g.bins * g.chunks);
         k_digit_scan<<<g.bins, NT, 0, s>>>(counts, g.chunks, totals, g);
     }
     const size_t smem = sizeof(ScatterSmem);
-    ProfScope ps("radix_downsweep", s, alg_bytes, 1, (double)g.n * (Loader::REC_BYTES + st.rec_bytes()));
+    ProfScope ps("radix_downsweep", s, alg_bytes, 1, mv * (double)g.n * (Loader::REC_BYTES + st.rec_bytes()));
     if (bulk_enabled() && ld.tma_ok()) {
         static std::atomic<uint64_t> done{0};  // per instantiation and device
         WTRI_TRY(smem_optin((const void*)k_scatter<Loader, Storer, true>, (int)smem, done));
@@ -755,18 +758,19 @@ int lsd_sort_device_width(const First& first, const Last& last, int64_t n, int m
         SwitchStorer<Last> sw{last, as, wmax, shift + MAX_BITS, false};
         AosLoader al{cur};
         StoredDigits sd{dig};
-        const double a = p < expected_passes ? alg : 0.0;
+        const bool ex = p < expected_passes;
+        const double a = ex ? alg : 0.0;
         if (p == 0) {
             KeyDigits<First> kd{first, g.shift, g.mask};
             if (passes == 1) {
-                WTRI_TRY(run_pass(kd, first, last, g, scratch, s, err, 4.0, a));
+                WTRI_TRY(run_pass(kd, first, last, g, scratch, s, err, 4.0, a, ex));
             } else {
-                WTRI_TRY(run_pass(kd, first, sw, g, scratch, s, err, 4.0, a));
+                WTRI_TRY(run_pass(kd, first, sw, g, scratch, s, err, 4.0, a, ex));
             }
         } else if (p == passes - 1) {
-            WTRI_TRY(run_pass(sd, al, last, g, scratch, s, err, 2.0, a));
+            WTRI_TRY(run_pass(sd, al, last, g, scratch, s, err, 2.0, a, ex));
         } else {
-            WTRI_TRY(run_pass(sd, al, sw, g, scratch, s, err, 2.0, a));
+            WTRI_TRY(run_pass(sd, al, sw, g, scratch, s, err, 2.0, a, ex));
         }
         std::swap(cur, nxt);
     }

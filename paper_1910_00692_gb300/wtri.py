@@ -100,6 +100,8 @@ def lib():
     L.wtri_sample_edges.argtypes = [vp, f64, i64, ctypes.c_uint64, vp, i64]
     L.wtri_wedge_topk.argtypes = [vp, f64, i32, i64, ctypes.c_uint64, ctypes.POINTER(_Result)]
     L.wtri_sample_wedges.argtypes = [vp, f64, i64, ctypes.c_uint64, vp, vp, vp, vp]
+    L.wtri_sample_cliques.argtypes = [vp, i32, f64, i32, i64, ctypes.c_uint64, vp, vp, vp,
+                                      ctypes.POINTER(i32)]
     L.wtri_topk_batch.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_Result)]
     L.wtri_topk_shard.argtypes = [vp, f64, i32, i32, i32, ctypes.POINTER(_Result), vp]
     L.wtri_autotune.argtypes = [vp, i32, i32, ctypes.POINTER(_TuneInfo)]
@@ -130,6 +132,7 @@ def lib():
               L.wtri_topk_batch, L.wtri_server_create, L.wtri_server_add_graph, L.wtri_submit,
               L.wtri_poll, L.wtri_poll_timed, L.wtri_server_stats, L.wtri_topk_shard,
               L.wtri_merge_topk, L.wtri_autotune, L.wtri_set_tune, L.wtri_wedge_topk,
+              L.wtri_sample_cliques,
               L.wtri_sample_wedges):
         f.restype = ctypes.c_int
     _lib = L
@@ -301,6 +304,22 @@ def topk_shard(g: Graph, p: float, k: int, shard: int, nshards: int):
                                  keys.ctypes.data_as(ctypes.c_void_p)))
     c = res.count
     return tris[:c].copy(), wts[:c].copy(), keys[:c].copy()
+
+
+def sample_cliques(g: Graph, q: int, p: float, k: int, nsamples: int, seed: int):
+    """wtri_sample_cliques: top-k q-cliques (q = 4, 5) on the edges drawn by
+    edge sampling (nsamples < 0: every edge, the exact top-k).  Returns
+    (cliques (count x q), weights, keys)."""
+    cl = np.zeros((max(k, 1), q), dtype=np.int32)
+    wts = np.zeros(max(k, 1), dtype=np.float64)
+    keys = np.zeros(max(k, 1), dtype=np.uint64)
+    cnt = ctypes.c_int32(0)
+    _check(lib().wtri_sample_cliques(g.handle, int(q), float(p), int(k), int(nsamples),
+                                     ctypes.c_uint64(int(seed) & (2**64 - 1)), cl.ctypes.data_as(ctypes.c_void_p),
+                                     wts.ctypes.data_as(ctypes.c_void_p), keys.ctypes.data_as(ctypes.c_void_p),
+                                     ctypes.byref(cnt)))
+    c = cnt.value
+    return cl[:c].copy(), wts[:c].copy(), keys[:c].copy()
 
 
 def merge_topk(parts, k: int):

@@ -183,6 +183,16 @@ def scaled_mid_graph(n: int, m: int, seed: int = 1, gamma: float = 2.1,
     return Graph(n, u, v, w, name=f"chung-lu n={n} m={m} g={gamma} zipf({s},{cap})")
 
 
+def clique_graph(n: int, m: int, seed: int = 4) -> Graph:
+    """Stand-in for the small, dense clique datasets (Appendix A, Table 3:
+    hundreds to a thousand vertices, thousands to tens of thousands of
+    edges, heavy-tailed co-occurrence counts): Chung-Lu with exponent 2.1 and
+    d_max = n / 2, Zipf(1.7) weights capped at 5e4."""
+    u, v = chung_lu(n, m, 2.1, n / 2.0, seed, substream=(30,))
+    w = zipf_weights(m, 1.7, 50_000, _rng(seed, 31))
+    return Graph(n, u, v, w, name=f"clique chung-lu n={n} m={m} zipf(1.7,5e4)")
+
+
 def batch_graph(g: int, seed: int = 3, n_hi: int = 200_000) -> Graph:
     """Graph ``g`` of the 4,096-graph batch: n log-uniform in [100, n_hi]
     (2e5 for the batch workload), m = 10 n, exponent 2.2, Zipf(2) weights
