@@ -245,6 +245,38 @@ def bench_sampler(wt, g, stream, k):
         d.free()
 
 
+def bench_cliques(wt, k=1000):
+    """Top weighted 4- and 5-cliques (Section 4.5, Appendix A) on the
+    stand-in for the email-Eu dataset of Table 3 (979 vertices, 29,000
+    edges, Zipf(1.7) weights), p = 1 as in Appendix A: the exact top-k on the
+    GPU (every edge), and edge sampling at growing draw counts with its time
+    and accuracy (the fraction of the exact top-k it finds), the measure of
+    Table 4."""
+    import synth
+    g = synth.clique_graph(979, 29_000)
+    d = wt.build_csr(g.n, g.u, g.v, g.w)
+    out = {"graph": {"n": g.n, "m": g.m, "recipe": g.name}, "p": 1, "k": k}
+    try:
+        for q in (4, 5):
+            wt.sample_cliques(d, q, 1.0, k, -1, 0)  # warm-up
+            t0 = time.perf_counter()
+            exact, _, _ = wt.sample_cliques(d, q, 1.0, k, -1, 0)
+            t_exact = time.perf_counter() - t0
+            ref = set(map(tuple, exact.tolist()))
+            runs = []
+            for ns in (1_000, 3_000, 10_000, 30_000):
+                t0 = time.perf_counter()
+                got, _, _ = wt.sample_cliques(d, q, 1.0, k, ns, 5)
+                t_s = time.perf_counter() - t0
+                runs.append({"nsamples": ns, "ms": 1e3 * t_s,
+                             "accuracy": len(ref & set(map(tuple, got.tolist()))) / max(1, len(ref))})
+            out[f"q{q}"] = {"exact_ms": 1e3 * t_exact, "sampled": runs}
+        out["api"] = "wtri_sample_cliques (host results); exact mode = every edge"
+        return out
+    finally:
+        d.free()
+
+
 def bench_batch(wt, stream, count=1024, n_hi=20_000):
     """Batched form: `count` graphs (n log-uniform in [100, n_hi], m = 10 n,
     exponent 2.2, Zipf(2)), per-graph k ~ U[10,1000], p ~ U{-inf,1,2,+inf}:
@@ -319,7 +351,8 @@ def bench_batch_full(wt, count=4096, n_hi=200_000, reps=3):
         # the query schedule autotuned per size bucket in the library
         # (wtri_autotune_buckets: the largest graph of each power-of-two
         # edge-count bucket is tuned, its setting applies to the bucket; the
-        # batched call runs every query with its own graph's schedule)
+        # batched call keeps one round schedule for the whole batch and each
+        # graph's short/long scan boundary)
         t0 = time.perf_counter()
         nb = wt.autotune_buckets(ds, k=1000, reps=2)
         t_tune = time.perf_counter() - t0
@@ -829,9 +862,10 @@ def run_step_workload(args, world, rank, local):
         del hu, hv, hw, hub, hvb, hwb
 
     # ---- weighted edge sampling (Algorithm 3) and the mid extras -----------
-    samp = batch = serve = None
+    samp = batch = serve = cliques = None
     if rank == 0 and not args.no_extras and args.workload in ("mid", "large"):
         samp = bench_sampler(wt, g, stream, k)
+        cliques = bench_cliques(wt)
         if not large:
             batch = bench_batch(wt, stream)
             serve = bench_serve(wt, g)
@@ -858,6 +892,14 @@ def run_step_workload(args, world, rank, local):
                "sample": (f"one brute-force top-{k} query at p = 1 on {desc}, oracle CSR build "
                           f"included, {t_q:.2f} s; value = sampled edges / that time"),
                "dhl": dhl}
+        if cliques:
+            # the oracle's brute force on the clique graph, beside the GPU's exact mode
+            import synth
+            gc = synth.clique_graph(979, 29_000)
+            for q in (4, 5):
+                t0 = time.perf_counter()
+                oracle.clique_topk(gc.n, gc.u, gc.v, gc.w, q, 1.0, k)
+                cpu[f"cliques_q{q}_s"] = time.perf_counter() - t0
 
     if rank == 0:
         line = {
@@ -877,7 +919,7 @@ def run_step_workload(args, world, rank, local):
             "query_ms": {k_: v["ms"] for k_, v in queries.items()}, "queries": queries,
             "phase_ms_per_step": step_ms_parts, "step_hbm": step_hbm,
             "tune": tune, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "sampler": samp, "batch": batch, "serve": serve,
+            "sampler": samp, "cliques": cliques, "batch": batch, "serve": serve,
             "gpu_launches": int(launches), "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -276,8 +276,9 @@ WTRI_API int wtri_server_set_option(wtri_server* s, int option, int64_t value);
  * 1024}, growth in {4, 8, 16}, t_short in {8, 16, 32, 64, 128}) on the
  * graph itself with CUDA events — one exact top-k query at each of
  * p = -inf, 1, 2, +inf, median of `reps` — and keeps the fastest for every
- * later query on that graph (single, device, sampled and batched queries
- * read it; results do not depend on it).  Not thread-safe against queries
+ * later query on that graph (single, device and sampled queries read it;
+ * a batched query reads its t_short, the batch keeping one round schedule,
+ * the defaults, for all its queries; results do not depend on it).  Not thread-safe against queries
  * running on the same graph.  wtri_set_tune sets the values directly.
  */
 typedef struct {
@@ -295,8 +296,9 @@ WTRI_API int wtri_autotune(wtri_graph* g, int32_t k, int32_t reps, wtri_tune_inf
  * Tuning for a collection of graphs (e.g. the graphs of a batch): graphs
  * are grouped by size (the bit length of their edge count); the largest
  * graph of each group is tuned with wtri_autotune and its setting applied
- * to every graph of the group.  The batched call runs each query with its
- * own graph's schedule, so one batch mixes the settings of all its groups.
+ * to every graph of the group.  In a batched call each query takes its
+ * own graph's t_short (the short/long scan boundary), so one batch mixes
+ * the boundaries of all its groups; the rounds are the batch's own.
  * *buckets_tuned (may be NULL) receives the number of groups.
  */
 WTRI_API int wtri_autotune_buckets(wtri_graph* const* gs, int32_t ngraphs, int32_t k, int32_t reps,

@@ -234,18 +234,19 @@ BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes,
         P->caps[(size_t)i] = batch_query_cap(ks[i], gs[i]->d.m);
         P->cand_total += P->caps[(size_t)i];
     }
-    // Round schedules: each query follows its own graph's schedule (first
-    // round, growth: the graph's tune, as a single query would); round r of
-    // the batch runs round r of every query (empty once a query's schedule
-    // has covered its edges).
+    // Round schedule: one for the whole batch, the library default (first
+    // round, growth), since every batch round costs a launch sequence and a
+    // select over all queries and the smallest growth would set the round
+    // count of all; each query keeps its own graph's short/long boundary
+    // (t_short).  Round r of the batch runs round r of every query (empty
+    // once a query's schedule has covered its edges).
     (void)mmax;
+    const Tune def;
     int R = 0;
     std::vector<std::vector<int64_t>> his((size_t)nq);
     for (int i = 0; i < nq; i++) {
         const int64_t m = gs[i]->d.m;
-        const int64_t first = std::max<int64_t>(1, gs[i]->tune.first_round);
-        const int64_t growth = std::max<int32_t>(2, gs[i]->tune.growth);
-        for (int64_t lo = 0, size = first; lo < m; lo += size, size *= growth)
+        for (int64_t lo = 0, size = def.first_round; lo < m; lo += size, size *= def.growth)
             his[(size_t)i].push_back(std::min(m, lo + size));
         R = std::max<int>(R, (int)his[(size_t)i].size());
     }
