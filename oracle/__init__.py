@@ -96,6 +96,10 @@ def lib():
                                ctypes.c_int64, ctypes.c_double, i32p, u64p, f64p, I64P, i64p]
         L.dhl_alpha.argtypes = [ctypes.c_int, ctypes.c_double]
         L.dhl_alpha.restype = ctypes.c_double
+        f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+        L.or_topk_real.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, f32p, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_int64, i32p, u64p, f64p, I64P, I64P]
+        L.or_topk_real.restype = ctypes.c_int
         L.or_clique_topk.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, i32p, u64p, f64p,
                                      I64P, I64P]
@@ -433,3 +437,24 @@ def sampled_edge_flags(w, p, nsamples, seed):
     flags = np.zeros(len(w), np.uint8)
     flags[perm[hits > 0]] = 1
     return flags
+
+
+def topk_real(n, u, v, w, p, k):
+    """Top-k triangles of a graph with positive finite fp32 weights (Eq. 1
+    over reals), ranked by the fp64 mean.  Returns dict(tri, key, value,
+    count, ntri) like topk()."""
+    u, v = _arr(u), _arr(v)
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    k = int(k)
+    tri = np.zeros(max(k, 1) * 3, np.int32)
+    key = np.zeros(max(k, 1), np.uint64)
+    val = np.zeros(max(k, 1), np.float64)
+    cnt = ctypes.c_int64(0)
+    nt = ctypes.c_int64(0)
+    rc = lib().or_topk_real(n, u.shape[0], u, v, w, pcode(p), float(p), k, tri, key, val,
+                            ctypes.byref(cnt), ctypes.byref(nt))
+    if rc != 0:
+        raise OracleError(f"or_topk_real failed (rc={rc})")
+    c = cnt.value
+    return {"tri": tri[:3 * c].reshape(-1, 3), "key": key[:c], "value": val[:c], "count": c,
+            "ntri": nt.value}

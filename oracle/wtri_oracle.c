@@ -1246,3 +1246,110 @@ int or_clique_topk(int32_t n, int64_t m, const int32_t* u, const int32_t* v, con
     free(eid);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Real (fp32) edge weights: Eq. 1 over positive reals.                       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * m_p of three positive fp32 weights, in fp64: min, max (p = -inf, +inf),
+ * (a+b+c)/3 (p = 1), sqrt((a^2+b^2+c^2)/3) (p = 2), cbrt(a*b*c) (p = 0), and
+ * Eq. 1 with the largest (p > 0) or smallest (p < 0) weight factored out for
+ * any other finite p.  The weights are taken in ascending order.
+ */
+static double real_mean(int pcode, double p, float fa, float fb, float fc) {
+    double t3[3] = {fa, fb, fc}, x;
+    if (t3[0] > t3[1]) { x = t3[0]; t3[0] = t3[1]; t3[1] = x; }
+    if (t3[1] > t3[2]) { x = t3[1]; t3[1] = t3[2]; t3[2] = x; }
+    if (t3[0] > t3[1]) { x = t3[0]; t3[0] = t3[1]; t3[1] = x; }
+    switch (pcode) {
+        case 0: return t3[0];
+        case 3: return t3[2];
+        case 1: return (t3[0] + t3[1] + t3[2]) / 3.0;
+        case 2: return sqrt((t3[0] * t3[0] + t3[1] * t3[1] + t3[2] * t3[2]) / 3.0);
+        case 4: return cbrt(t3[0] * t3[1] * t3[2]);
+        default: {
+            const double s = p > 0 ? t3[2] : t3[0];
+            const double t = (pow(t3[0] / s, p) + pow(t3[1] / s, p) + pow(t3[2] / s, p)) / 3.0;
+            return s * pow(t, 1.0 / p);
+        }
+    }
+}
+
+/*
+ * Top-k triangles of a graph with positive finite fp32 weights (Eq. 1 over
+ * reals), p code as or_topk (general p: preal).  The key is the fp64 mean's
+ * bit pattern (positive doubles order like their values).  Every triangle
+ * {a < b < c} is enumerated once from the id-sorted rows, then all are
+ * sorted by (key desc, triple asc).  Weights are checked: a non-finite or
+ * non-positive weight is OR_EINVAL.
+ */
+int or_topk_real(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const float* w, int pcode,
+                 double preal, int64_t k, int32_t* tri, uint64_t* key, double* value, int64_t* count,
+                 int64_t* ntri) {
+    *count = 0;
+    *ntri = 0;
+    if (pcode < 0 || pcode > OR_PCODE_MAX || k <= 0) return OR_EINVAL;
+    if (pcode == 5 && !(isfinite(preal) && preal != 0.0 && preal != 1.0 && preal != 2.0)) return OR_EINVAL;
+    int32_t* bits = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    int64_t* rowptr = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    int32_t* col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
+    int32_t* wt = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
+    int64_t* eid = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * m + 1));
+    int rc = (bits && rowptr && col && wt && eid) ? OR_OK : OR_ENOMEM;
+    for (int64_t i = 0; i < m && rc == OR_OK; i++) {
+        if (!(isfinite(w[i]) && w[i] > 0.0f)) rc = OR_EINVAL;
+        memcpy(&bits[i], &w[i], 4); /* positive: a positive int32 */
+    }
+    if (rc == OR_OK) rc = or_sym_csr(n, m, u, v, bits, rowptr, col, wt, eid);
+    int64_t cap = 1024, len = 0;
+    or_tri* all = rc == OR_OK ? (or_tri*)malloc(sizeof(or_tri) * (size_t)cap) : NULL;
+    if (rc == OR_OK && !all) rc = OR_ENOMEM;
+    for (int32_t a = 0; a < n && rc == OR_OK; a++)
+        for (int64_t i = rowptr[a]; i < rowptr[a + 1] && rc == OR_OK; i++) {
+            const int32_t b = col[i];
+            if (b <= a) continue;
+            for (int64_t j = i + 1; j < rowptr[a + 1]; j++) {
+                const int32_t c = col[j];  /* c > b: the row is id-sorted */
+                const int64_t pbc = row_find(rowptr, col, b, c);
+                if (pbc < 0) continue;
+                float fab, fac, fbc;
+                memcpy(&fab, &wt[i], 4);
+                memcpy(&fac, &wt[j], 4);
+                memcpy(&fbc, &wt[pbc], 4);
+                const double mp = real_mean(pcode, preal, fab, fac, fbc);
+                if (len == cap) {
+                    or_tri* grown = (or_tri*)realloc(all, sizeof(or_tri) * (size_t)(2 * cap));
+                    if (!grown) {
+                        rc = OR_ENOMEM;
+                        break;
+                    }
+                    all = grown;
+                    cap *= 2;
+                }
+                memcpy(&all[len].key, &mp, 8);
+                all[len].t[0] = a;
+                all[len].t[1] = b;
+                all[len].t[2] = c;
+                len++;
+            }
+        }
+    if (rc == OR_OK) {
+        qsort(all, (size_t)len, sizeof(or_tri), cmp_tri);
+        const int64_t out = len < k ? len : k;
+        for (int64_t i = 0; i < out; i++) {
+            for (int t = 0; t < 3; t++) tri[3 * i + t] = all[i].t[t];
+            key[i] = all[i].key;
+            memcpy(&value[i], &all[i].key, 8);
+        }
+        *count = out;
+        *ntri = len;
+    }
+    free(all);
+    free(bits);
+    free(rowptr);
+    free(col);
+    free(wt);
+    free(eid);
+    return rc;
+}
