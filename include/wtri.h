@@ -115,6 +115,22 @@ WTRI_API int wtri_build_csr(int32_t n, int64_t m, const int32_t* u, const int32_
                             const int32_t* w, int on_device, void* cuda_stream,
                             wtri_graph** out);
 
+/*
+ * The same build for real weights (Eq. 1 over positive reals): w holds m
+ * positive finite fp32 values (WTRI_EINVAL for zero, negative, infinite or
+ * NaN weights).  Positive floats order like their bit patterns, so the
+ * graph keeps the bits and the edge order is weight descending as above.
+ * Queries on such a graph rank p = -inf and +inf by the exact min / max and
+ * every other finite p (0 included: the geometric mean) by the fp64 mean,
+ * with the set-equality rule of the fp64 keys (two means closer than fp64
+ * rounding may rank either way).  wtri_graph_info's max_weight is then the
+ * largest weight's bit pattern.  The samplers, the batched call and the
+ * server take integer weights only (WTRI_EUNSUPPORTED).
+ */
+WTRI_API int wtri_build_csr_f32(int32_t n, int64_t m, const int32_t* u, const int32_t* v,
+                                const float* w, int on_device, void* cuda_stream,
+                                wtri_graph** out);
+
 /* Frees the graph's device memory.  NULL is a no-op. */
 WTRI_API void wtri_graph_free(wtri_graph* g);
 

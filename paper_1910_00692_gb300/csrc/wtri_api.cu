@@ -41,8 +41,18 @@ int p_to_code(double p, int* code) {
 
 int p_to_code_for(double p, const wtri_graph* g, int* code) {
     WTRI_TRY(p_to_code(p, code));
+    if (g && g->d.fw) {  // real weights: every finite p ranks by the fp64 mean
+        if (*code == P_ONE || *code == P_TWO || *code == P_GEO) *code = P_GEN;
+        return WTRI_OK;
+    }
     if (*code == P_GEO && g && g->d.wmax > GEO_WMAX)
         return set_error(WTRI_EUNSUPPORTED, "p = 0 needs weights below 2^21 (exact product key)");
+    return WTRI_OK;
+}
+
+int need_integer_weights(const wtri_graph* g, const char* what) {
+    if (g && g->d.fw)
+        return set_error(WTRI_EUNSUPPORTED, std::string(what) + " takes integer weights (exact w^p or keys)");
     return WTRI_OK;
 }
 
@@ -153,6 +163,16 @@ WTRI_API int wtri_build_csr(int32_t n, int64_t m, const int32_t* u, const int32_
     *out = nullptr;
     t_last_error.clear();
     return build_graph(n, m, u, v, w, on_device, (cudaStream_t)cuda_stream, out);
+}
+
+WTRI_API int wtri_build_csr_f32(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const float* w,
+                                int on_device, void* cuda_stream, wtri_graph** out) {
+    if (!out) return set_error(WTRI_EINVAL, "out is NULL");
+    *out = nullptr;
+    t_last_error.clear();
+    // positive floats order like their bit patterns: the build sorts the bits
+    return build_graph(n, m, u, v, reinterpret_cast<const int32_t*>(w), on_device,
+                       (cudaStream_t)cuda_stream, out, 1);
 }
 
 WTRI_API void wtri_graph_free(wtri_graph* g) {
@@ -402,6 +422,7 @@ WTRI_API int wtri_sample_topk(const wtri_graph* g, double p, int32_t k, int64_t 
     int code = 0;
     WTRI_TRY(check_query(g, k));
     WTRI_TRY(p_to_code_for(p, g, &code));
+    WTRI_TRY(need_integer_weights(g, "edge sampling"));
     if (code != P_ONE && code != P_TWO && code != P_GEO)
         return set_error(WTRI_EUNSUPPORTED, "edge sampling needs p = 0, 1 or 2 (exact integer w^p)");
     if (nsamples < 0) return set_error(WTRI_EINVAL, "nsamples must be non-negative");
@@ -423,6 +444,7 @@ WTRI_API int wtri_wedge_topk(const wtri_graph* g, double p, int32_t k, int64_t n
     int code = 0;
     WTRI_TRY(check_query(g, k));
     WTRI_TRY(p_to_code_for(p, g, &code));
+    WTRI_TRY(need_integer_weights(g, "wedge sampling"));
     if (code != P_ONE && code != P_TWO && code != P_GEO)
         return set_error(WTRI_EUNSUPPORTED, "wedge sampling needs p = 0, 1 or 2 (exact integer w^p)");
     if (nsamples < 0) return set_error(WTRI_EINVAL, "nsamples must be non-negative");
@@ -442,6 +464,7 @@ WTRI_API int wtri_sample_wedges(const wtri_graph* g, double p, int64_t nsamples,
     if (!g) return set_error(WTRI_EINVAL, "graph is NULL");
     int code = 0;
     WTRI_TRY(p_to_code_for(p, g, &code));
+    WTRI_TRY(need_integer_weights(g, "wedge sampling"));
     if (code != P_ONE && code != P_TWO && code != P_GEO)
         return set_error(WTRI_EUNSUPPORTED, "wedge sampling needs p = 0, 1 or 2 (exact integer w^p)");
     if (nsamples < 0) return set_error(WTRI_EINVAL, "nsamples must be non-negative");
@@ -467,6 +490,7 @@ WTRI_API int wtri_sample_cliques(const wtri_graph* g, int32_t q, double p, int32
     if (!cliques || !weights || !count) return set_error(WTRI_EINVAL, "output arrays are NULL");
     int code = 0;
     WTRI_TRY(p_to_code(p, &code));
+    WTRI_TRY(need_integer_weights(g, "clique sampling"));
     if (code != P_MIN && code != P_ONE && code != P_TWO && code != P_MAX)
         return set_error(WTRI_EUNSUPPORTED, "cliques rank at p in {-inf, 1, 2, +inf}");
     if (nsamples >= 0 && code != P_ONE && code != P_TWO)
@@ -491,6 +515,7 @@ WTRI_API int wtri_topk_batch(const wtri_graph* const* gs, const double* p, const
         if (gs[i]->device != dev) return set_error(WTRI_EINVAL, "batch graphs on different devices");
         int c = 0;
         int rc = p_to_code_for(p[i], gs[i], &c);
+        if (rc == WTRI_OK) rc = need_integer_weights(gs[i], "the batched call");
         if (rc != WTRI_OK) return rc;
         if (c == P_GEN)
             return set_error(WTRI_EUNSUPPORTED,
@@ -509,6 +534,7 @@ WTRI_API int wtri_sample_edges(const wtri_graph* g, double p, int64_t nsamples, 
     if (!g) return set_error(WTRI_EINVAL, "graph is NULL");
     int code = 0;
     WTRI_TRY(p_to_code(p, &code));
+    WTRI_TRY(need_integer_weights(g, "edge sampling"));
     if (code != P_ONE && code != P_TWO && code != P_GEO)
         return set_error(WTRI_EUNSUPPORTED, "edge sampling needs p = 0, 1 or 2 (exact integer w^p)");
     if (nsamples < 0) return set_error(WTRI_EINVAL, "nsamples must be non-negative");

@@ -342,6 +342,7 @@ int batch_plan_launch(BatchPlan* P, void* dbuf, cudaStream_t s, int use_graph) {
         q.t_short = P->tshort[(size_t)i];
         q.qbytes = nullptr;
         q.gp = 0.0;  // batched queries take the exact-key p values only
+        q.fw = 0;    // and integer weights
         q.wait_first = WAIT_LIMIT;
         c0 += P->caps[(size_t)i];
     }

@@ -47,9 +47,11 @@ struct BuildStatus {
                                    // pair, the smallest x << 32 | c of its oriented row
 };
 
+// Float weights (fw): positive finite fp32 values, whose bit patterns are
+// the positive int32 below 0x7f800000 (+inf; NaN lies above it).
 __global__ void k_validate(int32_t n, int64_t m, const int32_t* __restrict__ u,
                            const int32_t* __restrict__ v, const int32_t* __restrict__ w,
-                           BuildStatus* st) {
+                           int fw, BuildStatus* st) {
     int32_t wloc = 0;
     uint32_t eloc = 0;
     unsigned long long bad = ~0ull;
@@ -59,7 +61,7 @@ __global__ void k_validate(int32_t n, int64_t m, const int32_t* __restrict__ u,
         uint32_t e = 0;
         if (a < 0 || a >= n || b < 0 || b >= n) e |= DEV_ERR_RANGE;
         else if (a == b) e |= DEV_ERR_SELF_LOOP;
-        if (x <= 0) e |= DEV_ERR_WEIGHT;
+        if (x <= 0 || (fw && x >= 0x7f800000)) e |= DEV_ERR_WEIGHT;
         if (e) {
             eloc |= e;
             if ((unsigned long long)i < bad) bad = (unsigned long long)i;
@@ -400,7 +402,7 @@ int sort_rows(const rows::RowsOut& R, unsigned long long* g0, unsigned long long
 }  // namespace
 
 int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
-                const int32_t* w_in, int on_device, cudaStream_t s, wtri_graph** out) {
+                const int32_t* w_in, int on_device, cudaStream_t s, wtri_graph** out, int fw) {
     *out = nullptr;
     if (n <= 0) return set_error(WTRI_EINVAL, "n must be positive");
     if (m < 0) return set_error(WTRI_EINVAL, "m must be non-negative");
@@ -481,10 +483,11 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     // 1. validation + max weight
     if (m > 0) {
         ProfScope ps("validate", s, 12.0 * m, 1);  // the COO input, read once
-        k_validate<<<grid_for(m), BLK, 0, s>>>(n, m, u, v, w, d_st);
+        k_validate<<<grid_for(m), BLK, 0, s>>>(n, m, u, v, w, fw, d_st);
     }
     g->d.n = n;
     g->d.m = m;
+    g->d.fw = fw;
     g->d.wmax = 0;
     g->d.maxdeg = 0;
 
@@ -595,7 +598,8 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     if (h_st.err & (DEV_ERR_RANGE | DEV_ERR_SELF_LOOP | DEV_ERR_WEIGHT)) {
         std::string what = (h_st.err & DEV_ERR_RANGE) ? "vertex id outside [0, n)"
                            : (h_st.err & DEV_ERR_SELF_LOOP) ? "self-loop"
-                                                            : "non-positive weight";
+                                                            : (fw ? "weight not a positive finite float"
+                                                                  : "non-positive weight");
         return fail(set_error(WTRI_EINVAL, "invalid edge " + std::to_string(h_st.first_bad) +
                                                ": " + what));
     }

@@ -56,6 +56,8 @@ constexpr int32_t GEO_WMAX = (1 << 21) - 1;
 int p_to_code(double p, int* code);  // any finite p (general p -> P_GEN)
 // p_to_code, and p = 0 only for graphs whose weights keep the product key exact.
 int p_to_code_for(double p, const wtri_graph* g, int* code);
+// WTRI_EUNSUPPORTED for a float-weight graph: `what` needs integer weights.
+int need_integer_weights(const wtri_graph* g, const char* what);
 
 // ---------------------------------------------------------------------------
 // Device-resident graph (all arrays library-owned device memory).
@@ -77,6 +79,7 @@ struct DevGraph {
     int64_t m;
     int32_t wmax;
     int32_t maxdeg;
+    int32_t fw;  // weights are positive fp32 bit patterns (1) or integers (0)
     const int64_t* rowptr;
     const int64_t* orowptr;
     const int32_t* ord_u;
@@ -116,8 +119,9 @@ struct wtri_graph {
 namespace wtri {
 
 // Build (wtri_build.cu).
+// fw: w holds positive fp32 values (their bit patterns), else integers.
 int build_graph(int32_t n, int64_t m, const int32_t* u, const int32_t* v, const int32_t* w,
-                int on_device, cudaStream_t stream, wtri_graph** out);
+                int on_device, cudaStream_t stream, wtri_graph** out, int fw = 0);
 
 // Exact top-k (wtri_topk.cu).  Writes device outputs; status (count or a
 // negative code) to d_count.  'retry_scale' enlarges the scratch buffers.

@@ -103,6 +103,9 @@ struct Query {
     unsigned long long* qbytes;
     // The value of p for P_GEN queries.
     double gp;
+    // Weights are positive fp32 bit patterns (a float-weight graph), not
+    // integers: the means and reported values read them as floats.
+    int32_t fw;
     // Polls of the first wait for a staged row (WAIT_LIMIT in production;
     // tests lower it to take the timeout path).
     uint32_t wait_first;
@@ -146,13 +149,18 @@ __device__ __forceinline__ bool owns(const Query& q, int32_t r, int32_t rxc, int
 // ascending order (equal multisets give equal bits), scaled by the largest
 // (p > 0) or the smallest (p < 0) so that no power overflows:
 //   m_p = s * (((a/s)^p + (b/s)^p + (c/s)^p) / 3)^(1/p).
-__device__ __forceinline__ double general_mean(double p, uint32_t a, uint32_t b, uint32_t c) {
+__device__ __forceinline__ double general_mean(double p, uint32_t a, uint32_t b, uint32_t c, bool fw = false) {
     uint32_t t;
     if (a > b) { t = a; a = b; b = t; }
     if (b > c) { t = b; b = c; c = t; }
     if (a > b) { t = a; a = b; b = t; }
-    const double s = p > 0 ? (double)c : (double)a;
-    const double m = (pow((double)a / s, p) + pow((double)b / s, p) + pow((double)c / s, p)) / 3.0;
+    // positive fp32 bit patterns order like their values, so the sort holds
+    const double x = fw ? (double)__uint_as_float(a) : (double)a;
+    const double y = fw ? (double)__uint_as_float(b) : (double)b;
+    const double z = fw ? (double)__uint_as_float(c) : (double)c;
+    if (p == 0.0) return cbrt(x * y * z);  // the geometric mean (real weights only)
+    const double s = p > 0 ? z : x;
+    const double m = (pow(x / s, p) + pow(y / s, p) + pow(z / s, p)) / 3.0;
     return s * pow(m, 1.0 / p);
 }
 
@@ -160,13 +168,13 @@ __device__ __forceinline__ double general_mean(double p, uint32_t a, uint32_t b,
 // p in {-inf, 0, 1, 2, +inf}; the mean's fp64 bit pattern for P_GEN.
 template <int P>
 __device__ __forceinline__ unsigned long long keyof(uint32_t a, uint32_t b, uint32_t c,
-                                                    double gp = 0.0) {
+                                                    double gp = 0.0, bool fw = false) {
     if (P == P_ONE) return (unsigned long long)a + b + c;
     if (P == P_TWO)
         return (unsigned long long)a * a + (unsigned long long)b * b + (unsigned long long)c * c;
     if (P == P_MAX) return (unsigned long long)max(a, max(b, c));
     if (P == P_GEO) return (unsigned long long)a * b * c;  // weights < 2^21: below 2^63
-    if (P == P_GEN) return (unsigned long long)__double_as_longlong(general_mean(gp, a, b, c));
+    if (P == P_GEN) return (unsigned long long)__double_as_longlong(general_mean(gp, a, b, c, fw));
     return (unsigned long long)min(a, min(b, c));
 }
 
@@ -176,9 +184,9 @@ __device__ __forceinline__ unsigned long long keyof(uint32_t a, uint32_t b, uint
 // for smaller ones.
 template <int P>
 __device__ __forceinline__ unsigned long long boundof(uint32_t a, uint32_t b, uint32_t c,
-                                                      double gp = 0.0) {
+                                                      double gp = 0.0, bool fw = false) {
     if (P == P_GEN)
-        return (unsigned long long)__double_as_longlong(general_mean(gp, a, b, c) * (1.0 + 1e-12));
+        return (unsigned long long)__double_as_longlong(general_mean(gp, a, b, c, fw) * (1.0 + 1e-12));
     return keyof<P>(a, b, c);
 }
 
@@ -280,7 +288,7 @@ __device__ __forceinline__ void scan_wedges(const DevGraph& G, const Query& q,
     for (; j < jstop; j++) {
         const uint32_t wxc = (uint32_t)__ldg(G.wwt + j);
         tb.add(4);
-        if (boundof<P>(w, wxc, ymax, q.gp) < tau) {  // wedge bound, non-increasing along the list
+        if (boundof<P>(w, wxc, ymax, q.gp, q.fw != 0) < tau) {  // wedge bound, non-increasing along the list
             done = true;
             return;
         }
@@ -290,7 +298,7 @@ __device__ __forceinline__ void scan_wedges(const DevGraph& G, const Query& q,
         int32_t wyc, ryc;
         if (probe_oriented(G, y, dy, c, wyc, ryc, tb) &&
             (tb.add(4), owns<SAMPLED>(q, r, __ldg(G.wrk + j), ryc))) {
-            const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc, q.gp);
+            const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc, q.gp, q.fw != 0);
             if (key >= tau) {
                 int32_t a = x, b = y, cc = c;
                 sort3(a, b, cc);
@@ -308,7 +316,7 @@ __device__ __forceinline__ bool process_edge(const DevGraph& G, const Query& q,
     const int32_t r = SAMPLED ? __ldg(q.slist + idx) : idx;
     const uint32_t w = (uint32_t)__ldg(G.ord_w + r);
     tb.add(4);
-    if (!SAMPLED && boundof<P>(w, w, w, q.gp) < tau) {
+    if (!SAMPLED && boundof<P>(w, w, w, q.gp, q.fw != 0) < tau) {
         // every later edge has a bound no larger: record the first such edge
         atomicMax(&q.st->stop_rev, STOP_NONE - (uint32_t)r);
         return false;
@@ -327,7 +335,7 @@ __device__ __forceinline__ bool process_edge(const DevGraph& G, const Query& q,
     if (su >= eu || sv >= ev) return true;  // no edge after r on one side: owns nothing
     const uint32_t umax = (uint32_t)__ldg(G.wwt + su), vmax = (uint32_t)__ldg(G.wwt + sv);
     tb.add(8);
-    if (boundof<P>(w, umax, vmax, q.gp) < tau) return true;  // edge bound
+    if (boundof<P>(w, umax, vmax, q.gp, q.fw != 0) < tau) return true;  // edge bound
     // Scan the shorter suffix; probe the other endpoint.
     const bool xu = (eu - su) <= (ev - sv);
     const int32_t x = xu ? u : v, y = xu ? v : u;
@@ -560,7 +568,7 @@ __device__ __forceinline__ void long_scan(const DevGraph& G, const Query& q, uns
         if (j < item.j1) {
             wxc = (uint32_t)__ldg(G.wwt + j);
             tb.add(4);
-            live = boundof<P>(w, wxc, ymax, q.gp) >= tau;
+            live = boundof<P>(w, wxc, ymax, q.gp, q.fw != 0) >= tau;
         }
         if (__ballot_sync(0xffffffffu, live) == 0) break;
         int32_t c = 0;
@@ -593,7 +601,7 @@ __device__ __forceinline__ void long_scan(const DevGraph& G, const Query& q, uns
                 found = search_oriented(G, c, y, wyc, ryc, tb);
             }
             if (found && (tb.add(4), owns<SAMPLED>(q, r, __ldg(G.wrk + j), ryc))) {
-                const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc, q.gp);
+                const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc, q.gp, q.fw != 0);
                 if (key >= tau) {
                     int32_t a = x, b = y, cc = c;
                     sort3(a, b, cc);
@@ -977,7 +985,7 @@ __device__ __forceinline__ void rank_one(const Query& q, uint32_t i, wtri_tri* o
         else if (P == P_TWO) val = sqrt((double)ki / 3.0);
         else if (P == P_GEO) val = cbrt((double)ki);
         else if (P == P_GEN) val = __longlong_as_double((long long)ki);
-        else val = (double)ki;
+        else val = q.fw ? (double)__uint_as_float((uint32_t)ki) : (double)ki;  // min, max
         out_w[rank] = val;
         if (out_key) out_key[rank] = ki;
     }

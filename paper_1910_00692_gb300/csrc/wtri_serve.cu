@@ -317,6 +317,7 @@ WTRI_API int wtri_server_add_graph(wtri_server* S, wtri_graph* g, int32_t* graph
     if (!S || !g || !graph_id) return set_error(WTRI_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(S->mu);
     if (g->device != S->device) return set_error(WTRI_EINVAL, "graph on another device");
+    WTRI_TRY(need_integer_weights(g, "the server"));
     if (S->graph_bytes + (uint64_t)g->bytes > S->budget)
         return set_error(WTRI_ENOMEM, "graph does not fit the server's HBM budget");
     S->graph_bytes += (uint64_t)g->bytes;

@@ -51,6 +51,7 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
     q.t_short = g->tune.t_short;
     q.qbytes = query_bytes_on() ? query_bytes_counter() : nullptr;
     q.gp = gp;
+    q.fw = g->d.fw;
     q.wait_first = stage_wait_limit();
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
 
@@ -330,6 +331,7 @@ int run_sample(const wtri_graph* g, int32_t k, int64_t nsamples, uint64_t seed, 
     q.t_short = g->tune.t_short;
     q.qbytes = nullptr;
     q.gp = 0.0;
+    q.fw = 0;
     q.wait_first = stage_wait_limit();
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
     ProfScope whole(P == P_ONE ? "sample_p=1" : (P == P_TWO ? "sample_p=2" : "sample_p=0"), s, 0.0, 0);
@@ -477,6 +479,7 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
     q.t_short = g->tune.t_short;
     q.qbytes = nullptr;
     q.gp = gp;
+    q.fw = g->d.fw;
     q.wait_first = stage_wait_limit();
     // The array keeps the previous call's contents: reset the status word
     // (counters, threshold, stop flag, error bits).

@@ -434,6 +434,7 @@ int run_wedge_topk(const wtri_graph* g, int32_t k, int64_t nsamples, uint64_t se
     q.t_short = g->tune.t_short;
     q.qbytes = nullptr;
     q.gp = 0.0;
+    q.fw = 0;
     q.wait_first = WAIT_LIMIT;
     WTRI_CUDA(cudaMemsetAsync(q.st, 0, sizeof(QState), s));
     WTRI_CUDA(cudaMemsetAsync(W.err, 0, 4, s));

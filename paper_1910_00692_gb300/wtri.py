@@ -88,6 +88,7 @@ def lib():
         raise WtriUnavailable(str(e)) from e
     vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
     L.wtri_build_csr.argtypes = [i32, i64, vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)]
+    L.wtri_build_csr_f32.argtypes = [i32, i64, vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)]
     L.wtri_graph_free.argtypes = [vp]
     L.wtri_graph_free.restype = None
     L.wtri_graph_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32),
@@ -126,7 +127,7 @@ def lib():
     L.wtri_last_error.restype = ctypes.c_char_p
     L.wtri_last_error.argtypes = []
     L.wtri_version.restype = ctypes.c_char_p
-    for f in (L.wtri_build_csr, L.wtri_graph_info, L.wtri_topk, L.wtri_topk_device,
+    for f in (L.wtri_build_csr, L.wtri_build_csr_f32, L.wtri_graph_info, L.wtri_topk, L.wtri_topk_device,
               L.wtri_topk_device_noalloc,
               L.wtri_sample_topk, L.wtri_graph_copy_array, L.wtri_sample_edges,
               L.wtri_topk_batch, L.wtri_server_create, L.wtri_server_add_graph, L.wtri_submit,
@@ -213,26 +214,30 @@ class Graph:
 
 
 def build_csr(n: int, u, v, w, stream=None) -> Graph:
-    """u, v, w: int32 numpy arrays (host) or int32 torch CUDA tensors (device)."""
+    """u, v: int32; w: int32 (wtri_build_csr) or float32 (wtri_build_csr_f32,
+    real weights).  numpy arrays (host) or torch CUDA tensors (device)."""
     on_device = 0
     keep = []
+    real = str(getattr(w, "dtype", "")) in ("float32", "torch.float32")
     if hasattr(u, "is_cuda") and u.is_cuda:
-        for t in (u, v, w):
-            if not (hasattr(t, "is_cuda") and t.is_cuda) or str(t.dtype) != "torch.int32":
-                raise TypeError("device inputs must all be int32 CUDA tensors")
+        for t, want in ((u, "torch.int32"), (v, "torch.int32"),
+                        (w, "torch.float32" if real else "torch.int32")):
+            if not (hasattr(t, "is_cuda") and t.is_cuda) or str(t.dtype) != want:
+                raise TypeError("device inputs must be CUDA tensors: int32 ids, int32 or float32 weights")
             if not t.is_contiguous():
                 raise TypeError("device inputs must be contiguous")
         ptrs = [_dev_ptr(t) for t in (u, v, w)]
         m = int(u.shape[0])
         on_device = 1
     else:
-        arrs = [np.ascontiguousarray(x, dtype=np.int32) for x in (u, v, w)]
+        arrs = [np.ascontiguousarray(u, dtype=np.int32), np.ascontiguousarray(v, dtype=np.int32),
+                np.ascontiguousarray(w, dtype=np.float32 if real else np.int32)]
         keep = arrs
         ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in arrs]
         m = int(arrs[0].shape[0])
     h = ctypes.c_void_p()
-    rc = lib().wtri_build_csr(int(n), m, ptrs[0], ptrs[1], ptrs[2], on_device,
-                              _stream_ptr(stream), ctypes.byref(h))
+    build = lib().wtri_build_csr_f32 if real else lib().wtri_build_csr
+    rc = build(int(n), m, ptrs[0], ptrs[1], ptrs[2], on_device, _stream_ptr(stream), ctypes.byref(h))
     del keep
     _check(rc)
     return Graph(h.value)
