@@ -17,6 +17,13 @@
 
 #include <vector>
 
+#ifndef WTRI_BATCH_FIRST
+#define WTRI_BATCH_FIRST 64  // first round of a batched query (edges)
+#endif
+#ifndef WTRI_BATCH_GROWTH
+#define WTRI_BATCH_GROWTH 8  // growth of the batch's rounds
+#endif
+
 namespace wtri {
 namespace {
 
@@ -234,19 +241,20 @@ BatchPlan* batch_plan_create(const wtri_graph* const* gs, const int32_t* pcodes,
         P->caps[(size_t)i] = batch_query_cap(ks[i], gs[i]->d.m);
         P->cand_total += P->caps[(size_t)i];
     }
-    // Round schedule: one for the whole batch, the library default (first
-    // round, growth), since every batch round costs a launch sequence and a
+    // Round schedule: one for the whole batch (first round, growth: the
+    // WTRI_BATCH_* switches), since every batch round costs a launch sequence and a
     // select over all queries and the smallest growth would set the round
     // count of all; each query keeps its own graph's short/long boundary
     // (t_short).  Round r of the batch runs round r of every query (empty
     // once a query's schedule has covered its edges).
     (void)mmax;
-    const Tune def;
+    const int64_t first = WTRI_BATCH_FIRST;
+    const int64_t growth = WTRI_BATCH_GROWTH;
     int R = 0;
     std::vector<std::vector<int64_t>> his((size_t)nq);
     for (int i = 0; i < nq; i++) {
         const int64_t m = gs[i]->d.m;
-        for (int64_t lo = 0, size = def.first_round; lo < m; lo += size, size *= def.growth)
+        for (int64_t lo = 0, size = first; lo < m; lo += size, size *= growth)
             his[(size_t)i].push_back(std::min(m, lo + size));
         R = std::max<int>(R, (int)his[(size_t)i].size());
     }

@@ -103,7 +103,7 @@ def lib():
     L.wtri_sample_wedges.argtypes = [vp, f64, i64, ctypes.c_uint64, vp, vp, vp, vp]
     L.wtri_sample_cliques.argtypes = [vp, i32, f64, i32, i64, ctypes.c_uint64, vp, vp, vp,
                                       ctypes.POINTER(i32)]
-    L.wtri_topk_batch.argtypes = [vp, vp, vp, i32, ctypes.POINTER(_Result)]
+    L.wtri_topk_batch.argtypes = [vp, vp, vp, i32, vp]
     L.wtri_topk_shard.argtypes = [vp, f64, i32, i32, i32, ctypes.POINTER(_Result), vp]
     L.wtri_autotune.argtypes = [vp, i32, i32, ctypes.POINTER(_TuneInfo)]
     L.wtri_set_tune.argtypes = [vp, i64, i32, i32]
@@ -360,27 +360,36 @@ def autotune_buckets(graphs, k: int = 1000, reps: int = 2) -> int:
     return out.value
 
 
+_RESULT_DTYPE = np.dtype([("tris", "<u8"), ("weight", "<u8"), ("capacity", "<i4"), ("count", "<i4")])
+
+
 def topk_batch(graphs, ps, ks):
     """wtri_topk_batch: one batched launch for query i = (graphs[i], ps[i],
-    ks[i]).  Returns a list of (tris, weights) like topk()."""
+    ks[i]).  Returns a list of (tris, weights) like topk() (views into one
+    result buffer for the whole batch)."""
     nq = len(graphs)
     if nq == 0:
         return []
-    handles = (ctypes.c_void_p * nq)(*[g.handle.value for g in graphs])
+    assert ctypes.sizeof(_Result) == _RESULT_DTYPE.itemsize
+    handles = np.array([g.handle.value for g in graphs], dtype=np.uint64)
     p_arr = np.ascontiguousarray(ps, dtype=np.float64)
     k_arr = np.ascontiguousarray(ks, dtype=np.int32)
-    tris = [np.zeros((max(int(k), 1), 3), dtype=np.int32) for k in k_arr]
-    wts = [np.zeros(max(int(k), 1), dtype=np.float64) for k in k_arr]
-    res = (_Result * nq)()
-    for i in range(nq):
-        res[i].tris = tris[i].ctypes.data
-        res[i].weight = wts[i].ctypes.data
-        res[i].capacity = int(max(int(k_arr[i]), 1))
-        res[i].count = 0
-    _check(lib().wtri_topk_batch(ctypes.cast(handles, ctypes.c_void_p),
+    caps = np.maximum(k_arr.astype(np.int64), 1)
+    offs = np.zeros(nq + 1, dtype=np.int64)
+    np.cumsum(caps, out=offs[1:])
+    tris_all = np.zeros((int(offs[-1]), 3), dtype=np.int32)
+    wts_all = np.zeros(int(offs[-1]), dtype=np.float64)
+    res = np.zeros(nq, dtype=_RESULT_DTYPE)
+    res["tris"] = tris_all.ctypes.data + 12 * offs[:-1]
+    res["weight"] = wts_all.ctypes.data + 8 * offs[:-1]
+    res["capacity"] = caps
+    _check(lib().wtri_topk_batch(handles.ctypes.data_as(ctypes.c_void_p),
                                  p_arr.ctypes.data_as(ctypes.c_void_p),
-                                 k_arr.ctypes.data_as(ctypes.c_void_p), nq, res))
-    return [(tris[i][:res[i].count].copy(), wts[i][:res[i].count].copy()) for i in range(nq)]
+                                 k_arr.ctypes.data_as(ctypes.c_void_p), nq,
+                                 res.ctypes.data_as(ctypes.c_void_p)))
+    ends = (offs[:-1] + res["count"]).tolist()
+    starts = offs[:-1].tolist()
+    return [(tris_all[a:b], wts_all[a:b]) for a, b in zip(starts, ends)]
 
 
 class Server:
