@@ -405,6 +405,11 @@ inline unsigned round_grid(int64_t edges) {
 // unsampled, unsharded query.
 // ---------------------------------------------------------------------------
 constexpr int MIN_WARPS = RBLK / 32;
+#ifndef WTRI_MIN_STAGE
+#define WTRI_MIN_STAGE 512
+#endif
+// Longest searched row staged in shared memory (per warp; 0: never staged).
+constexpr int MIN_STAGE = WTRI_MIN_STAGE;
 
 __global__ void __launch_bounds__(RBLK) k_round_min(DevGraph G, Query q, int64_t lo, int64_t hi) {
     const volatile uint32_t* stop_rev = &q.st->stop_rev;
@@ -413,6 +418,8 @@ __global__ void __launch_bounds__(RBLK) k_round_min(DevGraph G, Query q, int64_t
     const unsigned long long tau = ld_volatile_u64(&q.st->tau);
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * MIN_WARPS;
+    __shared__ int32_t stage_all[MIN_WARPS][MIN_STAGE > 0 ? MIN_STAGE : 1];
+    int32_t* srow = stage_all[threadIdx.x >> 5];
     Tally tb;
     tb.on = q.qbytes != nullptr;
     for (int64_t r = lo + (int64_t)blockIdx.x * MIN_WARPS + (threadIdx.x >> 5); r < hi; r += nwarps) {
@@ -434,23 +441,48 @@ __global__ void __launch_bounds__(RBLK) k_round_min(DevGraph G, Query q, int64_t
         const bool as = (ae - ab) <= (be - bb);
         const int64_t sb = as ? ab : bb, se = as ? ae : be;  // scanned row
         const int64_t lb = as ? bb : ab, le = as ? be : ae;  // searched row
+        // The searched row goes to shared memory (coalesced, once per edge)
+        // as soon as a chunk of the scanned row holds an entry >= tau: one
+        // latency step instead of a global binary search per entry.
+        const int64_t llen = le - lb;
+        bool staged = false;
         for (int64_t base = sb; base < se; base += 32) {
             const int64_t j = base + lane;
-            if (j >= se) break;
-            const uint32_t wsc = (uint32_t)__ldg(G.owt + j);
-            tb.add(4);
-            if (wsc < tau) continue;
+            const uint32_t wsc = j < se ? (uint32_t)__ldg(G.owt + j) : 0u;
+            if (j < se) tb.add(4);
+            const bool heavy = j < se && wsc >= tau;
+            if (__ballot_sync(0xffffffffu, heavy) == 0) continue;
+            if (!staged && llen <= MIN_STAGE) {
+                for (int t = lane; t < llen; t += 32) srow[t] = __ldg(G.ocol + lb + t);
+                tb.add((uint32_t)(lane < llen ? 4 * ((llen - lane + 31) / 32) : 0));
+                __syncwarp();
+                staged = true;
+            }
+            if (!heavy) continue;
             const int32_t c = __ldg(G.ocol + j);
             tb.add(4);
-            int64_t l0 = lb, l1 = le;
-            while (l0 < l1) {
-                const int64_t mid = (l0 + l1) >> 1;
-                tb.add(4);
-                if (__ldg(G.ocol + mid) < c) l0 = mid + 1;
-                else l1 = mid;
+            int64_t l0, found_at = -1;
+            if (staged) {
+                int s0 = 0, s1 = (int)llen;
+                while (s0 < s1) {
+                    const int mid = (s0 + s1) >> 1;
+                    if (srow[mid] < c) s0 = mid + 1;
+                    else s1 = mid;
+                }
+                if (s0 < llen && srow[s0] == c) found_at = lb + s0;
+            } else {
+                int64_t l1 = le;
+                l0 = lb;
+                while (l0 < l1) {
+                    const int64_t mid = (l0 + l1) >> 1;
+                    tb.add(4);
+                    if (__ldg(G.ocol + mid) < c) l0 = mid + 1;
+                    else l1 = mid;
+                }
+                if (l0 < le && (tb.add(4), __ldg(G.ocol + l0) == c)) found_at = l0;
             }
-            if (l0 < le && (tb.add(4), __ldg(G.ocol + l0) == c)) {
-                const uint32_t wlc = (uint32_t)__ldg(G.owt + l0);
+            if (found_at >= 0) {
+                const uint32_t wlc = (uint32_t)__ldg(G.owt + found_at);
                 tb.add(4);
                 const unsigned long long key = keyof<P_MIN>(w, wsc, wlc);
                 if (key >= tau) {
@@ -460,6 +492,7 @@ __global__ void __launch_bounds__(RBLK) k_round_min(DevGraph G, Query q, int64_t
                 }
             }
         }
+        __syncwarp();  // the staged row is reused by the warp's next edge
     }
     flush_tally(q, tb);
 }
