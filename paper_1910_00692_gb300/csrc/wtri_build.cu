@@ -49,26 +49,48 @@ struct BuildStatus {
 
 // Float weights (fw): positive finite fp32 values, whose bit patterns are
 // the positive int32 below 0x7f800000 (+inf; NaN lies above it).
-__global__ void k_validate(int32_t n, int64_t m, const int32_t* __restrict__ u,
-                           const int32_t* __restrict__ v, const int32_t* __restrict__ w,
-                           int fw, BuildStatus* st) {
-    int32_t wloc = 0;
-    uint32_t eloc = 0;
+struct ValidateAcc {
+    int32_t wmax = 0;
+    uint32_t err = 0;
     unsigned long long bad = ~0ull;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t a = __ldg(u + i), b = __ldg(v + i), x = __ldg(w + i);
+    __device__ __forceinline__ void edge(int32_t n, int fw, int64_t i, int32_t a, int32_t b, int32_t x) {
         uint32_t e = 0;
         if (a < 0 || a >= n || b < 0 || b >= n) e |= DEV_ERR_RANGE;
         else if (a == b) e |= DEV_ERR_SELF_LOOP;
         if (x <= 0 || (fw && x >= 0x7f800000)) e |= DEV_ERR_WEIGHT;
         if (e) {
-            eloc |= e;
+            err |= e;
             if ((unsigned long long)i < bad) bad = (unsigned long long)i;
-            continue;
+            return;
         }
-        wloc = max(wloc, x);
+        wmax = max(wmax, x);
     }
+};
+
+// VEC: the three arrays are 16-byte aligned; four edges per 16-byte load of
+// each (enough bytes in flight to stream the input at HBM rate), the last
+// m % 4 edges one by one.
+template <bool VEC>
+__global__ void k_validate(int32_t n, int64_t m, const int32_t* __restrict__ u,
+                           const int32_t* __restrict__ v, const int32_t* __restrict__ w,
+                           int fw, BuildStatus* st) {
+    ValidateAcc acc;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nq = VEC ? m / 4 : 0;
+    for (int64_t q = tid; q < nq; q += nth) {
+        const int4 a = __ldg(reinterpret_cast<const int4*>(u) + q);
+        const int4 b = __ldg(reinterpret_cast<const int4*>(v) + q);
+        const int4 x = __ldg(reinterpret_cast<const int4*>(w) + q);
+        acc.edge(n, fw, 4 * q, a.x, b.x, x.x);
+        acc.edge(n, fw, 4 * q + 1, a.y, b.y, x.y);
+        acc.edge(n, fw, 4 * q + 2, a.z, b.z, x.z);
+        acc.edge(n, fw, 4 * q + 3, a.w, b.w, x.w);
+    }
+    for (int64_t i = 4 * nq + tid; i < m; i += nth) acc.edge(n, fw, i, __ldg(u + i), __ldg(v + i), __ldg(w + i));
+    int32_t wloc = acc.wmax;
+    uint32_t eloc = acc.err;
+    unsigned long long bad = acc.bad;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         wloc = max(wloc, __shfl_xor_sync(0xffffffffu, wloc, o));
@@ -263,21 +285,39 @@ struct RowsStorer {
 
 // Row offsets from the row-sorted entry stream: entry i starts row x for
 // every x in (row[i-1], row[i]]; rows past the last entry start at n2.
+// Rows start where the sorted row keys change.  Four keys per thread from one
+// 16-byte load (row is 16-byte aligned), the key before them from the
+// previous quad.
 __global__ void k_rowptr_from_rows(int32_t n, int64_t n2, const int32_t* __restrict__ row,
                                    int64_t* __restrict__ rowptr, const uint32_t* gate) {
     if (*(volatile const uint32_t*)gate) return;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t cur = __ldg(row + i);
-        const int32_t prev = i == 0 ? -1 : __ldg(row + i - 1);
-        for (int32_t x = prev + 1; x <= cur; x++) rowptr[x] = i;
-        if (i == n2 - 1)
-            for (int64_t x = (int64_t)cur + 1; x <= n; x++) rowptr[x] = n2;
+    const int64_t nq = (n2 + 3) / 4;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = 4 * q;
+        int32_t cur[4];
+        if (i0 + 4 <= n2) {
+            const int4 r = __ldg(reinterpret_cast<const int4*>(row) + q);
+            cur[0] = r.x;
+            cur[1] = r.y;
+            cur[2] = r.z;
+            cur[3] = r.w;
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; t++) cur[t] = i0 + t < n2 ? __ldg(row + i0 + t) : n;
+        }
+        int32_t prev = q == 0 ? -1 : __ldg(row + i0 - 1);
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            // past the end the key is n: rows after the last key start at n2
+            const int64_t i = i0 + t < n2 ? i0 + t : n2;
+            for (int64_t x = (int64_t)prev + 1; x <= cur[t]; x++) rowptr[x] = i;
+            prev = max(prev, cur[t]);
+        }
+        if (i0 + 4 == n2)
+            for (int64_t x = (int64_t)prev + 1; x <= n; x++) rowptr[x] = n2;
     }
 }
-
-// Degrees saturated to 16 bits (the form the orientation test gathers: two
-// bytes per vertex, small enough to stay mostly in L2) and the maximum degree.
 __global__ void k_degrees(int32_t n, const int64_t* __restrict__ rowptr, uint16_t* __restrict__ deg16,
                           BuildStatus* st) {
     if (*(volatile const uint32_t*)&st->err) return;
@@ -417,14 +457,16 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     Scratch in_buf(s);
     const int32_t *u = u_in, *v = v_in, *w = w_in;
     if (!on_device && m > 0) {
-        WTRI_CUDA(cudaMallocAsync(&in_buf.p, sizeof(int32_t) * 3 * (size_t)m, s));
+        // each array starts 16-byte aligned (validation loads four edges at once)
+        const size_t mp = align_up((size_t)m, 4);
+        WTRI_CUDA(cudaMallocAsync(&in_buf.p, sizeof(int32_t) * 3 * mp, s));
         int32_t* d = (int32_t*)in_buf.p;
         WTRI_CUDA(cudaMemcpyAsync(d, u_in, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
-        WTRI_CUDA(cudaMemcpyAsync(d + m, v_in, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
-        WTRI_CUDA(cudaMemcpyAsync(d + 2 * m, w_in, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+        WTRI_CUDA(cudaMemcpyAsync(d + mp, v_in, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+        WTRI_CUDA(cudaMemcpyAsync(d + 2 * mp, w_in, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
         u = d;
-        v = d + m;
-        w = d + 2 * m;
+        v = d + mp;
+        w = d + 2 * mp;
     }
 
     // One allocation for every resident array (256-byte aligned pieces, with
@@ -483,7 +525,10 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
     // 1. validation + max weight
     if (m > 0) {
         ProfScope ps("validate", s, 12.0 * m, 1);  // the COO input, read once
-        k_validate<<<grid_for(m), BLK, 0, s>>>(n, m, u, v, w, fw, d_st);
+        if ((((uintptr_t)u | (uintptr_t)v | (uintptr_t)w) & 15) == 0)
+            k_validate<true><<<grid_for(m / 4 + 1), BLK, 0, s>>>(n, m, u, v, w, fw, d_st);
+        else
+            k_validate<false><<<grid_for(m), BLK, 0, s>>>(n, m, u, v, w, fw, d_st);
     }
     g->d.n = n;
     g->d.m = m;
@@ -498,8 +543,9 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         // entry, 16-bit degrees, oriented out-degrees, the class lists.
         const int64_t n2 = 2 * m;
         const size_t rec_words = 4 * (size_t)n2 + 4;
-        const size_t dig_words = ((size_t)n2 + 1) / 2 + 4;
-        const size_t cnt_words = radix::scratch_words(n2);
+        // (multiples of four words: wrow below starts 16-byte aligned)
+        const size_t dig_words = align_up(((size_t)n2 + 1) / 2 + 4, 4);
+        const size_t cnt_words = align_up(radix::scratch_words(n2), 4);
         const size_t words = 2 * rec_words + dig_words + cnt_words + (size_t)n2 + (N1 + 1) / 2 + 4 +
                              N1 + 4 + N1 + 4 + 64;
         Scratch tmp(s);
@@ -548,7 +594,7 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         // 4. row offsets, degrees
         {
             ProfScope ps("row_offsets", s, 8.0 * (n + 1), 2, 4.0 * n2 + 8.0 * (n + 1) + 2.0 * n);
-            k_rowptr_from_rows<<<grid_for(n2), BLK, 0, s>>>(n, n2, wrow, rowptr, gate);
+            k_rowptr_from_rows<<<grid_for(n2 / 4 + 1), BLK, 0, s>>>(n, n2, wrow, rowptr, gate);
             k_degrees<<<grid_for(n), BLK, 0, s>>>(n, rowptr, deg16, d_st);
         }
         // 5. orientation of every entry and the oriented out-degrees (the
@@ -573,9 +619,10 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
             WTRI_TRY(exclusive_scan_i32_to_i64(odeg, orowptr, n, s));
             {
                 ProfScope pc("orient_classes", s, 0.0, 3, 4.0 * n + 8.0 * n);
-                rows::k_class_count<<<grid_for(n, rows::NT), rows::NT, 0, s>>>(n, odeg, cls_cnt, gate);
+                const unsigned cg = grid_for(n, rows::NT * rows::CLS_V);
+                rows::k_class_count<<<cg, rows::NT, 0, s>>>(n, odeg, cls_cnt, gate);
                 rows::k_class_offsets<<<1, 32, 0, s>>>(cls_cnt, cls_off, cls_cur, gate);
-                rows::k_class_fill<<<grid_for(n, rows::NT), rows::NT, 0, s>>>(n, odeg, cls_cur, list, gate);
+                rows::k_class_fill<<<cg, rows::NT, 0, s>>>(n, odeg, cls_cur, list, gate);
             }
             rows::RowsOut R{rowptr, wwt, wrk, pk, odeg, orowptr, ocol, owt, ork,
                             &d_st->err, &d_st->first_bad, list, cls_off};

@@ -118,18 +118,46 @@ __device__ __forceinline__ void flag_dup(const RowsOut& R, int32_t x, int32_t c)
 // ---------------------------------------------------------------------------
 // Row classes by oriented degree: counts, then the list of rows of each class.
 // ---------------------------------------------------------------------------
+// A block step covers NT * CLS_V rows: CLS_V strips of 32 rows per warp.
+constexpr int CLS_V = 8;
+
+// The classes of one warp's CLS_V strips, and (in lane k, 0 < k < NCLS) how
+// many of them are of class k.
+__device__ __forceinline__ int class_strips(int32_t n, const int32_t* __restrict__ odeg, int64_t xw,
+                                            int (&cls)[CLS_V]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < CLS_V; j++) {
+        const int64_t x = xw + j * 32 + lane;
+        cls[j] = x < n ? row_class(__ldg(odeg + x)) : CLS_NONE;
+    }
+    int mine = 0;
+#pragma unroll
+    for (int k = 1; k < NCLS; k++) {
+        int t = 0;
+#pragma unroll
+        for (int j = 0; j < CLS_V; j++) t += __popc(__ballot_sync(0xffffffffu, cls[j] == k));
+        if (lane == k) mine = t;
+    }
+    return mine;
+}
+
 __global__ void __launch_bounds__(NT) k_class_count(int32_t n, const int32_t* __restrict__ odeg,
                                                     int32_t* __restrict__ cls_cnt, const uint32_t* gate) {
     if (rows_gate_closed(gate)) return;
     __shared__ int32_t sc[NCLS];
     if (threadIdx.x < NCLS) sc[threadIdx.x] = 0;
     __syncthreads();
-    for (int64_t x = (int64_t)blockIdx.x * NT + threadIdx.x; x < n; x += (int64_t)gridDim.x * NT) {
-        const int c = row_class(__ldg(odeg + x));
-        if (c != CLS_NONE) atomicAdd(&sc[c], 1);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    int acc = 0;  // lane k: rows of class k seen by this warp
+    const int64_t span = (int64_t)NT * CLS_V;
+    for (int64_t x0 = (int64_t)blockIdx.x * span; x0 < n; x0 += (int64_t)gridDim.x * span) {
+        int cls[CLS_V];
+        acc += class_strips(n, odeg, x0 + (int64_t)wp * 32 * CLS_V, cls);
     }
+    if (lane > 0 && lane < NCLS && acc) atomicAdd(&sc[lane], acc);
     __syncthreads();
-    if (threadIdx.x < NCLS && sc[threadIdx.x]) atomicAdd(cls_cnt + threadIdx.x, sc[threadIdx.x]);
+    if (threadIdx.x > 0 && threadIdx.x < NCLS && sc[threadIdx.x]) atomicAdd(cls_cnt + threadIdx.x, sc[threadIdx.x]);
 }
 
 // cls_cnt (NCLS counts) -> cls_off (NCLS + 1 offsets); fill cursors in cls_cur.
@@ -147,23 +175,47 @@ __global__ void k_class_offsets(const int32_t* cls_cnt, int32_t* cls_off, int32_
     }
 }
 
+// Rows of each class into list[]: per block step, each warp's count of
+// each class goes to shared memory, one global atomic per class reserves the
+// block's slots, and each warp writes its rows at its offset in them.
 __global__ void __launch_bounds__(NT) k_class_fill(int32_t n, const int32_t* __restrict__ odeg,
                                                    int32_t* __restrict__ cls_cur, int32_t* __restrict__ list,
                                                    const uint32_t* gate) {
     if (rows_gate_closed(gate)) return;
-    const int lane = threadIdx.x & 31;
-    for (int64_t x0 = (int64_t)blockIdx.x * NT; x0 < n; x0 += (int64_t)gridDim.x * NT) {
-        const int64_t x = x0 + threadIdx.x;
-        const int c = x < n ? row_class(__ldg(odeg + x)) : CLS_NONE;
-        // one atomic per class present in the warp
-        for (int k = 1; k < NCLS; k++) {
-            const uint32_t b = __ballot_sync(0xffffffffu, c == k);
-            if (!b) continue;
-            int32_t base = 0;
-            if (lane == __ffs(b) - 1) base = atomicAdd(cls_cur + k, __popc(b));
-            base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
-            if (c == k) list[base + __popc(b & ((1u << lane) - 1u))] = (int32_t)x;
+    constexpr int NWP = NT / 32;
+    __shared__ int32_t woff[NWP][NCLS];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t span = (int64_t)NT * CLS_V;
+    for (int64_t x0 = (int64_t)blockIdx.x * span; x0 < n; x0 += (int64_t)gridDim.x * span) {
+        const int64_t xw = x0 + (int64_t)wp * 32 * CLS_V;
+        int cls[CLS_V];
+        const int mine = class_strips(n, odeg, xw, cls);
+        if (lane < NCLS) woff[wp][lane] = mine;
+        __syncthreads();
+        if (threadIdx.x > 0 && threadIdx.x < NCLS) {  // class k: warps' offsets, then the block's slots
+            const int k = threadIdx.x;
+            int32_t tot = 0;
+            for (int w = 0; w < NWP; w++) {
+                const int32_t c = woff[w][k];
+                woff[w][k] = tot;
+                tot += c;
+            }
+            const int32_t base = tot ? atomicAdd(cls_cur + k, tot) : 0;
+            for (int w = 0; w < NWP; w++) woff[w][k] += base;
         }
+        __syncthreads();
+#pragma unroll
+        for (int k = 1; k < NCLS; k++) {
+            int32_t off = woff[wp][k];
+#pragma unroll
+            for (int j = 0; j < CLS_V; j++) {
+                const uint32_t b = __ballot_sync(0xffffffffu, cls[j] == k);
+                if (cls[j] == k) list[off + __popc(b & lt)] = (int32_t)(xw + j * 32 + lane);
+                off += __popc(b);
+            }
+        }
+        __syncthreads();  // woff is rewritten by the next step
     }
 }
 
