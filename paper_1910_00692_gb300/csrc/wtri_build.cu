@@ -285,36 +285,42 @@ struct RowsStorer {
 
 // Row offsets from the row-sorted entry stream: entry i starts row x for
 // every x in (row[i-1], row[i]]; rows past the last entry start at n2.
-// Rows start where the sorted row keys change.  Four keys per thread from one
-// 16-byte load (row is 16-byte aligned), the key before them from the
-// previous quad.
+// Rows start where the sorted row keys change.  Eight keys per thread from
+// two 16-byte loads (row is 16-byte aligned), the key before them from the
+// previous group.
 __global__ void k_rowptr_from_rows(int32_t n, int64_t n2, const int32_t* __restrict__ row,
                                    int64_t* __restrict__ rowptr, const uint32_t* gate) {
     if (*(volatile const uint32_t*)gate) return;
-    const int64_t nq = (n2 + 3) / 4;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+    constexpr int G = 8;
+    const int64_t ng = (n2 + G - 1) / G;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ng;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i0 = 4 * q;
-        int32_t cur[4];
-        if (i0 + 4 <= n2) {
-            const int4 r = __ldg(reinterpret_cast<const int4*>(row) + q);
-            cur[0] = r.x;
-            cur[1] = r.y;
-            cur[2] = r.z;
-            cur[3] = r.w;
+        const int64_t i0 = G * q;
+        int32_t cur[G];
+        if (i0 + G <= n2) {
+            const int4 r0 = __ldg(reinterpret_cast<const int4*>(row) + 2 * q);
+            const int4 r1 = __ldg(reinterpret_cast<const int4*>(row) + 2 * q + 1);
+            cur[0] = r0.x;
+            cur[1] = r0.y;
+            cur[2] = r0.z;
+            cur[3] = r0.w;
+            cur[4] = r1.x;
+            cur[5] = r1.y;
+            cur[6] = r1.z;
+            cur[7] = r1.w;
         } else {
 #pragma unroll
-            for (int t = 0; t < 4; t++) cur[t] = i0 + t < n2 ? __ldg(row + i0 + t) : n;
+            for (int t = 0; t < G; t++) cur[t] = i0 + t < n2 ? __ldg(row + i0 + t) : n;
         }
         int32_t prev = q == 0 ? -1 : __ldg(row + i0 - 1);
 #pragma unroll
-        for (int t = 0; t < 4; t++) {
+        for (int t = 0; t < G; t++) {
             // past the end the key is n: rows after the last key start at n2
             const int64_t i = i0 + t < n2 ? i0 + t : n2;
             for (int64_t x = (int64_t)prev + 1; x <= cur[t]; x++) rowptr[x] = i;
             prev = max(prev, cur[t]);
         }
-        if (i0 + 4 == n2)
+        if (i0 + G == n2)
             for (int64_t x = (int64_t)prev + 1; x <= n; x++) rowptr[x] = n2;
     }
 }
@@ -594,7 +600,7 @@ int build_graph(int32_t n, int64_t m, const int32_t* u_in, const int32_t* v_in,
         // 4. row offsets, degrees
         {
             ProfScope ps("row_offsets", s, 8.0 * (n + 1), 2, 4.0 * n2 + 8.0 * (n + 1) + 2.0 * n);
-            k_rowptr_from_rows<<<grid_for(n2 / 4 + 1), BLK, 0, s>>>(n, n2, wrow, rowptr, gate);
+            k_rowptr_from_rows<<<grid_for(n2 / 8 + 1), BLK, 0, s>>>(n, n2, wrow, rowptr, gate);
             k_degrees<<<grid_for(n), BLK, 0, s>>>(n, rowptr, deg16, d_st);
         }
         // 5. orientation of every entry and the oriented out-degrees (the
