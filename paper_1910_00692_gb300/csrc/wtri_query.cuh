@@ -503,6 +503,139 @@ inline unsigned round_grid_warps(int64_t edges) {
 }
 
 // ---------------------------------------------------------------------------
+// Round with one warp per edge, for the small early rounds (up to
+// WTRI_WARP_ROUND_MAX edges), where a thread per edge leaves the GPU almost
+// idle and each thread scans its entries one dependent search after another.
+// Same sweep as k_round: the edge checks and the two suffix searches once
+// per warp (lanes 0 and 1 search u's and v's lists at once), then the first
+// t_short entries (rounded up to a multiple of 32) of the shorter suffix,
+// one entry and one probe per lane; the rest is deferred to k_long.  The
+// wedge bound does not increase along a list, so the lanes that pass it are
+// exactly the entries a serial scan would reach.
+// ---------------------------------------------------------------------------
+#ifndef WTRI_WARP_ROUND_MAX
+#define WTRI_WARP_ROUND_MAX 4096
+#endif
+constexpr int64_t WARP_ROUND_MAX = WTRI_WARP_ROUND_MAX;
+
+// Scans [jb, je) of x's list, 32 entries per step; true once an entry fails
+// the wedge bound (and so does every later one).  Warp-uniform result.
+template <int P>
+__device__ __forceinline__ bool scan_wedges_warp(const DevGraph& G, const Query& q, unsigned long long tau,
+                                                 int32_t r, uint32_t w, int32_t x, int32_t y, int64_t dy,
+                                                 uint32_t ymax, int64_t jb, int64_t je, Tally& tb) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = jb; base < je; base += 32) {
+        const int64_t j = base + lane;
+        const bool live = j < je;
+        uint32_t wxc = 0;
+        if (live) {
+            wxc = (uint32_t)__ldg(G.wwt + j);
+            tb.add(4);
+        }
+        const bool fail = live && boundof<P>(w, wxc, ymax, q.gp, q.fw != 0) < tau;
+        const bool stop = __any_sync(0xffffffffu, fail);
+        if (live && !fail) {
+            const int32_t c = __ldg(G.wcol + j);
+            tb.add(4);
+            int32_t wyc, ryc;
+            if (probe_oriented(G, y, dy, c, wyc, ryc, tb) &&
+                (tb.add(4), owns<false>(q, r, __ldg(G.wrk + j), ryc))) {
+                const unsigned long long key = keyof<P>(w, wxc, (uint32_t)wyc, q.gp, q.fw != 0);
+                if (key >= tau) {
+                    int32_t a = x, b = y, cc = c;
+                    sort3(a, b, cc);
+                    append(q, key, a, b, cc);
+                }
+            }
+        }
+        if (stop) return true;
+    }
+    return false;
+}
+
+// process_edge with the warp: false once the edge's bound is below tau.
+// tu counts the warp's shared loads once (lane 0).
+template <int P>
+__device__ __forceinline__ bool process_edge_warp(const DevGraph& G, const Query& q, unsigned long long tau,
+                                                  int32_t r, Tally& tb, Tally& tu) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t w = (uint32_t)__ldg(G.ord_w + r);
+    tu.add(4);
+    if (boundof<P>(w, w, w, q.gp, q.fw != 0) < tau) {
+        if (lane == 0) atomicMax(&q.st->stop_rev, STOP_NONE - (uint32_t)r);
+        return false;
+    }
+    if (q.nshards > 1 && (int32_t)(((uint32_t)r >> SHARD_SHIFT) % (uint32_t)q.nshards) != q.shard)
+        return true;  // owned by another shard
+    const int32_t u = __ldg(G.ord_u + r), v = __ldg(G.ord_v + r);
+    const int64_t bu = __ldg(G.rowptr + u), eu = __ldg(G.rowptr + u + 1);
+    const int64_t bv = __ldg(G.rowptr + v), ev = __ldg(G.rowptr + v + 1);
+    tu.add(40);
+    Tally ts;  // lanes 0 and 1 count their own search; the others repeat lane 0's
+    ts.on = tb.on && lane < 2;
+    const bool side_v = lane == 1;
+    const int64_t s1 = suffix_start(G, side_v ? bv : bu, side_v ? ev : eu, r, &q.st->err, ts);
+    tb.n += ts.n;
+    const int64_t su = __shfl_sync(0xffffffffu, s1, 0), sv = __shfl_sync(0xffffffffu, s1, 1);
+    if (su >= eu || sv >= ev) return true;  // no edge after r on one side: owns nothing
+    const uint32_t umax = (uint32_t)__ldg(G.wwt + su), vmax = (uint32_t)__ldg(G.wwt + sv);
+    tu.add(8);
+    if (boundof<P>(w, umax, vmax, q.gp, q.fw != 0) < tau) return true;  // edge bound
+    const bool xu = (eu - su) <= (ev - sv);
+    const int32_t x = xu ? u : v, y = xu ? v : u;
+    const int64_t sx = xu ? su : sv, ex = xu ? eu : ev;
+    const uint32_t ymax = xu ? vmax : umax;
+    const int64_t dy = xu ? ev - bv : eu - bu;
+    const int64_t budget = q.t_short > 32 ? ((int64_t)q.t_short + 31) / 32 * 32 : 32;
+    const int64_t jlim = ex < sx + budget ? ex : sx + budget;
+    if (scan_wedges_warp<P>(G, q, tau, r, w, x, y, dy, ymax, sx, jlim, tb) || jlim >= ex) return true;
+    uint32_t slot = 0;
+    if (lane == 0) slot = atomicAdd(q.long_count, 1u);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (slot < q.long_cap) {
+        if (lane == 0) {
+            LongItem it;
+            it.r = r;
+            it.x = x;
+            it.y = y;
+            it.w = (int32_t)w;
+            it.ymax = (int32_t)ymax;
+            it.pad = q.qid;
+            it.j0 = jlim;
+            it.j1 = ex;
+            q.longs[slot] = it;
+        }
+    } else {
+        // Deferred list full: finish the scan here.
+        scan_wedges_warp<P>(G, q, tau, r, w, x, y, dy, ymax, jlim, ex, tb);
+    }
+    return true;
+}
+
+template <int P>
+__global__ void __launch_bounds__(RBLK) k_round_warp(DevGraph G, Query q, int64_t lo, int64_t hi) {
+    const volatile uint32_t* stop_rev = &q.st->stop_rev;
+    if (lo >= (int64_t)(STOP_NONE - *stop_rev)) return;
+    if (*(volatile const uint32_t*)&q.st->err) return;  // the query has already failed
+    const unsigned long long tau = ld_volatile_u64(&q.st->tau);
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * MIN_WARPS;
+    Tally tb, tu;
+    tb.on = q.qbytes != nullptr;
+    tu.on = tb.on && lane == 0;
+    for (int64_t r = lo + (int64_t)blockIdx.x * MIN_WARPS + (threadIdx.x >> 5); r < hi; r += nwarps) {
+        uint32_t sr = 0;
+        if (lane == 0) sr = *stop_rev;
+        sr = __shfl_sync(0xffffffffu, sr, 0);  // one reading for the whole warp
+        if (r >= (int64_t)(STOP_NONE - sr)) break;
+        if (!process_edge_warp<P>(G, q, tau, (int32_t)r, tb, tu)) break;
+    }
+    tb.n += tu.n;
+    flush_tally(q, tb);
+}
+
+// ---------------------------------------------------------------------------
 // Deferred long scans: one block per item.  y's oriented row (ids) is
 // staged in shared memory with a bulk async copy completed on an mbarrier;
 // closing edges that y owns are binary searches there, the others searches

@@ -70,7 +70,10 @@ int run_query(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* d_weight
         } else {
             {
                 ProfScope ps("topk_round", s, 0.0, 1);
-                k_round<P><<<round_grid(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
+                if (hi - lo <= WARP_ROUND_MAX)  // small early rounds: a warp per edge
+                    k_round_warp<P><<<round_grid_warps(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
+                else
+                    k_round<P><<<round_grid(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
             }
             {
                 ProfScope ps("topk_long", s, 0.0, 1);
@@ -495,7 +498,10 @@ int run_query_noalloc(const wtri_graph* g, int32_t k, wtri_tri* d_tris, double* 
             k_round_min<<<round_grid_warps(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
             count_launches(1);
         } else {
-            k_round<P><<<round_grid(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
+            if (hi - lo <= WARP_ROUND_MAX)
+                k_round_warp<P><<<round_grid_warps(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
+            else
+                k_round<P><<<round_grid(hi - lo), RBLK, 0, s>>>(G, q, lo, hi);
             k_long<P><<<long_grid, LBLK, lsmem, s>>>(G, q);
             count_launches(2);
         }
