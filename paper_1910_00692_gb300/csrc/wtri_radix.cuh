@@ -54,8 +54,17 @@ constexpr int MAX_BINS = 1 << MAX_BITS;
 #endif
 constexpr int NT = WTRI_RADIX_NT;          // threads of the histogram and scatter CTAs
 constexpr int NW = NT / 32;
+// Ranking within a warp: peer masks built by shared-memory atomicOr, one
+// word per (warp, digit) (1), or ballots over the digit's bits (0).
+#ifndef WTRI_RANK_SMEM
+#define WTRI_RANK_SMEM 1
+#endif
 #ifndef WTRI_RADIX_IT
+#if WTRI_RANK_SMEM
+#define WTRI_RADIX_IT (WTRI_RADIX_NT == 512 ? 9 : 21)  // tiles, counters, masks and staging fit 227 KB
+#else
 #define WTRI_RADIX_IT (WTRI_RADIX_NT == 512 ? 11 : 24)  // the tiles, counters and staging fit 227 KB
+#endif
 #endif
 #ifndef WTRI_RADIX_CTAS
 #define WTRI_RADIX_CTAS 1
@@ -270,6 +279,9 @@ __device__ __forceinline__ bool bar_try_wait(uint64_t* bar, uint32_t parity) {
 struct ScatterSmem {
     uint4 buf[2][TT];              // a tile's sources, then its records in digit order
     uint16_t cnt[NW][MAX_BINS];    // per (warp, digit): count, then staging offset
+#if WTRI_RANK_SMEM
+    uint32_t match[NW][MAX_BINS];  // per (warp, digit): lanes of the current strip; zero between strips
+#endif
     uint32_t delta[MAX_BINS];      // output position of a staged record = delta[d] + index
     uint32_t warp_tot[32];
     uint32_t total;
@@ -366,9 +378,32 @@ __device__ __forceinline__ void scatter_tile(const uint4 (&rec)[IT], int tcount,
         for (int k = 0; k < NW; k++) reinterpret_cast<uint4*>(&S.cnt[k][0])[q] = make_uint4(0, 0, 0, 0);
     }
     __syncthreads();
+    uint32_t rank[IT];
+#if WTRI_RANK_SMEM
+    // 2. rank within the warp, strip by strip: each lane sets its bit in its
+    //    digit's mask word, reads the word back (its peers), and the lowest
+    //    peer advances the digit's counter and clears the word
+    uint32_t* mm = S.match[w];
+#pragma unroll
+    for (int j = 0; j < IT; j++) {
+        const int li = w * 32 * IT + j * 32 + lane;
+        const bool valid = FULL || li < tcount;
+        const uint32_t d = (rec[j].x >> g.shift) & g.mask;
+        if (valid) atomicOr(&mm[d], 1u << lane);
+        __syncwarp();
+        const uint32_t peers = valid ? mm[d] : 0u;
+        const uint32_t b = valid ? (uint32_t)S.cnt[w][d] : 0u;
+        rank[j] = b + __popc(peers & lt);
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) {
+            S.cnt[w][d] = (uint16_t)(b + __popc(peers));
+            mm[d] = 0u;
+        }
+        __syncwarp();
+    }
+#else
     // 2. rank within the warp: first every item's peers (ballots, independent
     //    across strips), then the running per-warp counters strip by strip
-    uint32_t rank[IT];
 #pragma unroll
     for (int j = 0; j < IT; j++) {
         const int li = w * 32 * IT + j * 32 + lane;
@@ -386,6 +421,7 @@ __device__ __forceinline__ void scatter_tile(const uint4 (&rec)[IT], int tcount,
         if (valid && lane == __ffs(peers) - 1) S.cnt[w][d] = (uint16_t)(b + __popc(peers));
         __syncwarp();
     }
+#endif
     __syncthreads();
     // 3. per digit: offsets of each warp, tile start, output delta.  Thread t
     //    owns digits DPT t .. DPT t + DPT - 1: one word of each warp's counters.
@@ -490,6 +526,9 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_scatter(Loader ld, Storer s
     const int64_t nfull = USE_BULK && end > beg ? (end - beg) / TT : 0;
     constexpr uint32_t ARR_BYTES = Loader::TILE_WORDS * 4u;
     static_assert(Loader::NARR * Loader::TILE_WORDS <= 4 * TT, "a tile's sources fit one buffer");
+#if WTRI_RANK_SMEM
+    for (int t = threadIdx.x; t < NW * MAX_BINS; t += NT) (&S.match[0][0])[t] = 0u;
+#endif
     if (threadIdx.x == 0) {
         bar_init(&S.bar[0]);
         bar_init(&S.bar[1]);
