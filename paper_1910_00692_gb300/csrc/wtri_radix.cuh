@@ -32,7 +32,8 @@
 // scan over chunks, and the scatter.  The scatter streams its chunk tile by
 // tile; the next tile's sources arrive by bulk asynchronous copies
 // (cp.async.bulk, one mbarrier per half of a double buffer) while the
-// current one is ranked (warp match + per-warp counters, stable), staged in
+// current one is ranked (per-warp peer masks built by shared-memory
+// atomicOr, per-warp counters; stable), staged in
 // digit order in the same shared-memory buffer it was read from, and written
 // out so that consecutive threads store consecutive positions of one
 // digit's run.
