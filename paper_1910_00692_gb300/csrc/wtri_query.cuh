@@ -422,21 +422,45 @@ __global__ void __launch_bounds__(RBLK) k_round_min(DevGraph G, Query q, int64_t
     int32_t* srow = stage_all[threadIdx.x >> 5];
     Tally tb;
     tb.on = q.qbytes != nullptr;
-    for (int64_t r = lo + (int64_t)blockIdx.x * MIN_WARPS + (threadIdx.x >> 5); r < hi; r += nwarps) {
+    // The warp's next edge is fetched while this one is scanned: its weight
+    // and endpoints at the top of the iteration, its degrees once this
+    // edge's oriented-row bounds are issued.
+    int64_t r = lo + (int64_t)blockIdx.x * MIN_WARPS + (threadIdx.x >> 5);
+    uint32_t w_nx = 0;
+    int32_t u_nx = 0, v_nx = 0;
+    int64_t du_nx = 0, dv_nx = 0;
+    if (r < hi) {
+        w_nx = (uint32_t)__ldg(G.ord_w + r);
+        u_nx = __ldg(G.ord_u + r);
+        v_nx = __ldg(G.ord_v + r);
+        du_nx = __ldg(G.rowptr + u_nx + 1) - __ldg(G.rowptr + u_nx);
+        dv_nx = __ldg(G.rowptr + v_nx + 1) - __ldg(G.rowptr + v_nx);
+    }
+    for (; r < hi; r += nwarps) {
+        const uint32_t w = w_nx;
+        const int32_t u = u_nx, v = v_nx;
+        const int64_t du = du_nx, dv = dv_nx;
+        const int64_t rn = r + nwarps;
+        const bool more = rn < hi;
+        if (more) {
+            w_nx = (uint32_t)__ldg(G.ord_w + rn);
+            u_nx = __ldg(G.ord_u + rn);
+            v_nx = __ldg(G.ord_v + rn);
+        }
         if (r >= (int64_t)(STOP_NONE - *stop_rev)) break;
-        const uint32_t w = (uint32_t)__ldg(G.ord_w + r);
         if (w < tau) {
             // every later edge is lighter: record the first such edge
             if (lane == 0) atomicMax(&q.st->stop_rev, STOP_NONE - (uint32_t)r);
             break;
         }
-        const int32_t u = __ldg(G.ord_u + r), v = __ldg(G.ord_v + r);
-        const int64_t du = __ldg(G.rowptr + u + 1) - __ldg(G.rowptr + u);
-        const int64_t dv = __ldg(G.rowptr + v + 1) - __ldg(G.rowptr + v);
         const bool ua = du < dv || (du == dv && u < v);
         const int32_t a = ua ? u : v, b = ua ? v : u;
         const int64_t ab = __ldg(G.orowptr + a), ae = __ldg(G.orowptr + a + 1);
         const int64_t bb = __ldg(G.orowptr + b), be = __ldg(G.orowptr + b + 1);
+        if (more) {
+            du_nx = __ldg(G.rowptr + u_nx + 1) - __ldg(G.rowptr + u_nx);
+            dv_nx = __ldg(G.rowptr + v_nx + 1) - __ldg(G.rowptr + v_nx);
+        }
         if (lane == 0) tb.add(12 + 32 + 32);
         const bool as = (ae - ab) <= (be - bb);
         const int64_t sb = as ? ab : bb, se = as ? ae : be;  // scanned row
